@@ -1,0 +1,88 @@
+"""Dose-comparison tools used by the tests (test infrastructure, numpy only).
+
+* batch statistics of Sec. II.B.2 (total and its standard error from B groups)
+* R80 of an integrated depth-dose curve
+* per-voxel z-scores between two independent estimates
+* brute-force 3-D gamma index (Low et al.), global dose criterion, on the grid
+  without interpolation -- the comparison metric of Sec. II.D
+"""
+from __future__ import annotations
+
+import numpy as np
+
+MEV_TO_J = 1.602176634e-13
+
+
+def batch_stats(tally: np.ndarray):
+    """tally[V, B] -> (total[V], sigma[V]): sigma = sqrt(B/(B-1) * sum_b (D_b - D/B)^2)."""
+    t = np.asarray(tally, dtype=np.float64)
+    B = t.shape[1]
+    tot = t.sum(1)
+    if B < 2:
+        return tot, np.zeros_like(tot)
+    dev = t - tot[:, None] / B
+    return tot, np.sqrt(B / (B - 1) * (dev * dev).sum(1))
+
+
+def to_gray(energy_mev: np.ndarray, rho: np.ndarray, voxel_cm3: float) -> np.ndarray:
+    """Energy (MeV) per voxel -> dose (Gy) = E * 1.602e-13 J / (rho * V * 1e-3 kg)."""
+    return energy_mev * MEV_TO_J / (rho * voxel_cm3 * 1e-3)
+
+
+def depth_dose(D3: np.ndarray) -> np.ndarray:
+    """Integrated depth-dose (sum over each z slice) of a [nz, ny, nx] array."""
+    return D3.reshape(D3.shape[0], -1).sum(1)
+
+
+def r80(idd: np.ndarray, dz: float, z0: float = 0.0) -> float:
+    """Depth distal to the maximum where the curve falls to 80 % of it; linear interpolation
+    between voxel centres."""
+    idd = np.asarray(idd, dtype=np.float64)
+    k = int(np.argmax(idd))
+    lvl = 0.8 * idd[k]
+    zc = z0 + (np.arange(len(idd)) + 0.5) * dz
+    for j in range(k, len(idd) - 1):
+        if idd[j] >= lvl > idd[j + 1]:
+            return float(zc[j] + (idd[j] - lvl) / (idd[j] - idd[j + 1]) * dz)
+    return float(zc[-1])
+
+
+def zscores(Da, sa, Db, sb, frac_of_max=0.1):
+    """z = (Da - Db) / sqrt(sa^2 + sb^2) over voxels where Db exceeds frac_of_max of its max."""
+    Da, sa, Db, sb = (np.asarray(x, dtype=np.float64).ravel() for x in (Da, sa, Db, sb))
+    m = Db > frac_of_max * Db.max()
+    den = np.sqrt(sa[m] ** 2 + sb[m] ** 2)
+    den[den == 0] = np.inf
+    return (Da[m] - Db[m]) / den
+
+
+def gamma_pass_rate(D_ref, D_eval, voxel, dose_pct=2.0, dta_mm=2.0, threshold=0.1, search_mm=None):
+    """Fraction of reference voxels above threshold * max(D_ref) with gamma <= 1.
+
+    D_ref, D_eval: [nz, ny, nx]; voxel: (dx, dy, dz) in cm.  Global criterion:
+    dose tolerance = dose_pct % of max(D_ref).  Gamma^2 = min over evaluated voxels within
+    the search radius of (r^2 / dta^2 + dD^2 / tol^2)."""
+    D_ref = np.asarray(D_ref, dtype=np.float64)
+    D_eval = np.asarray(D_eval, dtype=np.float64)
+    dx, dy, dz = (v * 10.0 for v in voxel)  # mm
+    tol = dose_pct / 100.0 * D_ref.max()
+    search = 1.5 * dta_mm if search_mm is None else search_mm
+    nx_, ny_, nz_ = int(search // dx), int(search // dy), int(search // dz)
+    g2 = np.full(D_ref.shape, np.inf)
+    nz, ny, nx = D_ref.shape
+    for kz in range(-nz_, nz_ + 1):
+        for ky in range(-ny_, ny_ + 1):
+            for kx in range(-nx_, nx_ + 1):
+                r2 = (kx * dx) ** 2 + (ky * dy) ** 2 + (kz * dz) ** 2
+                if r2 > search * search:
+                    continue
+                zs, ze = max(0, -kz), min(nz, nz - kz)
+                ys, ye = max(0, -ky), min(ny, ny - ky)
+                xs, xe = max(0, -kx), min(nx, nx - kx)
+                ref = D_ref[zs:ze, ys:ye, xs:xe]
+                ev = D_eval[zs + kz:ze + kz, ys + ky:ye + ky, xs + kx:xe + kx]
+                val = r2 / dta_mm ** 2 + (ev - ref) ** 2 / tol ** 2
+                sub = g2[zs:ze, ys:ye, xs:xe]
+                np.minimum(sub, val, out=sub)
+    m = D_ref > threshold * D_ref.max()
+    return float(np.mean(g2[m] <= 1.0 + 1e-12))

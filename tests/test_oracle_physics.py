@@ -1,0 +1,301 @@
+"""Pins of the FP64 oracle's physics routines against values and laws fixed outside it:
+published reference data (Random123 known answers, PDG radiation lengths, NIST PSTAR),
+closed forms derived independently of the code, conservation laws, and brute-force
+sampling statistics.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, optimize, stats
+
+from conftest import golden
+from oracle import oracle as O
+from paper_1409_8336_gb300 import workloads as W
+
+M_P, M_N, AMU = 938.272088, 939.565420, 931.49410242
+WATER_ZA = 0.111894 * 1 / 1.00794 + 0.888106 * 8 / 15.9994
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    for row in golden("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in row]
+        assert O.philox(v[0:4], v[4:6]) == v[6:10]
+
+
+def test_uniform_stream_is_uniform():
+    u = np.concatenate([O.draw4(7, pid, k, 0) for pid in range(200) for k in range(100)])
+    assert np.all((u > 0) & (u < 1))
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+    # distinct tags and counters give distinct streams
+    assert not np.allclose(O.draw4(7, 3, 5, 0), O.draw4(7, 3, 5, 1))
+    assert not np.allclose(O.draw4(7, 3, 5, 0), O.draw4(8, 3, 5, 0))
+
+
+# ---------------------------------------------------------------- tables
+def test_radiation_length_matches_pdg():
+    X0 = O.f("or_radiation_length_element")
+    for Z, A, ref in golden("pdg_radiation_length.txt"):
+        if Z == "0":
+            p = W.config1()
+            got = O.material_info(p, 0)["X0mass"]
+        else:
+            got = X0(int(Z), float(A))
+        assert abs(got - float(ref)) / float(ref) < 2e-3, (Z, got, ref)
+
+
+def test_stopping_power_and_range_match_pstar():
+    S = O.f("or_mass_stopping_power")
+    p = W.config1()
+    for E, Sref, Rref in golden("pstar_water.txt"):
+        E, Sref, Rref = float(E), float(Sref), float(Rref)
+        assert abs(S(E, WATER_ZA, 75.0) - Sref) / Sref < 5e-3
+        assert abs(O.range_csda(p, 0, E) - Rref) / Rref < 5e-3
+
+
+def test_bethe_is_linear_in_electron_density():
+    S = O.f("or_mass_stopping_power")
+    for E in (5.0, 50.0, 200.0):
+        assert S(E, 0.4, 80.0) / S(E, 0.5, 80.0) == pytest.approx(0.8, rel=1e-12)
+    # higher mean excitation energy lowers the stopping power
+    assert S(100.0, 0.5, 100.0) < S(100.0, 0.5, 75.0)
+
+
+def test_range_equals_independent_quadrature_and_inverse():
+    S = O.f("or_mass_stopping_power")
+    E = np.array([0.3, 1.0, 3.0, 20.0, 70.0, 150.0, 230.0, 290.0])
+    R, Eb = O.range_roundtrip(WATER_ZA, 75.0, E)
+    S1 = S(1.0, WATER_ZA, 75.0)
+    for e, r in zip(E, R):
+        if e <= 1.0:
+            ref = 2.0 * math.sqrt(e) / S1          # closed form of the sqrt(E) continuation
+        else:
+            ref = 2.0 / S1 + integrate.quad(lambda x: 1.0 / S(x, WATER_ZA, 75.0), 1.0, e,
+                                            epsabs=0, epsrel=1e-12, limit=200)[0]
+        assert r == pytest.approx(ref, rel=1e-9)
+    assert np.allclose(Eb, E, rtol=1e-10, atol=0)
+
+
+def test_material_scaling_factor_definition():
+    p = W.config2()
+    info_w = O.material_info(p, 0)
+    S = O.f("or_mass_stopping_power")
+    for m in (1, 2):
+        mi = O.material_info(p, m)
+        assert mi["f"] == pytest.approx(S(100.0, mi["ZA"], mi["I_eV"]) / S(100.0, info_w["ZA"], 75.0), rel=1e-12)
+    assert O.material_info(p, 3)["f"] == 1.0   # titanium keeps its own table
+
+
+# ---------------------------------------------------------------- MCS / straggling
+def test_highland_worked_example():
+    # 100 MeV proton, 1 cm of water (X0 = 36.08 cm): pc = 444.58 MeV, beta = 0.42819,
+    # x/X0 = 0.027716, ln(x/(X0 beta^2)) = -1.8893 -> 13.6/190.37 * 0.16648 * 0.92821 = 11.040 mrad,
+    # times the paper's 1.07 = 11.81 mrad.
+    th = O.f("or_highland_theta0")(100.0, 1.0, 36.08)
+    assert th == pytest.approx(0.011813, rel=2e-3)
+    assert O.f("or_highland_theta0")(100.0, 0.0, 36.08) == 0.0
+
+
+def test_bohr_variance_nonrelativistic_limit():
+    # Bohr: sigma^2 = 4 pi N_A r_e^2 (m_e c^2)^2 rho Z/A x -> 0.1569 rho Z/A x MeV^2 as beta -> 0
+    v = O.f("or_bohr_variance")(1e-6, 1.0, 0.5, 1.0)
+    assert v == pytest.approx(0.15691 * 0.5, rel=1e-3)
+    # relativistic factor (1 - b^2/2)/(1 - b^2) at 200 MeV
+    g = 1 + 200.0 / M_P
+    b2 = 1 - 1 / g ** 2
+    assert O.f("or_bohr_variance")(200.0, 1.0, 0.5, 1.0) / v == pytest.approx((1 - b2 / 2) / (1 - b2), rel=1e-6)
+
+
+# ---------------------------------------------------------------- cross-sections
+def test_cross_section_properties():
+    si, se, snn = O.f("or_sigma_inelastic"), O.f("or_sigma_elastic"), O.f("or_sigma_nn")
+    assert si(1, 1, 200.0) == 0.0                         # no non-elastic channel on free protons
+    for Z, A in ((6, 12), (8, 16), (20, 40), (22, 48)):
+        bc = 1.439964548 * Z / (1.16 * (A ** (1 / 3) + 1))
+        assert si(Z, A, 0.999 * bc) == 0.0                  # closed below the Coulomb barrier
+        geo = 0.65 * math.pi * 1.16 ** 2 * (A ** (1 / 3) + 0.8) ** 2 * 10.0   # mb
+        assert si(Z, A, 1e6) == pytest.approx(geo, rel=1e-4)
+        assert 150 < si(Z, A, 150.0) < 1500                 # hundreds of mb, like measured data
+    assert se(1, 1, 100.0) == snn(100.0, 1)
+    assert snn(5.0, 1) == snn(10.0, 1)                     # clamped below 10 MeV
+    assert 15 < snn(200.0, 1) < 35 and 25 < snn(200.0, 0) < 60
+
+
+def test_mass_formula_against_measured_binding():
+    B = O.f("or_binding_energy")
+    # measured binding energies (MeV), Atomic Mass Evaluation
+    for Z, A, ref, tol in ((6, 12, 92.162, 0.04), (8, 16, 127.619, 0.02), (20, 40, 342.052, 0.02),
+                           (22, 48, 418.699, 0.02), (2, 4, 28.2957, 1e-5), (1, 2, 2.22457, 1e-5)):
+        assert abs(B(Z, A) - ref) / ref < tol
+    assert O.f("or_nuclear_mass")(1, 1) == M_P and O.f("or_nuclear_mass")(0, 1) == M_N
+
+
+# ---------------------------------------------------------------- elastic
+@pytest.mark.parametrize("Z,A,E", [(1, 1, 150.0), (8, 16, 150.0), (8, 16, 20.0), (22, 48, 230.0), (6, 12, 70.0)])
+def test_elastic_two_body_conserves_four_momentum(Z, A, E):
+    rng = np.random.default_rng(1)
+    M = O.f("or_nuclear_mass")(Z, A)
+    plab = math.sqrt(E * E + 2 * E * M_P)
+    for _ in range(200):
+        T1, c1, T2, c2, _ = O.elastic(Z, A, E, rng.uniform(size=3))
+        assert T1 + T2 == pytest.approx(E, abs=1e-10)
+        p1 = math.sqrt(T1 * T1 + 2 * T1 * M_P)
+        p2 = math.sqrt(T2 * T2 + 2 * T2 * M)
+        s1, s2 = math.sqrt(max(0, 1 - c1 * c1)), math.sqrt(max(0, 1 - c2 * c2))
+        assert p1 * c1 + p2 * c2 == pytest.approx(plab, rel=1e-8)
+        assert p1 * s1 == pytest.approx(p2 * s2, abs=1e-6 * plab)
+
+
+def test_ranft_momentum_transfer_distribution():
+    """|t| = 2 p*^2 (1 - cos theta*) follows the mixture of the two truncated exponentials of Eq. 3."""
+    Z, A, E = 8, 16, 150.0
+    M = O.f("or_nuclear_mass")(Z, A)
+    plab = math.sqrt(E * E + 2 * E * M_P)
+    s = M_P ** 2 + M ** 2 + 2 * M * (E + M_P)
+    p = plab * M / math.sqrt(s) / 1000.0
+    rng = np.random.default_rng(2)
+    t = []
+    for _ in range(20000):
+        *_, ccm = O.elastic(Z, A, E, rng.uniform(size=3))
+        t.append(2 * p * p * (1 - ccm))
+    a1, b1, a2, b2 = A ** 1.63, 14.5 * A ** 0.66, 1.4 * A ** 0.33, 10.0
+    tmax = 4 * p * p
+    w1, w2 = a1 * (1 - math.exp(-b1 * tmax)) / b1, a2 * (1 - math.exp(-b2 * tmax)) / b2
+
+    def cdf(x):
+        x = np.minimum(np.asarray(x), tmax)
+        return (a1 * (1 - np.exp(-b1 * x)) / b1 + a2 * (1 - np.exp(-b2 * x)) / b2) / (w1 + w2)
+
+    assert stats.kstest(np.array(t), cdf).pvalue > 1e-3
+
+
+# ---------------------------------------------------------------- evaporation
+@pytest.mark.parametrize("X,a", [(0.05, 2.0), (1.0, 1.5), (12.0, 2.0), (40.0, 5.0)])
+def test_evaporation_width_integral_closed_form(X, a):
+    # int_0^X (X-x) exp(2 sqrt(a x)) dx = (1/a^2)[exp(2Y)(Y^2 - 3Y/2 + 3/4) + Y^2/2 - 3/4], Y = sqrt(aX)
+    Y = math.sqrt(a * X)
+    ref = (math.exp(2 * Y) * (Y * Y - 1.5 * Y + 0.75) + 0.5 * Y * Y - 0.75) / (a * a)
+    assert O.f("or_evap_integral")(X, a) == pytest.approx(ref, rel=1e-8)
+
+
+@pytest.mark.parametrize("X,a", [(0.1, 2.0), (3.0, 1.0), (20.0, 2.0)])
+def test_evaporation_energy_sampler(X, a):
+    z = O.evap_samples(X, a, 5, 77, 20000)
+    assert np.all((z >= 0) & (z <= X))
+    norm = integrate.quad(lambda x: x * math.exp(2 * math.sqrt(a * (X - x))), 0, X)[0]
+    grid = np.linspace(0, X, 401)
+    cum = np.concatenate([[0.0], np.cumsum([integrate.quad(lambda x: x * math.exp(2 * math.sqrt(a * (X - x))),
+                                                           grid[i], grid[i + 1])[0] for i in range(400)])]) / norm
+    assert stats.kstest(z, lambda v: np.interp(v, grid, cum)).pvalue > 1e-3
+
+
+def test_evaporation_is_isotropic_and_branches_by_widths():
+    Z, A, Ex = 8, 16, 30.0
+    n = 20000
+    out = O.evap_batch(Z, A, Ex, 9, 1000, n)
+    em = out[out[:, 0] >= 0]
+    c = em[:, 2]
+    assert abs(c.mean()) < 3 * c.std() / math.sqrt(len(c))          # isotropic in the rest frame
+    assert stats.kstest(c, "uniform", args=(-1, 2)).pvalue > 1e-3
+    # first-emission branching equals the Weisskopf-Ewing widths computed here by quadrature
+    mass = O.f("or_nuclear_mass")
+    ej = [(0, 1, 2.0), (1, 1, 2.0), (1, 2, 3.0), (1, 3, 2.0), (2, 3, 2.0), (2, 4, 1.0)]
+    G = []
+    for z, a, g in ej:
+        Zd, Ad = Z - z, A - a
+        S = mass(Zd, Ad) + mass(z, a) - mass(Z, A)
+        R = 1.5 * (Ad ** (1 / 3) + a ** (1 / 3))
+        V = 1.439964548 * z * Zd / R if z > 0 else 0.0
+        Xj, ad = Ex - S - V, Ad / 8.0
+        if Xj <= 0:
+            G.append(0.0)
+            continue
+        width = integrate.quad(lambda e: (e - V) * math.exp(2 * math.sqrt(ad * (Ex - S - e))), V, Ex - S)[0]
+        G.append(g * (a * Ad / (a + Ad)) * R * R * width)
+    G = np.array(G) / sum(G)
+    counts = np.array([(em[:, 0] == j).sum() for j in range(6)])
+    mask = G * len(em) > 5
+    assert stats.chisquare(counts[mask], G[mask] * len(em) * counts[mask].sum() / (G[mask] * len(em)).sum()).pvalue > 1e-3
+
+
+# ---------------------------------------------------------------- nucleus model and cascade
+@pytest.mark.parametrize("Z,A", [(6, 12), (8, 16), (20, 40), (22, 48)])
+def test_fermi_gas_shells(Z, A):
+    nu = O.nucleus_info(Z, A)
+    r = nu["r"]
+    vol = 4 / 3 * math.pi * (r[1:] ** 3 - r[:-1] ** 3)
+    assert np.sum((nu["rho_p"] + nu["rho_n"]) * vol) == pytest.approx(A, rel=1e-12)
+    assert np.allclose(nu["rho_p"] * (A - Z), nu["rho_n"] * Z)
+    assert len(r) == 16 and r[0] == 0.0                                 # 15 shells
+    assert 0.12 < (nu["rho_p"][0] + nu["rho_n"][0]) < 0.20              # near nuclear saturation density
+    # Fermi energy of symmetric matter at 0.16 fm^-3 is about 37 MeV
+    assert 20 < nu["TF_p"][0] < 45
+    assert np.all(np.diff(nu["rho_p"]) <= 1e-15)                        # density falls outward
+    assert np.allclose(nu["V_p"] - nu["TF_p"], nu["S_p"]) and np.allclose(nu["V_n"] - nu["TF_n"], nu["S_n"])
+
+
+SPECIES_ZA = {0: (0, 1), 1: (1, 1), 2: (1, 2), 3: (1, 3), 4: (2, 3), 5: (2, 4)}
+
+
+@pytest.mark.parametrize("Z,A,E", [(6, 12, 90.0), (8, 16, 200.0), (20, 40, 200.0), (22, 48, 120.0), (7, 14, 30.0)])
+def test_cascade_conservation_and_pauli(Z, A, E):
+    n = 400
+    summ, prod, extra = O.inc_batch(Z, A, E, 11, 5000, n)
+    mass = O.f("or_nuclear_mass")
+    p_in = math.sqrt(E * E + 2 * E * M_P)
+    for i in range(n):
+        k = int(summ[i, 0])
+        if summ[i, 7]:
+            continue
+        sp = prod[i, :k, 0].astype(int)
+        T = prod[i, :k, 1]
+        Zs = sum(SPECIES_ZA[s][0] for s in sp) + summ[i, 1]
+        As = sum(SPECIES_ZA[s][1] for s in sp) + summ[i, 2]
+        assert (Zs, As) == (Z + 1, A + 1)                         # charge and baryon number
+        assert np.all(T >= 0) and summ[i, 4] >= 0 and summ[i, 3] >= 0
+        # total energy: E = sum T + T_residual + E*_left + binding, binding from the mass table
+        assert T.sum() + summ[i, 3] + summ[i, 4] + summ[i, 5] == pytest.approx(E, abs=1e-9)
+        bind = sum(mass(*SPECIES_ZA[s]) for s in sp) + mass(int(summ[i, 1]), int(summ[i, 2])) - mass(Z, A) - M_P
+        assert summ[i, 5] == pytest.approx(bind, abs=1e-7)
+        assert extra[i, 0] >= 1                                   # at least one allowed NN collision
+        assert extra[i, 1] >= 0.0                                 # every accepted product above its Fermi energy
+        # momentum balance: |p_in - sum p| = |p_residual|
+        pv = np.zeros(3)
+        for s, t, d in zip(sp, T, prod[i, :k, 2:5]):
+            pv += (math.sqrt(t * t + 2 * t * (M_P if s == 1 else M_N)) if s <= 1 else
+                   math.sqrt(2 * SPECIES_ZA[s][1] * AMU * t)) * d
+        pres = math.sqrt(2 * summ[i, 2] * AMU * summ[i, 3])
+        # cascade nucleons carry relativistic momenta, evaporated ones Galilean: allow small slack
+        assert np.linalg.norm(np.array([0, 0, p_in]) - pv) == pytest.approx(pres, abs=0.02 * p_in + 1e-6)
+    assert summ[:, 7].sum() == 0
+
+
+def test_cascade_yields_are_physical():
+    summ, prod, _ = O.inc_batch(8, 16, 200.0, 3, 0, 1000)
+    k = summ[:, 0].astype(int)
+    sp = prod[:, :, 0]
+    valid = np.arange(prod.shape[1])[None, :] < k[:, None]
+    n_p = ((sp == 1) & valid).sum(1).mean()
+    n_n = ((sp == 0) & valid).sum(1).mean()
+    assert 0.8 < n_p < 4.0 and 0.5 < n_n < 3.5
+    assert summ[:, 6].mean() < 10                                # few retries per event
+
+
+# ---------------------------------------------------------------- bookkeeping
+def test_batch_statistics():
+    rng = np.random.default_rng(0)
+    t = rng.normal(5.0, 1.0, size=(1000, 10))
+    tot, sig = O.batch_stats(t)
+    assert np.allclose(tot, t.sum(1))
+    assert np.allclose(sig, np.sqrt(10) * t.std(1, ddof=1))
+    tot, sig = O.batch_stats(np.full((10, 10), 3.0))
+    assert np.all(sig == 0.0)
+
+
+def test_largest_remainder_allocation():
+    p = W.config3(shape=(8, 16, 16), n_layers=4)
+    w = p.spots[:, 9]
+    for n in (1, 7, 1000, 99991):
+        cnt = O.allocate_histories(p, n).astype(np.int64)
+        assert cnt.sum() == n
+        assert np.all(np.abs(cnt - n * w / w.sum()) < 1.0)
