@@ -110,8 +110,9 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
     out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
 }
 
-/* Uniform in (0,1): the top 24 bits of a word, offset by half a step. */
-static double u01(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
+/* Uniform in (0,1): the top 23 bits of a word, offset by half a step (a value
+ * that single precision also represents exactly). */
+static double u01(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 /* Four uniforms of stream (pid, word2, tag) under key = seed. */
 static void draw4(uint64_t seed, uint64_t pid, uint32_t word2, uint32_t tag, double u[4])
