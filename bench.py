@@ -1,0 +1,290 @@
+#!/usr/bin/env python
+"""Throughput benchmark: proton histories per second on one GB300.
+
+Workload (default): the heterogeneous slab phantom -- 128^3 voxels of 1.5 mm
+(water / cortical bone / lung / water with a 1 cm titanium insert), 1e6 protons
+split over 70, 150 and 230 MeV pencil beams of sigma 4 mm, full physics with
+the intranuclear cascade.  One step = one complete transport of all 1e6
+histories (graph launch of primaries, secondary generations and cascades, then
+the batch-statistics kernel), inputs resident in HBM.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "proton histories/s on 1 GB300 (full cascade)"
+UNIT = "histories/s"
+N_HISTORIES = 1_000_000
+FIX = 2.0 ** -24
+# Algorithmic single-precision arithmetic operations of one condensed-history step
+# (Philox x2, voxel lookup, range/inverse-range splines, cross-section table,
+# boundary distances x2, Highland + rotation, Bohr + Box-Muller, deposit); the
+# count is derived in the design doc.
+OPS_PER_STEP = 620
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--histories", type=int, default=N_HISTORIES)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1409_8336_gb300 import workloads as W
+
+    return W.config2()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = max(mx, float(r[1]))
+                for n, v in zip(names, r[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(prob, n_total, seconds, seed=1):
+    """Times the CPU oracle (single thread) on an even sample of the workload's spots."""
+    from oracle import oracle as O
+
+    cnt = O.allocate_histories(prob, n_total)
+    first = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    # pilot to size the sample
+    t0 = time.perf_counter()
+    for s in range(len(cnt)):
+        O.run(prob, n_total, seed, h_begin=int(first[s]), h_end=int(first[s]) + 30)
+    pilot = time.perf_counter() - t0
+    per = max(1, int(seconds / max(pilot, 1e-6) * 30))
+    t0 = time.perf_counter()
+    done = 0
+    for s in range(len(cnt)):
+        k = min(per, int(cnt[s]))
+        O.run(prob, n_total, seed, h_begin=int(first[s]), h_end=int(first[s]) + k)
+        done += k
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    prob = workload()
+    times, dones = [], []
+    for i in range(args.warmup + args.steps):
+        rate, done, dt = oracle_rate(prob, args.histories, max(2.0, args.cpu_seconds / 3), seed=1 + i)
+        if i >= args.warmup:
+            times.append(dt)
+            dones.append(done)
+    value = sum(dones) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.histories / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": prob.name, "histories": args.histories, "spots": "70/150/230 MeV"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d histories per step, even over the three spots" % (sum(dones) // len(dones))},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_1409_8336_gb300 import Engine, build
+
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    prob = workload()
+    n = args.histories
+    stream = torch.cuda.current_stream()
+    eng = Engine(device=local, n_batches=prob.n_batches)
+    eng.load_problem(prob)
+    eng.enable_profile(True)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def one(seed):
+        flush.fill_(float(seed))                           # evict L2 between steps
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        eng.transport(n, seed, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        prof, steps0 = eng.read_profile()
+        return a.elapsed_time(b), prof, steps0, eng.read_ledger()
+
+    for i in range(args.warmup):
+        one(1000 + i)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, prof_ms, prof_n, steps_primary, ledgers, launches = [], 0.0, 0, 0, [], 0
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            t, prof, s0, led = one(rank * 100003 + i + 1)
+            ms.append(t)
+            prof_ms += prof["transport_primary"]["ms"]
+            prof_n += prof["transport_primary"]["launches"]
+            steps_primary += s0
+            ledgers.append(led)
+            launches += sum(p["launches"] for p in prof.values())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API with host buffers (pinned): H2D of the phantom and spots,
+    # transport, D2H of dose and error, every step
+    mat_h = torch.from_numpy(np.ascontiguousarray(prob.mat)).pin_memory()
+    rho_h = torch.from_numpy(np.ascontiguousarray(prob.rho)).pin_memory()
+    dose_h = torch.empty(prob.n_voxels, dtype=torch.float64).pin_memory()
+    sig_h = torch.empty(prob.n_voxels, dtype=torch.float64).pin_memory()
+    eng.enable_profile(False)
+    e2e_t = []
+    for i in range(max(2, min(args.steps, 5)) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eng.load_phantom(prob.shape, prob.voxel, prob.origin, mat=mat_h, rho=rho_h)
+        eng.clear_spots()
+        eng.add_spots(prob.spots)
+        eng.transport(n, 77 + i, stream=stream)
+        eng.read_dose(dose_h, sig_h)
+        dt = time.perf_counter() - t0
+        if i > 0:
+            e2e_t.append(dt)
+    e2e = world * n / statistics.median(e2e_t)
+    h2d = prob.n_voxels * 5 + len(prob.spots) * 80
+    d2h = prob.n_voxels * 16
+
+    pk, src = peaks()
+    led = ledgers[-1]
+    steps_per_launch = steps_primary / max(prof_n, 1)
+    launch_ms = prof_ms / max(prof_n, 1)
+    achieved = OPS_PER_STEP * steps_per_launch / (launch_ms * 1e-3) / 1e12
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12       # FP32 lanes x clock, TOP/s
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, done, dt = oracle_rate(prob, n, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d histories (equal thirds of the 70/150/230 MeV spots) in %.1f s" % (done, dt)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": prob.name, "histories_per_step": n, "spots": "70/150/230 MeV, sigma 4 mm",
+                       "batches": prob.n_batches, "physics": "full cascade", "l2": "flushed between steps",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "kernel": "transport_kernel (primaries)", "achieved": achieved,
+                         "peak": alu_peak, "unit": "TOP/s", "frac": achieved / alu_peak, "traffic": None,
+                         "peak_source": "%s sm_max_mhz x 152 SMs x 128 FP32 lanes" % src,
+                         "ops_per_step": OPS_PER_STEP, "steps_per_launch": steps_per_launch,
+                         "launch_ms": launch_ms},
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+            "stats": {"steps_per_history": led["steps"] / n, "inelastic": led["inelastic"],
+                      "elastic": led["elastic"], "secondaries": led["secondaries"],
+                      "ledger_imbalance": (led["incident"] - led["deposited"] - led["escaped"] - led["binding"]) /
+                      max(1, led["incident"])},
+        }
+        print(json.dumps(line))
+    eng.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * pmc.h -- C ABI of the GB300 proton Monte Carlo engine.
+ *
+ * The engine implements the condensed-history proton transport method of
+ * Wan Chan Tseung, Ma & Beltran (arXiv:1409.8336): transport through a
+ * voxelised geometry with tabulated stopping power and CSDA range (Sec. II.A.2,
+ * Eq. 1 and Eq. 2), Gaussian energy-loss straggling, Highland multiple
+ * scattering scaled by 1.07 with a random hinge (Sec. II.A.2-3), coherent
+ * nuclear elastic scattering with the Ranft angular distribution (Sec. II.A.5,
+ * Eq. 3), non-elastic collisions handed to an intranuclear-cascade plus
+ * evaporation event generator (Sec. II.A.4), and dose scoring in ten groups for
+ * a per-voxel statistical error (Sec. II.B.2).
+ *
+ * Conventions for every entry point:
+ *   - units are MeV, cm, g/cm^3; volumes are indexed x fastest:
+ *     v = (iz * ny + iy) * nx + ix;
+ *   - host arrays passed in are owned by the caller and copied during the call;
+ *     device memory is owned by the context (allocated through the optional
+ *     allocator in pmc_options, else cudaMalloc) and released by pmc_destroy;
+ *   - the return value is PMC_OK (0) or a negative PMC_E_* code; the message of
+ *     the last failure is available from pmc_last_error.  No C++ exception
+ *     crosses this boundary.  A context is not thread safe.
+ */
+#ifndef PMC_H
+#define PMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PMC_OK 0
+#define PMC_E_INVALID (-1)        /* bad argument or call order */
+#define PMC_E_OOM (-2)            /* device allocation failed */
+#define PMC_E_QUEUE_OVERFLOW (-3) /* a particle queue was full: results incomplete */
+#define PMC_E_TIMEOUT (-4)        /* a bounded device loop hit its limit */
+#define PMC_E_CUDA (-5)           /* CUDA runtime error */
+
+/* physics switches (pmc_options.physics_flags); 0 = full physics */
+#define PMC_NO_STRAGGLING 1u
+#define PMC_NO_MCS 2u
+#define PMC_NO_ELASTIC 4u
+#define PMC_NO_INELASTIC 8u
+
+/* transport modes */
+#define PMC_FULL_CASCADE 0        /* non-elastic events by cascade + evaporation */
+#define PMC_SURROGATE 1           /* non-elastic events by the trained quantile network */
+
+#define PMC_MAX_NUCLIDES 16
+#define PMC_MAX_MATERIALS 16
+#define PMC_MAX_NUC_PER_MAT 12
+#define PMC_MAX_HU_BINS 16
+
+typedef struct pmc_ctx pmc_ctx;
+
+/* Optional device allocator (e.g. a framework's caching allocator). */
+typedef void* (*pmc_alloc_fn)(size_t bytes, void* user);
+typedef void (*pmc_free_fn)(void* ptr, void* user);
+
+typedef struct {
+    int device;               /* CUDA device ordinal */
+    int n_batches;            /* statistical groups, 2..1024 (paper: 10, Sec. II.B.2) */
+    unsigned physics_flags;   /* PMC_NO_* */
+    int block_size;           /* transport block size; 0 = autotuned on first transport */
+    int64_t chunk;            /* histories per sub-group (Sec. II.B.2); 0 = automatic */
+    pmc_alloc_fn alloc;       /* NULL = cudaMalloc */
+    pmc_free_fn free;
+    void* alloc_user;
+} pmc_options;
+
+/* A target nuclide (Z, A), its molar mass (g/mol) and mean excitation energy (eV). */
+typedef struct { int Z, A; double mass_u, I_eV; } pmc_nuclide;
+
+/* A material: mass fractions w of nuclides nuc[0..n-1], nominal density, mean
+ * excitation energy (0 = Bragg additivity), and whether it keeps its own
+ * stopping-power table (air and titanium, Sec. II.A.2) instead of the scaled
+ * water table of Eq. 1.  Material 0 is the reference water. */
+typedef struct {
+    int n;
+    int nuc[PMC_MAX_NUC_PER_MAT];
+    double w[PMC_MAX_NUC_PER_MAT];
+    double rho;
+    double I_eV;
+    int own_table;
+} pmc_material;
+
+/* HU bin [lo, hi) -> material, density rho = rho_a + rho_b * HU (Sec. II.A.1). */
+typedef struct { int lo, hi, material; double rho_a, rho_b; } pmc_hu_bin;
+
+/* A Gaussian pencil-beam spot entering the phantom through its z = z0 face:
+ * mean energy and spread, centre and widths (cm), direction, relative weight. */
+typedef struct { double E, sigma_E, x, y, sigma_x, sigma_y, u, v, w, weight; } pmc_spot;
+
+/* Energy ledger of the last transport, in units of 2^-24 MeV:
+ * incident = deposited + escaped + binding (+ rounding of a few units per event). */
+typedef struct {
+    int64_t incident, deposited, escaped, binding;
+    int64_t histories, steps, elastic, inelastic, secondaries, transparent, inc_retries;
+    int64_t queue_high_water, generations, dropped, errors;
+} pmc_ledger;
+
+/* Creates a context on opt->device (opt may be NULL for defaults). */
+int pmc_create(pmc_ctx** out, const pmc_options* opt);
+void pmc_destroy(pmc_ctx* ctx);
+const char* pmc_last_error(const pmc_ctx* ctx);
+
+/* Builds the physics tables (Sec. II.A.2, II.A.4-5) for the nuclides and
+ * materials and uploads them.  n_hu may be 0 when the phantom is given by
+ * material indices.  Errors: PMC_E_INVALID for counts beyond the PMC_MAX_*
+ * limits, fractions that do not sum to 1 within 1e-6, or material 0 not a
+ * scaled-table material. */
+int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc,
+                       const pmc_material* mat, int n_mat,
+                       const pmc_hu_bin* hu, int n_hu);
+
+/* Uploads the voxel geometry (Sec. II.A.1): either hu (int16 HU, mapped by
+ * the HU bins) or mat (uint8 material index) with rho (float density); the
+ * other pointer(s) NULL.  Pointers are host memory. */
+int pmc_load_phantom(pmc_ctx* ctx, int nx, int ny, int nz,
+                     double dx, double dy, double dz, double x0, double y0, double z0,
+                     const int16_t* hu, const uint8_t* mat, const float* rho);
+
+/* Appends n spots; pmc_clear_spots removes them all. */
+int pmc_add_spots(pmc_ctx* ctx, const pmc_spot* spots, int n);
+int pmc_clear_spots(pmc_ctx* ctx);
+
+/* Simulates n_histories primary protons, spread over the spots in proportion
+ * to weight (largest remainder), with random numbers keyed by seed.  History h
+ * scores into group h mod n_batches.  Tallies are zeroed first; the call ends
+ * with the batch-statistics kernel, so dose and error are ready on the device.
+ * stream: a cudaStream_t or NULL (the context's own stream).  The call blocks
+ * until the run has finished. */
+int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, void* stream);
+
+/* Dose (Gy) and its statistical standard error per voxel, to host arrays of
+ * n_voxels doubles (either may be NULL). */
+int pmc_read_dose(pmc_ctx* ctx, double* dose_gy, double* sigma_gy, size_t n_voxels);
+
+/* Raw group tallies [n_voxels][n_batches] in units of 2^-24 MeV (host array). */
+int pmc_read_tally(pmc_ctx* ctx, int64_t* tally, size_t n);
+
+int pmc_read_ledger(pmc_ctx* ctx, pmc_ledger* out);
+
+/* Per-history ledger for the first max_histories histories of the next
+ * transports ([h][4]: incident, deposited, escaped, binding in 2^-24 MeV);
+ * 0 disables it.  Read with pmc_read_history_ledger. */
+int pmc_enable_history_ledger(pmc_ctx* ctx, uint64_t max_histories);
+int pmc_read_history_ledger(pmc_ctx* ctx, int64_t* out, uint64_t n_histories);
+
+/* Records up to cap protons leaving the grid in the next transports
+ * ([i][8] floats: E, x, y, z, u, v, w, history); 0 disables it. */
+int pmc_enable_escape_record(pmc_ctx* ctx, uint64_t cap);
+int pmc_read_escape_record(pmc_ctx* ctx, float* out, uint64_t cap, uint64_t* n);
+
+/* Sets the transport launch shape (block size, histories per sub-group)
+ * chosen by the caller's own autotuning; 0 keeps the current value. */
+int pmc_set_launch(pmc_ctx* ctx, int block_size, int64_t chunk);
+
+/* Kernel timing: when enabled, the run records CUDA events around every
+ * kernel launch on the run's stream (inside the captured graph).
+ * pmc_read_profile returns, per kernel kind (0 primary transport, 1 secondary
+ * transport, 2 cascade, 3 dose statistics), the summed milliseconds of the
+ * last transport in ms[4] and the number of launches in launches[4], and the
+ * primary-transport step count in *primary_steps. */
+int pmc_enable_profile(pmc_ctx* ctx, int on);
+int pmc_read_profile(pmc_ctx* ctx, double* ms, int64_t* launches, int64_t* primary_steps);
+
+/* Device-side evaluation of single routines, for tests.
+ * pmc_debug_philox: Philox4x32-10 of n counters ctr[n][4] under key[2]
+ *   (Salmon et al., SC'11) into out[n][4].
+ * pmc_debug_tables: range R (g/cm^2) and inverse E(R) of material m's table
+ *   at n energies (Sec. II.A.2): r_out[i] = R(E[i]), e_out[i] = E(r_out[i]).
+ * pmc_debug_inc: n non-elastic events of a proton of energy E on nuclide
+ *   index `nuclide` (Sec. II.A.4) with pids pid0 + i, in the frame where the
+ *   proton moves along +z.  summary[n][8] = n_products, Z_res, A_res, T_res,
+ *   E*_left, binding, retries, transparent; products[n][cap][5] = species
+ *   (0 n, 1 p, 2 d, 3 t, 4 He3, 5 alpha), T, direction.
+ * pmc_debug_elastic: n elastic scatterings on nuclide index `nuclide` at
+ *   energy E (Sec. II.A.5, Eq. 3) from uniforms u[n][3];
+ *   out[n][5] = T1, cos1, T2, cos2, cos_cm. */
+int pmc_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n);
+int pmc_debug_tables(pmc_ctx* ctx, int material, const double* E, double* r_out, double* e_out, int n);
+int pmc_debug_inc(pmc_ctx* ctx, int nuclide, double E, uint64_t seed, uint64_t pid0, int n,
+                  double* summary, double* products, int cap);
+int pmc_debug_elastic(pmc_ctx* ctx, int nuclide, double E, const double* u, double* out, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMC_H */

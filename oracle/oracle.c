@@ -684,11 +684,12 @@ void or_inc_event(const or_nucleus* nu, double E, uint64_t seed, uint64_t pid, o
         int esc_idx[INC_MAX_PARTICLES], n_esc = 0;
         for (int ip = 0; ip < n; ++ip) {
             inc_particle* p = &P[ip];
-            int q = p->q, crossings = 0;
+            int q = p->q, crossings = 0, iters = 0;
             double m = mq[q];
             for (;;) {
                 int i = p->shell;
                 if (p->T - nu->V[q][i] <= 0.0) { p->done = 2; break; }   /* bound: captured */
+                if (++iters > 100000) { p->done = 2; break; }             /* flight cap: captured */
                 double s_out = dist_out(p->r, p->d, nu->r[i + 1]);
                 double s_in = (i > 0) ? dist_in(p->r, p->d, nu->r[i]) : -1.0;
                 int inner = (s_in >= 0.0 && s_in < s_out);

@@ -1,0 +1,1034 @@
+// host.cu -- C ABI of the engine (include/pmc.h): physics-table construction in
+// double precision (Sec. II.A.2, II.A.4-5), device memory, the per-run kernel
+// sequence captured in a CUDA graph (Sec. II.B.2: primaries, then generations
+// of transport -> cascade until no secondary proton is left, then the dose
+// statistics), and the result read-back.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/pmc.h"
+#include "pmc_kernels.cuh"
+
+using namespace pmc;
+
+namespace {
+
+constexpr int kGenerations = 10;        // transport -> cascade rounds captured per sub-group
+constexpr double kNA = 6.02214076e23;
+
+// ---------------------------------------------------------------------------
+// physics used to build the tables (double precision)
+// ---------------------------------------------------------------------------
+double bethe_mass(double E, double ZA, double I_eV) {
+  // Bethe mass stopping power without shell or density corrections; below
+  // 1 MeV continued as S(1 MeV) sqrt(E).
+  const double me = 0.51099895, mp = 938.272088, K = 0.307075;
+  const double e = E < 1.0 ? 1.0 : E;
+  const double g = 1.0 + e / mp, b2 = 1.0 - 1.0 / (g * g), bg2 = b2 * g * g, r = me / mp;
+  const double tmax = 2.0 * me * bg2 / (1.0 + 2.0 * g * r + r * r);
+  const double I = I_eV * 1e-6;
+  const double s = K * ZA / b2 * (0.5 * std::log(2.0 * me * bg2 * tmax / (I * I)) - b2);
+  return E < 1.0 ? s * std::sqrt(E) : s;
+}
+
+double tsai_x0(int Z, double A) {
+  double Lr, Lp;
+  if (Z == 1) { Lr = 5.31; Lp = 6.144; }
+  else if (Z == 2) { Lr = 4.79; Lp = 5.621; }
+  else if (Z == 3) { Lr = 4.74; Lp = 5.805; }
+  else if (Z == 4) { Lr = 4.71; Lp = 5.924; }
+  else { Lr = std::log(184.15 * std::pow(Z, -1.0 / 3.0)); Lp = std::log(1194.0 * std::pow(Z, -2.0 / 3.0)); }
+  const double a = Z / 137.035999084, a2 = a * a;
+  const double f = a2 * (1.0 / (1.0 + a2) + 0.20206 - 0.0369 * a2 + 0.0083 * a2 * a2 - 0.002 * a2 * a2 * a2);
+  return 716.408 * A / (Z * Z * (Lr - f) + Z * Lp);
+}
+
+double binding_energy(int Z, int A) {
+  const int N = A - Z;
+  if (A <= 1 || Z < 0 || N < 0) return 0.0;
+  if (A == 2) return Z == 1 ? 2.224566 : 0.0;
+  if (A == 3) return Z == 1 ? 8.481798 : (Z == 2 ? 7.718043 : 0.0);
+  if (A == 4) return Z == 2 ? 28.295660 : 0.0;
+  // Weizsaecker: volume, surface, Coulomb, asymmetry and pairing terms
+  const double a = A;
+  double b = 15.75 * a - 17.8 * std::cbrt(a * a) - 0.711 * Z * (Z - 1.0) / std::cbrt(a) -
+             23.7 * (N - Z) * double(N - Z) / a;
+  if (Z % 2 == 0 && N % 2 == 0) b += 11.18 / std::sqrt(a);
+  if (Z % 2 == 1 && N % 2 == 1) b -= 11.18 / std::sqrt(a);
+  return b > 0.0 ? b : 0.0;
+}
+
+double nuclear_mass(int Z, int A) { return Z * 938.272088 + (A - Z) * 939.565420 - binding_energy(Z, A); }
+
+double sigma_nn_h(double T, bool like) {
+  const double t = T < 10.0 ? 10.0 : T, g = 1.0 + t / 938.272088, b = std::sqrt(1.0 - 1.0 / (g * g));
+  return like ? 10.63 / (b * b) - 29.92 / b + 42.9 : 34.10 / (b * b) - 82.2 / b + 82.2;
+}
+
+double sigma_inel_h(int Z, int A, double E) {
+  if (A <= 1 || E <= 0.0) return 0.0;
+  const double a13 = std::cbrt(double(A)), bc = 1.439964548 * Z / (1.16 * (a13 + 1.0));
+  if (E <= bc) return 0.0;
+  return 0.65 * M_PI * 1.16 * 1.16 * (a13 + 0.8) * (a13 + 0.8) * 10.0 * (1.0 - bc / E) * (1.0 - std::exp(-E / 15.0));
+}
+
+double sigma_el_h(int A, double E) {
+  if (E <= 0.0) return 0.0;
+  if (A == 1) return sigma_nn_h(E, true);
+  return 12.0 * std::pow(double(A), 2.0 / 3.0) * (1.0 + 20.0 / (E + 10.0));
+}
+
+const double GL8X[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+const double GL8W[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+
+double integrate_inv_s(double a, double b, double ZA, double I) {
+  const double m = 0.5 * (a + b), h = 0.5 * (b - a);
+  double s = 0.0;
+  for (int k = 0; k < 4; ++k)
+    s += GL8W[k] * (1.0 / bethe_mass(m - h * GL8X[k], ZA, I) + 1.0 / bethe_mass(m + h * GL8X[k], ZA, I));
+  return s * h;
+}
+
+// Clamped cubic spline on a uniform grid: returns (y, M h^2/6) pairs.
+std::vector<float2> spline(const std::vector<double>& y, double h, double d0, double dn) {
+  const int n = static_cast<int>(y.size());
+  std::vector<double> a(n), b(n), c(n), r(n), M(n);
+  b[0] = 2.0; c[0] = 1.0; r[0] = 6.0 / h * ((y[1] - y[0]) / h - d0);
+  for (int i = 1; i < n - 1; ++i) {
+    a[i] = 1.0; b[i] = 4.0; c[i] = 1.0;
+    r[i] = 6.0 * (y[i + 1] - 2.0 * y[i] + y[i - 1]) / (h * h);
+  }
+  a[n - 1] = 1.0; b[n - 1] = 2.0; r[n - 1] = 6.0 / h * (dn - (y[n - 1] - y[n - 2]) / h);
+  for (int i = 1; i < n; ++i) {
+    const double w = a[i] / b[i - 1];
+    b[i] -= w * c[i - 1];
+    r[i] -= w * r[i - 1];
+  }
+  M[n - 1] = r[n - 1] / b[n - 1];
+  for (int i = n - 2; i >= 0; --i) M[i] = (r[i] - c[i] * M[i + 1]) / b[i];
+  std::vector<float2> out(n);
+  for (int i = 0; i < n; ++i) out[i] = make_float2(static_cast<float>(y[i]), static_cast<float>(M[i] * h * h / 6.0));
+  return out;
+}
+
+struct RangeClass {
+  double ZA, I;
+  std::vector<double> E, R;     // nodes on ln E
+  double range(double e) const {  // accurate range at any energy >= 1 MeV
+    const double dl = std::log(300.0) / (kNE - 1);
+    int j = static_cast<int>(std::log(e) / dl);
+    j = std::max(0, std::min(j, kNE - 1));
+    while (j > 0 && E[j] > e) --j;
+    return R[j] + integrate_inv_s(E[j], e, ZA, I);
+  }
+};
+
+void build_range_class(double ZA, double I, RangeClass& rc, std::vector<float2>& rt, std::vector<float2>& et,
+                       float& S1, float& R1, float& lnR0, float& inv_dlnR) {
+  rc.ZA = ZA; rc.I = I;
+  const double dl = std::log(300.0) / (kNE - 1);
+  rc.E.resize(kNE); rc.R.resize(kNE);
+  const double s1 = bethe_mass(1.0, ZA, I);
+  for (int j = 0; j < kNE; ++j) rc.E[j] = std::exp(j * dl);
+  rc.E[0] = 1.0;
+  rc.R[0] = 2.0 / s1;
+  for (int j = 1; j < kNE; ++j) rc.R[j] = rc.R[j - 1] + integrate_inv_s(rc.E[j - 1], rc.E[j], ZA, I);
+  // forward: R as a function of x = ln E, dR/dx = E / S
+  rt = spline(rc.R, dl, rc.E[0] / bethe_mass(rc.E[0], ZA, I), rc.E[kNE - 1] / bethe_mass(rc.E[kNE - 1], ZA, I));
+  // inverse: E as a function of y = ln R on a uniform grid, dE/dy = R S
+  const double y0 = std::log(rc.R[0]), y1 = std::log(rc.R[kNE - 1]), dy = (y1 - y0) / (kNE - 1);
+  std::vector<double> Ey(kNE);
+  for (int j = 0; j < kNE; ++j) {
+    const double Rt = std::exp(y0 + j * dy);
+    double e = rc.E[std::min(kNE - 1, std::max(0, static_cast<int>((y0 + j * dy - y0) / dy)))];
+    // bracket from the node table, then Newton on R(E) - Rt (dR/dE = 1/S)
+    int lo = 0, hi = kNE - 1;
+    while (hi - lo > 1) { const int mid = (lo + hi) / 2; if (rc.R[mid] <= Rt) lo = mid; else hi = mid; }
+    e = rc.E[lo] + (rc.E[hi] - rc.E[lo]) * (Rt - rc.R[lo]) / (rc.R[hi] - rc.R[lo]);
+    for (int it = 0; it < 30; ++it) {
+      const double de = (rc.range(e) - Rt) * bethe_mass(e, ZA, I);
+      e -= de;
+      if (std::fabs(de) < 1e-14 * e) break;
+    }
+    Ey[j] = (j == 0) ? 1.0 : (j == kNE - 1 ? 300.0 : e);
+  }
+  et = spline(Ey, dy, rc.R[0] * bethe_mass(1.0, ZA, I), rc.R[kNE - 1] * bethe_mass(300.0, ZA, I));
+  S1 = static_cast<float>(s1);
+  R1 = static_cast<float>(rc.R[0]);
+  lnR0 = static_cast<float>(y0);
+  inv_dlnR = static_cast<float>(1.0 / dy);
+}
+
+void build_nucleus(int Z, int A, NucleusModel& nm) {
+  std::memset(&nm, 0, sizeof(nm));
+  nm.Z = Z; nm.A = A;
+  const double a13 = std::cbrt(double(A));
+  const double R = 1.16 * a13 * (1.0 - 1.16 / (a13 * a13)), aws = 0.55;
+  const double Rout = R + aws * std::log(99.0);
+  double norm = 0.0, f[kShells], r[kShells + 1];
+  for (int i = 0; i <= kShells; ++i) r[i] = Rout * i / kShells;
+  for (int i = 0; i < kShells; ++i) {
+    f[i] = 1.0 / (1.0 + std::exp((0.5 * (r[i] + r[i + 1]) - R) / aws));
+    norm += f[i] * 4.0 / 3.0 * M_PI * (r[i + 1] * r[i + 1] * r[i + 1] - r[i] * r[i] * r[i]);
+  }
+  const double Sn = nuclear_mass(Z, A - 1) + 939.565420 - nuclear_mass(Z, A);
+  const double Sp = nuclear_mass(Z - 1, A - 1) + 938.272088 - nuclear_mass(Z, A);
+  for (int i = 0; i <= kShells; ++i) nm.r[i] = static_cast<float>(r[i]);
+  for (int i = 0; i < kShells; ++i) {
+    const double rho = f[i] * A / norm;
+    for (int q = 0; q < 2; ++q) {
+      const double rq = rho * (q ? double(Z) / A : double(A - Z) / A);
+      const double m = q ? 938.272088 : 939.565420;
+      const double pF = 197.3269804 * std::cbrt(3.0 * M_PI * M_PI * rq);
+      const double TF = std::sqrt(pF * pF + m * m) - m;
+      nm.rho[q][i] = static_cast<float>(rq);
+      nm.pF[q][i] = static_cast<float>(pF);
+      nm.TF[q][i] = static_cast<float>(TF);
+      nm.V[q][i] = static_cast<float>(TF + (q ? Sp : Sn));
+    }
+  }
+  nm.Rout = static_cast<float>(Rout);
+}
+
+// ---------------------------------------------------------------------------
+// device memory
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+}  // namespace
+
+struct pmc_ctx {
+  pmc_options opt{};
+  int n_sm = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // physics
+  bool have_materials = false;
+  Physics phys{};
+  std::vector<pmc_material> mats;
+  std::vector<pmc_nuclide> nucs;
+  std::vector<pmc_hu_bin> hus;
+  DevBuf d_phys, d_rt, d_et, d_st, d_nuclei, d_btab;
+  // geometry
+  bool have_phantom = false;
+  Geometry geo{};
+  long long n_vox = 0;
+  DevBuf d_mat, d_rho, d_hu;
+  // spots
+  std::vector<pmc_spot> spots;
+  // run buffers
+  DevBuf d_tally, d_dose, d_sigma, d_counters, d_counts, d_seed, d_spots, d_q[4];
+  DevBuf d_hist, d_esc;
+  uint64_t hist_n = 0, esc_cap = 0;
+  size_t q_cap = 0;
+  int block = 0;
+  int64_t chunk = 0;
+  // kernel timing
+  bool profile = false;
+  std::vector<cudaEvent_t> events;      // pairs around launches
+  std::vector<int> event_kind;          // kind per pair
+  size_t n_events_used = 0;
+  double prof_ms[4] = {0, 0, 0, 0};
+  int64_t prof_launches[4] = {0, 0, 0, 0};
+  int64_t steps_primary = 0;
+  // graph
+  cudaGraphExec_t gexec = nullptr;
+  std::string gkey;
+  bool have_run = false;
+  pmc_ledger last{};
+};
+
+namespace {
+
+int fail(pmc_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail(ctx, PMC_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int dalloc(pmc_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (b.p && b.n >= bytes) return PMC_OK;
+  if (b.p) {
+    if (ctx->opt.free) ctx->opt.free(b.p, ctx->opt.alloc_user); else cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+  }
+  if (bytes == 0) return PMC_OK;
+  if (ctx->opt.alloc) {
+    b.p = ctx->opt.alloc(bytes, ctx->opt.alloc_user);
+    if (!b.p) return fail(ctx, PMC_E_OOM, "allocator returned NULL for %zu bytes", bytes);
+  } else if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(ctx, PMC_E_OOM, "cudaMalloc of %zu bytes failed", bytes);
+  }
+  b.n = bytes;
+  // any captured graph may point at the old buffer
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  return PMC_OK;
+}
+
+void dfree(pmc_ctx* ctx, DevBuf& b) {
+  if (!b.p) return;
+  if (ctx->opt.free) ctx->opt.free(b.p, ctx->opt.alloc_user); else cudaFree(b.p);
+  b.p = nullptr;
+  b.n = 0;
+}
+
+int upload(pmc_ctx* ctx, DevBuf& b, const void* src, size_t bytes) {
+  int rc = dalloc(ctx, b, bytes);
+  if (rc) return rc;
+  if (bytes) CK(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PMC_OK;
+}
+
+// Histories per spot in proportion to weight, largest remainder (ties to the lower index).
+std::vector<uint64_t> split_histories(const std::vector<pmc_spot>& sp, uint64_t n) {
+  double W = 0.0;
+  for (const auto& s : sp) W += s.weight;
+  std::vector<uint64_t> cnt(sp.size());
+  std::vector<double> rem(sp.size());
+  uint64_t used = 0;
+  for (size_t i = 0; i < sp.size(); ++i) {
+    const double q = static_cast<double>(n) * sp[i].weight / W;
+    cnt[i] = static_cast<uint64_t>(std::floor(q));
+    rem[i] = q - std::floor(q);
+    used += cnt[i];
+  }
+  while (used < n) {
+    size_t best = 0;
+    for (size_t i = 1; i < sp.size(); ++i) if (rem[i] > rem[best]) best = i;
+    cnt[best]++;
+    rem[best] = -1.0;
+    ++used;
+  }
+  return cnt;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pmc_create(pmc_ctx** out, const pmc_options* opt) {
+  if (!out) return PMC_E_INVALID;
+  *out = nullptr;
+  pmc_ctx* ctx = new (std::nothrow) pmc_ctx();
+  if (!ctx) return PMC_E_OOM;
+  if (opt) ctx->opt = *opt;
+  if (ctx->opt.n_batches == 0) ctx->opt.n_batches = 10;
+  if (ctx->opt.n_batches < 2 || ctx->opt.n_batches > 1024) {
+    delete ctx;
+    return PMC_E_INVALID;
+  }
+  if (cudaSetDevice(ctx->opt.device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->opt.device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return PMC_E_CUDA;
+  }
+  ctx->block = ctx->opt.block_size > 0 ? ctx->opt.block_size : 256;
+  ctx->chunk = ctx->opt.chunk;
+  *out = ctx;
+  return PMC_OK;
+}
+
+void pmc_destroy(pmc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->opt.device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+  DevBuf* bufs[] = {&ctx->d_phys, &ctx->d_rt, &ctx->d_et, &ctx->d_st, &ctx->d_nuclei, &ctx->d_btab, &ctx->d_mat,
+                    &ctx->d_rho, &ctx->d_hu, &ctx->d_tally, &ctx->d_dose, &ctx->d_sigma, &ctx->d_counters,
+                    &ctx->d_counts, &ctx->d_seed, &ctx->d_spots, &ctx->d_q[0], &ctx->d_q[1], &ctx->d_q[2],
+                    &ctx->d_q[3], &ctx->d_hist, &ctx->d_esc};
+  for (DevBuf* b : bufs) dfree(ctx, *b);
+  cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* pmc_last_error(const pmc_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc, const pmc_material* mat, int n_mat,
+                       const pmc_hu_bin* hu, int n_hu) {
+  if (!ctx) return PMC_E_INVALID;
+  try {
+    if (!nuc || !mat || n_nuc < 1 || n_nuc > PMC_MAX_NUCLIDES || n_mat < 1 || n_mat > PMC_MAX_MATERIALS ||
+        n_hu < 0 || n_hu > PMC_MAX_HU_BINS || (n_hu > 0 && !hu))
+      return fail(ctx, PMC_E_INVALID, "material counts out of range");
+    if (mat[0].own_table) return fail(ctx, PMC_E_INVALID, "material 0 must be the scaled reference water");
+    cudaSetDevice(ctx->opt.device);
+    Physics& ph = ctx->phys;
+    std::memset(&ph, 0, sizeof(ph));
+    ph.n_mat = n_mat; ph.n_nuc = n_nuc; ph.n_hu = n_hu;
+    ph.flags = ctx->opt.physics_flags;
+    for (int i = 0; i < n_nuc; ++i) {
+      const pmc_nuclide& q = nuc[i];
+      if (q.Z < 1 || q.A < q.Z || q.A >= kMaxA - 1 || q.Z >= kMaxZ - 1 || q.mass_u <= 0.0 || q.I_eV <= 0.0)
+        return fail(ctx, PMC_E_INVALID, "nuclide %d invalid", i);
+      NucConst& c = ph.nuc[i];
+      c.Z = q.Z; c.A = q.A;
+      const double a13 = std::cbrt(double(q.A));
+      c.a13 = static_cast<float>(a13);
+      c.bc = static_cast<float>(q.A > 1 ? 1.439964548 * q.Z / (1.16 * (a13 + 1.0)) : 0.0);
+      c.geo = static_cast<float>(0.65 * M_PI * 1.16 * 1.16 * (a13 + 0.8) * (a13 + 0.8) * 10.0);
+      c.el = static_cast<float>(12.0 * a13 * a13);
+      c.mass = static_cast<float>(nuclear_mass(q.Z, q.A));
+    }
+    // materials: Z/A, mean excitation energy, Eq. 1 factor, radiation length, classes
+    std::vector<double> ZA(n_mat), Iv(n_mat);
+    for (int m = 0; m < n_mat; ++m) {
+      const pmc_material& M = mat[m];
+      if (M.n < 1 || M.n > PMC_MAX_NUC_PER_MAT || M.rho <= 0.0) return fail(ctx, PMC_E_INVALID, "material %d invalid", m);
+      double wsum = 0.0, za = 0.0, lnI = 0.0, ix0 = 0.0;
+      for (int k = 0; k < M.n; ++k) {
+        if (M.nuc[k] < 0 || M.nuc[k] >= n_nuc || M.w[k] < 0.0) return fail(ctx, PMC_E_INVALID, "material %d entry %d", m, k);
+        const pmc_nuclide& q = nuc[M.nuc[k]];
+        wsum += M.w[k];
+        za += M.w[k] * q.Z / q.mass_u;
+        lnI += M.w[k] * q.Z / q.mass_u * std::log(q.I_eV);
+        ix0 += M.w[k] / tsai_x0(q.Z, q.mass_u);
+      }
+      if (std::fabs(wsum - 1.0) > 1e-6) return fail(ctx, PMC_E_INVALID, "material %d fractions sum to %g", m, wsum);
+      ZA[m] = za;
+      Iv[m] = M.I_eV > 0.0 ? M.I_eV : std::exp(lnI / za);
+      MatConst& mc = ph.mat[m];
+      mc.ZA = static_cast<float>(za);
+      mc.inv_X0 = static_cast<float>(ix0);
+      mc.bohr_k = static_cast<float>(0.307075 * 0.51099895 * za);
+      mc.n = M.n;
+      for (int k = 0; k < M.n; ++k) {
+        mc.nuc[k] = M.nuc[k];
+        mc.n_per_g[k] = static_cast<float>(M.w[k] * kNA / nuc[M.nuc[k]].mass_u * 1e-27);
+      }
+    }
+    int ncls = 1;
+    for (int m = 0; m < n_mat; ++m) {
+      MatConst& mc = ph.mat[m];
+      if (m > 0 && mat[m].own_table) {
+        if (ncls >= kMaxCls) return fail(ctx, PMC_E_INVALID, "at most %d own-table materials", kMaxCls - 1);
+        mc.cls = ncls++;
+        mc.f = 1.0f;
+      } else {
+        mc.cls = 0;
+        mc.f = static_cast<float>(m == 0 ? 1.0 : bethe_mass(100.0, ZA[m], Iv[m]) / bethe_mass(100.0, ZA[0], Iv[0]));
+      }
+    }
+    ph.n_cls = ncls;
+    std::vector<float2> rt(ncls * kNE), et(ncls * kNE);
+    for (int m = 0; m < n_mat; ++m) {
+      const int c = ph.mat[m].cls;
+      if (m > 0 && c == 0) continue;
+      RangeClass rc;
+      std::vector<float2> a, b;
+      build_range_class(ZA[m], Iv[m], rc, a, b, ph.S1[c], ph.R1[c], ph.lnR0[c], ph.inv_dlnR[c]);
+      std::copy(a.begin(), a.end(), rt.begin() + c * kNE);
+      std::copy(b.begin(), b.end(), et.begin() + c * kNE);
+    }
+    ph.dlnE = static_cast<float>(std::log(300.0) / (kNE - 1));
+    ph.inv_dlnE = static_cast<float>((kNE - 1) / std::log(300.0));
+    const double ls0 = std::log(0.1), ls1 = std::log(300.0), dls = (ls1 - ls0) / (kNS - 1);
+    ph.lnS0 = static_cast<float>(ls0);
+    ph.inv_dlnS = static_cast<float>(1.0 / dls);
+    std::vector<float> st(n_mat * kNS);
+    for (int m = 0; m < n_mat; ++m) {
+      for (int j = 0; j < kNS; ++j) {
+        const double E = std::exp(ls0 + j * dls);
+        double s = 0.0;
+        for (int k = 0; k < mat[m].n; ++k) {
+          const pmc_nuclide& q = nuc[mat[m].nuc[k]];
+          double sg = 0.0;
+          if (!(ph.flags & kNoInelastic)) sg += sigma_inel_h(q.Z, q.A, E);
+          if (!(ph.flags & kNoElastic)) sg += sigma_el_h(q.A, E);
+          s += mat[m].w[k] * kNA / q.mass_u * sg * 1e-27;
+        }
+        st[m * kNS + j] = static_cast<float>(s);
+      }
+    }
+    for (int i = 0; i < n_hu; ++i) {
+      if (hu[i].material < 0 || hu[i].material >= n_mat || hu[i].hi <= hu[i].lo)
+        return fail(ctx, PMC_E_INVALID, "HU bin %d invalid", i);
+      ph.hu[i].lo = hu[i].lo; ph.hu[i].hi = hu[i].hi; ph.hu[i].mat = hu[i].material;
+      ph.hu[i].a = static_cast<float>(hu[i].rho_a); ph.hu[i].b = static_cast<float>(hu[i].rho_b);
+    }
+    std::vector<NucleusModel> nm(n_nuc);
+    for (int i = 0; i < n_nuc; ++i) {
+      if (nuc[i].A >= 2) build_nucleus(nuc[i].Z, nuc[i].A, nm[i]);
+      else std::memset(&nm[i], 0, sizeof(NucleusModel));
+    }
+    std::vector<float> bt(kMaxZ * kMaxA);
+    for (int z = 0; z < kMaxZ; ++z)
+      for (int a = 0; a < kMaxA; ++a) bt[z * kMaxA + a] = static_cast<float>(binding_energy(z, a));
+    int rc;
+    if ((rc = upload(ctx, ctx->d_phys, &ph, sizeof(Physics)))) return rc;
+    if ((rc = upload(ctx, ctx->d_rt, rt.data(), rt.size() * sizeof(float2)))) return rc;
+    if ((rc = upload(ctx, ctx->d_et, et.data(), et.size() * sizeof(float2)))) return rc;
+    if ((rc = upload(ctx, ctx->d_st, st.data(), st.size() * sizeof(float)))) return rc;
+    if ((rc = upload(ctx, ctx->d_nuclei, nm.data(), nm.size() * sizeof(NucleusModel)))) return rc;
+    if ((rc = upload(ctx, ctx->d_btab, bt.data(), bt.size() * sizeof(float)))) return rc;
+    ctx->mats.assign(mat, mat + n_mat);
+    ctx->nucs.assign(nuc, nuc + n_nuc);
+    ctx->hus.assign(hu, hu + n_hu);
+    ctx->have_materials = true;
+    if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+    return PMC_OK;
+  } catch (...) {
+    return fail(ctx, PMC_E_INVALID, "exception while building tables");
+  }
+}
+
+int pmc_load_phantom(pmc_ctx* ctx, int nx, int ny, int nz, double dx, double dy, double dz, double x0, double y0,
+                     double z0, const int16_t* hu, const uint8_t* mat, const float* rho) {
+  if (!ctx) return PMC_E_INVALID;
+  if (nx < 1 || ny < 1 || nz < 1 || dx <= 0 || dy <= 0 || dz <= 0)
+    return fail(ctx, PMC_E_INVALID, "bad grid");
+  if (!hu && !(mat && rho)) return fail(ctx, PMC_E_INVALID, "give hu, or mat and rho");
+  if (hu && !ctx->have_materials) return fail(ctx, PMC_E_INVALID, "load materials (with HU bins) first");
+  if (hu && ctx->phys.n_hu < 1) return fail(ctx, PMC_E_INVALID, "HU phantom needs HU bins");
+  const long long n = static_cast<long long>(nx) * ny * nz;
+  if (n > (1ll << 31) - 1) return fail(ctx, PMC_E_INVALID, "at most 2^31-1 voxels");
+  cudaSetDevice(ctx->opt.device);
+  const bool shape_changed = n != ctx->n_vox || (hu != nullptr) != (ctx->geo.hu != nullptr);
+  Geometry& g = ctx->geo;
+  g.nx = nx; g.ny = ny; g.nz = nz;
+  g.dx = static_cast<float>(dx); g.dy = static_cast<float>(dy); g.dz = static_cast<float>(dz);
+  g.x0 = static_cast<float>(x0); g.y0 = static_cast<float>(y0); g.z0 = static_cast<float>(z0);
+  g.idx = static_cast<float>(1.0 / dx); g.idy = static_cast<float>(1.0 / dy); g.idz = static_cast<float>(1.0 / dz);
+  int rc;
+  if (hu) {
+    if ((rc = dalloc(ctx, ctx->d_hu, n * sizeof(int16_t)))) return rc;
+    CK(cudaMemcpyAsync(ctx->d_hu.p, hu, n * sizeof(int16_t), cudaMemcpyHostToDevice, ctx->stream));
+    g.hu = static_cast<const int16_t*>(ctx->d_hu.p);
+    g.mat = nullptr; g.rho = nullptr;
+  } else {
+    if ((rc = dalloc(ctx, ctx->d_mat, n))) return rc;
+    if ((rc = dalloc(ctx, ctx->d_rho, n * sizeof(float)))) return rc;
+    CK(cudaMemcpyAsync(ctx->d_mat.p, mat, n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_rho.p, rho, n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    g.mat = static_cast<const uint8_t*>(ctx->d_mat.p);
+    g.rho = static_cast<const float*>(ctx->d_rho.p);
+    g.hu = nullptr;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->n_vox = n;
+  ctx->have_phantom = true;
+  if (shape_changed && ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  return PMC_OK;
+}
+
+int pmc_add_spots(pmc_ctx* ctx, const pmc_spot* s, int n) {
+  if (!ctx || n < 0 || (n > 0 && !s)) return PMC_E_INVALID;
+  for (int i = 0; i < n; ++i) {
+    const double dn = std::sqrt(s[i].u * s[i].u + s[i].v * s[i].v + s[i].w * s[i].w);
+    if (!(s[i].weight >= 0.0) || !(s[i].E >= 0.0) || !(dn > 0.0))
+      return fail(ctx, PMC_E_INVALID, "spot %d invalid", i);
+  }
+  ctx->spots.insert(ctx->spots.end(), s, s + n);
+  return PMC_OK;
+}
+
+int pmc_clear_spots(pmc_ctx* ctx) {
+  if (!ctx) return PMC_E_INVALID;
+  ctx->spots.clear();
+  return PMC_OK;
+}
+
+int pmc_set_launch(pmc_ctx* ctx, int block_size, int64_t chunk) {
+  if (!ctx) return PMC_E_INVALID;
+  if (block_size != 0 && (block_size < 32 || block_size > 256 || block_size % 32))
+    return fail(ctx, PMC_E_INVALID, "block size must be a multiple of 32 in [32, 256]");
+  if (chunk < 0) return fail(ctx, PMC_E_INVALID, "chunk must be >= 0");
+  if (block_size) ctx->block = block_size;
+  if (chunk) ctx->chunk = chunk;
+  return PMC_OK;
+}
+
+int pmc_enable_profile(pmc_ctx* ctx, int on) {
+  if (!ctx) return PMC_E_INVALID;
+  ctx->profile = on != 0;
+  return PMC_OK;
+}
+
+int pmc_read_profile(pmc_ctx* ctx, double* ms, int64_t* launches, int64_t* primary_steps) {
+  if (!ctx) return PMC_E_INVALID;
+  for (int k = 0; k < 4; ++k) {
+    if (ms) ms[k] = ctx->prof_ms[k];
+    if (launches) launches[k] = ctx->prof_launches[k];
+  }
+  if (primary_steps) *primary_steps = ctx->steps_primary;
+  return PMC_OK;
+}
+
+int pmc_enable_history_ledger(pmc_ctx* ctx, uint64_t max_histories) {
+  if (!ctx) return PMC_E_INVALID;
+  cudaSetDevice(ctx->opt.device);
+  if (max_histories == 0) { dfree(ctx, ctx->d_hist); ctx->hist_n = 0; }
+  else {
+    int rc = dalloc(ctx, ctx->d_hist, max_histories * 4 * sizeof(long long));
+    if (rc) return rc;
+    ctx->hist_n = max_histories;
+  }
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  return PMC_OK;
+}
+
+int pmc_enable_escape_record(pmc_ctx* ctx, uint64_t cap) {
+  if (!ctx) return PMC_E_INVALID;
+  cudaSetDevice(ctx->opt.device);
+  if (cap == 0) { dfree(ctx, ctx->d_esc); ctx->esc_cap = 0; }
+  else {
+    int rc = dalloc(ctx, ctx->d_esc, cap * 8 * sizeof(float));
+    if (rc) return rc;
+    ctx->esc_cap = cap;
+  }
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  return PMC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct RunPlan {
+  uint64_t n;
+  int64_t chunk;
+  int n_chunks;
+  int grid_t, grid_c;
+  size_t smem;
+};
+
+// Records a timing event (kind >= 0 opens a pair, -1 closes it) when profiling.
+int mark(pmc_ctx* ctx, cudaStream_t s, int kind) {
+  if (!ctx->profile) return PMC_OK;
+  if (ctx->n_events_used == ctx->events.size()) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    ctx->events.push_back(e);
+  }
+  cudaEvent_t e = ctx->events[ctx->n_events_used++];
+  if (kind >= 0) ctx->event_kind.push_back(kind);
+  CK(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+  return PMC_OK;
+}
+
+// Kernel arguments of one generation.
+TransportArgs transport_args(pmc_ctx* ctx) {
+  TransportArgs a{};
+  a.phys = static_cast<const Physics*>(ctx->d_phys.p);
+  a.rtab = static_cast<const float2*>(ctx->d_rt.p);
+  a.etab = static_cast<const float2*>(ctx->d_et.p);
+  a.stab = static_cast<const float*>(ctx->d_st.p);
+  a.g = ctx->geo;
+  a.tally = static_cast<unsigned long long*>(ctx->d_tally.p);
+  a.B = ctx->opt.n_batches;
+  a.seed = static_cast<const unsigned long long*>(ctx->d_seed.p);
+  a.spots = static_cast<const SpotDev*>(ctx->d_spots.p);
+  a.n_spots = static_cast<int>(ctx->spots.size());
+  a.cnt = static_cast<Counters*>(ctx->d_counters.p);
+  a.hist = static_cast<long long*>(ctx->d_hist.p);
+  a.hist_n = ctx->hist_n;
+  a.esc = static_cast<float*>(ctx->d_esc.p);
+  a.esc_cap = ctx->esc_cap;
+  return a;
+}
+
+CascadeArgs cascade_args(pmc_ctx* ctx) {
+  CascadeArgs c{};
+  c.nuclei = static_cast<const NucleusModel*>(ctx->d_nuclei.p);
+  c.btab = static_cast<const float*>(ctx->d_btab.p);
+  c.n_nuc = ctx->phys.n_nuc;
+  c.g = ctx->geo;
+  c.tally = static_cast<unsigned long long*>(ctx->d_tally.p);
+  c.B = ctx->opt.n_batches;
+  c.seed = static_cast<const unsigned long long*>(ctx->d_seed.p);
+  c.cnt = static_cast<Counters*>(ctx->d_counters.p);
+  c.hist = static_cast<long long*>(ctx->d_hist.p);
+  c.hist_n = ctx->hist_n;
+  return c;
+}
+
+// Enqueues one transport -> cascade generation.
+int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int source, uint64_t w0, uint64_t w1,
+                       Particle* qin, unsigned* qin_count, Particle* qout, unsigned* qout_count, Particle* qne,
+                       unsigned* qne_count, unsigned* work) {
+  TransportArgs a = transport_args(ctx);
+  a.source = source;
+  a.w_begin = w0;
+  a.w_end = w1;
+  a.qin = qin;
+  a.qin_count = qin_count;
+  a.qin_cap = static_cast<unsigned>(ctx->q_cap);
+  a.qsec = qout;
+  a.qsec_count = qout_count;
+  a.qsec_cap = static_cast<unsigned>(ctx->q_cap);
+  a.qne = qne;
+  a.qne_count = qne_count;
+  a.qne_cap = static_cast<unsigned>(ctx->q_cap);
+  a.work = work;
+  int rc;
+  if ((rc = mark(ctx, s, source == 0 ? 0 : 1))) return rc;
+  CK(launch_transport(a, rp.grid_t, ctx->block, rp.smem, s));
+  if ((rc = mark(ctx, s, -1))) return rc;
+  CascadeArgs c = cascade_args(ctx);
+  c.qne = qne;
+  c.qne_count = qne_count;
+  c.qne_cap = static_cast<unsigned>(ctx->q_cap);
+  c.qsec = qout;
+  c.qsec_count = qout_count;
+  c.qsec_cap = static_cast<unsigned>(ctx->q_cap);
+  if ((rc = mark(ctx, s, 2))) return rc;
+  CK(launch_cascade(c, rp.grid_c, 128, s));
+  if ((rc = mark(ctx, s, -1))) return rc;
+  return PMC_OK;
+}
+
+StatsArgs stats_args(pmc_ctx* ctx) {
+  StatsArgs sa{};
+  sa.tally = static_cast<const unsigned long long*>(ctx->d_tally.p);
+  sa.B = ctx->opt.n_batches;
+  sa.n_vox = ctx->n_vox;
+  sa.g = ctx->geo;
+  sa.phys = static_cast<const Physics*>(ctx->d_phys.p);
+  sa.dose = static_cast<double*>(ctx->d_dose.p);
+  sa.sigma = static_cast<double*>(ctx->d_sigma.p);
+  return sa;
+}
+
+// Count slots per sub-group: [0, G]: secondary queue counts; [G+1, 2G]: event
+// queue counts; [2G+1, 3G]: work counters.  A final slot holds the carry count.
+constexpr int kSlots = 3 * kGenerations + 1;
+
+int enqueue_run(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s) {
+  ctx->n_events_used = 0;
+  ctx->event_kind.clear();
+  CK(cudaMemsetAsync(ctx->d_tally.p, 0, static_cast<size_t>(ctx->n_vox) * ctx->opt.n_batches * 8, s));
+  CK(cudaMemsetAsync(ctx->d_counters.p, 0, sizeof(Counters), s));
+  CK(cudaMemsetAsync(ctx->d_counts.p, 0, (static_cast<size_t>(rp.n_chunks) * kSlots + 1) * sizeof(unsigned), s));
+  if (ctx->d_hist.p) CK(cudaMemsetAsync(ctx->d_hist.p, 0, ctx->hist_n * 4 * sizeof(long long), s));
+  unsigned* counts = static_cast<unsigned*>(ctx->d_counts.p);
+  unsigned* carry_count = counts + static_cast<size_t>(rp.n_chunks) * kSlots;
+  Particle* q[4];
+  for (int i = 0; i < 4; ++i) q[i] = static_cast<Particle*>(ctx->d_q[i].p);   // 0,1 ping-pong; 2 events; 3 carry
+  for (int c = 0; c < rp.n_chunks; ++c) {
+    unsigned* cs = counts + static_cast<size_t>(c) * kSlots;
+    const uint64_t w0 = static_cast<uint64_t>(c) * rp.chunk;
+    const uint64_t w1 = std::min<uint64_t>(rp.n, w0 + rp.chunk);
+    for (int g = 0; g < kGenerations; ++g) {
+      const bool last = g == kGenerations - 1;
+      Particle* out = last ? q[3] : q[(g + 1) & 1];
+      unsigned* out_count = last ? carry_count : cs + g + 1;
+      int rc = enqueue_generation(ctx, rp, s, g == 0 ? 0 : 1, w0, w1, q[g & 1], cs + g, out, out_count, q[2],
+                                  cs + kGenerations + 1 + g, cs + 2 * kGenerations + 1 + g);
+      if (rc) return rc;
+    }
+  }
+  int rc;
+  if ((rc = mark(ctx, s, 3))) return rc;
+  CK(launch_stats(stats_args(ctx), s));
+  if ((rc = mark(ctx, s, -1))) return rc;
+  return PMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, void* stream) {
+  if (!ctx) return PMC_E_INVALID;
+  if (!ctx->have_materials || !ctx->have_phantom) return fail(ctx, PMC_E_INVALID, "load materials and phantom first");
+  if (ctx->spots.empty()) return fail(ctx, PMC_E_INVALID, "no spots");
+  if (mode != PMC_FULL_CASCADE) return fail(ctx, PMC_E_INVALID, "mode %d not available in this build", mode);
+  if (n_histories == 0) return fail(ctx, PMC_E_INVALID, "n_histories must be > 0");
+  if (n_histories > 0xFFFFFFFFull) return fail(ctx, PMC_E_INVALID, "at most 2^32-1 histories per call");
+  double wsum = 0.0;
+  for (const auto& sp : ctx->spots) wsum += sp.weight;
+  if (!(wsum > 0.0)) return fail(ctx, PMC_E_INVALID, "spot weights sum to zero");
+  try {
+    cudaSetDevice(ctx->opt.device);
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    // spots in work order (highest energy first; long histories start early)
+    std::vector<uint64_t> cnt = split_histories(ctx->spots, n_histories);
+    std::vector<uint64_t> hfirst(ctx->spots.size());
+    uint64_t acc = 0;
+    for (size_t i = 0; i < cnt.size(); ++i) { hfirst[i] = acc; acc += cnt[i]; }
+    std::vector<size_t> order(ctx->spots.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return ctx->spots[a].E > ctx->spots[b].E; });
+    std::vector<SpotDev> sd;
+    uint64_t wacc = 0;
+    for (size_t k : order) {
+      if (cnt[k] == 0) continue;
+      const pmc_spot& p = ctx->spots[k];
+      const double dn = std::sqrt(p.u * p.u + p.v * p.v + p.w * p.w);
+      SpotDev d{};
+      d.E = static_cast<float>(p.E); d.sE = static_cast<float>(p.sigma_E);
+      d.x = static_cast<float>(p.x); d.y = static_cast<float>(p.y);
+      d.sx = static_cast<float>(p.sigma_x); d.sy = static_cast<float>(p.sigma_y);
+      d.u = static_cast<float>(p.u / dn); d.v = static_cast<float>(p.v / dn); d.w = static_cast<float>(p.w / dn);
+      d.h_first = hfirst[k];
+      d.w_first = wacc;
+      wacc += cnt[k];
+      sd.push_back(d);
+    }
+    RunPlan rp{};
+    rp.n = n_histories;
+    int64_t chunk = ctx->chunk > 0 ? ctx->chunk : (1ll << 22);
+    rp.chunk = std::min<int64_t>(chunk, static_cast<int64_t>(n_histories));
+    rp.n_chunks = static_cast<int>((n_histories + rp.chunk - 1) / rp.chunk);
+    rp.smem = transport_smem_bytes(ctx->phys.n_cls, ctx->phys.n_mat);
+    int bps = 0;
+    CK(transport_occupancy(ctx->block, rp.smem, &bps));
+    if (bps < 1) return fail(ctx, PMC_E_CUDA, "transport kernel does not fit (block %d, smem %zu)", ctx->block, rp.smem);
+    rp.grid_t = ctx->n_sm * bps;
+    rp.grid_c = ctx->n_sm * 8;
+    // buffers
+    int rc;
+    const size_t B = ctx->opt.n_batches;
+    if ((rc = dalloc(ctx, ctx->d_tally, static_cast<size_t>(ctx->n_vox) * B * 8))) return rc;
+    if ((rc = dalloc(ctx, ctx->d_dose, static_cast<size_t>(ctx->n_vox) * 8))) return rc;
+    if ((rc = dalloc(ctx, ctx->d_sigma, static_cast<size_t>(ctx->n_vox) * 8))) return rc;
+    if ((rc = dalloc(ctx, ctx->d_counters, sizeof(Counters)))) return rc;
+    if ((rc = dalloc(ctx, ctx->d_counts, (static_cast<size_t>(rp.n_chunks) * kSlots + 1) * sizeof(unsigned)))) return rc;
+    if ((rc = dalloc(ctx, ctx->d_seed, sizeof(uint64_t)))) return rc;
+    if ((rc = dalloc(ctx, ctx->d_spots, sd.size() * sizeof(SpotDev)))) return rc;
+    const size_t qcap = static_cast<size_t>(std::max<int64_t>(rp.chunk, 1024));
+    for (int i = 0; i < 4; ++i)
+      if ((rc = dalloc(ctx, ctx->d_q[i], qcap * sizeof(Particle)))) return rc;
+    ctx->q_cap = ctx->d_q[0].n / sizeof(Particle);
+    CK(cudaMemcpyAsync(ctx->d_spots.p, sd.data(), sd.size() * sizeof(SpotDev), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_seed.p, &seed, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    // graph of the whole run, rebuilt when its shape changes
+    char key[256];
+    std::snprintf(key, sizeof(key), "%llu/%lld/%zu/%d/%d/%lld/%p/%p/%d", (unsigned long long)n_histories,
+                  (long long)rp.chunk, sd.size(), ctx->block, ctx->opt.n_batches, ctx->n_vox, ctx->d_tally.p,
+                  ctx->d_hist.p, ctx->profile ? 1 : 0);
+    if (!ctx->gexec || ctx->gkey != key) {
+      if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+      cudaGraph_t graph;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue_run(ctx, rp, s);
+      cudaError_t e = cudaStreamEndCapture(s, &graph);
+      if (rc) { if (e == cudaSuccess) cudaGraphDestroy(graph); return rc; }
+      if (e != cudaSuccess) return fail(ctx, PMC_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) { ctx->gexec = nullptr; return fail(ctx, PMC_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+      ctx->gkey = key;
+    }
+    CK(cudaGraphLaunch(ctx->gexec, s));
+    // secondaries beyond the captured generations: drain them eagerly
+    unsigned* counts = static_cast<unsigned*>(ctx->d_counts.p);
+    unsigned* carry_count = counts + static_cast<size_t>(rp.n_chunks) * kSlots;
+    unsigned carry = 0;
+    CK(cudaMemcpyAsync(&carry, carry_count, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int k = 0; k < 4; ++k) { ctx->prof_ms[k] = 0.0; ctx->prof_launches[k] = 0; }
+    if (ctx->profile) {
+      for (size_t i = 0; i < ctx->event_kind.size(); ++i) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, ctx->events[2 * i], ctx->events[2 * i + 1]));
+        ctx->prof_ms[ctx->event_kind[i]] += ms;
+        ctx->prof_launches[ctx->event_kind[i]] += 1;
+      }
+    }
+    int extra = 0;
+    if (carry > 0) {
+      Particle* q[4];
+      for (int i = 0; i < 4; ++i) q[i] = static_cast<Particle*>(ctx->d_q[i].p);
+      unsigned* cs = counts;   // reuse the first sub-group's slots
+      CK(cudaMemcpyAsync(q[0], q[3], static_cast<size_t>(std::min<size_t>(carry, ctx->q_cap)) * sizeof(Particle),
+                         cudaMemcpyDeviceToDevice, s));
+      unsigned n_in = carry;
+      while (n_in > 0) {
+        if (++extra > 100000) return fail(ctx, PMC_E_TIMEOUT, "secondary generations did not terminate");
+        unsigned zero3[3] = {0, 0, 0};
+        CK(cudaMemcpyAsync(cs, &n_in, sizeof(unsigned), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(cs + 1, zero3, 3 * sizeof(unsigned), cudaMemcpyHostToDevice, s));
+        int r2 = enqueue_generation(ctx, rp, s, 1, 0, 0, q[0], cs, q[1], cs + 1, q[2], cs + 2, cs + 3);
+        if (r2) return r2;
+        CK(cudaMemcpyAsync(&n_in, cs + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        n_in = std::min<unsigned>(n_in, static_cast<unsigned>(ctx->q_cap));
+        if (n_in) CK(cudaMemcpyAsync(q[0], q[1], n_in * sizeof(Particle), cudaMemcpyDeviceToDevice, s));
+      }
+      CK(launch_stats(stats_args(ctx), s));
+    }
+    Counters hc{};
+    CK(cudaMemcpyAsync(&hc, ctx->d_counters.p, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    pmc_ledger& L = ctx->last;
+    L.incident = static_cast<int64_t>(hc.incident);
+    L.deposited = static_cast<int64_t>(hc.deposited);
+    L.escaped = static_cast<int64_t>(hc.escaped);
+    L.binding = static_cast<int64_t>(hc.binding);
+    L.histories = static_cast<int64_t>(n_histories);
+    L.steps = static_cast<int64_t>(hc.steps);
+    L.elastic = static_cast<int64_t>(hc.elastic);
+    L.inelastic = static_cast<int64_t>(hc.inelastic);
+    L.secondaries = static_cast<int64_t>(hc.secondaries);
+    L.transparent = static_cast<int64_t>(hc.transparent);
+    L.inc_retries = static_cast<int64_t>(hc.inc_retries);
+    L.queue_high_water = 0;
+    L.generations = kGenerations + extra;
+    L.dropped = static_cast<int64_t>(hc.dropped);
+    L.errors = static_cast<int64_t>(hc.errors);
+    ctx->steps_primary = static_cast<int64_t>(hc.steps_primary);
+    ctx->have_run = true;
+    if (hc.dropped) return fail(ctx, PMC_E_QUEUE_OVERFLOW, "%llu particles did not fit a queue", (unsigned long long)hc.dropped);
+    if (hc.errors) return fail(ctx, PMC_E_TIMEOUT, "%llu particles exceeded the step limit", (unsigned long long)hc.errors);
+    return PMC_OK;
+  } catch (...) {
+    return fail(ctx, PMC_E_INVALID, "exception in transport");
+  }
+}
+
+int pmc_read_dose(pmc_ctx* ctx, double* dose, double* sigma, size_t n) {
+  if (!ctx) return PMC_E_INVALID;
+  if (!ctx->have_run) return fail(ctx, PMC_E_INVALID, "no transport has run");
+  if (n != static_cast<size_t>(ctx->n_vox)) return fail(ctx, PMC_E_INVALID, "n_voxels %zu != %lld", n, ctx->n_vox);
+  cudaSetDevice(ctx->opt.device);
+  if (dose) CK(cudaMemcpyAsync(dose, ctx->d_dose.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (sigma) CK(cudaMemcpyAsync(sigma, ctx->d_sigma.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PMC_OK;
+}
+
+int pmc_read_tally(pmc_ctx* ctx, int64_t* tally, size_t n) {
+  if (!ctx || !tally) return PMC_E_INVALID;
+  if (!ctx->have_run) return fail(ctx, PMC_E_INVALID, "no transport has run");
+  const size_t need = static_cast<size_t>(ctx->n_vox) * ctx->opt.n_batches;
+  if (n != need) return fail(ctx, PMC_E_INVALID, "tally has %zu entries", need);
+  cudaSetDevice(ctx->opt.device);
+  CK(cudaMemcpyAsync(tally, ctx->d_tally.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PMC_OK;
+}
+
+int pmc_read_ledger(pmc_ctx* ctx, pmc_ledger* out) {
+  if (!ctx || !out) return PMC_E_INVALID;
+  *out = ctx->last;
+  return PMC_OK;
+}
+
+int pmc_read_history_ledger(pmc_ctx* ctx, int64_t* out, uint64_t n) {
+  if (!ctx || !out) return PMC_E_INVALID;
+  if (n > ctx->hist_n) return fail(ctx, PMC_E_INVALID, "history ledger holds %llu histories", (unsigned long long)ctx->hist_n);
+  cudaSetDevice(ctx->opt.device);
+  CK(cudaMemcpyAsync(out, ctx->d_hist.p, n * 4 * sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PMC_OK;
+}
+
+int pmc_read_escape_record(pmc_ctx* ctx, float* out, uint64_t cap, uint64_t* n) {
+  if (!ctx || !out || !n) return PMC_E_INVALID;
+  cudaSetDevice(ctx->opt.device);
+  Counters hc{};
+  CK(cudaMemcpy(&hc, ctx->d_counters.p, sizeof(Counters), cudaMemcpyDeviceToHost));
+  const uint64_t m = std::min<uint64_t>(std::min<uint64_t>(hc.esc_count, ctx->esc_cap), cap);
+  if (m) CK(cudaMemcpy(out, ctx->d_esc.p, m * 8 * sizeof(float), cudaMemcpyDeviceToHost));
+  *n = m;
+  return PMC_OK;
+}
+
+int pmc_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n) {
+  if (!ctr || !key || !out || n < 0) return PMC_E_INVALID;
+  if (n == 0) return PMC_OK;
+  void *dc = nullptr, *dout = nullptr;
+  if (cudaMalloc(&dc, n * 16ull) != cudaSuccess || cudaMalloc(&dout, n * 16ull) != cudaSuccess) {
+    cudaFree(dc);
+    return PMC_E_OOM;
+  }
+  int rc = PMC_OK;
+  if (cudaMemcpy(dc, ctr, n * 16ull, cudaMemcpyHostToDevice) != cudaSuccess ||
+      launch_debug_philox(static_cast<const uint4*>(dc), make_uint2(key[0], key[1]), static_cast<uint4*>(dout), n,
+                          nullptr) != cudaSuccess ||
+      cudaMemcpy(out, dout, n * 16ull, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = PMC_E_CUDA;
+  cudaFree(dc);
+  cudaFree(dout);
+  return rc;
+}
+
+int pmc_debug_tables(pmc_ctx* ctx, int material, const double* E, double* r_out, double* e_out, int n) {
+  if (!ctx || !E || !r_out || !e_out || n < 0) return PMC_E_INVALID;
+  if (!ctx->have_materials || material < 0 || material >= ctx->phys.n_mat)
+    return fail(ctx, PMC_E_INVALID, "bad material");
+  cudaSetDevice(ctx->opt.device);
+  DevBuf b;
+  int rc = dalloc(ctx, b, n * 24ull);
+  if (rc) return rc;
+  double* dE = static_cast<double*>(b.p);
+  CK(cudaMemcpy(dE, E, n * 8ull, cudaMemcpyHostToDevice));
+  CK(launch_debug_tables(static_cast<const Physics*>(ctx->d_phys.p), static_cast<const float2*>(ctx->d_rt.p),
+                         static_cast<const float2*>(ctx->d_et.p), ctx->phys.mat[material].cls, dE, dE + n, dE + 2 * n,
+                         n, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(r_out, dE + n, n * 8ull, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(e_out, dE + 2 * n, n * 8ull, cudaMemcpyDeviceToHost));
+  dfree(ctx, b);
+  return PMC_OK;
+}
+
+int pmc_debug_inc(pmc_ctx* ctx, int nuclide, double E, uint64_t seed, uint64_t pid0, int n, double* summary,
+                  double* products, int cap) {
+  if (!ctx || !summary || !products || n < 0 || cap < 1) return PMC_E_INVALID;
+  if (!ctx->have_materials || nuclide < 0 || nuclide >= ctx->phys.n_nuc || ctx->nucs[nuclide].A < 2)
+    return fail(ctx, PMC_E_INVALID, "bad nuclide");
+  cudaSetDevice(ctx->opt.device);
+  DevBuf b;
+  const size_t ns = n * 8ull, np = static_cast<size_t>(n) * cap * 5;
+  int rc = dalloc(ctx, b, (ns + np) * 8);
+  if (rc) return rc;
+  double* d = static_cast<double*>(b.p);
+  CK(cudaMemset(d, 0, (ns + np) * 8));
+  CK(launch_debug_inc(static_cast<const NucleusModel*>(ctx->d_nuclei.p) + nuclide,
+                      static_cast<const float*>(ctx->d_btab.p), static_cast<float>(E), seed, pid0, n, d, d + ns, cap,
+                      ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(summary, d, ns * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(products, d + ns, np * 8, cudaMemcpyDeviceToHost));
+  dfree(ctx, b);
+  return PMC_OK;
+}
+
+int pmc_debug_elastic(pmc_ctx* ctx, int nuclide, double E, const double* u, double* out, int n) {
+  if (!ctx || !u || !out || n < 0) return PMC_E_INVALID;
+  if (!ctx->have_materials || nuclide < 0 || nuclide >= ctx->phys.n_nuc) return fail(ctx, PMC_E_INVALID, "bad nuclide");
+  cudaSetDevice(ctx->opt.device);
+  DevBuf b;
+  int rc = dalloc(ctx, b, n * 64ull);
+  if (rc) return rc;
+  double* d = static_cast<double*>(b.p);
+  CK(cudaMemcpy(d, u, n * 24ull, cudaMemcpyHostToDevice));
+  CK(launch_debug_elastic(static_cast<const Physics*>(ctx->d_phys.p), nuclide, static_cast<float>(E), d, d + 3 * n, n,
+                          ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(out, d + 3 * n, n * 40ull, cudaMemcpyDeviceToHost));
+  dfree(ctx, b);
+  return PMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,291 @@
+// pmc_device.cuh -- device data layout and single-precision physics routines
+// of the GB300 proton transport engine.  Method: Wan Chan Tseung, Ma & Beltran,
+// arXiv:1409.8336, Sec. II.A (physics) and II.B (GPU organisation).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pmc {
+
+// ---------------------------------------------------------------------------
+// constants (MeV, cm, g)
+// ---------------------------------------------------------------------------
+constexpr float kMp = 938.272088f;
+constexpr float kMn = 939.565420f;
+constexpr double kMpD = 938.272088;
+constexpr double kMnD = 939.565420;
+constexpr double kAmuD = 931.49410242;
+constexpr float kEcut = 0.1f;                  // Sec. II.A.3
+constexpr float kFix = 16777216.0f;            // tally unit 2^-24 MeV
+constexpr double kFixD = 16777216.0;
+constexpr float kCoulomb = 1.439964548f;       // e^2 / 4 pi eps0, MeV fm
+constexpr float kFm2PerMb = 0.1f;
+constexpr int kNE = 512;                       // range table nodes on ln E in [0, ln 300]
+constexpr int kNS = 512;                       // cross-section table nodes on ln E in [ln 0.1, ln 300]
+constexpr int kMaxMat = 16, kMaxNuc = 16, kMaxNucPerMat = 12, kMaxHu = 16, kMaxCls = 4;
+constexpr int kShells = 15;                    // Woods-Saxon shells, Sec. II.A.4
+constexpr int kMaxZ = 24, kMaxA = 52;          // binding-energy table extent
+constexpr int kIncStack = 32;                  // cascade particles per event
+constexpr int kIncRetries = 1000;
+constexpr int kIncCrossings = 1000;
+constexpr int kIncIterations = 100000;          // flights per nucleon
+constexpr int kEvapSteps = 64;
+constexpr unsigned kMaxSteps = 100000u;        // per particle; exceeding it is an error
+constexpr unsigned kNoStraggling = 1u, kNoMcs = 2u, kNoElastic = 4u, kNoInelastic = 8u;
+
+// ---------------------------------------------------------------------------
+// device data
+// ---------------------------------------------------------------------------
+struct MatConst {
+  float ZA;                        // Z/A of the mixture, mol/g
+  float f;                         // Eq. 1 scaling factor (1 for own-table materials)
+  float inv_X0;                    // 1 / X0, cm^2/g
+  float bohr_k;                    // K m_e c^2 Z/A: Bohr variance per (rho x), MeV^2 cm^2/g
+  int cls;                         // range-table class
+  int n;
+  int nuc[kMaxNucPerMat];
+  float n_per_g[kMaxNucPerMat];    // atoms per gram x 1e-27 (so that n * sigma[mb] is cm^2/g)
+};
+
+struct NucConst {
+  int Z, A;
+  float a13;                       // A^(1/3)
+  float bc;                        // Coulomb barrier of the non-elastic cross-section, MeV
+  float geo;                       // 0.65 x geometric cross-section, mb
+  float el;                        // elastic prefactor 12 mb A^(2/3)
+  float mass;                      // nuclear mass, MeV
+  int pad;
+};
+
+struct HuBin { int lo, hi, mat; float a, b; };
+
+// Everything the kernels read besides the big tables; staged in shared memory.
+struct alignas(16) Physics {
+  int n_mat, n_nuc, n_hu, n_cls;
+  unsigned flags;
+  float dlnE, inv_dlnE;            // range grid step (ln E from 0)
+  float lnS0, inv_dlnS;            // cross-section grid origin and inverse step
+  float S1[kMaxCls];               // mass stopping power at 1 MeV per class
+  float R1[kMaxCls];               // mass range at 1 MeV per class
+  float lnR0[kMaxCls], inv_dlnR[kMaxCls];   // inverse table grid (ln R)
+  MatConst mat[kMaxMat];
+  NucConst nuc[kMaxNuc];
+  HuBin hu[kMaxHu];
+};
+
+// Shell model of one target nucleus for the cascade (Sec. II.A.4).
+struct NucleusModel {
+  float r[kShells + 1];            // shell radii, fm
+  float rho[2][kShells];           // [0] neutrons, [1] protons, fm^-3
+  float pF[2][kShells];            // Fermi momentum, MeV/c
+  float TF[2][kShells];            // Fermi kinetic energy, MeV
+  float V[2][kShells];             // well depth = T_F + separation energy, MeV
+  float Rout;
+  int Z, A, pad;
+};
+
+// A queued particle: a secondary proton (Q_sec) or a non-elastic event (Q_ne).
+struct __align__(16) Particle {
+  float x, y, z, u;
+  float v, w, E;
+  int voxel;                       // linear voxel index
+  unsigned long long pid;          // identity: keys its random numbers
+  unsigned root;                   // primary history index (group = root % B)
+  int target;                      // nuclide index (Q_ne only)
+};
+static_assert(sizeof(Particle) == 48, "particle record is 48 bytes");
+
+// Run counters; energies in units of 2^-24 MeV (signed, two's complement).
+struct Counters {
+  unsigned long long incident, deposited, escaped, binding;
+  unsigned long long steps, elastic, inelastic, secondaries, transparent, inc_retries;
+  unsigned long long dropped, errors, esc_count, steps_primary;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Uniform in (0,1) from the top 23 bits (exact in single precision).
+__device__ __forceinline__ float u01(unsigned x) {
+  return (static_cast<float>(x >> 9) + 0.5f) * (1.0f / 8388608.0f);
+}
+
+// Four uniforms of stream (pid, word2, tag).  Tags: 0, 1 step uniforms;
+// 2 nuclear elastic; 3 cascade/evaporation draws; 4 birth; 5 child identity.
+__device__ __forceinline__ float4 draw4(uint2 key, unsigned long long pid, unsigned w2, unsigned tag) {
+  const uint4 r = philox4x32_10(make_uint4((unsigned)pid, (unsigned)(pid >> 32), w2, tag), key);
+  return make_float4(u01(r.x), u01(r.y), u01(r.z), u01(r.w));
+}
+
+__device__ __forceinline__ unsigned long long child_pid(uint2 key, unsigned long long pid, unsigned idx) {
+  const uint4 r = philox4x32_10(make_uint4((unsigned)pid, (unsigned)(pid >> 32), idx, 5u), key);
+  return (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+}
+
+// Fixed-point energy: deposits are differences of these, so a particle's
+// deposits telescope exactly to its energy.
+__device__ __forceinline__ long long fix(float e) { return __float2ll_rn(e * kFix); }
+__device__ __forceinline__ long long fixd(double e) { return __double2ll_rn(e * kFixD); }
+
+// ---------------------------------------------------------------------------
+// tables (Sec. II.A.2): cubic splines stored as (y, M h^2 / 6) pairs
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float spline_eval(const float2* __restrict__ t, float s, int n) {
+  int j = static_cast<int>(s);
+  j = j < 0 ? 0 : (j > n - 2 ? n - 2 : j);
+  const float t1 = s - static_cast<float>(j), t0 = 1.0f - t1;
+  const float2 a = t[j], b = t[j + 1];
+  return t0 * a.x + t1 * b.x + (t0 * t0 - 1.0f) * t0 * a.y + (t1 * t1 - 1.0f) * t1 * b.y;
+}
+
+// Mass CSDA range (g/cm^2) of a proton of energy E; lnE = log(E).
+__device__ __forceinline__ float range_mass(const Physics& ph, const float2* __restrict__ rt, int cls, float E,
+                                            float lnE) {
+  if (E <= 1.0f) return 2.0f * sqrtf(E) / ph.S1[cls];
+  return spline_eval(rt + cls * kNE, lnE * ph.inv_dlnE, kNE);
+}
+
+// Inverse of range_mass.
+__device__ __forceinline__ float energy_of_range(const Physics& ph, const float2* __restrict__ et, int cls, float R) {
+  if (R <= 0.0f) return 0.0f;
+  if (R <= ph.R1[cls]) {
+    const float h = 0.5f * R * ph.S1[cls];
+    return h * h;
+  }
+  return spline_eval(et + cls * kNE, (logf(R) - ph.lnR0[cls]) * ph.inv_dlnR[cls], kNE);
+}
+
+// Total macroscopic nuclear cross-section per unit density (cm^2/g), linear in ln E.
+__device__ __forceinline__ float sigma_table(const Physics& ph, const float* __restrict__ st, int m, float lnE) {
+  float s = (lnE - ph.lnS0) * ph.inv_dlnS;
+  s = fminf(fmaxf(s, 0.0f), static_cast<float>(kNS - 1) - 1e-3f);
+  const int j = static_cast<int>(s);
+  const float t = s - static_cast<float>(j);
+  const float* p = st + m * kNS + j;
+  return p[0] + t * (p[1] - p[0]);
+}
+
+// ---------------------------------------------------------------------------
+// cross-sections (mb), the engine's analytic forms
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float sigma_nn(float T, bool like) {
+  const float t = fmaxf(T, 10.0f);
+  const float g = 1.0f + t / kMp;
+  const float b2 = 1.0f - 1.0f / (g * g);
+  const float ib = rsqrtf(b2), ib2 = 1.0f / b2;
+  return like ? (10.63f * ib2 - 29.92f * ib + 42.9f) : (34.10f * ib2 - 82.2f * ib + 82.2f);
+}
+
+__device__ __forceinline__ float sigma_inel(const NucConst& n, float E) {
+  if (n.A <= 1 || E <= n.bc) return 0.0f;
+  return n.geo * (1.0f - n.bc / E) * (1.0f - expf(-E * (1.0f / 15.0f)));
+}
+
+__device__ __forceinline__ float sigma_el(const NucConst& n, float E) {
+  if (E <= 0.0f) return 0.0f;
+  if (n.A == 1) return sigma_nn(E, true);
+  return n.el * (1.0f + 20.0f / (E + 10.0f));
+}
+
+// ---------------------------------------------------------------------------
+// directions
+// ---------------------------------------------------------------------------
+// Rotates (u,v,w) to polar angle (ct, st) and azimuth (cp, sp) about itself.
+__device__ __forceinline__ void rotate(float& u, float& v, float& w, float ct, float st, float cp, float sp) {
+  const float s2 = 1.0f - w * w;
+  float nu, nv, nw;
+  if (s2 < 1e-10f) {
+    nu = st * cp;
+    nv = st * sp;
+    nw = w >= 0.0f ? ct : -ct;
+  } else {
+    const float is = rsqrtf(s2), s = s2 * is;
+    nu = u * ct + st * (u * w * cp - v * sp) * is;
+    nv = v * ct + st * (v * w * cp + u * sp) * is;
+    nw = w * ct - st * cp * s;
+  }
+  const float in = rsqrtf(nu * nu + nv * nv + nw * nw);
+  u = nu * in;
+  v = nv * in;
+  w = nw * in;
+}
+
+// Vector (a0, a1, a2) given in the frame whose third axis is (u, v, w).
+__device__ __forceinline__ float3 frame_to_lab(float u, float v, float w, float a0, float a1, float a2) {
+  const float s2 = 1.0f - w * w;
+  float3 o;
+  if (s2 < 1e-10f) {
+    o = make_float3(a0, a1, w >= 0.0f ? a2 : -a2);
+  } else {
+    const float is = rsqrtf(s2), s = s2 * is;
+    o.x = a0 * u * w * is - a1 * v * is + a2 * u;
+    o.y = a0 * v * w * is + a1 * u * is + a2 * v;
+    o.z = -a0 * s + a2 * w;
+  }
+  const float in = rsqrtf(o.x * o.x + o.y * o.y + o.z * o.z);
+  return make_float3(o.x * in, o.y * in, o.z * in);
+}
+
+// ---------------------------------------------------------------------------
+// nuclear elastic kinematics (Sec. II.A.5, Eq. 3)
+// ---------------------------------------------------------------------------
+struct ElasticOut { float T1, c1, T2, c2, ccm; };
+
+__device__ __forceinline__ ElasticOut elastic_kinematics(const NucConst& n, float E, float u0, float u1) {
+  const float m = kMp, M = n.mass;
+  const float plab = sqrtf(E * E + 2.0f * E * m), Elab = E + m;
+  const float s = m * m + M * M + 2.0f * M * Elab;
+  const float rs = sqrtf(s);
+  const float pcm = plab * M / rs;
+  float ct;
+  if (n.A == 1) {
+    ct = 2.0f * u1 - 1.0f;
+  } else {
+    const float A = static_cast<float>(n.A);
+    float a1, b1, a2, b2;
+    if (n.A <= 62) {
+      a1 = powf(A, 1.63f); b1 = 14.5f * powf(A, 0.66f); a2 = 1.4f * powf(A, 0.33f); b2 = 10.0f;
+    } else {
+      a1 = powf(A, 1.33f); b1 = 60.0f * powf(A, 0.33f); a2 = 0.4f * powf(A, 0.4f); b2 = 10.0f;
+    }
+    const float p = pcm * 1e-3f, tmax = 4.0f * p * p;
+    const float e1 = -expm1f(-b1 * tmax), e2 = -expm1f(-b2 * tmax);
+    const float w1 = a1 * e1 / b1, w2 = a2 * e2 / b2;
+    const bool first = u0 * (w1 + w2) < w1;
+    const float b = first ? b1 : b2, eb = first ? e1 : e2;
+    const float t = -log1pf(-u1 * eb) / b;
+    ct = fminf(fmaxf(1.0f - t / (2.0f * p * p), -1.0f), 1.0f);
+  }
+  const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+  const float beta = plab / (Elab + M), gam = (Elab + M) / rs;
+  const float e1 = sqrtf(pcm * pcm + m * m), e2 = sqrtf(pcm * pcm + M * M);
+  const float p1z = gam * (pcm * ct + beta * e1), pt = pcm * st;
+  const float p2z = gam * (-pcm * ct + beta * e2);
+  // kinetic energy from the momentum (no cancellation against the rest mass)
+  const float p1sq = p1z * p1z + pt * pt;
+  float T1 = p1sq / (sqrtf(p1sq + m * m) + m);
+  T1 = fminf(fmaxf(T1, 0.0f), E);
+  ElasticOut o;
+  o.T1 = T1;
+  o.T2 = E - T1;
+  o.c1 = p1z * rsqrtf(p1sq);
+  const float n2 = p2z * p2z + pt * pt;
+  o.c2 = n2 > 0.0f ? p2z * rsqrtf(n2) : 1.0f;
+  o.ccm = ct;
+  return o;
+}
+
+}  // namespace pmc

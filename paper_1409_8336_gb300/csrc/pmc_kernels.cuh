@@ -1,0 +1,114 @@
+// pmc_kernels.cuh -- kernel argument blocks and launch wrappers of the engine.
+#pragma once
+
+#include "pmc_device.cuh"
+
+namespace pmc {
+
+struct Geometry {
+  int nx, ny, nz;
+  float dx, dy, dz, x0, y0, z0, idx, idy, idz;
+  const uint8_t* mat;              // per voxel material (or NULL when hu is used)
+  const float* rho;                // per voxel density
+  const int16_t* hu;               // per voxel HU (or NULL)
+};
+
+// A spot in work order (highest energy first), with the first history index
+// it owns and its offset in the work order.
+struct SpotDev {
+  float E, sE, x, y, sx, sy, u, v, w, pad0;
+  unsigned long long h_first, w_first;
+};
+
+struct TransportArgs {
+  const Physics* phys;
+  const float2* rtab;              // [n_cls][kNE] range splines
+  const float2* etab;              // [n_cls][kNE] inverse splines
+  const float* stab;               // [n_mat][kNS] total cross-section per unit density
+  Geometry g;
+  unsigned long long* tally;       // [n_voxels][B]
+  int B;
+  const unsigned long long* seed;  // device scalar
+  int source;                      // 0: primaries w_begin..w_end; 1: queue qin
+  const SpotDev* spots;
+  int n_spots;
+  unsigned long long w_begin, w_end;
+  const Particle* qin;
+  const unsigned* qin_count;
+  unsigned qin_cap;
+  Particle* qsec;
+  unsigned* qsec_count;
+  unsigned qsec_cap;
+  Particle* qne;
+  unsigned* qne_count;
+  unsigned qne_cap;
+  unsigned* work;                  // work counter of this launch
+  Counters* cnt;
+  long long* hist;                 // per-history ledger [hist_n][4] or NULL
+  unsigned long long hist_n;
+  float* esc;                      // escape record [esc_cap][8] or NULL
+  unsigned long long esc_cap;
+};
+
+struct CascadeArgs {
+  const NucleusModel* nuclei;      // [n_nuc]
+  const float* btab;               // binding energies [kMaxZ][kMaxA]
+  int n_nuc;
+  Geometry g;
+  unsigned long long* tally;
+  int B;
+  const unsigned long long* seed;
+  const Particle* qne;
+  const unsigned* qne_count;
+  unsigned qne_cap;
+  Particle* qsec;
+  unsigned* qsec_count;
+  unsigned qsec_cap;
+  Counters* cnt;
+  long long* hist;
+  unsigned long long hist_n;
+};
+
+struct StatsArgs {
+  const unsigned long long* tally;
+  int B;
+  long long n_vox;
+  Geometry g;
+  const Physics* phys;
+  double* dose;
+  double* sigma;
+};
+
+size_t transport_smem_bytes(int n_cls, int n_mat);
+cudaError_t launch_transport(const TransportArgs& a, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t transport_occupancy(int block, size_t smem, int* blocks_per_sm);
+cudaError_t launch_cascade(const CascadeArgs& a, int grid, int block, cudaStream_t s);
+cudaError_t launch_stats(const StatsArgs& a, cudaStream_t s);
+
+// debug entry points
+cudaError_t launch_debug_philox(const uint4* ctr, uint2 key, uint4* out, int n, cudaStream_t s);
+cudaError_t launch_debug_tables(const Physics* ph, const float2* rt, const float2* et, int cls, const double* E,
+                                double* r, double* e, int n, cudaStream_t s);
+cudaError_t launch_debug_inc(const NucleusModel* nu, const float* btab, float E, unsigned long long seed,
+                             unsigned long long pid0, int n, double* summary, double* products, int cap,
+                             cudaStream_t s);
+cudaError_t launch_debug_elastic(const Physics* ph, int nuclide, float E, const double* u, double* out, int n,
+                                 cudaStream_t s);
+
+__device__ __forceinline__ void voxel_props(const Physics& ph, const Geometry& g, int v, int& m, float& rho) {
+  if (g.hu) {
+    const int h = g.hu[v];
+    int b = ph.n_hu - 1;
+    for (int k = 0; k < ph.n_hu; ++k) {
+      if (h >= ph.hu[k].lo && h < ph.hu[k].hi) { b = k; break; }
+    }
+    if (h < ph.hu[0].lo) b = 0;
+    m = ph.hu[b].mat;
+    rho = ph.hu[b].a + ph.hu[b].b * static_cast<float>(h);
+  } else {
+    m = g.mat[v];
+    rho = g.rho[v];
+  }
+}
+
+}  // namespace pmc

@@ -1,0 +1,315 @@
+"""Python binding of the engine's C ABI (include/pmc.h): argument marshalling only.
+
+Every step of the transport runs in the CUDA library libpmc.so built in-tree
+by build.py.  There is no CPU fallback: if the library is missing, loading it
+raises.  PyTorch is used only as plumbing: optionally its caching allocator
+for the library's device memory and its current CUDA stream for launches.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpmc.so")
+
+PMC_OK = 0
+ERRORS = {-1: "PMC_E_INVALID", -2: "PMC_E_OOM", -3: "PMC_E_QUEUE_OVERFLOW", -4: "PMC_E_TIMEOUT", -5: "PMC_E_CUDA"}
+NO_STRAGGLING, NO_MCS, NO_ELASTIC, NO_INELASTIC = 1, 2, 4, 8
+FULL_CASCADE, SURROGATE = 0, 1
+MAX_NUC_PER_MAT = 12
+
+EXPORTS = [
+    "pmc_create", "pmc_destroy", "pmc_last_error", "pmc_load_materials", "pmc_load_phantom", "pmc_add_spots",
+    "pmc_clear_spots", "pmc_transport", "pmc_read_dose", "pmc_read_tally", "pmc_read_ledger",
+    "pmc_enable_history_ledger", "pmc_read_history_ledger", "pmc_enable_escape_record", "pmc_read_escape_record",
+    "pmc_set_launch", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables", "pmc_debug_inc", "pmc_debug_elastic",
+]
+
+AllocFn = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FreeFn = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Options(C.Structure):
+    _fields_ = [("device", C.c_int), ("n_batches", C.c_int), ("physics_flags", C.c_uint), ("block_size", C.c_int),
+                ("chunk", C.c_int64), ("alloc", AllocFn), ("free", FreeFn), ("alloc_user", C.c_void_p)]
+
+
+class Nuclide(C.Structure):
+    _fields_ = [("Z", C.c_int), ("A", C.c_int), ("mass_u", C.c_double), ("I_eV", C.c_double)]
+
+
+class Material(C.Structure):
+    _fields_ = [("n", C.c_int), ("nuc", C.c_int * MAX_NUC_PER_MAT), ("w", C.c_double * MAX_NUC_PER_MAT),
+                ("rho", C.c_double), ("I_eV", C.c_double), ("own_table", C.c_int)]
+
+
+class HuBin(C.Structure):
+    _fields_ = [("lo", C.c_int), ("hi", C.c_int), ("material", C.c_int), ("rho_a", C.c_double), ("rho_b", C.c_double)]
+
+
+class Spot(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("E", "sigma_E", "x", "y", "sigma_x", "sigma_y", "u", "v", "w", "weight")]
+
+
+class Ledger(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("incident", "deposited", "escaped", "binding", "histories", "steps",
+                                         "elastic", "inelastic", "secondaries", "transparent", "inc_retries",
+                                         "queue_high_water", "generations", "dropped", "errors")]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Loads libpmc.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError("libpmc.so not built: run `python -m paper_1409_8336_gb300.build` "
+                                  "(or __graft_entry__.build())")
+            L = C.CDLL(LIB_PATH)
+            vp, i, u64, d = C.c_void_p, C.c_int, C.c_uint64, C.c_double
+            pd, pi64 = C.POINTER(C.c_double), C.POINTER(C.c_int64)
+            L.pmc_create.argtypes = [C.POINTER(vp), C.POINTER(Options)]
+            L.pmc_destroy.argtypes = [vp]
+            L.pmc_destroy.restype = None
+            L.pmc_last_error.argtypes = [vp]
+            L.pmc_last_error.restype = C.c_char_p
+            L.pmc_load_materials.argtypes = [vp, C.POINTER(Nuclide), i, C.POINTER(Material), i, C.POINTER(HuBin), i]
+            L.pmc_load_phantom.argtypes = [vp, i, i, i, d, d, d, d, d, d, vp, vp, vp]
+            L.pmc_add_spots.argtypes = [vp, C.POINTER(Spot), i]
+            L.pmc_clear_spots.argtypes = [vp]
+            L.pmc_transport.argtypes = [vp, u64, u64, i, vp]
+            L.pmc_read_dose.argtypes = [vp, vp, vp, C.c_size_t]
+            L.pmc_read_tally.argtypes = [vp, pi64, C.c_size_t]
+            L.pmc_read_ledger.argtypes = [vp, C.POINTER(Ledger)]
+            L.pmc_enable_history_ledger.argtypes = [vp, u64]
+            L.pmc_read_history_ledger.argtypes = [vp, pi64, u64]
+            L.pmc_enable_escape_record.argtypes = [vp, u64]
+            L.pmc_read_escape_record.argtypes = [vp, C.POINTER(C.c_float), u64, C.POINTER(C.c_uint64)]
+            L.pmc_set_launch.argtypes = [vp, i, C.c_int64]
+            L.pmc_enable_profile.argtypes = [vp, i]
+            L.pmc_read_profile.argtypes = [vp, pd, pi64, pi64]
+            L.pmc_debug_philox.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), i]
+            L.pmc_debug_tables.argtypes = [vp, i, pd, pd, pd, i]
+            L.pmc_debug_inc.argtypes = [vp, i, d, u64, u64, i, pd, pd, i]
+            L.pmc_debug_elastic.argtypes = [vp, i, d, pd, pd, i]
+            _lib = L
+    return _lib
+
+
+class PmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _torch_allocator(device):
+    import torch
+
+    def alloc(n, _user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(n), device=device)
+        except Exception:  # noqa: BLE001 - reported to the library as a NULL allocation
+            return None
+
+    def free(p, _user):
+        torch.cuda.caching_allocator_delete(int(p))
+
+    return AllocFn(alloc), FreeFn(free)
+
+
+class Engine:
+    """One engine context on one GPU.  Method names follow the C ABI."""
+
+    def __init__(self, device: int = 0, n_batches: int = 10, physics_flags: int = 0, block_size: int = 0,
+                 chunk: int = 0, torch_allocator: bool = False):
+        self._L = lib()
+        opt = Options()
+        opt.device, opt.n_batches, opt.physics_flags = device, n_batches, physics_flags
+        opt.block_size, opt.chunk = block_size, chunk
+        self._keep = None
+        if torch_allocator:
+            self._keep = _torch_allocator(device)
+            opt.alloc, opt.free = self._keep
+        self._ctx = C.c_void_p()
+        rc = self._L.pmc_create(C.byref(self._ctx), C.byref(opt))
+        if rc != PMC_OK:
+            raise PmcError(rc, "pmc_create failed")
+        self.n_batches = n_batches
+        self.shape = None
+
+    def close(self):
+        if self._ctx:
+            self._L.pmc_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def _check(self, rc):
+        if rc != PMC_OK:
+            raise PmcError(rc, self._L.pmc_last_error(self._ctx).decode())
+
+    # --- inputs ---------------------------------------------------------
+    def load_materials(self, nuclides, materials, hu_bins=()):
+        nuc = (Nuclide * len(nuclides))(*[Nuclide(*n) for n in nuclides])
+        mats = []
+        for m in materials:
+            M = Material()
+            M.n = len(m["nuc"])
+            for k, (ni, w) in enumerate(zip(m["nuc"], m["w"])):
+                M.nuc[k], M.w[k] = ni, w
+            M.rho, M.I_eV, M.own_table = m["rho"], m.get("I_eV", 0.0), int(m.get("own_table", 0))
+            mats.append(M)
+        mat = (Material * len(mats))(*mats)
+        hu = (HuBin * max(1, len(hu_bins)))(*[HuBin(*b) for b in hu_bins])
+        self._check(self._L.pmc_load_materials(self._ctx, nuc, len(nuclides), mat, len(mats), hu, len(hu_bins)))
+
+    def load_phantom(self, shape, voxel, origin, hu=None, mat=None, rho=None):
+        """shape (nz, ny, nx); arrays [nz, ny, nx] in host memory (pinned or pageable)."""
+        nz, ny, nx = shape
+        self._arrays = []
+
+        def ptr(a, dt):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):          # a pinned torch tensor
+                assert a.is_contiguous() and not a.is_cuda
+                return a.data_ptr()
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._arrays.append(a)
+            return a.ctypes.data
+
+        self._check(self._L.pmc_load_phantom(self._ctx, nx, ny, nz, *voxel, *origin, ptr(hu, np.int16),
+                                             ptr(mat, np.uint8), ptr(rho, np.float32)))
+        self.shape = tuple(shape)
+
+    def add_spots(self, spots):
+        s = np.ascontiguousarray(spots, dtype=np.float64).reshape(-1, 10)
+        self._check(self._L.pmc_add_spots(self._ctx, s.ctypes.data_as(C.POINTER(Spot)), len(s)))
+
+    def clear_spots(self):
+        self._check(self._L.pmc_clear_spots(self._ctx))
+
+    def load_problem(self, prob):
+        """Loads a workloads.Problem (materials, phantom, spots)."""
+        self.load_materials(prob.nuclides, prob.materials, prob.hu_bins)
+        self.load_phantom(prob.shape, prob.voxel, prob.origin, hu=prob.hu, mat=prob.mat, rho=prob.rho)
+        self.clear_spots()
+        self.add_spots(prob.spots)
+
+    def set_launch(self, block_size=0, chunk=0):
+        self._check(self._L.pmc_set_launch(self._ctx, block_size, chunk))
+
+    # --- run ------------------------------------------------------------
+    def transport(self, n_histories: int, seed: int, mode: int = FULL_CASCADE, stream=None):
+        s = None
+        if stream is not None:
+            s = stream if isinstance(stream, int) else stream.cuda_stream
+        self._check(self._L.pmc_transport(self._ctx, n_histories, seed, mode, s))
+
+    # --- outputs --------------------------------------------------------
+    @property
+    def n_voxels(self):
+        return int(np.prod(self.shape))
+
+    def read_dose(self, dose=None, sigma=None):
+        n = self.n_voxels
+        dose = np.empty(n) if dose is None else dose
+        sigma = np.empty(n) if sigma is None else sigma
+
+        def ptr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+        self._check(self._L.pmc_read_dose(self._ctx, ptr(dose), ptr(sigma), n))
+        return dose, sigma
+
+    def read_tally(self):
+        t = np.empty((self.n_voxels, self.n_batches), dtype=np.int64)
+        self._check(self._L.pmc_read_tally(self._ctx, t.ctypes.data_as(C.POINTER(C.c_int64)), t.size))
+        return t
+
+    def read_ledger(self):
+        led = Ledger()
+        self._check(self._L.pmc_read_ledger(self._ctx, C.byref(led)))
+        return {k: getattr(led, k) for k, _ in Ledger._fields_}
+
+    def enable_history_ledger(self, n):
+        self._check(self._L.pmc_enable_history_ledger(self._ctx, n))
+        self._hist_n = n
+
+    def read_history_ledger(self, n):
+        out = np.empty((n, 4), dtype=np.int64)
+        self._check(self._L.pmc_read_history_ledger(self._ctx, out.ctypes.data_as(C.POINTER(C.c_int64)), n))
+        return out
+
+    def enable_escape_record(self, cap):
+        self._check(self._L.pmc_enable_escape_record(self._ctx, cap))
+        self._esc_cap = cap
+
+    def read_escape_record(self):
+        cap = self._esc_cap
+        out = np.empty((cap, 8), dtype=np.float32)
+        n = C.c_uint64(0)
+        self._check(self._L.pmc_read_escape_record(self._ctx, out.ctypes.data_as(C.POINTER(C.c_float)), cap,
+                                                   C.byref(n)))
+        return out[: n.value]
+
+    def enable_profile(self, on=True):
+        self._check(self._L.pmc_enable_profile(self._ctx, 1 if on else 0))
+
+    def read_profile(self):
+        """Per kernel kind (primary transport, secondary transport, cascade, statistics):
+        summed ms and launches of the last transport, and the primary-transport step count."""
+        ms = np.zeros(4)
+        n = np.zeros(4, dtype=np.int64)
+        steps = C.c_int64(0)
+        self._check(self._L.pmc_read_profile(self._ctx, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64)),
+                                             C.byref(steps)))
+        kinds = ("transport_primary", "transport_secondary", "cascade", "stats")
+        return {k: {"ms": float(ms[i]), "launches": int(n[i])} for i, k in enumerate(kinds)}, int(steps.value)
+
+    # --- single-routine device checks ------------------------------------
+    def debug_tables(self, material, E):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        r, e = np.empty_like(E), np.empty_like(E)
+        self._check(self._L.pmc_debug_tables(self._ctx, material, _dp(E), _dp(r), _dp(e), len(E)))
+        return r, e
+
+    def debug_inc(self, nuclide, E, seed, pid0, n, cap=160):
+        summ = np.zeros((n, 8))
+        prod = np.zeros((n, cap, 5))
+        self._check(self._L.pmc_debug_inc(self._ctx, nuclide, E, seed, pid0, n, _dp(summ), _dp(prod), cap))
+        return summ, prod
+
+    def debug_elastic(self, nuclide, E, u):
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1, 3)
+        out = np.empty((len(u), 5))
+        self._check(self._L.pmc_debug_elastic(self._ctx, nuclide, E, _dp(u), _dp(out), len(u)))
+        return out
+
+
+def debug_philox(ctr, key):
+    """Philox4x32-10 on the device: ctr [n, 4] uint32, key (2,) -> [n, 4] uint32."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.empty_like(ctr)
+    P = C.POINTER(C.c_uint32)
+    rc = lib().pmc_debug_philox(ctr.ctypes.data_as(P), key.ctypes.data_as(P), out.ctypes.data_as(P), len(ctr))
+    if rc != PMC_OK:
+        raise PmcError(rc, "pmc_debug_philox failed")
+    return out

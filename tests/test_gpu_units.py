@@ -1,0 +1,93 @@
+"""Single routines on the device against the CPU oracle on identical inputs (GPU)."""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from conftest import golden
+from oracle import oracle as O
+from paper_1409_8336_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_1409_8336_gb300 import Engine, build
+
+    build.build()
+    e = Engine(device=0, n_batches=10)
+    p = W.config3(shape=(16, 32, 32), n_layers=2)
+    e.load_problem(p)
+    yield e, p
+    e.close()
+
+
+def test_philox_device_matches_known_answers_and_oracle():
+    from paper_1409_8336_gb300 import debug_philox
+
+    for row in golden("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in row]
+        assert list(debug_philox(np.array([v[0:4]]), np.array(v[4:6]))[0]) == v[6:10]
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(512, 4), dtype=np.uint64).astype(np.uint32)
+    key = np.array([0x12345678, 0x9abcdef0], dtype=np.uint32)
+    dev = debug_philox(ctr, key)
+    for c, d in zip(ctr[:64], dev[:64]):
+        assert O.philox([int(x) for x in c], [int(x) for x in key]) == [int(x) for x in d]
+
+
+def test_range_tables_match_oracle(eng):
+    e, p = eng
+    E = np.geomspace(0.12, 290.0, 200)
+    for m in range(len(p.materials)):
+        r, eb = e.debug_tables(m, E)
+        info = O.material_info(p, m)
+        # the scaled materials share the reference water table (Eq. 1 / Eq. 2)
+        base = 0 if not p.materials[m].get("own_table") else m
+        ref = np.array([O.range_csda(p, base, x) for x in E])
+        assert np.allclose(r, ref, rtol=2e-5, atol=1e-9), (m, np.max(np.abs(r / ref - 1)))
+        assert np.allclose(eb, E, rtol=3e-5), (m, np.max(np.abs(eb / E - 1)))
+        assert info["f"] > 0
+
+
+@pytest.mark.parametrize("nuc,E", [(0, 150.0), (3, 150.0), (3, 20.0), (6, 230.0), (1, 70.0)])
+def test_elastic_kinematics_match_oracle(eng, nuc, E):
+    e, p = eng
+    Z, A = p.nuclides[nuc][0], p.nuclides[nuc][1]
+    u = np.random.default_rng(nuc).uniform(size=(2000, 3)).astype(np.float32).astype(np.float64)
+    dev = e.debug_elastic(nuc, E, u)
+    ref = np.array([O.elastic(Z, A, E, row) for row in u[:300]])
+    assert np.allclose(dev[:300, 0], ref[:, 0], rtol=1e-4, atol=2e-4 * E)
+    assert np.allclose(dev[:300, 1], ref[:, 1], atol=2e-4)
+    assert np.allclose(dev[:300, 4], ref[:, 4], atol=2e-4)
+    assert np.allclose(dev[:, 0] + dev[:, 2], E, rtol=1e-6)
+
+
+@pytest.mark.parametrize("nuc,E", [(3, 200.0), (5, 200.0), (1, 90.0), (6, 150.0)])
+def test_cascade_events_match_oracle(eng, nuc, E):
+    e, p = eng
+    Z, A = p.nuclides[nuc][0], p.nuclides[nuc][1]
+    n, seed, pid0 = 4000, 17, 1000
+    ds, dp = e.debug_inc(nuc, E, seed, pid0, n)
+    os_, op, _ = O.inc_batch(Z, A, E, seed, pid0, n)
+    # identical random streams: most events take the same discrete path
+    same = np.mean((ds[:, 0] == os_[:, 0]) & (np.abs(dp[:, 0, 1] - op[:, 0, 1]) < 1e-3 * E))
+    assert same > 0.5, same
+    # distributions agree (KS) for proton and neutron spectra and excitation left over
+    for sp in (0, 1):
+        dT = dp[:, :, 1][(dp[:, :, 0] == sp) & (np.arange(dp.shape[1])[None, :] < ds[:, :1])]
+        oT = op[:, :, 1][(op[:, :, 0] == sp) & (np.arange(op.shape[1])[None, :] < os_[:, :1])]
+        assert stats.ks_2samp(dT, oT).pvalue > 1e-3
+        assert abs(len(dT) - len(oT)) < 4 * math.sqrt(len(oT)) + 10
+    # device events conserve charge, baryon number and energy
+    spec = {0: (0, 1), 1: (1, 1), 2: (1, 2), 3: (1, 3), 4: (2, 3), 5: (2, 4)}
+    for i in range(0, n, 7):
+        k = int(ds[i, 0])
+        if ds[i, 7]:
+            continue
+        sps = dp[i, :k, 0].astype(int)
+        assert sum(spec[s][0] for s in sps) + ds[i, 1] == Z + 1
+        assert sum(spec[s][1] for s in sps) + ds[i, 2] == A + 1
+        assert dp[i, :k, 1].sum() + ds[i, 3] + ds[i, 4] + ds[i, 5] == pytest.approx(E, abs=2e-4)
