@@ -204,6 +204,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     ms, prof_ms, prof_n, steps_primary, ledgers, launches = [], 0.0, 0, 0, [], 0
+    kinds = {}
     with Clocks(local) as clk:
         for i in range(args.steps):
             t, prof, s0, led = one(rank * 100003 + i + 1)
@@ -213,6 +214,10 @@ def main():
             steps_primary += s0
             ledgers.append(led)
             launches += sum(p["launches"] for p in prof.values())
+            for k, v in prof.items():
+                kinds.setdefault(k, [0.0, 0])
+                kinds[k][0] += v["ms"] / args.steps
+                kinds[k][1] = v["launches"]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -274,6 +279,7 @@ def main():
                          "ops_per_step": OPS_PER_STEP, "steps_per_launch": steps_per_launch,
                          "launch_ms": launch_ms},
             "clocks": clk.summary(),
+            "kernels_ms_per_step": {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in kinds.items()},
             "cpu_baseline": cpu,
             "stats": {"steps_per_history": led["steps"] / n, "inelastic": led["inelastic"],
                       "elastic": led["elastic"], "secondaries": led["secondaries"],

@@ -185,6 +185,42 @@ def run(prob, n_hist: int, seed: int, h_begin: int = 0, h_end: int | None = None
     return tally, totals, hl
 
 
+_PROBLEM_FIELDS = ("nuclides", "materials", "hu_bins", "spots", "shape", "voxel", "origin", "hu", "mat", "rho",
+                   "n_batches", "flags")
+
+
+def _run_range(job):
+    import types
+
+    fields, n_hist, seed, h0, h1 = job
+    tally, tot, _ = run(types.SimpleNamespace(**fields), n_hist, seed, h_begin=h0, h_end=h1)
+    return tally, tot
+
+
+def run_parallel(prob, n_hist: int, seed: int, procs: int | None = None):
+    """The same computation as run(), split over history ranges in spawned worker processes
+    (each range is an independent set of histories; tallies are summed in range order)."""
+    import multiprocessing as mp
+
+    procs = procs or os.cpu_count() or 1
+    procs = max(1, min(procs, n_hist // 200 or 1))
+    fields = {k: getattr(prob, k) for k in _PROBLEM_FIELDS}
+    cuts = [n_hist * i // procs for i in range(procs + 1)]
+    jobs = [(fields, n_hist, seed, cuts[i], cuts[i + 1]) for i in range(procs)]
+    if procs == 1:
+        parts = [_run_range(jobs[0])]
+    else:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            parts = pool.map(_run_range, jobs)
+    tally = np.zeros_like(parts[0][0])
+    totals = {k: 0.0 for k in parts[0][1]}
+    for t, tot in parts:
+        tally += t
+        for k in totals:
+            totals[k] += tot[k]
+    return tally, totals
+
+
 def material_info(prob, m: int):
     L = lib()
     mm = _Marshalled(prob)

@@ -15,6 +15,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpmc.so")
+# The engine is built twice: with IEEE single-precision math, and with
+# -use_fast_math (hardware approximations of division, sqrt, log, exp, sin/cos),
+# the build option the method's authors timed and verified equivalent.
+VARIANTS = {"libpmc.so": [], "libpmc_fast.so": ["-use_fast_math"]}
 SOURCES = ["transport.cu", "cascade.cu", "stats.cu", "host.cu"]
 HEADERS = ["pmc_device.cuh", "pmc_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,19 +40,26 @@ def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src] + [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "pmc.h")]
+    deps = [src] + [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "pmc.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    jobs = []
-    for s in SOURCES:
-        src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
-        if force or ptxas_info or _stale(obj, src):
-            extra = ["-Xptxas", "-v"] if ptxas_info else []
-            jobs.append((obj, [nvcc(), *flags(extra), "-c", src, "-o", obj]))
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, extra=(), out_dir: str | None = None):
+    """Compiles every variant; returns the path of the default library."""
+    out_dir = out_dir or HERE
+    jobs, links = [], []
+    for lib_name, vflags in VARIANTS.items():
+        bdir = os.path.join(BUILD if out_dir == HERE else os.path.join(out_dir, "_build"), lib_name.split(".")[0])
+        os.makedirs(bdir, exist_ok=True)
+        objs = []
+        for s in SOURCES:
+            src = os.path.join(CSRC, s)
+            obj = os.path.join(bdir, s.replace(".cu", ".o"))
+            objs.append(obj)
+            if force or ptxas_info or extra or _stale(obj, src):
+                px = ["-Xptxas", "-v"] if ptxas_info else []
+                jobs.append((obj, [nvcc(), *flags([*vflags, *px, *extra]), "-c", src, "-o", obj]))
+        links.append((os.path.join(out_dir, lib_name), objs))
 
     def run(job):
         obj, cmd = job
@@ -57,16 +68,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (obj, r.stdout, r.stderr))
         return r.stdout + r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(8, max(1, len(jobs)))) as ex:
         for out in ex.map(run, jobs):
             if verbose and out:
                 print(out)
-    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+    for lib, objs in links:
+        if jobs or not os.path.exists(lib):
+            tmp = lib + ".tmp%d" % os.getpid()
+            subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+            os.replace(tmp, lib)
+    return os.path.join(out_dir, "libpmc.so")
 
 
 if __name__ == "__main__":

@@ -120,50 +120,58 @@ std::vector<float2> spline(const std::vector<double>& y, double h, double d0, do
 
 struct RangeClass {
   double ZA, I;
-  std::vector<double> E, R;     // nodes on ln E
+  std::vector<double> E, R;     // forward nodes: ln E = j / 64
   double range(double e) const {  // accurate range at any energy >= 1 MeV
-    const double dl = std::log(300.0) / (kNE - 1);
-    int j = static_cast<int>(std::log(e) / dl);
+    int j = static_cast<int>(std::log(e) * 64.0);
     j = std::max(0, std::min(j, kNE - 1));
     while (j > 0 && E[j] > e) --j;
     return R[j] + integrate_inv_s(E[j], e, ZA, I);
   }
 };
 
-void build_range_class(double ZA, double I, RangeClass& rc, std::vector<float2>& rt, std::vector<float2>& et,
-                       float& S1, float& R1, float& lnR0, float& inv_dlnR) {
+// Range and inverse-range splines of one stopping-power class (Sec. II.A.2):
+// R(E) = R(1 MeV) + integral of 1/S from 1 MeV, with R(1 MeV) = 2/S(1 MeV) from
+// the sqrt(E) continuation below 1 MeV; nodes uniform in ln E and ln R with
+// spacing 2^-6; clamped splines with the exact end slopes.
+int build_range_class(double ZA, double I, std::vector<float2>& rt, std::vector<float2>& et, float& S1, float& R1,
+                      float& lnR0, int& nR) {
+  RangeClass rc;
   rc.ZA = ZA; rc.I = I;
-  const double dl = std::log(300.0) / (kNE - 1);
+  const double h = 1.0 / 64.0;
   rc.E.resize(kNE); rc.R.resize(kNE);
   const double s1 = bethe_mass(1.0, ZA, I);
-  for (int j = 0; j < kNE; ++j) rc.E[j] = std::exp(j * dl);
+  for (int j = 0; j < kNE; ++j) rc.E[j] = std::exp(j * h);
   rc.E[0] = 1.0;
   rc.R[0] = 2.0 / s1;
   for (int j = 1; j < kNE; ++j) rc.R[j] = rc.R[j - 1] + integrate_inv_s(rc.E[j - 1], rc.E[j], ZA, I);
-  // forward: R as a function of x = ln E, dR/dx = E / S
-  rt = spline(rc.R, dl, rc.E[0] / bethe_mass(rc.E[0], ZA, I), rc.E[kNE - 1] / bethe_mass(rc.E[kNE - 1], ZA, I));
-  // inverse: E as a function of y = ln R on a uniform grid, dE/dy = R S
-  const double y0 = std::log(rc.R[0]), y1 = std::log(rc.R[kNE - 1]), dy = (y1 - y0) / (kNE - 1);
-  std::vector<double> Ey(kNE);
-  for (int j = 0; j < kNE; ++j) {
-    const double Rt = std::exp(y0 + j * dy);
-    double e = rc.E[std::min(kNE - 1, std::max(0, static_cast<int>((y0 + j * dy - y0) / dy)))];
-    // bracket from the node table, then Newton on R(E) - Rt (dR/dE = 1/S)
+  rt = spline(rc.R, h, rc.E[0] / bethe_mass(rc.E[0], ZA, I), rc.E[kNE - 1] / bethe_mass(rc.E[kNE - 1], ZA, I));
+  const double y0 = std::floor(std::log(rc.R[0]) * 64.0) / 64.0;
+  const int n = static_cast<int>(std::ceil((std::log(rc.R[kNE - 1]) - y0) * 64.0)) + 1;
+  if (n > kNR) return -1;
+  std::vector<double> Ey(n);
+  for (int j = 0; j < n; ++j) {
+    const double Rt = std::exp(y0 + j * h);
+    if (Rt <= rc.R[0]) { const double q = 0.5 * Rt * s1; Ey[j] = q * q; continue; }
     int lo = 0, hi = kNE - 1;
     while (hi - lo > 1) { const int mid = (lo + hi) / 2; if (rc.R[mid] <= Rt) lo = mid; else hi = mid; }
-    e = rc.E[lo] + (rc.E[hi] - rc.E[lo]) * (Rt - rc.R[lo]) / (rc.R[hi] - rc.R[lo]);
-    for (int it = 0; it < 30; ++it) {
+    double e = Rt < rc.R[kNE - 1] ? rc.E[lo] + (rc.E[hi] - rc.E[lo]) * (Rt - rc.R[lo]) / (rc.R[hi] - rc.R[lo])
+                                  : rc.E[kNE - 1];
+    for (int it = 0; it < 40; ++it) {   // Newton on R(E) - Rt, dR/dE = 1/S
       const double de = (rc.range(e) - Rt) * bethe_mass(e, ZA, I);
       e -= de;
       if (std::fabs(de) < 1e-14 * e) break;
     }
-    Ey[j] = (j == 0) ? 1.0 : (j == kNE - 1 ? 300.0 : e);
+    Ey[j] = e;
   }
-  et = spline(Ey, dy, rc.R[0] * bethe_mass(1.0, ZA, I), rc.R[kNE - 1] * bethe_mass(300.0, ZA, I));
+  const double d0 = std::exp(y0) * (Ey[0] < 1.0 ? s1 * std::sqrt(Ey[0]) : bethe_mass(Ey[0], ZA, I));
+  const double dn = std::exp(y0 + (n - 1) * h) * bethe_mass(Ey[n - 1], ZA, I);
+  et = spline(Ey, h, d0, dn);
+  et.resize(kNR, make_float2(0.0f, 0.0f));
   S1 = static_cast<float>(s1);
   R1 = static_cast<float>(rc.R[0]);
   lnR0 = static_cast<float>(y0);
-  inv_dlnR = static_cast<float>(1.0 / dy);
+  nR = n;
+  return 0;
 }
 
 void build_nucleus(int Z, int A, NucleusModel& nm) {
@@ -437,25 +445,20 @@ int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc, const pm
       }
     }
     ph.n_cls = ncls;
-    std::vector<float2> rt(ncls * kNE), et(ncls * kNE);
+    std::vector<float2> rt(ncls * kNE), et(ncls * kNR);
     for (int m = 0; m < n_mat; ++m) {
       const int c = ph.mat[m].cls;
       if (m > 0 && c == 0) continue;
-      RangeClass rc;
       std::vector<float2> a, b;
-      build_range_class(ZA[m], Iv[m], rc, a, b, ph.S1[c], ph.R1[c], ph.lnR0[c], ph.inv_dlnR[c]);
+      if (build_range_class(ZA[m], Iv[m], a, b, ph.S1[c], ph.R1[c], ph.lnR0[c], ph.nR[c]))
+        return fail(ctx, PMC_E_INVALID, "material %d: range table exceeds %d nodes", m, kNR);
       std::copy(a.begin(), a.end(), rt.begin() + c * kNE);
-      std::copy(b.begin(), b.end(), et.begin() + c * kNE);
+      std::copy(b.begin(), b.end(), et.begin() + c * kNR);
     }
-    ph.dlnE = static_cast<float>(std::log(300.0) / (kNE - 1));
-    ph.inv_dlnE = static_cast<float>((kNE - 1) / std::log(300.0));
-    const double ls0 = std::log(0.1), ls1 = std::log(300.0), dls = (ls1 - ls0) / (kNS - 1);
-    ph.lnS0 = static_cast<float>(ls0);
-    ph.inv_dlnS = static_cast<float>(1.0 / dls);
     std::vector<float> st(n_mat * kNS);
     for (int m = 0; m < n_mat; ++m) {
       for (int j = 0; j < kNS; ++j) {
-        const double E = std::exp(ls0 + j * dls);
+        const double E = std::exp(static_cast<double>(kLnS0) + j / 64.0);
         double s = 0.0;
         for (int k = 0; k < mat[m].n; ++k) {
           const pmc_nuclide& q = nuc[mat[m].nuc[k]];

@@ -21,8 +21,14 @@ constexpr float kFix = 16777216.0f;            // tally unit 2^-24 MeV
 constexpr double kFixD = 16777216.0;
 constexpr float kCoulomb = 1.439964548f;       // e^2 / 4 pi eps0, MeV fm
 constexpr float kFm2PerMb = 0.1f;
-constexpr int kNE = 512;                       // range table nodes on ln E in [0, ln 300]
-constexpr int kNS = 512;                       // cross-section table nodes on ln E in [ln 0.1, ln 300]
+// Tables are uniform in ln E or ln R with spacing 2^-6, so the table coordinate
+// (ln x - origin) * 64 is computed without a rounded scale factor: a rounded
+// 1/h would bias every step's energy loss the same way and drift the range.
+constexpr float kTabScale = 64.0f;             // 1 / grid spacing
+constexpr int kNE = 384;                       // range nodes: ln E in [0, 383/64], E in [1, 396] MeV
+constexpr int kNR = 768;                       // inverse-range nodes per class: ln R from lnR0[cls]
+constexpr int kNS = 544;                       // cross-section nodes: ln E from kLnS0
+constexpr float kLnS0 = -2.3125f;              // floor(64 ln 0.1) / 64
 constexpr int kMaxMat = 16, kMaxNuc = 16, kMaxNucPerMat = 12, kMaxHu = 16, kMaxCls = 4;
 constexpr int kShells = 15;                    // Woods-Saxon shells, Sec. II.A.4
 constexpr int kMaxZ = 24, kMaxA = 52;          // binding-energy table extent
@@ -64,11 +70,10 @@ struct HuBin { int lo, hi, mat; float a, b; };
 struct alignas(16) Physics {
   int n_mat, n_nuc, n_hu, n_cls;
   unsigned flags;
-  float dlnE, inv_dlnE;            // range grid step (ln E from 0)
-  float lnS0, inv_dlnS;            // cross-section grid origin and inverse step
   float S1[kMaxCls];               // mass stopping power at 1 MeV per class
   float R1[kMaxCls];               // mass range at 1 MeV per class
-  float lnR0[kMaxCls], inv_dlnR[kMaxCls];   // inverse table grid (ln R)
+  float lnR0[kMaxCls];             // origin of the inverse table (a multiple of 2^-6)
+  int nR[kMaxCls];                 // inverse-table nodes used per class
   MatConst mat[kMaxMat];
   NucConst nuc[kMaxNuc];
   HuBin hu[kMaxHu];
@@ -155,7 +160,7 @@ __device__ __forceinline__ float spline_eval(const float2* __restrict__ t, float
 __device__ __forceinline__ float range_mass(const Physics& ph, const float2* __restrict__ rt, int cls, float E,
                                             float lnE) {
   if (E <= 1.0f) return 2.0f * sqrtf(E) / ph.S1[cls];
-  return spline_eval(rt + cls * kNE, lnE * ph.inv_dlnE, kNE);
+  return spline_eval(rt + cls * kNE, lnE * kTabScale, kNE);
 }
 
 // Inverse of range_mass.
@@ -165,12 +170,12 @@ __device__ __forceinline__ float energy_of_range(const Physics& ph, const float2
     const float h = 0.5f * R * ph.S1[cls];
     return h * h;
   }
-  return spline_eval(et + cls * kNE, (logf(R) - ph.lnR0[cls]) * ph.inv_dlnR[cls], kNE);
+  return spline_eval(et + cls * kNR, (logf(R) - ph.lnR0[cls]) * kTabScale, ph.nR[cls]);
 }
 
 // Total macroscopic nuclear cross-section per unit density (cm^2/g), linear in ln E.
 __device__ __forceinline__ float sigma_table(const Physics& ph, const float* __restrict__ st, int m, float lnE) {
-  float s = (lnE - ph.lnS0) * ph.inv_dlnS;
+  float s = (lnE - kLnS0) * kTabScale;
   s = fminf(fmaxf(s, 0.0f), static_cast<float>(kNS - 1) - 1e-3f);
   const int j = static_cast<int>(s);
   const float t = s - static_cast<float>(j);

@@ -23,7 +23,7 @@ struct SpotDev {
 struct TransportArgs {
   const Physics* phys;
   const float2* rtab;              // [n_cls][kNE] range splines
-  const float2* etab;              // [n_cls][kNE] inverse splines
+  const float2* etab;              // [n_cls][kNR] inverse splines
   const float* stab;               // [n_mat][kNS] total cross-section per unit density
   Geometry g;
   unsigned long long* tally;       // [n_voxels][B]

@@ -283,7 +283,11 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   return true;
 }
 
-__global__ void __launch_bounds__(256) transport_kernel(const TransportArgs a) {
+#ifndef PMC_TRANSPORT_MIN_BLOCKS
+#define PMC_TRANSPORT_MIN_BLOCKS 3   // measured best on GB300: 3 resident blocks of 256 per SM
+#endif
+
+__global__ void __launch_bounds__(256, PMC_TRANSPORT_MIN_BLOCKS) transport_kernel(const TransportArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned long long n_items =
       a.source == 0 ? (a.w_end - a.w_begin) : static_cast<unsigned long long>(min(*a.qin_count, a.qin_cap));
@@ -302,8 +306,9 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportArgs a) {
   const size_t off_rt = (sizeof(Physics) + 15) / 16 * 16;
   float2* rt = reinterpret_cast<float2*>(smem + off_rt);
   float2* et = rt + ncls * kNE;
-  float* st = reinterpret_cast<float*>(et + ncls * kNE);
-  for (int i = threadIdx.x; i < ncls * kNE; i += blockDim.x) { rt[i] = a.rtab[i]; et[i] = a.etab[i]; }
+  float* st = reinterpret_cast<float*>(et + ncls * kNR);
+  for (int i = threadIdx.x; i < ncls * kNE; i += blockDim.x) rt[i] = a.rtab[i];
+  for (int i = threadIdx.x; i < ncls * kNR; i += blockDim.x) et[i] = a.etab[i];
   for (int i = threadIdx.x; i < nmat * kNS; i += blockDim.x) st[i] = a.stab[i];
   __syncthreads();
   const Physics& ph = *php;
@@ -367,7 +372,8 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportArgs a) {
 }  // namespace
 
 size_t transport_smem_bytes(int n_cls, int n_mat) {
-  return (sizeof(Physics) + 15) / 16 * 16 + 2ull * n_cls * kNE * sizeof(float2) + 1ull * n_mat * kNS * sizeof(float);
+  return (sizeof(Physics) + 15) / 16 * 16 + 1ull * n_cls * (kNE + kNR) * sizeof(float2) +
+         1ull * n_mat * kNS * sizeof(float);
 }
 
 cudaError_t transport_occupancy(int block, size_t smem, int* blocks_per_sm) {

@@ -15,6 +15,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpmc.so")
+LIB_FAST_PATH = os.path.join(HERE, "libpmc_fast.so")   # the -use_fast_math build
 
 PMC_OK = 0
 ERRORS = {-1: "PMC_E_INVALID", -2: "PMC_E_OOM", -3: "PMC_E_QUEUE_OVERFLOW", -4: "PMC_E_TIMEOUT", -5: "PMC_E_CUDA"}
@@ -61,19 +62,18 @@ class Ledger(C.Structure):
                                          "queue_high_water", "generations", "dropped", "errors")]
 
 
-_lib = None
+_libs = {}
 _lock = threading.Lock()
 
 
-def lib():
-    """Loads libpmc.so (raises if it has not been built: there is no fallback)."""
-    global _lib
+def lib(path: str = LIB_PATH):
+    """Loads the engine library (raises if it has not been built: there is no fallback)."""
     with _lock:
-        if _lib is None:
-            if not os.path.exists(LIB_PATH):
-                raise ImportError("libpmc.so not built: run `python -m paper_1409_8336_gb300.build` "
-                                  "(or __graft_entry__.build())")
-            L = C.CDLL(LIB_PATH)
+        if path not in _libs:
+            if not os.path.exists(path):
+                raise ImportError("%s not built: run `python -m paper_1409_8336_gb300.build` "
+                                  "(or __graft_entry__.build())" % os.path.basename(path))
+            L = C.CDLL(path)
             vp, i, u64, d = C.c_void_p, C.c_int, C.c_uint64, C.c_double
             pd, pi64 = C.POINTER(C.c_double), C.POINTER(C.c_int64)
             L.pmc_create.argtypes = [C.POINTER(vp), C.POINTER(Options)]
@@ -100,8 +100,8 @@ def lib():
             L.pmc_debug_tables.argtypes = [vp, i, pd, pd, pd, i]
             L.pmc_debug_inc.argtypes = [vp, i, d, u64, u64, i, pd, pd, i]
             L.pmc_debug_elastic.argtypes = [vp, i, d, pd, pd, i]
-            _lib = L
-    return _lib
+            _libs[path] = L
+    return _libs[path]
 
 
 class PmcError(RuntimeError):
@@ -133,8 +133,9 @@ class Engine:
     """One engine context on one GPU.  Method names follow the C ABI."""
 
     def __init__(self, device: int = 0, n_batches: int = 10, physics_flags: int = 0, block_size: int = 0,
-                 chunk: int = 0, torch_allocator: bool = False):
-        self._L = lib()
+                 chunk: int = 0, torch_allocator: bool = False, fast_math: bool = False, library: str | None = None):
+        self._L = lib(library or (LIB_FAST_PATH if fast_math else LIB_PATH))
+        self.fast_math = fast_math
         opt = Options()
         opt.device, opt.n_batches, opt.physics_flags = device, n_batches, physics_flags
         opt.block_size, opt.chunk = block_size, chunk
@@ -303,13 +304,13 @@ class Engine:
         return out
 
 
-def debug_philox(ctr, key):
+def debug_philox(ctr, key, fast_math=False):
     """Philox4x32-10 on the device: ctr [n, 4] uint32, key (2,) -> [n, 4] uint32."""
     ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
     key = np.ascontiguousarray(key, dtype=np.uint32)
     out = np.empty_like(ctr)
     P = C.POINTER(C.c_uint32)
-    rc = lib().pmc_debug_philox(ctr.ctypes.data_as(P), key.ctypes.data_as(P), out.ctypes.data_as(P), len(ctr))
+    rc = lib(LIB_FAST_PATH if fast_math else LIB_PATH).pmc_debug_philox(ctr.ctypes.data_as(P), key.ctypes.data_as(P), out.ctypes.data_as(P), len(ctr))
     if rc != PMC_OK:
         raise PmcError(rc, "pmc_debug_philox failed")
     return out

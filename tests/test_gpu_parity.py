@@ -15,10 +15,26 @@ pytestmark = pytest.mark.gpu
 FIX = 2.0 ** -24
 
 
-def run_gpu(prob, n, seed, ledger=0, escapes=0, block=0, chunk=0):
+_ORACLE = {}
+
+
+@pytest.fixture(params=[False, True], ids=["ieee", "fastmath"])
+def fast(request):
+    """Both builds of the engine: IEEE single precision and -use_fast_math."""
+    return request.param
+
+
+def oracle_parallel(prob, n, seed):
+    key = (prob.name, prob.shape, len(prob.spots), prob.flags, n, seed)
+    if key not in _ORACLE:
+        _ORACLE[key] = O.run_parallel(prob, n, seed)
+    return _ORACLE[key]
+
+
+def run_gpu(prob, n, seed, ledger=0, escapes=0, block=0, chunk=0, fast=False):
     from paper_1409_8336_gb300 import Engine
 
-    e = Engine(device=0, n_batches=prob.n_batches, physics_flags=prob.flags)
+    e = Engine(device=0, n_batches=prob.n_batches, physics_flags=prob.flags, fast_math=fast)
     e.load_problem(prob)
     if block or chunk:
         e.set_launch(block, chunk)
@@ -37,9 +53,13 @@ def run_gpu(prob, n, seed, ledger=0, escapes=0, block=0, chunk=0):
     return out
 
 
-def compare(prob, n, seed, min_z=0.99, gamma_min=0.99, r80_tol=0.01):
-    g = run_gpu(prob, n, seed)
-    ref, tot, _ = O.run(prob, n, seed)
+def compare(prob, n, seed, fast, min_z=0.99, gamma_min=0.99, r80_tol=0.01):
+    """n is chosen so that the statistical noise of both runs stays well below the 2 % gamma
+    dose criterion in the voxels above 10 % of the maximum: two independent oracle runs of
+    1e5-2e5 histories pass only 94-99 % at 2 %/2 mm, i.e. at that size the gamma test measures
+    the noise.  The oracle side runs over all host cores (history ranges, spawned workers)."""
+    g = run_gpu(prob, n, seed, fast=fast)
+    ref, tot = oracle_parallel(prob, n, seed)
     Dg, sg = A.batch_stats(g["tally"].astype(np.float64) * FIX)
     Do, so = A.batch_stats(ref)
     z = A.zscores(Dg, sg, Do, so)
@@ -62,46 +82,53 @@ def compare(prob, n, seed, min_z=0.99, gamma_min=0.99, r80_tol=0.01):
     return g, info
 
 
-def test_csda_only_matches_oracle_voxel_by_voxel():
+def test_csda_only_matches_oracle_voxel_by_voxel(fast):
     flags = W.NO_STRAGGLING | W.NO_MCS | W.NO_ELASTIC | W.NO_INELASTIC
     p = W.water_box((200, 3, 3), 0.1, np.array([W.spot_row(150.0, sigma=0.0)]), n_batches=2, flags=flags)
-    g = run_gpu(p, 64, 1)
+    g = run_gpu(p, 64, 1, fast=fast)
     ref, _, _ = O.run(p, 64, 1)
-    dg = g["tally"].sum(1).reshape(p.shape).sum((1, 2)) * FIX
-    do = ref.sum(1).reshape(p.shape).sum((1, 2))
-    assert np.allclose(dg, do, rtol=2e-4, atol=2e-3), np.max(np.abs(dg - do))
-    assert dg.sum() == pytest.approx(64 * 150.0, rel=1e-7)
+    dg = g["tally"].sum(1).reshape(p.shape).sum((1, 2)) * FIX / 64
+    do = ref.sum(1).reshape(p.shape).sum((1, 2)) / 64
+    stop = int(np.nonzero(do)[0][-1])
+    assert int(np.nonzero(dg)[0][-1]) == stop                      # stops in the same voxel
+    # plateau voxels agree to single-precision rounding (no drift of the range) ...
+    tol = 5e-4 if fast else 2e-4
+    assert np.allclose(dg[: stop - 2], do[: stop - 2], rtol=tol), np.max(np.abs(dg / np.maximum(do, 1e-30) - 1)[: stop - 2])
+    # ... and the energy deposited up to any depth differs by < 0.03 MeV, a few micrometres of
+    # range at the stopping powers near the end of range
+    assert np.max(np.abs(np.cumsum(dg - do))) < 0.03
+    assert dg.sum() == pytest.approx(150.0, rel=1e-7)
 
 
-def test_water_pencil_beam_150mev():
+def test_water_pencil_beam_150mev(fast):
     """64x64x128 water of 2 mm, 150 MeV, sigma 3 mm, full physics."""
-    compare(W.config1(), 20000, 1)
+    compare(W.config1(), 1_000_000, 1, fast)
 
 
-def test_heterogeneous_slab_three_energies():
+def test_heterogeneous_slab_three_energies(fast):
     """128^3 slab phantom of 1.5 mm (water/bone/lung/water + Ti), 70/150/230 MeV."""
-    compare(W.config2(), 12000, 2, gamma_min=0.99)
+    compare(W.config2(), 1_000_000, 2, fast)
 
 
-def test_ct_plan_hu_path():
+def test_ct_plan_hu_path(fast):
     """HU volume with the 6-bin table, a 4-layer plan of 200 spots."""
     p = W.config3(shape=(60, 64, 64), n_layers=4)
-    compare(p, 12000, 3, gamma_min=0.99)
+    compare(p, 1_000_000, 3, fast)
 
 
-def test_tally_is_bit_reproducible():
+def test_tally_is_bit_reproducible(fast):
     p = W.config2()
-    a = run_gpu(p, 30000, 5)["tally"]
-    b = run_gpu(p, 30000, 5, block=128, chunk=7001)["tally"]
+    a = run_gpu(p, 30000, 5, fast=fast)["tally"]
+    b = run_gpu(p, 30000, 5, block=128, chunk=7001, fast=fast)["tally"]
     assert np.array_equal(a, b)
-    c = run_gpu(p, 30000, 6)["tally"]
+    c = run_gpu(p, 30000, 6, fast=fast)["tally"]
     assert not np.array_equal(a, c)
 
 
-def test_history_ledger_conserves_energy():
+def test_history_ledger_conserves_energy(fast):
     p = W.config2()
     n = 4000
-    g = run_gpu(p, n, 9, ledger=n)
+    g = run_gpu(p, n, 9, ledger=n, fast=fast)
     h = g["hist"].astype(np.float64) * FIX
     res = h[:, 0] - h[:, 1] - h[:, 2] - h[:, 3]
     assert np.all(np.abs(res) <= 1e-6 * h[:, 0]), np.max(np.abs(res) / h[:, 0])
@@ -110,12 +137,12 @@ def test_history_ledger_conserves_energy():
     assert np.allclose(h[:, 0], ho[:, 0], rtol=1e-6)
 
 
-def test_full_size_slab_run_sampled_against_oracle():
-    """Config 2 at its full 1e6 histories, in the bench's launch configuration: the first
-    2000 histories' ledgers against the oracle's, and conservation over the whole run."""
+def test_full_size_slab_run_sampled_against_oracle(fast):
+    """The slab workload at its full 1e6 histories, in the bench's launch configuration: the
+    first 2000 histories' ledgers against the oracle's, and conservation over the whole run."""
     p = W.config2()
     n = 1_000_000
-    g = run_gpu(p, n, 1, ledger=2000)
+    g = run_gpu(p, n, 1, ledger=2000, fast=fast)
     L = g["ledger"]
     assert L["dropped"] == 0 and L["errors"] == 0
     assert abs(L["incident"] - L["deposited"] - L["escaped"] - L["binding"]) < 1e-6 * L["incident"]
@@ -129,12 +156,12 @@ def test_full_size_slab_run_sampled_against_oracle():
     assert abs(h[:, 1].mean() - ho[:, 1].mean()) < 4 * ho[:, 1].std() / np.sqrt(2000)
 
 
-def test_escape_record_angular_spread_matches_highland():
+def test_escape_record_angular_spread_matches_highland(fast):
     p = W.water_box((1, 1, 1), 1000.0, np.array([W.spot_row(100.0, sigma=0.0)]), n_batches=2,
                     flags=W.NO_STRAGGLING | W.NO_ELASTIC | W.NO_INELASTIC)
     p = p.with_(voxel=(1000.0, 1000.0, 1.0), origin=(-500.0, -500.0, 0.0))
     n = 40000
-    g = run_gpu(p, n, 3, escapes=n)
+    g = run_gpu(p, n, 3, escapes=n, fast=fast)
     esc = g["esc"]
     assert len(esc) == n
     th0 = O.f("or_highland_theta0")(100.0, 1.0, 36.08294323509874)

@@ -12,28 +12,29 @@ from paper_1409_8336_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def eng():
+@pytest.fixture(scope="module", params=[False, True], ids=["ieee", "fastmath"])
+def eng(request):
     from paper_1409_8336_gb300 import Engine, build
 
     build.build()
-    e = Engine(device=0, n_batches=10)
+    e = Engine(device=0, n_batches=10, fast_math=request.param)
     p = W.config3(shape=(16, 32, 32), n_layers=2)
     e.load_problem(p)
     yield e, p
     e.close()
 
 
-def test_philox_device_matches_known_answers_and_oracle():
+@pytest.mark.parametrize("fast", [False, True], ids=["ieee", "fastmath"])
+def test_philox_device_matches_known_answers_and_oracle(fast):
     from paper_1409_8336_gb300 import debug_philox
 
     for row in golden("philox4x32_10_kat.txt"):
         v = [int(x, 16) for x in row]
-        assert list(debug_philox(np.array([v[0:4]]), np.array(v[4:6]))[0]) == v[6:10]
+        assert list(debug_philox(np.array([v[0:4]]), np.array(v[4:6]), fast)[0]) == v[6:10]
     rng = np.random.default_rng(0)
     ctr = rng.integers(0, 2 ** 32, size=(512, 4), dtype=np.uint64).astype(np.uint32)
     key = np.array([0x12345678, 0x9abcdef0], dtype=np.uint32)
-    dev = debug_philox(ctr, key)
+    dev = debug_philox(ctr, key, fast)
     for c, d in zip(ctr[:64], dev[:64]):
         assert O.philox([int(x) for x in c], [int(x) for x in key]) == [int(x) for x in d]
 
@@ -47,8 +48,9 @@ def test_range_tables_match_oracle(eng):
         # the scaled materials share the reference water table (Eq. 1 / Eq. 2)
         base = 0 if not p.materials[m].get("own_table") else m
         ref = np.array([O.range_csda(p, base, x) for x in E])
-        assert np.allclose(r, ref, rtol=2e-5, atol=1e-9), (m, np.max(np.abs(r / ref - 1)))
-        assert np.allclose(eb, E, rtol=3e-5), (m, np.max(np.abs(eb / E - 1)))
+        tol = 1e-4 if e.fast_math else 2e-5
+        assert np.allclose(r, ref, rtol=tol, atol=1e-9), (m, np.max(np.abs(r / ref - 1)))
+        assert np.allclose(eb, E, rtol=1.5 * tol), (m, np.max(np.abs(eb / E - 1)))
         assert info["f"] > 0
 
 
@@ -59,9 +61,10 @@ def test_elastic_kinematics_match_oracle(eng, nuc, E):
     u = np.random.default_rng(nuc).uniform(size=(2000, 3)).astype(np.float32).astype(np.float64)
     dev = e.debug_elastic(nuc, E, u)
     ref = np.array([O.elastic(Z, A, E, row) for row in u[:300]])
-    assert np.allclose(dev[:300, 0], ref[:, 0], rtol=1e-4, atol=2e-4 * E)
-    assert np.allclose(dev[:300, 1], ref[:, 1], atol=2e-4)
-    assert np.allclose(dev[:300, 4], ref[:, 4], atol=2e-4)
+    tol = 1e-3 if e.fast_math else 2e-4
+    assert np.allclose(dev[:300, 0], ref[:, 0], rtol=tol / 2, atol=tol * E)
+    assert np.allclose(dev[:300, 1], ref[:, 1], atol=tol)
+    assert np.allclose(dev[:300, 4], ref[:, 4], atol=tol)
     assert np.allclose(dev[:, 0] + dev[:, 2], E, rtol=1e-6)
 
 

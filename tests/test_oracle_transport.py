@@ -141,3 +141,11 @@ def test_results_depend_only_on_seed():
     d1, _, _ = O.run(p, 300, 11, h_begin=0, h_end=150)
     d2, _, _ = O.run(p, 300, 11, h_begin=150, h_end=300)
     assert np.allclose(d1 + d2, a, rtol=1e-12, atol=1e-12)
+
+
+def test_parallel_runner_equals_serial():
+    p = W.config1()
+    a, ta = O.run_parallel(p, 3000, 13, procs=3)
+    b, tb, _ = O.run(p, 3000, 13)
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-9)
+    assert ta["inelastic"] == tb["inelastic"] and ta["steps"] == tb["steps"]
