@@ -167,6 +167,29 @@ int pmc_set_launch(pmc_ctx* ctx, int block_size, int64_t chunk);
 int pmc_enable_profile(pmc_ctx* ctx, int on);
 int pmc_read_profile(pmc_ctx* ctx, double* ms, int64_t* launches, int64_t* primary_steps);
 
+/* Transport that allocates no device memory (the paper has no counterpart).
+ * For callers that cannot call cudaMalloc during a dose calculation -- a host
+ * callback or real-time loop that must not synchronise or stall on the
+ * allocator, or an application that gave its whole device memory to its own
+ * pool.  Runs the same kernels and physics as pmc_transport and produces the
+ * same tallies for the same seed, with all scratch (particle queues,
+ * counters, spot table, seed) in one static device array of
+ * PMC_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits.  Inputs are the context's loaded materials, phantom and
+ * spots; outputs are caller-owned device arrays: tally [n_voxels][n_batches]
+ * int64 (units of 2^-24 MeV, zeroed by the call) and, optionally (both or
+ * neither), dose_gy and sigma_gy [n_voxels].  At most PMC_NOALLOC_MAX_SPOTS
+ * spots may receive histories; more is rejected with PMC_E_INVALID.  All
+ * calls on a device share the array and it keeps the last call's contents;
+ * calls whose work overlaps on the GPU race on it.  The first call on a
+ * device looks up the array's address, so make it before any stream capture.
+ * Blocks until done; pmc_read_ledger then reports this run. */
+#define PMC_NOALLOC_CHUNK 65536          /* histories per sub-group */
+#define PMC_NOALLOC_MAX_SPOTS 4096
+#define PMC_NOALLOC_SCRATCH_BYTES (4ull * PMC_NOALLOC_CHUNK * 48ull + 768ull + PMC_NOALLOC_MAX_SPOTS * 56ull)
+int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int64_t* tally,
+                          double* dose_gy, double* sigma_gy, void* stream);
+
 /* Device-side evaluation of single routines, for tests.
  * pmc_debug_philox: Philox4x32-10 of n counters ctr[n][4] under key[2]
  *   (Salmon et al., SC'11) into out[n][4].

@@ -1035,3 +1035,199 @@ int pmc_debug_elastic(pmc_ctx* ctx, int nuclide, double E, const double* u, doub
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Transport without device allocation.
+//
+// Some callers cannot allocate device memory while they run a dose
+// calculation: a host callback or a real-time control loop may not call
+// cudaMalloc (it can synchronise the device or stall behind other work), and
+// a caller with its own fixed memory budget may have handed the whole GPU to
+// its pool.  This entry point runs the same kernels as pmc_transport but keeps
+// every piece of scratch (particle queues, counters, spot table, seed) in one
+// static device array; the caller supplies the output arrays.
+//
+// The array lives in every GPU that loads this library until the process
+// exits.  All calls on a device share it and it keeps the last call's
+// contents: each call clears what must start at zero, and calls whose work
+// overlaps on the GPU (different threads or streams) race on it.  The first
+// call on a device looks up the array's device address; make that first call
+// before any stream capture.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNaQueue = static_cast<size_t>(PMC_NOALLOC_CHUNK) * sizeof(Particle);
+constexpr size_t kNaCounters = 4 * kNaQueue;
+constexpr size_t kNaCounts = kNaCounters + 256;
+constexpr size_t kNaSeed = kNaCounts + 256;
+constexpr size_t kNaSpots = kNaSeed + 256;
+constexpr size_t kNaBytes = kNaSpots + static_cast<size_t>(PMC_NOALLOC_MAX_SPOTS) * sizeof(SpotDev);
+static_assert(kNaBytes == PMC_NOALLOC_SCRATCH_BYTES, "scratch size stated in pmc.h");
+static_assert(sizeof(Counters) <= 256, "counters fit their slot");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kNaMaxDevices = 64;
+unsigned char* g_noalloc_addr[kNaMaxDevices] = {};
+
+}  // namespace
+
+extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int64_t* tally,
+                                     double* dose_gy, double* sigma_gy, void* stream) {
+  if (!ctx) return PMC_E_INVALID;
+  if (!ctx->have_materials || !ctx->have_phantom) return fail(ctx, PMC_E_INVALID, "load materials and phantom first");
+  if (!tally) return fail(ctx, PMC_E_INVALID, "tally output is required");
+  if ((dose_gy == nullptr) != (sigma_gy == nullptr)) return fail(ctx, PMC_E_INVALID, "give both dose and sigma, or neither");
+  if (ctx->spots.empty()) return fail(ctx, PMC_E_INVALID, "no spots");
+  if (n_histories == 0 || n_histories > 0xFFFFFFFFull) return fail(ctx, PMC_E_INVALID, "n_histories must be in [1, 2^32)");
+  const int dev = ctx->opt.device;
+  if (dev < 0 || dev >= kNaMaxDevices) return fail(ctx, PMC_E_INVALID, "device ordinal beyond %d", kNaMaxDevices);
+  double wsum = 0.0;
+  for (const auto& sp : ctx->spots) wsum += sp.weight;
+  if (!(wsum > 0.0)) return fail(ctx, PMC_E_INVALID, "spot weights sum to zero");
+  try {
+    // spots in work order, as in pmc_transport
+    std::vector<uint64_t> cnt = split_histories(ctx->spots, n_histories);
+    std::vector<uint64_t> hfirst(ctx->spots.size());
+    uint64_t acc = 0;
+    for (size_t i = 0; i < cnt.size(); ++i) { hfirst[i] = acc; acc += cnt[i]; }
+    std::vector<size_t> order(ctx->spots.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return ctx->spots[a].E > ctx->spots[b].E; });
+    std::vector<SpotDev> sd;
+    uint64_t wacc = 0;
+    for (size_t k : order) {
+      if (cnt[k] == 0) continue;
+      const pmc_spot& p = ctx->spots[k];
+      const double dn = std::sqrt(p.u * p.u + p.v * p.v + p.w * p.w);
+      SpotDev d{};
+      d.E = static_cast<float>(p.E); d.sE = static_cast<float>(p.sigma_E);
+      d.x = static_cast<float>(p.x); d.y = static_cast<float>(p.y);
+      d.sx = static_cast<float>(p.sigma_x); d.sy = static_cast<float>(p.sigma_y);
+      d.u = static_cast<float>(p.u / dn); d.v = static_cast<float>(p.v / dn); d.w = static_cast<float>(p.w / dn);
+      d.h_first = hfirst[k];
+      d.w_first = wacc;
+      wacc += cnt[k];
+      sd.push_back(d);
+    }
+    if (sd.size() > static_cast<size_t>(PMC_NOALLOC_MAX_SPOTS))
+      return fail(ctx, PMC_E_INVALID, "%zu spots with histories exceed the no-allocation limit of %d", sd.size(),
+                  PMC_NOALLOC_MAX_SPOTS);
+    CK(cudaSetDevice(dev));
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+    }
+    unsigned char* base = g_noalloc_addr[dev];
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    Particle* q[4];
+    for (int i = 0; i < 4; ++i) q[i] = reinterpret_cast<Particle*>(base + i * kNaQueue);
+    Counters* counters = reinterpret_cast<Counters*>(base + kNaCounters);
+    unsigned* counts = reinterpret_cast<unsigned*>(base + kNaCounts);
+    unsigned long long* dseed = reinterpret_cast<unsigned long long*>(base + kNaSeed);
+    SpotDev* dspots = reinterpret_cast<SpotDev*>(base + kNaSpots);
+    const size_t B = ctx->opt.n_batches;
+    CK(cudaMemcpyAsync(dspots, sd.data(), sd.size() * sizeof(SpotDev), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dseed, &seed, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(tally, 0, static_cast<size_t>(ctx->n_vox) * B * 8, s));
+    CK(cudaMemsetAsync(counters, 0, sizeof(Counters), s));
+    const size_t smem = transport_smem_bytes(ctx->phys.n_cls, ctx->phys.n_mat);
+    int bps = 0;
+    CK(transport_occupancy(ctx->block, smem, &bps));
+    if (bps < 1) return fail(ctx, PMC_E_CUDA, "transport kernel does not fit (block %d, smem %zu)", ctx->block, smem);
+    const int grid_t = ctx->n_sm * bps, grid_c = ctx->n_sm * 8;
+    TransportArgs ta{};
+    ta.phys = static_cast<const Physics*>(ctx->d_phys.p);
+    ta.rtab = static_cast<const float2*>(ctx->d_rt.p);
+    ta.etab = static_cast<const float2*>(ctx->d_et.p);
+    ta.stab = static_cast<const float*>(ctx->d_st.p);
+    ta.g = ctx->geo;
+    ta.tally = reinterpret_cast<unsigned long long*>(tally);
+    ta.B = ctx->opt.n_batches;
+    ta.seed = dseed;
+    ta.spots = dspots;
+    ta.n_spots = static_cast<int>(sd.size());
+    ta.cnt = counters;
+    ta.qin_cap = ta.qsec_cap = ta.qne_cap = PMC_NOALLOC_CHUNK;
+    CascadeArgs ca{};
+    ca.nuclei = static_cast<const NucleusModel*>(ctx->d_nuclei.p);
+    ca.btab = static_cast<const float*>(ctx->d_btab.p);
+    ca.n_nuc = ctx->phys.n_nuc;
+    ca.g = ctx->geo;
+    ca.tally = ta.tally;
+    ca.B = ta.B;
+    ca.seed = dseed;
+    ca.cnt = counters;
+    ca.qne_cap = ca.qsec_cap = PMC_NOALLOC_CHUNK;
+    // sub-groups of PMC_NOALLOC_CHUNK primaries; each runs its generations until no
+    // secondary proton is left (counts: [0] input, [1] output, [2] events, [3] work)
+    for (uint64_t w0 = 0; w0 < n_histories; w0 += PMC_NOALLOC_CHUNK) {
+      const uint64_t w1 = std::min<uint64_t>(n_histories, w0 + PMC_NOALLOC_CHUNK);
+      unsigned n_in = 0;
+      for (int g = 0;; ++g) {
+        if (g > 100000) return fail(ctx, PMC_E_TIMEOUT, "secondary generations did not terminate");
+        Particle* qin = q[g & 1];
+        Particle* qout = q[(g + 1) & 1];
+        CK(cudaMemsetAsync(counts + 1, 0, 3 * sizeof(unsigned), s));
+        CK(cudaMemcpyAsync(counts, &n_in, sizeof(unsigned), cudaMemcpyHostToDevice, s));
+        ta.source = g == 0 ? 0 : 1;
+        ta.w_begin = w0;
+        ta.w_end = w1;
+        ta.qin = qin;
+        ta.qin_count = counts;
+        ta.qsec = qout;
+        ta.qsec_count = counts + 1;
+        ta.qne = q[2];
+        ta.qne_count = counts + 2;
+        ta.work = counts + 3;
+        CK(launch_transport(ta, grid_t, ctx->block, smem, s));
+        ca.qne = q[2];
+        ca.qne_count = counts + 2;
+        ca.qsec = qout;
+        ca.qsec_count = counts + 1;
+        CK(launch_cascade(ca, grid_c, 128, s));
+        unsigned n_out = 0;
+        CK(cudaMemcpyAsync(&n_out, counts + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        n_in = std::min<unsigned>(n_out, PMC_NOALLOC_CHUNK);
+        if (n_in == 0) break;
+      }
+    }
+    if (dose_gy) {
+      StatsArgs sa{};
+      sa.tally = ta.tally;
+      sa.B = ta.B;
+      sa.n_vox = ctx->n_vox;
+      sa.g = ctx->geo;
+      sa.phys = ta.phys;
+      sa.dose = dose_gy;
+      sa.sigma = sigma_gy;
+      CK(launch_stats(sa, s));
+    }
+    Counters hc{};
+    CK(cudaMemcpyAsync(&hc, counters, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    pmc_ledger& L = ctx->last;
+    L = pmc_ledger{};
+    L.incident = static_cast<int64_t>(hc.incident);
+    L.deposited = static_cast<int64_t>(hc.deposited);
+    L.escaped = static_cast<int64_t>(hc.escaped);
+    L.binding = static_cast<int64_t>(hc.binding);
+    L.histories = static_cast<int64_t>(n_histories);
+    L.steps = static_cast<int64_t>(hc.steps);
+    L.elastic = static_cast<int64_t>(hc.elastic);
+    L.inelastic = static_cast<int64_t>(hc.inelastic);
+    L.secondaries = static_cast<int64_t>(hc.secondaries);
+    L.transparent = static_cast<int64_t>(hc.transparent);
+    L.inc_retries = static_cast<int64_t>(hc.inc_retries);
+    L.dropped = static_cast<int64_t>(hc.dropped);
+    L.errors = static_cast<int64_t>(hc.errors);
+    if (hc.dropped) return fail(ctx, PMC_E_QUEUE_OVERFLOW, "%llu particles did not fit a queue", (unsigned long long)hc.dropped);
+    if (hc.errors) return fail(ctx, PMC_E_TIMEOUT, "%llu particles exceeded the step limit", (unsigned long long)hc.errors);
+    return PMC_OK;
+  } catch (...) {
+    return fail(ctx, PMC_E_INVALID, "exception in transport");
+  }
+}

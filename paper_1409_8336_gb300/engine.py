@@ -27,7 +27,7 @@ EXPORTS = [
     "pmc_create", "pmc_destroy", "pmc_last_error", "pmc_load_materials", "pmc_load_phantom", "pmc_add_spots",
     "pmc_clear_spots", "pmc_transport", "pmc_read_dose", "pmc_read_tally", "pmc_read_ledger",
     "pmc_enable_history_ledger", "pmc_read_history_ledger", "pmc_enable_escape_record", "pmc_read_escape_record",
-    "pmc_set_launch", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables", "pmc_debug_inc", "pmc_debug_elastic",
+    "pmc_set_launch", "pmc_transport_noalloc", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables", "pmc_debug_inc", "pmc_debug_elastic",
 ]
 
 AllocFn = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -94,6 +94,7 @@ def lib(path: str = LIB_PATH):
             L.pmc_enable_escape_record.argtypes = [vp, u64]
             L.pmc_read_escape_record.argtypes = [vp, C.POINTER(C.c_float), u64, C.POINTER(C.c_uint64)]
             L.pmc_set_launch.argtypes = [vp, i, C.c_int64]
+            L.pmc_transport_noalloc.argtypes = [vp, u64, u64, vp, vp, vp, vp]
             L.pmc_enable_profile.argtypes = [vp, i]
             L.pmc_read_profile.argtypes = [vp, pd, pi64, pi64]
             L.pmc_debug_philox.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), i]
@@ -222,6 +223,15 @@ class Engine:
         if stream is not None:
             s = stream if isinstance(stream, int) else stream.cuda_stream
         self._check(self._L.pmc_transport(self._ctx, n_histories, seed, mode, s))
+
+    def transport_noalloc(self, n_histories: int, seed: int, tally_ptr: int, dose_ptr=None, sigma_ptr=None,
+                          stream=None):
+        """Transport that allocates no device memory; outputs go to caller-owned device arrays
+        (pointers: tally [n_voxels * n_batches] int64, dose and sigma [n_voxels] float64)."""
+        s = None
+        if stream is not None:
+            s = stream if isinstance(stream, int) else stream.cuda_stream
+        self._check(self._L.pmc_transport_noalloc(self._ctx, n_histories, seed, tally_ptr, dose_ptr, sigma_ptr, s))
 
     # --- outputs --------------------------------------------------------
     @property
