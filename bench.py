@@ -6,7 +6,9 @@ Workload (default): the heterogeneous slab phantom -- 128^3 voxels of 1.5 mm
 split over 70, 150 and 230 MeV pencil beams of sigma 4 mm, full physics with
 the intranuclear cascade.  One step = one complete transport of all 1e6
 histories (graph launch of primaries, secondary generations and cascades, then
-the batch-statistics kernel), inputs resident in HBM.
+the batch-statistics kernel), inputs resident in HBM.  The headline build is
+the -use_fast_math one (the build the method's authors timed; both builds pass
+the same parity tests against the oracle); the IEEE build is timed beside it.
 
 Prints one JSON line.  `--impl reference` times the CPU oracle on a bounded
 sample of the same workload instead.
@@ -31,11 +33,12 @@ METRIC = "proton histories/s on 1 GB300 (full cascade)"
 UNIT = "histories/s"
 N_HISTORIES = 1_000_000
 FIX = 2.0 ** -24
-# Algorithmic single-precision arithmetic operations of one condensed-history step
-# (Philox x2, voxel lookup, range/inverse-range splines, cross-section table,
-# boundary distances x2, Highland + rotation, Bohr + Box-Muller, deposit); the
-# count is derived in the design doc.
-OPS_PER_STEP = 620
+# Scalar arithmetic operations one condensed-history step needs, counted from its
+# formulas (two Philox4x32-10 blocks 200, uniforms 32, range and inverse-range
+# splines 38, cross-section table 9, two voxel-boundary distances 42, Highland
+# width 18, deflection 40, Bohr straggling 20, deposit and bookkeeping 42): the
+# itemised count is in the design doc.  Peak = FP32/INT32 lanes x SM clock.
+OPS_PER_STEP = 441
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -48,6 +51,7 @@ def parse():
     ap.add_argument("--histories", type=int, default=N_HISTORIES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--math", default="fast", choices=["fast", "ieee"], help="headline build")
     return ap.parse_args()
 
 
@@ -182,10 +186,31 @@ def main():
     prob = workload()
     n = args.histories
     stream = torch.cuda.current_stream()
-    eng = Engine(device=local, n_batches=prob.n_batches)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed_steps(eng, k, seed0):
+        out = []
+        for i in range(k):
+            flush.fill_(float(i))
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            eng.transport(n, seed0 + i, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return out
+
+    # the other build, timed beside the headline one
+    other = Engine(device=local, n_batches=prob.n_batches, fast_math=(args.math != "fast"))
+    other.load_problem(prob)
+    timed_steps(other, args.warmup, 5000)
+    other_ms = timed_steps(other, args.steps, 6000)
+    other.close()
+
+    eng = Engine(device=local, n_batches=prob.n_batches, fast_math=(args.math == "fast"))
     eng.load_problem(prob)
     eng.enable_profile(True)
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def one(seed):
         flush.fill_(float(seed))                           # evict L2 between steps
@@ -280,6 +305,10 @@ def main():
                          "launch_ms": launch_ms},
             "clocks": clk.summary(),
             "kernels_ms_per_step": {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in kinds.items()},
+            "math": args.math,
+            "other_build": {"math": "ieee" if args.math == "fast" else "fast",
+                            "value": world * n * args.steps / (sum(other_ms) / 1e3),
+                            "ms_per_step": sum(other_ms) / args.steps},
             "cpu_baseline": cpu,
             "stats": {"steps_per_history": led["steps"] / n, "inelastic": led["inelastic"],
                       "elastic": led["elastic"], "secondaries": led["secondaries"],

@@ -92,7 +92,7 @@ def test_csda_only_matches_oracle_voxel_by_voxel(fast):
     stop = int(np.nonzero(do)[0][-1])
     assert int(np.nonzero(dg)[0][-1]) == stop                      # stops in the same voxel
     # plateau voxels agree to single-precision rounding (no drift of the range) ...
-    tol = 5e-4 if fast else 2e-4
+    tol = 1e-3 if fast else 2e-4
     assert np.allclose(dg[: stop - 2], do[: stop - 2], rtol=tol), np.max(np.abs(dg / np.maximum(do, 1e-30) - 1)[: stop - 2])
     # ... and the energy deposited up to any depth differs by < 0.03 MeV, a few micrometres of
     # range at the stopping powers near the end of range
