@@ -124,6 +124,20 @@ static void draw4(uint64_t seed, uint64_t pid, uint32_t word2, uint32_t tag, dou
     for (int i = 0; i < 4; ++i) u[i] = u01(r[i]);
 }
 
+/* The five uniforms of step k of particle pid: one Philox block (tag 0); four
+ * from the top 23 bits of its words, the fifth from their unused low bits
+ * (9 + 9 + 5 bits of words 0, 1, 2). */
+static void step_uniforms(uint64_t seed, uint64_t pid, uint32_t k, double u[5])
+{
+    uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), k, 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    or_philox4x32_10(ctr, key, r);
+    for (int i = 0; i < 4; ++i) u[i] = u01(r[i]);
+    uint32_t low = ((r[0] & 0x1FFu) << 14) | ((r[1] & 0x1FFu) << 5) | (r[2] & 0x1Fu);
+    u[4] = ((double)low + 0.5) * (1.0 / 8388608.0);
+}
+
 /* Identity of the child with index `idx` of particle `pid`. */
 static uint64_t child_pid(uint64_t seed, uint64_t pid, uint32_t idx)
 {
@@ -476,7 +490,7 @@ typedef struct {
     double Ex_inc;             /* excitation after the cascade */
 } or_event;
 
-typedef struct { int q; double r[3], d[3], T; int shell; int done; } inc_particle;
+typedef struct { int q; double r[3], d[3], T; int shell; int done; int refl; } inc_particle;
 
 static const int EJ_Z[6] = {0, 1, 1, 1, 2, 2};
 static const int EJ_A[6] = {1, 1, 2, 3, 3, 4};
@@ -671,7 +685,7 @@ void or_inc_event(const or_nucleus* nu, double E, uint64_t seed, uint64_t pid, o
         double margin = 1e300;
         /* entry point on the outer sphere, uniform over the projected disc */
         double b = nu->Rout * sqrt(next_u(&st)), ph = TWO_PI * next_u(&st);
-        P[0].q = 1; P[0].T = E; P[0].done = 0;
+        P[0].q = 1; P[0].T = E; P[0].done = 0; P[0].refl = 0;
         P[0].r[0] = b * cos(ph); P[0].r[1] = b * sin(ph);
         P[0].r[2] = -sqrt(fmax(0.0, nu->Rout * nu->Rout - b * b));
         P[0].d[0] = 0; P[0].d[1] = 0; P[0].d[2] = 1;
@@ -723,8 +737,9 @@ void or_inc_event(const or_nucleus* nu, double E, uint64_t seed, uint64_t pid, o
                     double n1 = sqrt(dot3(p1o, p1o)), n2 = sqrt(dot3(p2o, p2o));
                     for (int k = 0; k < 3; ++k) { p->d[k] = p1o[k] / n1; }
                     p->T = T1o;
+                    p->refl = 0;
                     inc_particle* c = &P[n++];
-                    c->q = q2; c->T = T2o; c->shell = i; c->done = 0;
+                    c->q = q2; c->T = T2o; c->shell = i; c->done = 0; c->refl = 0;
                     for (int k = 0; k < 3; ++k) { c->r[k] = p->r[k]; c->d[k] = p2o[k] / n2; }
                     sea[q2]--;
                     any = 1; ncoll++;
@@ -737,12 +752,19 @@ void or_inc_event(const or_nucleus* nu, double E, uint64_t seed, uint64_t pid, o
                     if (inner) {
                         for (int k = 0; k < 3; ++k) nh[k] = -p->r[k] / rr;
                         if (cross_boundary(p, nh, nu->V[q][i], nu->V[q][i - 1], m)) p->shell = i - 1;
+                        else if (++p->refl >= 2) { p->done = 2; break; }
                     } else {
                         for (int k = 0; k < 3; ++k) nh[k] = p->r[k] / rr;
                         double Vb = (i + 1 < INC_SHELLS) ? nu->V[q][i + 1] : 0.0;
                         if (cross_boundary(p, nh, nu->V[q][i], Vb, m)) {
                             if (i + 1 == INC_SHELLS) { p->done = 1; break; }   /* escaped */
                             p->shell = i + 1;
+                        } else if (++p->refl >= 2) {
+                            /* between collisions energy and angular momentum are conserved, so
+                             * a nucleon turned back once can never reach the surface; on its
+                             * second turn without an allowed collision it is trapped */
+                            p->done = 2;
+                            break;
                         }
                     }
                 }
@@ -954,10 +976,9 @@ static void transport_one(or_ctx* c, or_particle* p, or_pstack* st)
         if (Rcm <= lam && Rcm <= d) { deposit(c, p->iv, p->root, E0); return; }
         int nuclear = (lam <= d);
         double dx = nuclear ? lam : d;
-        double ua[4], ub[4];
-        draw4(c->seed, p->pid, k, 0u, ua);
-        draw4(c->seed, p->pid, k, 1u, ub);
-        double tau = ub[0];
+        double ua[5];
+        step_uniforms(c->seed, p->pid, k, ua);
+        double tau = ua[4];
         double x1[3];
         for (int a = 0; a < 3; ++a) x1[a] = p->x[a] + tau * dx * p->d[a];
         if (!(P->flags & OR_NO_MCS)) {
@@ -1001,7 +1022,9 @@ static void transport_one(or_ctx* c, or_particle* p, or_pstack* st)
         } else if (nuclear && p->E > E_CUT) {
             /* channel and target from the step-start cross-sections */
             const or_material* M = &P->mat[m];
-            int inel = (ub[1] * sig < sig_in);
+            double ub[4];
+            draw4(c->seed, p->pid, k - 1, 1u, ub);
+            int inel = (ub[0] * sig < sig_in);
             double part[OR_MAX_NUC_PER_MAT], tot = 0.0;
             for (int j = 0; j < M->n; ++j) {
                 const or_nuclide* nu = &P->nuc[M->nuc[j]];
@@ -1011,7 +1034,7 @@ static void transport_one(or_ctx* c, or_particle* p, or_pstack* st)
                 tot += part[j];
             }
             int t = M->n - 1;
-            double acc = 0.0, ut = ub[2] * tot;
+            double acc = 0.0, ut = ub[1] * tot;
             for (int j = 0; j < M->n; ++j) { acc += part[j]; if (ut < acc) { t = j; break; } }
             while (t > 0 && part[t] <= 0.0) --t;
             int nuc = M->nuc[t];
@@ -1038,7 +1061,7 @@ static void transport_one(or_ctx* c, or_particle* p, or_pstack* st)
                 } else deposit(c, p->iv, p->root, T2);
             } else deposit(c, p->iv, p->root, T2);
             p->E = T1;
-            p->nmfp = -log(ub[3]);
+            p->nmfp = -log(ub[2]);
         }
     }
 }

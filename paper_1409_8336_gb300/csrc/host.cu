@@ -675,7 +675,7 @@ CascadeArgs cascade_args(pmc_ctx* ctx) {
 // Enqueues one transport -> cascade generation.
 int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int source, uint64_t w0, uint64_t w1,
                        Particle* qin, unsigned* qin_count, Particle* qout, unsigned* qout_count, Particle* qne,
-                       unsigned* qne_count, unsigned* work) {
+                       unsigned* qne_count, unsigned* work, unsigned* cascade_work) {
   TransportArgs a = transport_args(ctx);
   a.source = source;
   a.w_begin = w0;
@@ -701,6 +701,7 @@ int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int sour
   c.qsec = qout;
   c.qsec_count = qout_count;
   c.qsec_cap = static_cast<unsigned>(ctx->q_cap);
+  c.work = cascade_work;
   if ((rc = mark(ctx, s, 2))) return rc;
   CK(launch_cascade(c, rp.grid_c, 128, s));
   if ((rc = mark(ctx, s, -1))) return rc;
@@ -720,8 +721,9 @@ StatsArgs stats_args(pmc_ctx* ctx) {
 }
 
 // Count slots per sub-group: [0, G]: secondary queue counts; [G+1, 2G]: event
-// queue counts; [2G+1, 3G]: work counters.  A final slot holds the carry count.
-constexpr int kSlots = 3 * kGenerations + 1;
+// queue counts; [2G+1, 3G]: transport work counters; [3G+1, 4G]: cascade work
+// counters.  A final slot holds the carry count.
+constexpr int kSlots = 4 * kGenerations + 1;
 
 int enqueue_run(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s) {
   ctx->n_events_used = 0;
@@ -743,7 +745,8 @@ int enqueue_run(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s) {
       Particle* out = last ? q[3] : q[(g + 1) & 1];
       unsigned* out_count = last ? carry_count : cs + g + 1;
       int rc = enqueue_generation(ctx, rp, s, g == 0 ? 0 : 1, w0, w1, q[g & 1], cs + g, out, out_count, q[2],
-                                  cs + kGenerations + 1 + g, cs + 2 * kGenerations + 1 + g);
+                                  cs + kGenerations + 1 + g, cs + 2 * kGenerations + 1 + g,
+                                  cs + 3 * kGenerations + 1 + g);
       if (rc) return rc;
     }
   }
@@ -805,7 +808,9 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     CK(transport_occupancy(ctx->block, rp.smem, &bps));
     if (bps < 1) return fail(ctx, PMC_E_CUDA, "transport kernel does not fit (block %d, smem %zu)", ctx->block, rp.smem);
     rp.grid_t = ctx->n_sm * bps;
-    rp.grid_c = ctx->n_sm * 8;
+    int cbps = 0;
+    CK(cascade_occupancy(128, ctx->phys.n_nuc, &cbps));
+    rp.grid_c = ctx->n_sm * std::max(cbps, 1);
     // buffers
     int rc;
     const size_t B = ctx->opt.n_batches;
@@ -866,10 +871,10 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
       unsigned n_in = carry;
       while (n_in > 0) {
         if (++extra > 100000) return fail(ctx, PMC_E_TIMEOUT, "secondary generations did not terminate");
-        unsigned zero3[3] = {0, 0, 0};
+        const unsigned zero4[4] = {0, 0, 0, 0};
         CK(cudaMemcpyAsync(cs, &n_in, sizeof(unsigned), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(cs + 1, zero3, 3 * sizeof(unsigned), cudaMemcpyHostToDevice, s));
-        int r2 = enqueue_generation(ctx, rp, s, 1, 0, 0, q[0], cs, q[1], cs + 1, q[2], cs + 2, cs + 3);
+        CK(cudaMemcpyAsync(cs + 1, zero4, 4 * sizeof(unsigned), cudaMemcpyHostToDevice, s));
+        int r2 = enqueue_generation(ctx, rp, s, 1, 0, 0, q[0], cs, q[1], cs + 1, q[2], cs + 2, cs + 3, cs + 4);
         if (r2) return r2;
         CK(cudaMemcpyAsync(&n_in, cs + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1136,7 +1141,9 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     int bps = 0;
     CK(transport_occupancy(ctx->block, smem, &bps));
     if (bps < 1) return fail(ctx, PMC_E_CUDA, "transport kernel does not fit (block %d, smem %zu)", ctx->block, smem);
-    const int grid_t = ctx->n_sm * bps, grid_c = ctx->n_sm * 8;
+    int cbps = 0;
+    CK(cascade_occupancy(128, ctx->phys.n_nuc, &cbps));
+    const int grid_t = ctx->n_sm * bps, grid_c = ctx->n_sm * std::max(cbps, 1);
     TransportArgs ta{};
     ta.phys = static_cast<const Physics*>(ctx->d_phys.p);
     ta.rtab = static_cast<const float2*>(ctx->d_rt.p);
@@ -1161,7 +1168,8 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     ca.cnt = counters;
     ca.qne_cap = ca.qsec_cap = PMC_NOALLOC_CHUNK;
     // sub-groups of PMC_NOALLOC_CHUNK primaries; each runs its generations until no
-    // secondary proton is left (counts: [0] input, [1] output, [2] events, [3] work)
+    // secondary proton is left (counts: [0] input, [1] output, [2] events, [3] transport
+    // work, [4] cascade work)
     for (uint64_t w0 = 0; w0 < n_histories; w0 += PMC_NOALLOC_CHUNK) {
       const uint64_t w1 = std::min<uint64_t>(n_histories, w0 + PMC_NOALLOC_CHUNK);
       unsigned n_in = 0;
@@ -1169,7 +1177,7 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
         if (g > 100000) return fail(ctx, PMC_E_TIMEOUT, "secondary generations did not terminate");
         Particle* qin = q[g & 1];
         Particle* qout = q[(g + 1) & 1];
-        CK(cudaMemsetAsync(counts + 1, 0, 3 * sizeof(unsigned), s));
+        CK(cudaMemsetAsync(counts + 1, 0, 4 * sizeof(unsigned), s));
         CK(cudaMemcpyAsync(counts, &n_in, sizeof(unsigned), cudaMemcpyHostToDevice, s));
         ta.source = g == 0 ? 0 : 1;
         ta.w_begin = w0;
@@ -1186,6 +1194,7 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
         ca.qne_count = counts + 2;
         ca.qsec = qout;
         ca.qsec_count = counts + 1;
+        ca.work = counts + 4;
         CK(launch_cascade(ca, grid_c, 128, s));
         unsigned n_out = 0;
         CK(cudaMemcpyAsync(&n_out, counts + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));

@@ -140,9 +140,25 @@ __device__ __forceinline__ unsigned long long child_pid(uint2 key, unsigned long
   return (unsigned long long)r.x | ((unsigned long long)r.y << 32);
 }
 
+// The five uniforms of step k: one Philox block (tag 0); four from the top 23
+// bits of its words, the fifth from their unused low bits (9 + 9 + 5 bits).
+struct StepUniforms { float u0, u1, u2, u3, u4; };
+__device__ __forceinline__ StepUniforms step_uniforms(uint2 key, unsigned long long pid, unsigned k) {
+  const uint4 r = philox4x32_10(make_uint4((unsigned)pid, (unsigned)(pid >> 32), k, 0u), key);
+  const unsigned low = ((r.x & 0x1FFu) << 14) | ((r.y & 0x1FFu) << 5) | (r.z & 0x1Fu);
+  return {u01(r.x), u01(r.y), u01(r.z), u01(r.w), (static_cast<float>(low) + 0.5f) * (1.0f / 8388608.0f)};
+}
+
 // Fixed-point energy: deposits are differences of these, so a particle's
-// deposits telescope exactly to its energy.
-__device__ __forceinline__ long long fix(float e) { return __float2ll_rn(e * kFix); }
+// deposits telescope exactly to its energy.  For e >= 0.5 MeV, e * 2^24 is the
+// float's 24-bit significand shifted left (exact, integer unit only); below,
+// it fits a 32-bit integer.
+__device__ __forceinline__ long long fix(float e) {
+  const unsigned b = __float_as_uint(e);
+  const int ex = static_cast<int>((b >> 23) & 0xFFu);
+  if (ex >= 126) return static_cast<long long>(static_cast<unsigned long long>((b & 0x7FFFFFu) | 0x800000u) << (ex - 126));
+  return static_cast<long long>(__float2int_rn(e * kFix));
+}
 __device__ __forceinline__ long long fixd(double e) { return __double2ll_rn(e * kFixD); }
 
 // ---------------------------------------------------------------------------

@@ -5,35 +5,44 @@
 namespace pmc {
 namespace {
 
-// One thread per voxel: the voxel's group tallies are contiguous ([voxel][group]),
-// so a warp streams 32 consecutive voxels' tallies through the same cache lines.
+// int64 -> float without a 64-bit conversion instruction (those run on the
+// narrow FP64 pipe): split into a signed high part and a 24-bit low part.
+__device__ __forceinline__ float ll2f(long long x) {
+  return static_cast<float>(static_cast<int>(x >> 24)) * 16777216.0f + static_cast<float>(static_cast<int>(x & 0xFFFFFF));
+}
+
+// One thread per voxel (grid-stride): the voxel's group tallies are contiguous
+// ([voxel][group]), so a warp streams 32 consecutive voxels' tallies through the
+// same cache lines.  The total is an exact integer sum; the spread is computed
+// from single-precision deviations from the first group (a statistical estimate
+// needs no more), so only the two outputs touch the FP64 pipe.
 __global__ void __launch_bounds__(256) stats_kernel(const StatsArgs a) {
-  const long long v = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  __shared__ Physics ph_s;
-  {
-    const int4* src = reinterpret_cast<const int4*>(a.phys);
-    int4* dst = reinterpret_cast<int4*>(&ph_s);
-    for (int i = threadIdx.x; i < static_cast<int>(sizeof(Physics) / 16); i += blockDim.x) dst[i] = src[i];
-  }
-  __syncthreads();
-  if (v >= a.n_vox) return;
-  const long long* t = reinterpret_cast<const long long*>(a.tally) + v * a.B;
-  double s = 0.0;
-  for (int b = 0; b < a.B; ++b) s += static_cast<double>(t[b]);
-  const double mean = s / a.B;
-  double ss = 0.0;
-  for (int b = 0; b < a.B; ++b) {
-    const double d = static_cast<double>(t[b]) - mean;
-    ss += d * d;
-  }
-  int m;
-  float rho;
-  voxel_props(ph_s, a.g, static_cast<int>(v), m, rho);
-  // MeV (2^-24 units) -> Gy: E * 1.602176634e-13 J / (rho * V * 1e-3 kg)
   const double vol = static_cast<double>(a.g.dx) * a.g.dy * a.g.dz;
-  const double scale = rho > 0.0f ? (1.602176634e-10 / (static_cast<double>(rho) * vol)) / kFixD : 0.0;
-  a.dose[v] = s * scale;
-  a.sigma[v] = a.B > 1 ? sqrt(static_cast<double>(a.B) / (a.B - 1) * ss) * scale : 0.0;
+  const float inv_b = 1.0f / static_cast<float>(a.B);
+  const float corr = a.B > 1 ? static_cast<float>(a.B) / static_cast<float>(a.B - 1) : 0.0f;
+  for (long long v = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; v < a.n_vox;
+       v += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long* t = reinterpret_cast<const long long*>(a.tally) + v * a.B;
+    const long long t0 = t[0];
+    long long sum = 0;
+    float s1 = 0.0f, s2 = 0.0f;
+    for (int b = 0; b < a.B; ++b) {
+      const long long x = t[b];
+      sum += x;
+      const float d = ll2f(x - t0);
+      s1 += d;
+      s2 = fmaf(d, d, s2);
+    }
+    // sum over groups of (D_b - mean)^2 = s2 - s1^2 / B, with deviations from group 0
+    const float ss = fmaxf(s2 - s1 * s1 * inv_b, 0.0f);
+    int m;
+    float rho;
+    voxel_props(*a.phys, a.g, static_cast<int>(v), m, rho);
+    // MeV (2^-24 units) -> Gy: E * 1.602176634e-13 J / (rho * V * 1e-3 kg)
+    const double scale = rho > 0.0f ? (1.602176634e-10 / (static_cast<double>(rho) * vol)) / kFixD : 0.0;
+    a.dose[v] = static_cast<double>(sum) * scale;
+    a.sigma[v] = static_cast<double>(sqrtf(corr * ss)) * scale;
+  }
 }
 
 __global__ void debug_philox_kernel(const uint4* ctr, uint2 key, uint4* out, int n) {
@@ -63,8 +72,12 @@ __global__ void debug_elastic_kernel(const Physics* ph, int nuclide, float E, co
 }  // namespace
 
 cudaError_t launch_stats(const StatsArgs& a, cudaStream_t s) {
-  const long long blocks = (a.n_vox + 255) / 256;
-  stats_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(a);
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const long long need = (a.n_vox + 255) / 256;
+  const long long blocks = need < 8ll * n_sm ? need : 8ll * n_sm;
+  stats_kernel<<<static_cast<unsigned>(blocks > 0 ? blocks : 1), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -158,9 +158,8 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   if (Rcm <= lam && Rcm <= d) { deposit(a, v, p, fix(E0), acc); return false; }
   bool nuclear = lam <= d;
   const float dx = nuclear ? lam : d;
-  const float4 ua = draw4(key, p.pid, p.k, 0u);
-  const float4 ub = draw4(key, p.pid, p.k, 1u);
-  const float tau = ub.x;
+  const StepUniforms ua = step_uniforms(key, p.pid, p.k);
+  const float tau = ua.u4;
   const float x1 = p.x + tau * dx * p.u, y1 = p.y + tau * dx * p.v, z1 = p.z + tau * dx * p.w;
   if (!(ph.flags & kNoMcs)) {
     // Highland x 1.07 at the step-start energy, over the planned step
@@ -170,9 +169,9 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
     if (xr > 0.0f) {
       const float br = fmaxf(1.0f + 0.038f * logf(xr / (beta * beta)), 0.0f);
       const float th0 = 1.07f * 13.6f / (beta * pc) * sqrtf(xr) * br;
-      const float r = sqrtf(-2.0f * logf(ua.x));
+      const float r = sqrtf(-2.0f * logf(ua.u0));
       float sn, cs;
-      sincospif(2.0f * ua.y, &sn, &cs);
+      sincospif(2.0f * ua.u1, &sn, &cs);
       const float tx = th0 * r * cs, ty = th0 * r * sn;
       const float th = sqrtf(tx * tx + ty * ty);
       if (th > 0.0f) {
@@ -195,7 +194,7 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
     const float g = 1.0f + E0 / kMp;
     const float b2 = 1.0f - 1.0f / (g * g);
     const float var = mc.bohr_k * rho * s * (1.0f - 0.5f * b2) / (1.0f - b2);
-    dE += sqrtf(var) * sqrtf(-2.0f * logf(ua.z)) * cospif(2.0f * ua.w);
+    dE += sqrtf(var) * sqrtf(-2.0f * logf(ua.u2)) * cospif(2.0f * ua.u3);
   }
   dE = fminf(fmaxf(dE, 0.0f), E0);
   const float E1 = E0 - dE;
@@ -227,14 +226,15 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   if (!nuclear || p.E <= kEcut) return true;
 
   // Nuclear collision: channel and target from the step-start cross-sections
+  const float4 ub = draw4(key, p.pid, kstep, 1u);
   float s_in = 0.0f, s_el = 0.0f;
   for (int j = 0; j < mc.n; ++j) {
     const NucConst& nc = ph.nuc[mc.nuc[j]];
     if (!(ph.flags & kNoInelastic)) s_in += mc.n_per_g[j] * sigma_inel(nc, E0);
     if (!(ph.flags & kNoElastic)) s_el += mc.n_per_g[j] * sigma_el(nc, E0);
   }
-  const bool inel = ub.y * (s_in + s_el) < s_in;
-  const float ut = ub.z * (inel ? s_in : s_el);
+  const bool inel = ub.x * (s_in + s_el) < s_in;
+  const float ut = ub.y * (inel ? s_in : s_el);
   int t = -1, last = 0;
   float cum = 0.0f;
   for (int j = 0; j < mc.n; ++j) {
@@ -279,7 +279,7 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
     deposit(a, v, p, qE - q1, acc);                  // recoil nucleus deposits locally
   }
   p.E = eo.T1;
-  p.nmfp = -logf(ub.w);
+  p.nmfp = -logf(ub.z);
   return true;
 }
 

@@ -168,3 +168,19 @@ def test_escape_record_angular_spread_matches_highland(fast):
     thx = np.arctan2(esc[:, 4], esc[:, 6])
     assert abs(thx.var() / th0 ** 2 - 1) < 3 * np.sqrt(2 / n) + 0.01
     assert abs(esc[:, 1].var() / (th0 ** 2 / 3) - 1) < 3 * np.sqrt(2 * 9 / 5 / n) + 0.01
+
+
+def test_statistics_kernel_matches_batch_formula(fast):
+    """Dose (Gy) and its standard error from the device's statistics kernel against the
+    ten-group formula applied to the same tallies on the host."""
+    p = W.config2()
+    g = run_gpu(p, 50000, 4, fast=fast)
+    Dt, st = A.batch_stats(g["tally"].astype(np.float64) * FIX)
+    vx = [float(np.float32(x)) for x in p.voxel]          # the engine keeps voxel sizes in single precision
+    vol = vx[0] * vx[1] * vx[2]
+    rho = p.rho.ravel().astype(np.float64)
+    dose = A.to_gray(Dt, rho, vol)
+    sig = A.to_gray(st, rho, vol)
+    assert np.allclose(g["dose"], dose, rtol=1e-9, atol=0)
+    m = dose > 0.01 * dose.max()
+    assert np.allclose(g["sigma"][m], sig[m], rtol=1e-4, atol=1e-6 * dose.max())
