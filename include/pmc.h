@@ -155,14 +155,25 @@ int pmc_enable_escape_record(pmc_ctx* ctx, uint64_t cap);
 int pmc_read_escape_record(pmc_ctx* ctx, float* out, uint64_t cap, uint64_t* n);
 
 /* Sets the transport launch shape (block size, histories per sub-group)
- * chosen by the caller's own autotuning; 0 keeps the current value. */
+ * chosen by the caller; 0 keeps the current value.  A non-zero block size
+ * also switches the autotuner off. */
 int pmc_set_launch(pmc_ctx* ctx, int block_size, int64_t chunk);
+
+/* Autotuner of the launch shape (the paper sizes sub-groups as multiples of
+ * the block size, Sec. II.B.2): times full transports of n_histories for
+ * block sizes {128, 192, 256} x sub-group sizes {n, n/2 when n >= 2^17} and
+ * keeps the fastest (written to *block_out, *chunk_out when not NULL).  It
+ * runs on the first pmc_transport of a context created with block_size 0;
+ * the trial runs overwrite the tallies. */
+int pmc_autotune(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int* block_out, int64_t* chunk_out);
 
 /* Kernel timing: when enabled, the run records CUDA events around every
  * kernel launch on the run's stream (inside the captured graph).
  * pmc_read_profile returns, per kernel kind (0 primary transport, 1 secondary
- * transport, 2 cascade, 3 dose statistics), the summed milliseconds of the
- * last transport in ms[4] and the number of launches in launches[4], and the
+ * transport, 2 cascade, 3 dose statistics), for the last transport: in ms[0..3]
+ * the summed milliseconds of its launches, in ms[4..7] the span from the first
+ * launch's start to the last launch's end (launches of two sub-groups may run
+ * concurrently), the number of launches in launches[4], and the
  * primary-transport step count in *primary_steps. */
 int pmc_enable_profile(pmc_ctx* ctx, int on);
 int pmc_read_profile(pmc_ctx* ctx, double* ms, int64_t* launches, int64_t* primary_steps);

@@ -1,7 +1,8 @@
 // cascade.cu -- non-elastic event generator: intranuclear cascade followed by
 // evaporation (Sec. II.A.4), one event per thread, fed by the event queue the
-// transport kernel fills (Sec. II.B.2: events are collected and processed in
-// parallel).
+// transport kernel fills (Sec. II.B.2: events are collected, sorted and
+// processed in parallel; here each block sorts its tile of events by target and
+// energy so that the lanes of a warp run events of similar length).
 //
 // Cascade: two-component Fermi gas in 15 constant-density shells of a
 // Woods-Saxon profile; the incident proton enters at a random point of the
@@ -44,7 +45,6 @@ struct Stream {
 };
 
 __device__ __forceinline__ float mom(float T, float m) { return sqrtf(T * T + 2.0f * T * m); }
-__device__ __forceinline__ double momd(double T, double m) { return sqrt(T * T + 2.0 * T * m); }
 
 __device__ __forceinline__ float binding(const float* bt, int Z, int A) {
   if (Z < 0 || A < 1 || Z > A || Z >= kMaxZ || A >= kMaxA) return 0.0f;
@@ -97,7 +97,7 @@ __device__ __forceinline__ float3 iso_dir(Stream& st) {
 
 struct IncP {
   float rx, ry, rz, dx, dy, dz, T;
-  int q, shell, done, refl;   // refl: reflections since the last allowed collision
+  int q, shell, done, refl;
 };
 
 __device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by, float bz) {
@@ -166,223 +166,151 @@ __device__ void nn_collide(float3 p1, float E1, float m1, float3 p2, float E2, f
   T2o = (Et - e1o) - m2;
 }
 
-// The event generator as a per-lane state machine.  One call of advance()
-// performs one short action -- start an attempt, one nucleon flight, move to the
-// next nucleon, evaluate the attempt, one evaporation step -- so that the lanes
-// of a warp, each at its own event, stay on the same few code paths, and a lane
-// whose event is done takes the next one instead of idling.  The random numbers
-// are consumed in the same order as by a straight-line implementation.
-enum Phase : int { kIdle = 0, kStart = 1, kFlight = 2, kNextNucleon = 3, kEvaluate = 4, kEvaporate = 5 };
-
-struct EventState {
-  int phase;
-  int nuc;                 // target nuclide index
-  float E;                 // incident kinetic energy
-  Stream st;
-  int attempt, retries;
-  int n, ip, sea0, sea1, crossings, iters;
-  bool any;
-  IncP p;                  // the nucleon being tracked
-  int Zc, Ac, k, esteps;   // evaporation: current nucleus, product index, steps
-  double Ex, pcx, pcy, pcz, bind;
-};
-
-__device__ __forceinline__ void begin_event(EventState& s, int nuc, float E, uint2 key, unsigned long long pid) {
-  s.phase = kStart;
-  s.nuc = nuc;
-  s.E = E;
-  s.st = Stream{key, pid, 0u, 4, make_float4(0.f, 0.f, 0.f, 0.f)};
-  s.attempt = 0;
-  s.retries = 0;
-}
-
+// The event.  Sink receives products (index, species, kinetic energy, direction
+// in the frame where the incident proton moves along +z), then the residual.
 template <class Sink>
-__device__ void advance(EventState& s, const NucleusModel& nu, const float* bt, IncP* P, Sink& sink) {
+__device__ void nonelastic_event(const NucleusModel& nu, const float* bt, float E, uint2 key, unsigned long long pid,
+                                 IncP* P, Sink& sink) {
+  Stream st{key, pid, 0u, 4, make_float4(0.f, 0.f, 0.f, 0.f)};
   const float mq[2] = {kMn, kMp};
   const int Z = nu.Z, A = nu.A;
-  switch (s.phase) {
-    case kStart: {
-      if (s.attempt >= kIncRetries) {
-        sink.transparent(s.retries);
-        s.phase = kIdle;
-        return;
-      }
-      ++s.attempt;
-      s.n = 1;
-      s.ip = 0;
-      s.sea0 = A - Z;
-      s.sea1 = Z;
-      s.any = false;
-      const float b = nu.Rout * sqrtf(s.st.next());
-      float sph, cph;
-      sincospif(2.0f * s.st.next(), &sph, &cph);
-      IncP& p0 = s.p;
-      p0.q = 1; p0.T = s.E; p0.done = 0; p0.refl = 0;
-      p0.rx = b * cph; p0.ry = b * sph; p0.rz = -sqrtf(fmaxf(0.0f, nu.Rout * nu.Rout - b * b));
-      p0.dx = 0.0f; p0.dy = 0.0f; p0.dz = 1.0f;
+  const double pin = static_cast<double>(mom(E, kMp));
+  int retries = 0;
+  for (int attempt = 0; attempt < kIncRetries; ++attempt) {
+    int n = 1, sea0 = A - Z, sea1 = Z;
+    bool any = false;
+    const float b = nu.Rout * sqrtf(st.next());
+    float sph, cph;
+    sincospif(2.0f * st.next(), &sph, &cph);
+    IncP& p0 = P[0];
+    p0.q = 1; p0.T = E; p0.done = 0; p0.refl = 0;
+    p0.rx = b * cph; p0.ry = b * sph; p0.rz = -sqrtf(fmaxf(0.0f, nu.Rout * nu.Rout - b * b));
+    p0.dx = 0.0f; p0.dy = 0.0f; p0.dz = 1.0f;
+    {
       const float ir = rsqrtf(p0.rx * p0.rx + p0.ry * p0.ry + p0.rz * p0.rz);
       cross_boundary(p0, -p0.rx * ir, -p0.ry * ir, -p0.rz * ir, 0.0f, nu.V[1][kShells - 1], kMp);
       p0.shell = kShells - 1;
-      s.crossings = 0;
-      s.iters = 0;
-      s.phase = kFlight;
-      return;
     }
-    case kFlight: {
-      IncP& p = s.p;
+    for (int ip = 0; ip < n; ++ip) {
+      IncP p = P[ip];
       const int q = p.q;
       const float m = mq[q];
-      const int i = p.shell;
-      if (p.T - nu.V[q][i] <= 0.0f || ++s.iters > kIncIterations) {   // bound, or flight cap: captured
-        p.done = 2;
-        s.phase = kNextNucleon;
-        return;
-      }
-      const float s_out = dist_out(p, nu.r[i + 1]);
-      const float s_in = i > 0 ? dist_in(p, nu.r[i]) : -1.0f;
-      const bool inner = s_in >= 0.0f && s_in < s_out;
-      const float s_b = inner ? s_in : s_out;
-      const float sl = sigma_nn(p.T, true) * kFm2PerMb, su = sigma_nn(p.T, false) * kFm2PerMb;
-      const float rate_p = s.sea1 > 0 ? nu.rho[1][i] * (q == 1 ? sl : su) : 0.0f;
-      const float rate_n = s.sea0 > 0 ? nu.rho[0][i] * (q == 0 ? sl : su) : 0.0f;
-      const float rate = rate_p + rate_n;
-      const float uc = s.st.next();
-      const float s_c = rate > 0.0f ? -logf(uc) / rate : 3.0e38f;
-      if (s_c < s_b) {
-        p.rx += s_c * p.dx; p.ry += s_c * p.dy; p.rz += s_c * p.dz;
-        const int q2 = s.st.next() * rate < rate_p ? 1 : 0;
-        const float m2 = mq[q2];
-        const float p2m = nu.pF[q2][i] * cbrtf(s.st.next());
-        const float3 d2 = iso_dir(s.st);
-        const float3 ns = iso_dir(s.st);
-        const float p1m = mom(p.T, m);
-        float3 p1o, p2o;
-        float T1o, T2o;
-        nn_collide(make_float3(p1m * p.dx, p1m * p.dy, p1m * p.dz), p.T + m, m,
-                   make_float3(p2m * d2.x, p2m * d2.y, p2m * d2.z), sqrtf(p2m * p2m + m2 * m2), m2, ns, p1o, T1o, p2o,
-                   T2o);
-        if (T1o < nu.TF[q][i] || T2o < nu.TF[q2][i]) return;   // Pauli blocked
-        if (s.n >= kIncStack) return;                            // stack full: treated as blocked
-        const float i1 = rsqrtf(p1o.x * p1o.x + p1o.y * p1o.y + p1o.z * p1o.z);
-        const float i2 = rsqrtf(p2o.x * p2o.x + p2o.y * p2o.y + p2o.z * p2o.z);
-        p.dx = p1o.x * i1; p.dy = p1o.y * i1; p.dz = p1o.z * i1;
-        p.T = T1o;
-        p.refl = 0;
-        IncP c;
-        c.q = q2; c.T = T2o; c.shell = i; c.done = 0; c.refl = 0;
-        c.rx = p.rx; c.ry = p.ry; c.rz = p.rz;
-        c.dx = p2o.x * i2; c.dy = p2o.y * i2; c.dz = p2o.z * i2;
-        P[s.n++] = c;
-        if (q2 == 1) --s.sea1; else --s.sea0;
-        s.any = true;
-        return;
-      }
-      p.rx += s_b * p.dx; p.ry += s_b * p.dy; p.rz += s_b * p.dz;
-      if (++s.crossings > kIncCrossings) {
-        p.done = 2;
-        s.phase = kNextNucleon;
-        return;
-      }
-      const float ir = rsqrtf(p.rx * p.rx + p.ry * p.ry + p.rz * p.rz);
-      bool crossed;
-      if (inner) {
-        crossed = cross_boundary(p, -p.rx * ir, -p.ry * ir, -p.rz * ir, nu.V[q][i], nu.V[q][i - 1], m);
-        if (crossed) p.shell = i - 1;
-      } else {
-        const float Vb = (i + 1 < kShells) ? nu.V[q][i + 1] : 0.0f;
-        crossed = cross_boundary(p, p.rx * ir, p.ry * ir, p.rz * ir, nu.V[q][i], Vb, m);
-        if (crossed) {
-          if (i + 1 == kShells) {   // escaped
-            p.done = 1;
-            s.phase = kNextNucleon;
-            return;
+      int crossings = 0, iters = 0;
+      for (;;) {
+        const int i = p.shell;
+        if (p.T - nu.V[q][i] <= 0.0f) { p.done = 2; break; }
+        if (++iters > kIncIterations) { p.done = 2; break; }   // bounded loop: captured
+        const float s_out = dist_out(p, nu.r[i + 1]);
+        const float s_in = i > 0 ? dist_in(p, nu.r[i]) : -1.0f;
+        const bool inner = s_in >= 0.0f && s_in < s_out;
+        const float s_b = inner ? s_in : s_out;
+        const float sl = sigma_nn(p.T, true) * kFm2PerMb, su = sigma_nn(p.T, false) * kFm2PerMb;
+        const float rate_p = sea1 > 0 ? nu.rho[1][i] * (q == 1 ? sl : su) : 0.0f;
+        const float rate_n = sea0 > 0 ? nu.rho[0][i] * (q == 0 ? sl : su) : 0.0f;
+        const float rate = rate_p + rate_n;
+        const float uc = st.next();
+        const float s_c = rate > 0.0f ? -logf(uc) / rate : 3.0e38f;
+        if (s_c < s_b) {
+          p.rx += s_c * p.dx; p.ry += s_c * p.dy; p.rz += s_c * p.dz;
+          const int q2 = st.next() * rate < rate_p ? 1 : 0;
+          const float m2 = mq[q2];
+          const float p2m = nu.pF[q2][i] * cbrtf(st.next());
+          const float3 d2 = iso_dir(st);
+          const float3 ns = iso_dir(st);
+          const float p1m = mom(p.T, m);
+          float3 p1o, p2o;
+          float T1o, T2o;
+          nn_collide(make_float3(p1m * p.dx, p1m * p.dy, p1m * p.dz), p.T + m, m,
+                     make_float3(p2m * d2.x, p2m * d2.y, p2m * d2.z), sqrtf(p2m * p2m + m2 * m2), m2, ns, p1o, T1o,
+                     p2o, T2o);
+          if (T1o < nu.TF[q][i] || T2o < nu.TF[q2][i]) continue;   // Pauli blocked
+          if (n >= kIncStack) continue;                              // stack full: treated as blocked
+          const float i1 = rsqrtf(p1o.x * p1o.x + p1o.y * p1o.y + p1o.z * p1o.z);
+          const float i2 = rsqrtf(p2o.x * p2o.x + p2o.y * p2o.y + p2o.z * p2o.z);
+          p.dx = p1o.x * i1; p.dy = p1o.y * i1; p.dz = p1o.z * i1;
+          p.T = T1o;
+          p.refl = 0;
+          IncP c;
+          c.q = q2; c.T = T2o; c.shell = i; c.done = 0; c.refl = 0;
+          c.rx = p.rx; c.ry = p.ry; c.rz = p.rz;
+          c.dx = p2o.x * i2; c.dy = p2o.y * i2; c.dz = p2o.z * i2;
+          P[n++] = c;
+          if (q2 == 1) --sea1; else --sea0;
+          any = true;
+        } else {
+          p.rx += s_b * p.dx; p.ry += s_b * p.dy; p.rz += s_b * p.dz;
+          if (++crossings > kIncCrossings) { p.done = 2; break; }
+          const float ir = rsqrtf(p.rx * p.rx + p.ry * p.ry + p.rz * p.rz);
+          bool crossed;
+          if (inner) {
+            crossed = cross_boundary(p, -p.rx * ir, -p.ry * ir, -p.rz * ir, nu.V[q][i], nu.V[q][i - 1], m);
+            if (crossed) p.shell = i - 1;
+          } else {
+            const float Vb = (i + 1 < kShells) ? nu.V[q][i + 1] : 0.0f;
+            crossed = cross_boundary(p, p.rx * ir, p.ry * ir, p.rz * ir, nu.V[q][i], Vb, m);
+            if (crossed) {
+              if (i + 1 == kShells) { p.done = 1; break; }
+              p.shell = i + 1;
+            }
           }
-          p.shell = i + 1;
+          if (!crossed && ++p.refl >= 2) { p.done = 2; break; }
         }
       }
-      // Between collisions energy and angular momentum are conserved, so a nucleon
-      // turned back once can never reach the surface; on its second turn without an
-      // allowed collision it is trapped.
-      if (!crossed && ++p.refl >= 2) {
-        p.done = 2;
-        s.phase = kNextNucleon;
-      }
-      return;
+      P[ip] = p;
     }
-    case kNextNucleon: {
-      P[s.ip] = s.p;
-      if (++s.ip < s.n) {
-        s.p = P[s.ip];
-        s.crossings = 0;
-        s.iters = 0;
-        s.phase = kFlight;
-      } else {
-        s.phase = kEvaluate;
-      }
-      return;
+    if (!any) { ++retries; continue; }
+    // residual nucleus and excitation (double precision bookkeeping)
+    int zesc = 0, nesc = 0;
+    double sumT = 0.0, prx = 0.0, pry = 0.0, prz = pin;
+    for (int ip = 0; ip < n; ++ip) {
+      if (P[ip].done != 1) continue;
+      ++nesc;
+      zesc += P[ip].q;
+      const double T = P[ip].T;
+      sumT += T;
+      const double pm = static_cast<double>(mom(P[ip].T, P[ip].q ? kMp : kMn));
+      prx -= pm * P[ip].dx; pry -= pm * P[ip].dy; prz -= pm * P[ip].dz;
     }
-    case kEvaluate: {
-      if (!s.any) { ++s.retries; s.phase = kStart; return; }
-      // residual nucleus and excitation from energy and momentum conservation
-      int zesc = 0, nesc = 0;
-      double sumT = 0.0, prx = 0.0, pry = 0.0, prz = static_cast<double>(mom(s.E, kMp));
-      for (int ip = 0; ip < s.n; ++ip) {
-        if (P[ip].done != 1) continue;
-        ++nesc;
-        zesc += P[ip].q;
-        sumT += static_cast<double>(P[ip].T);
-        const double pm = static_cast<double>(mom(P[ip].T, P[ip].q ? kMp : kMn));
-        prx -= pm * P[ip].dx; pry -= pm * P[ip].dy; prz -= pm * P[ip].dz;
-      }
-      const int Zr = Z + 1 - zesc, Ar = A + 1 - nesc;
-      if (Ar < 1 || Zr < 0 || Zr > Ar) { ++s.retries; s.phase = kStart; return; }
-      const double dM = static_cast<double>(binding(bt, Z, A)) - static_cast<double>(binding(bt, Zr, Ar));
-      const double Trec = (prx * prx + pry * pry + prz * prz) * static_cast<double>(0.5f / (Ar * static_cast<float>(kAmuD)));
-      const double Ex = static_cast<double>(s.E) - sumT - Trec - dM;
-      if (Ex < 0.0) { ++s.retries; s.phase = kStart; return; }
-      int k = 0;
-      for (int ip = 0; ip < s.n; ++ip) {
-        if (P[ip].done != 1) continue;
-        sink.product(k++, P[ip].q, static_cast<double>(P[ip].T), P[ip].dx, P[ip].dy, P[ip].dz);
-      }
-      s.k = k;
-      s.Zc = Zr; s.Ac = Ar; s.Ex = Ex; s.bind = dM;
-      s.pcx = prx; s.pcy = pry; s.pcz = prz;
-      s.esteps = 0;
-      s.phase = kEvaporate;
-      return;
+    const int Zr = Z + 1 - zesc, Ar = A + 1 - nesc;
+    if (Ar < 1 || Zr < 0 || Zr > Ar) { ++retries; continue; }
+    const double dM = static_cast<double>(binding(bt, Z, A)) - static_cast<double>(binding(bt, Zr, Ar));
+    const double Trec = (prx * prx + pry * pry + prz * prz) * static_cast<double>(0.5f / (Ar * static_cast<float>(kAmuD)));
+    double Ex = static_cast<double>(E) - sumT - Trec - dM;
+    if (Ex < 0.0) { ++retries; continue; }
+    int k = 0;
+    for (int ip = 0; ip < n; ++ip) {
+      if (P[ip].done != 1) continue;
+      sink.product(k++, P[ip].q, static_cast<double>(P[ip].T), P[ip].dx, P[ip].dy, P[ip].dz);
     }
-    case kEvaporate: {
+    // evaporation chain
+    double bind = dM;
+    int Zc = Zr, Ac = Ar;
+    double pcx = prx, pcy = pry, pcz = prz;
+    for (int stp = 0; stp < kEvapSteps; ++stp) {
       float G[6], X[6], Vj[6];
       double Sj[6];
       float Gs = 0.0f;
-      const int Zc = s.Zc, Ac = s.Ac;
-      if (s.esteps < kEvapSteps) {
-        const float Bc = binding(bt, Zc, Ac);
+      const float Bc = binding(bt, Zc, Ac);
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          G[j] = 0.0f; X[j] = 0.0f; Vj[j] = 0.0f; Sj[j] = 0.0;
-          const int Zd = Zc - kEjZ[j], Ad = Ac - kEjA[j];
-          if (Ad < 1 || Zd < 0 || Zd > Ad) continue;
-          Sj[j] = static_cast<double>(Bc) - static_cast<double>(binding(bt, Zd, Ad)) -
-                  static_cast<double>(binding(bt, kEjZ[j], kEjA[j]));
-          const float rsum = cbrtf(static_cast<float>(Ad)) + cbrtf(static_cast<float>(kEjA[j]));
-          Vj[j] = (kEjZ[j] > 0 && Zd > 0) ? kCoulomb * kEjZ[j] * Zd / (1.5f * rsum) : 0.0f;
-          X[j] = static_cast<float>(s.Ex - Sj[j] - static_cast<double>(Vj[j]));
-          if (X[j] <= 0.0f) continue;
-          const float mu = static_cast<float>(kEjA[j] * Ad) / static_cast<float>(kEjA[j] + Ad);
-          G[j] = kEjG[j] * mu * (1.5f * rsum) * (1.5f * rsum) * width_integral(X[j], Ad * 0.125f);
-          Gs += G[j];
-        }
+      for (int j = 0; j < 6; ++j) {
+        G[j] = 0.0f;
+        X[j] = 0.0f;
+        Vj[j] = 0.0f;
+        Sj[j] = 0.0;
+        const int Zd = Zc - kEjZ[j], Ad = Ac - kEjA[j];
+        if (Ad < 1 || Zd < 0 || Zd > Ad) continue;
+        Sj[j] = static_cast<double>(Bc) - static_cast<double>(binding(bt, Zd, Ad)) -
+                static_cast<double>(binding(bt, kEjZ[j], kEjA[j]));
+        const float rsum = cbrtf(static_cast<float>(Ad)) + cbrtf(static_cast<float>(kEjA[j]));
+        Vj[j] = (kEjZ[j] > 0 && Zd > 0) ? kCoulomb * kEjZ[j] * Zd / (1.5f * rsum) : 0.0f;
+        X[j] = static_cast<float>(Ex - Sj[j] - static_cast<double>(Vj[j]));
+        if (X[j] <= 0.0f) continue;
+        const float mu = static_cast<float>(kEjA[j] * Ad) / static_cast<float>(kEjA[j] + Ad);
+        G[j] = kEjG[j] * mu * (1.5f * rsum) * (1.5f * rsum) * width_integral(X[j], Ad * 0.125f);
+        Gs += G[j];
       }
-      if (!(Gs > 0.0f)) {   // no channel open (or step cap): residual recoil and leftover excitation
-        const double Tres = (s.pcx * s.pcx + s.pcy * s.pcy + s.pcz * s.pcz) *
-                            static_cast<double>(0.5f / (Ac * static_cast<float>(kAmuD)));
-        sink.residual(Zc, Ac, Tres, s.Ex, s.bind, s.retries);
-        s.phase = kIdle;
-        return;
-      }
-      const float uch = s.st.next() * Gs;
+      if (!(Gs > 0.0f)) break;
+      const float uch = st.next() * Gs;
       float acc = 0.0f;
       int j = 5;
       for (int c = 0; c < 6; ++c) {
@@ -391,36 +319,35 @@ __device__ void advance(EventState& s, const NucleusModel& nu, const float* bt, 
       }
       while (G[j] <= 0.0f) --j;
       const int Zd = Zc - kEjZ[j], Ad = Ac - kEjA[j];
-      const float z = evap_sample(s.st, X[j], Ad * 0.125f);
+      const float z = evap_sample(st, X[j], Ad * 0.125f);
       const double eps = static_cast<double>(Vj[j]) + z;
-      const double Exd = (s.Ex - Sj[j] - static_cast<double>(Vj[j])) - z;
+      const double Exd = (Ex - Sj[j] - static_cast<double>(Vj[j])) - z;
       const float aj = static_cast<float>(kEjA[j]);
       const float mu = aj * Ad / (aj + Ad) * static_cast<float>(kAmuD);
       const double ps = static_cast<double>(sqrtf(2.0f * mu * static_cast<float>(eps)));
-      const float3 nd = iso_dir(s.st);
+      const float3 nd = iso_dir(st);
       // Galilean split with masses A u: the parent's velocity is shared
-      const double vx = s.pcx * static_cast<double>(1.0f / (Ac * static_cast<float>(kAmuD)));
-      const double vy = s.pcy * static_cast<double>(1.0f / (Ac * static_cast<float>(kAmuD)));
-      const double vz = s.pcz * static_cast<double>(1.0f / (Ac * static_cast<float>(kAmuD)));
+      const double vfac = static_cast<double>(1.0f / (Ac * static_cast<float>(kAmuD)));
+      const double vx = pcx * vfac, vy = pcy * vfac, vz = pcz * vfac;
       const double mej = aj * kAmuD, md = Ad * kAmuD;
       const double ex = mej * vx + ps * nd.x, ey = mej * vy + ps * nd.y, ez = mej * vz + ps * nd.z;
-      s.pcx = md * vx - ps * nd.x;
-      s.pcy = md * vy - ps * nd.y;
-      s.pcz = md * vz - ps * nd.z;
+      pcx = md * vx - ps * nd.x;
+      pcy = md * vy - ps * nd.y;
+      pcz = md * vz - ps * nd.z;
       const double pe2 = ex * ex + ey * ey + ez * ez;
       const float ipe = rsqrtf(static_cast<float>(pe2));
-      sink.product(s.k++, j, pe2 * static_cast<double>(0.5f / (aj * static_cast<float>(kAmuD))),
+      sink.product(k++, j, pe2 * static_cast<double>(0.5f / (aj * static_cast<float>(kAmuD))),
                    static_cast<float>(ex) * ipe, static_cast<float>(ey) * ipe, static_cast<float>(ez) * ipe);
-      s.bind += Sj[j];
-      s.Zc = Zd;
-      s.Ac = Ad;
-      s.Ex = Exd;
-      ++s.esteps;
-      return;
+      bind += Sj[j];
+      Zc = Zd;
+      Ac = Ad;
+      Ex = Exd;
     }
-    default:
-      return;
+    const double Tres = (pcx * pcx + pcy * pcy + pcz * pcz) * static_cast<double>(0.5f / (Ac * static_cast<float>(kAmuD)));
+    sink.residual(Zc, Ac, Tres, Ex, bind, retries);
+    return;
   }
+  sink.transparent(retries);
 }
 
 // Sink of the transport path: products to the lab frame, protons queued.
@@ -431,6 +358,7 @@ struct TransportSink {
   unsigned b;
   long long dep, esc, bnd;
   unsigned long long sec, dropped, retries, n_transparent;
+  long long fE;            // fixed-point energy handed to the event
   __device__ void add_dep(long long q) {
     atomicAdd(a->tally + static_cast<size_t>(ev.voxel) * a->B + b, static_cast<unsigned long long>(q));
     dep += q;
@@ -506,30 +434,39 @@ __global__ void __launch_bounds__(128) cascade_kernel(const CascadeArgs a) {
   sk.dep = sk.esc = sk.bnd = 0;
   sk.sec = sk.dropped = sk.retries = sk.n_transparent = 0;
   IncP P[kIncStack];
-  EventState s;
-  s.phase = kIdle;
-  bool drained = false;
-  const unsigned lane = threadIdx.x & 31u;
-  for (;;) {
-    const unsigned need = __ballot_sync(0xffffffffu, s.phase == kIdle && !drained);
-    if (need) {
-      const int leader = __ffs(need) - 1;
-      unsigned base = 0;
-      if (static_cast<int>(lane) == leader) base = atomicAdd(a.work, static_cast<unsigned>(__popc(need)));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (s.phase == kIdle && !drained) {
-        const unsigned idx = base + __popc(need & ((1u << lane) - 1u));
-        if (idx < n) {
-          sk.ev = a.qne[idx];
-          sk.b = sk.ev.root % static_cast<unsigned>(a.B);
-          begin_event(s, sk.ev.target, sk.ev.E, sk.key, sk.ev.pid);
-        } else {
-          drained = true;
+  // Each block takes a tile of blockDim events and sorts it by (target, energy) in
+  // shared memory, so that the lanes of a warp run events of similar length.  The
+  // order of processing does not change any result (random numbers follow the
+  // particle's identity).
+  __shared__ unsigned long long keys[128];
+  for (unsigned base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const unsigned i = base + threadIdx.x;
+    unsigned long long key = ~0ull;
+    if (i < n) {
+      const Particle& e = a.qne[i];
+      key = (static_cast<unsigned long long>(e.target) << 56) |
+            (static_cast<unsigned long long>(__float_as_uint(e.E)) << 24) | threadIdx.x;
+    }
+    keys[threadIdx.x] = key;
+    __syncthreads();
+    for (unsigned k = 2; k <= 128; k <<= 1) {          // bitonic sort of the tile
+      for (unsigned j = k >> 1; j > 0; j >>= 1) {
+        const unsigned t = threadIdx.x, l = t ^ j;
+        if (l > t) {
+          const unsigned long long x = keys[t], y = keys[l];
+          const bool up = (t & k) == 0;
+          if ((x > y) == up) { keys[t] = y; keys[l] = x; }
         }
+        __syncthreads();
       }
     }
-    if (__all_sync(0xffffffffu, s.phase == kIdle && drained)) break;
-    if (s.phase != kIdle) advance(s, nuc[s.nuc], bt, P, sk);
+    const unsigned long long mine = keys[threadIdx.x];
+    __syncthreads();
+    if (mine != ~0ull) {
+      sk.ev = a.qne[base + static_cast<unsigned>(mine & 0xFFu)];
+      sk.b = sk.ev.root % static_cast<unsigned>(a.B);
+      nonelastic_event(nuc[sk.ev.target], bt, sk.ev.E, sk.key, sk.ev.pid, P, sk);
+    }
   }
   auto wsum = [](unsigned long long x) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -538,9 +475,8 @@ __global__ void __launch_bounds__(128) cascade_kernel(const CascadeArgs a) {
   const unsigned long long dep = wsum(static_cast<unsigned long long>(sk.dep));
   const unsigned long long esc = wsum(static_cast<unsigned long long>(sk.esc));
   const unsigned long long bnd = wsum(static_cast<unsigned long long>(sk.bnd));
-  const unsigned long long sec = wsum(sk.sec), dr = wsum(sk.dropped), rt = wsum(sk.retries);
-  const unsigned long long tr = wsum(sk.n_transparent);
-  if (lane == 0) {
+  const unsigned long long sec = wsum(sk.sec), dr = wsum(sk.dropped), rt = wsum(sk.retries), tr = wsum(sk.n_transparent);
+  if ((threadIdx.x & 31u) == 0) {
     Counters* c = a.cnt;
     if (dep) atomicAdd(&c->deposited, dep);
     if (esc) atomicAdd(&c->escaped, esc);
@@ -579,9 +515,8 @@ __global__ void debug_inc_kernel(const NucleusModel* nu, const float* bt, float 
   if (i >= n) return;
   IncP P[kIncStack];
   TableSink sk{summary + 8ull * i, products + 5ull * cap * i, cap, 0};
-  EventState s;
-  begin_event(s, 0, E, make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32)), pid0 + i);
-  while (s.phase != kIdle) advance(s, *nu, bt, P, sk);
+  nonelastic_event(*nu, bt, E, make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32)),
+                   pid0 + i, P, sk);
 }
 
 }  // namespace
@@ -590,11 +525,6 @@ cudaError_t launch_cascade(const CascadeArgs& a, int grid, int block, cudaStream
   const size_t smem = a.n_nuc * sizeof(NucleusModel) + kMaxZ * kMaxA * sizeof(float);
   cascade_kernel<<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
-}
-
-cudaError_t cascade_occupancy(int block, int n_nuc, int* blocks_per_sm) {
-  const size_t smem = n_nuc * sizeof(NucleusModel) + kMaxZ * kMaxA * sizeof(float);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, cascade_kernel, block, smem);
 }
 
 cudaError_t launch_debug_inc(const NucleusModel* nu, const float* btab, float E, unsigned long long seed,

@@ -64,7 +64,6 @@ struct CascadeArgs {
   Particle* qsec;
   unsigned* qsec_count;
   unsigned qsec_cap;
-  unsigned* work;                  // event counter of this launch
   Counters* cnt;
   long long* hist;
   unsigned long long hist_n;
@@ -84,7 +83,6 @@ size_t transport_smem_bytes(int n_cls, int n_mat);
 cudaError_t launch_transport(const TransportArgs& a, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t transport_occupancy(int block, size_t smem, int* blocks_per_sm);
 cudaError_t launch_cascade(const CascadeArgs& a, int grid, int block, cudaStream_t s);
-cudaError_t cascade_occupancy(int block, int n_nuc, int* blocks_per_sm);
 cudaError_t launch_stats(const StatsArgs& a, cudaStream_t s);
 
 // debug entry points

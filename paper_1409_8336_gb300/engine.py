@@ -27,7 +27,7 @@ EXPORTS = [
     "pmc_create", "pmc_destroy", "pmc_last_error", "pmc_load_materials", "pmc_load_phantom", "pmc_add_spots",
     "pmc_clear_spots", "pmc_transport", "pmc_read_dose", "pmc_read_tally", "pmc_read_ledger",
     "pmc_enable_history_ledger", "pmc_read_history_ledger", "pmc_enable_escape_record", "pmc_read_escape_record",
-    "pmc_set_launch", "pmc_transport_noalloc", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables", "pmc_debug_inc", "pmc_debug_elastic",
+    "pmc_set_launch", "pmc_autotune", "pmc_transport_noalloc", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables", "pmc_debug_inc", "pmc_debug_elastic",
 ]
 
 AllocFn = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -94,6 +94,7 @@ def lib(path: str = LIB_PATH):
             L.pmc_enable_escape_record.argtypes = [vp, u64]
             L.pmc_read_escape_record.argtypes = [vp, C.POINTER(C.c_float), u64, C.POINTER(C.c_uint64)]
             L.pmc_set_launch.argtypes = [vp, i, C.c_int64]
+            L.pmc_autotune.argtypes = [vp, u64, u64, C.POINTER(C.c_int), C.POINTER(C.c_int64)]
             L.pmc_transport_noalloc.argtypes = [vp, u64, u64, vp, vp, vp, vp]
             L.pmc_enable_profile.argtypes = [vp, i]
             L.pmc_read_profile.argtypes = [vp, pd, pi64, pi64]
@@ -217,6 +218,12 @@ class Engine:
     def set_launch(self, block_size=0, chunk=0):
         self._check(self._L.pmc_set_launch(self._ctx, block_size, chunk))
 
+    def autotune(self, n_histories: int, seed: int = 12345):
+        """Times the candidate launch shapes on full transports and keeps the fastest."""
+        b, c = C.c_int(0), C.c_int64(0)
+        self._check(self._L.pmc_autotune(self._ctx, n_histories, seed, C.byref(b), C.byref(c)))
+        return b.value, c.value
+
     # --- run ------------------------------------------------------------
     def transport(self, n_histories: int, seed: int, mode: int = FULL_CASCADE, stream=None):
         s = None
@@ -286,13 +293,14 @@ class Engine:
     def read_profile(self):
         """Per kernel kind (primary transport, secondary transport, cascade, statistics):
         summed ms and launches of the last transport, and the primary-transport step count."""
-        ms = np.zeros(4)
+        ms = np.zeros(8)
         n = np.zeros(4, dtype=np.int64)
         steps = C.c_int64(0)
         self._check(self._L.pmc_read_profile(self._ctx, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64)),
                                              C.byref(steps)))
         kinds = ("transport_primary", "transport_secondary", "cascade", "stats")
-        return {k: {"ms": float(ms[i]), "launches": int(n[i])} for i, k in enumerate(kinds)}, int(steps.value)
+        return {k: {"ms": float(ms[i]), "span_ms": float(ms[4 + i]), "launches": int(n[i])}
+                for i, k in enumerate(kinds)}, int(steps.value)
 
     # --- single-routine device checks ------------------------------------
     def debug_tables(self, material, E):
