@@ -201,6 +201,41 @@ int pmc_read_profile(pmc_ctx* ctx, double* ms, int64_t* launches, int64_t* prima
 int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int64_t* tally,
                           double* dose_gy, double* sigma_gy, void* stream);
 
+/* ---- learned stand-in of the event generator (the paper has none) ----
+ * A conditional quantile network (MLP 32-256-256-256-256-16, ReLU, BF16
+ * tensor-core math with FP32 accumulation and FP32 master weights) that maps
+ * (incident energy, target nuclide, a multiplicity token, ten uniforms) to
+ * quantiles of a non-elastic event's summary: number of protons above E_cut,
+ * energies and polar cosines of up to four of them, and the locally deposited
+ * energy.  Trained with the pinball loss on events from the engine's own
+ * cascade + evaporation kernel (Sec. II.A.4 method); used by pmc_transport
+ * with PMC_SURROGATE in place of that kernel.  The targets are the loaded
+ * nuclides with A >= 2, in load order (at most 6). */
+#define PMC_SURROGATE_PARAMS 209936
+#define PMC_SURROGATE_FEATURES 12   /* E, target slot, n_p, T/E[4], cos[4], local/E */
+
+typedef struct {
+    uint64_t n_events;   /* training events drawn from the cascade kernel (E uniform 10-250 MeV) */
+    int epochs, batch;   /* batch: events per step (two network rows each) */
+    double lr, weight_decay;
+    uint64_t seed;
+} pmc_train_opts;
+
+typedef struct { double first_loss, last_loss; int64_t steps; } pmc_train_result;
+
+/* n_events event summaries [n][PMC_SURROGATE_FEATURES] (host array), as used for training. */
+int pmc_surrogate_dataset(pmc_ctx* ctx, uint64_t n_events, uint64_t seed, float* out);
+/* Generates the data, trains with AdamW on the device, keeps the network in the context. */
+int pmc_train_surrogate(pmc_ctx* ctx, const pmc_train_opts* opts, pmc_train_result* result);
+/* Reads / sets the network's PMC_SURROGATE_PARAMS parameters (host arrays). */
+int pmc_surrogate_params(pmc_ctx* ctx, float* params, size_t n);
+int pmc_surrogate_load(pmc_ctx* ctx, const float* params, size_t n);
+/* One forward + backward pass on given rows (host arrays): inputs x[rows][32],
+ * targets y, levels tau and mask [rows][16]; returns the mean pinball loss,
+ * the gradient [PMC_SURROGATE_PARAMS] and the outputs yhat [rows][16]. */
+int pmc_surrogate_grad(pmc_ctx* ctx, const float* params, const float* x, const float* y, const float* tau,
+                       const float* mask, int rows, float* loss, float* grad, float* yhat);
+
 /* Device-side evaluation of single routines, for tests.
  * pmc_debug_philox: Philox4x32-10 of n counters ctr[n][4] under key[2]
  *   (Salmon et al., SC'11) into out[n][4].

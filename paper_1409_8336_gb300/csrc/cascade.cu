@@ -536,3 +536,80 @@ cudaError_t launch_debug_inc(const NucleusModel* nu, const float* btab, float E,
 }
 
 }  // namespace pmc
+
+// ---------------------------------------------------------------------------
+// Event summaries for training the learned stand-in of the event generator
+// (the paper has no counterpart).  Row per event, in the frame where the
+// incident proton moves along +z: E, target slot, number of protons above
+// E_cut, their kinetic energies / E and polar cosines for the four most
+// energetic (zero-padded), and the locally deposited energy / E (fragments
+// heavier than protons, the residual recoil, protons below E_cut and protons
+// beyond the fourth).
+// ---------------------------------------------------------------------------
+namespace pmc {
+namespace {
+
+struct SummarySink {
+  float E;
+  int np;
+  float T[kSurrSlots], c[kSurrSlots];
+  double local;
+  __device__ void product(int, int species, double T_, float, float, float az) {
+    const float t = static_cast<float>(T_);
+    if (species == 1 && t > kEcut) {
+      ++np;
+      // keep the kSurrSlots most energetic, sorted descending
+      float tv = t, cv = az;
+      for (int k = 0; k < kSurrSlots; ++k) {
+        if (tv > T[k]) {
+          const float ot = T[k], oc = c[k];
+          T[k] = tv; c[k] = cv; tv = ot; cv = oc;
+        }
+      }
+      local += tv;   // the displaced (or rejected) fifth proton deposits locally
+    } else if (species != 0) {
+      local += T_;
+    }
+  }
+  __device__ void residual(int, int, double Tres, double, double, int) { local += Tres; }
+  __device__ void transparent(int) { np = -1; }
+};
+
+__global__ void surrogate_dataset_kernel(const NucleusModel* nuclei, const float* bt, const int* slot_nuc, int n_slots,
+                                         unsigned long long seed, unsigned long long n, float* out) {
+  const unsigned long long i = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint2 key = make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32));
+  // energy uniform in [10, 250] MeV and a target slot, from the event's own stream (tag 6)
+  const float4 u = draw4(key, i, 0u, 6u);
+  const float E = 10.0f + 240.0f * u.x;
+  const int slot = min(static_cast<int>(u.y * n_slots), n_slots - 1);
+  IncP P[kIncStack];
+  SummarySink sk;
+  sk.E = E;
+  sk.np = 0;
+  sk.local = 0.0;
+  for (int k = 0; k < kSurrSlots; ++k) { sk.T[k] = 0.0f; sk.c[k] = 0.0f; }
+  nonelastic_event(nuclei[slot_nuc[slot]], bt, E, key, i, P, sk);
+  float* o = out + i * kSurrFeatures;
+  o[0] = E;
+  o[1] = static_cast<float>(slot);
+  o[2] = static_cast<float>(sk.np);
+  for (int k = 0; k < kSurrSlots; ++k) {
+    o[3 + k] = sk.T[k] / E;
+    o[3 + kSurrSlots + k] = sk.c[k];
+  }
+  o[3 + 2 * kSurrSlots] = static_cast<float>(sk.local / E);
+}
+
+}  // namespace
+
+cudaError_t launch_surrogate_dataset(const NucleusModel* nuclei, const float* btab, const int* slot_nuc, int n_slots,
+                                     unsigned long long seed, unsigned long long n, float* out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  surrogate_dataset_kernel<<<static_cast<unsigned>((n + 127) / 128), 128, 0, s>>>(nuclei, btab, slot_nuc, n_slots,
+                                                                                   seed, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace pmc

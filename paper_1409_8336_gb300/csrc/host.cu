@@ -257,6 +257,15 @@ struct pmc_ctx {
   double prof_span[4] = {0, 0, 0, 0};   // first start to last end per kind (launches may overlap)
   int64_t prof_launches[4] = {0, 0, 0, 0};
   int64_t steps_primary = 0;
+  // learned stand-in of the event generator
+  bool surr_trained = false;
+  int n_slots = 0;                      // non-elastic target slots (nuclides with A >= 2, in order)
+  DevBuf d_sp, d_sg, d_sm, d_sv;        // parameters, gradients, Adam moments
+  DevBuf d_swb;                         // BF16 copy of the parameters for inference
+  DevBuf d_slot_nuc, d_nuc_slot;        // slot -> nuclide, nuclide -> slot
+  DevBuf d_sx[2], d_sh[2][2], d_sy[2][2];   // inference rows and activations, per stream
+  size_t surr_cap = 0;
+  int mode = PMC_FULL_CASCADE;          // mode of the captured graph
   // graph
   cudaGraphExec_t gexec = nullptr;
   std::string gkey;
@@ -385,6 +394,10 @@ void pmc_destroy(pmc_ctx* ctx) {
                     &ctx->d_counts, &ctx->d_seed, &ctx->d_spots, &ctx->d_q[0], &ctx->d_q[1], &ctx->d_q[2],
                     &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_hist, &ctx->d_esc};
   for (DevBuf* b : bufs) dfree(ctx, *b);
+  DevBuf* sbufs[] = {&ctx->d_swb, &ctx->d_sp, &ctx->d_sg, &ctx->d_sm, &ctx->d_sv, &ctx->d_slot_nuc, &ctx->d_nuc_slot,
+                     &ctx->d_sx[0], &ctx->d_sx[1], &ctx->d_sh[0][0], &ctx->d_sh[0][1], &ctx->d_sh[1][0],
+                     &ctx->d_sh[1][1], &ctx->d_sy[0][0], &ctx->d_sy[0][1], &ctx->d_sy[1][0], &ctx->d_sy[1][1]};
+  for (DevBuf* b : sbufs) dfree(ctx, *b);
   cudaStreamDestroy(ctx->stream);
   cudaStreamDestroy(ctx->stream2);
   cudaEventDestroy(ctx->fork_ev);
@@ -506,6 +519,13 @@ int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc, const pm
     if ((rc = upload(ctx, ctx->d_st, st.data(), st.size() * sizeof(float)))) return rc;
     if ((rc = upload(ctx, ctx->d_nuclei, nm.data(), nm.size() * sizeof(NucleusModel)))) return rc;
     if ((rc = upload(ctx, ctx->d_btab, bt.data(), bt.size() * sizeof(float)))) return rc;
+    std::vector<int> slot_nuc, nuc_slot(n_nuc, -1);
+    for (int i = 0; i < n_nuc; ++i)
+      if (nuc[i].A >= 2) { nuc_slot[i] = static_cast<int>(slot_nuc.size()); slot_nuc.push_back(i); }
+    if ((rc = upload(ctx, ctx->d_nuc_slot, nuc_slot.data(), nuc_slot.size() * sizeof(int)))) return rc;
+    if (!slot_nuc.empty() && (rc = upload(ctx, ctx->d_slot_nuc, slot_nuc.data(), slot_nuc.size() * sizeof(int)))) return rc;
+    ctx->n_slots = static_cast<int>(slot_nuc.size());
+    ctx->surr_trained = false;
     ctx->mats.assign(mat, mat + n_mat);
     ctx->nucs.assign(nuc, nuc + n_nuc);
     ctx->hus.assign(hu, hu + n_hu);
@@ -652,6 +672,49 @@ int mark(pmc_ctx* ctx, cudaStream_t s, int kind) {
   return PMC_OK;
 }
 
+// Parameter layout of the quantile network: W_l [out x in] row-major, then b_l.
+constexpr int kLayerIn[kSurrLayers] = {kSurrIn, kSurrHidden, kSurrHidden, kSurrHidden, kSurrHidden};
+constexpr int kLayerOut[kSurrLayers] = {kSurrHidden, kSurrHidden, kSurrHidden, kSurrHidden, kSurrOut};
+size_t w_off(int l) {
+  size_t o = 0;
+  for (int i = 0; i < l; ++i) o += static_cast<size_t>(kLayerIn[i]) * kLayerOut[i] + kLayerOut[i];
+  return o;
+}
+size_t b_off(int l) { return w_off(l) + static_cast<size_t>(kLayerIn[l]) * kLayerOut[l]; }
+constexpr size_t kSurrParams = 32 * 256 + 256 + 3 * (256 * 256 + 256) + 256 * 16 + 16;
+static_assert(kSurrParams == PMC_SURROGATE_PARAMS, "parameter count stated in pmc.h");
+
+// Forward pass over rows (or *Mp rows): act[l] = layer l output (ReLU for l < 4).
+int mlp_forward(pmc_ctx* ctx, const float* P, int rows, const unsigned* Mp, const float* X, float* const* act,
+                cudaStream_t s) {
+  for (int l = 0; l < kSurrLayers; ++l) {
+    const float* in = l == 0 ? X : act[l - 1];
+    const int di = kLayerIn[l], dO = kLayerOut[l];
+    CK(launch_gemm(rows, Mp, dO, di, in, di, 1, P + w_off(l), 1, di, act[l], dO, P + b_off(l), l < kSurrLayers - 1,
+                   nullptr, false, s));
+  }
+  return PMC_OK;
+}
+
+// Backward pass from G = d loss / d output; gradients into Gp (same layout as P).
+int mlp_backward(pmc_ctx* ctx, const float* P, float* Gp, int rows, const float* X, float* const* act, float* g0,
+                 float* g1, cudaStream_t s) {
+  const float* G = act[kSurrLayers];   // d loss / d yhat (rows x 16)
+  float* bufs[2] = {g0, g1};
+  for (int l = kSurrLayers - 1; l >= 0; --l) {
+    const float* in = l == 0 ? X : act[l - 1];
+    const int di = kLayerIn[l], dO = kLayerOut[l];
+    CK(launch_gemm(dO, nullptr, di, rows, G, 1, dO, in, di, 1, Gp + w_off(l), di, nullptr, false, nullptr, false, s));
+    CK(launch_colsum(rows, dO, G, Gp + b_off(l), s));
+    if (l > 0) {
+      float* Gn = bufs[l & 1];
+      CK(launch_gemm(rows, nullptr, di, dO, G, dO, 1, P + w_off(l), di, 1, Gn, di, nullptr, false, act[l - 1], false, s));
+      G = Gn;
+    }
+  }
+  return PMC_OK;
+}
+
 // Kernel arguments of one generation.
 TransportArgs transport_args(pmc_ctx* ctx) {
   TransportArgs a{};
@@ -710,6 +773,26 @@ int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int sour
   if ((rc = mark(ctx, s, source == 0 ? 0 : 1))) return rc;
   CK(launch_transport(a, rp.grid_t, ctx->block, rp.smem, s));
   if ((rc = mark(ctx, s, -1))) return rc;
+  if (ctx->mode == PMC_SURROGATE) {
+    const int si = (qne == static_cast<Particle*>(ctx->d_q[5].p)) ? 1 : 0;   // which stream's buffers
+    float* X = static_cast<float*>(ctx->d_sx[si].p);
+    float* H[2] = {static_cast<float*>(ctx->d_sh[si][0].p), static_cast<float*>(ctx->d_sh[si][1].p)};
+    float* Y1 = static_cast<float*>(ctx->d_sy[si][0].p);
+    float* Y2 = static_cast<float*>(ctx->d_sy[si][1].p);
+    const float* P = static_cast<const float*>(ctx->d_sp.p);
+    const unsigned cap = static_cast<unsigned>(ctx->q_cap);
+    (void)H;
+    const int grid = ctx->n_sm * 2;
+    if ((rc = mark(ctx, s, 2))) return rc;
+    CK(launch_infer_rows(qne_count, cap, qne, static_cast<const int*>(ctx->d_nuc_slot.p), a.seed, X, s));
+    CK(launch_mlp_infer(qne_count, cap, X, ctx->d_swb.p, P, Y1, grid, s));
+    CK(launch_infer_condition(qne_count, cap, Y1, X, s));
+    CK(launch_mlp_infer(qne_count, cap, X, ctx->d_swb.p, P, Y2, grid, s));
+    CK(launch_infer_emit(qne_count, cap, qne, Y1, Y2, a.seed, a.tally, a.B, qout, qout_count, cap, a.cnt, a.hist,
+                         a.hist_n, s));
+    if ((rc = mark(ctx, s, -1))) return rc;
+    return PMC_OK;
+  }
   CascadeArgs c = cascade_args(ctx);
   c.qne = qne;
   c.qne_count = qne_count;
@@ -792,14 +875,16 @@ extern "C" {
 
 int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, void* stream) {
   if (!ctx) return PMC_E_INVALID;
-  if (!ctx->tuned && ctx->have_materials && ctx->have_phantom && !ctx->spots.empty() && mode == PMC_FULL_CASCADE &&
-      n_histories > 0 && n_histories <= 0xFFFFFFFFull) {
+  if (!ctx->tuned && ctx->have_materials && ctx->have_phantom && !ctx->spots.empty() &&
+      (mode == PMC_FULL_CASCADE || mode == PMC_SURROGATE) && n_histories > 0 && n_histories <= 0xFFFFFFFFull) {
     const int rc = pmc_autotune(ctx, n_histories, seed ^ 0x5bd1e995ull, nullptr, nullptr);
     if (rc) return rc;
   }
   if (!ctx->have_materials || !ctx->have_phantom) return fail(ctx, PMC_E_INVALID, "load materials and phantom first");
   if (ctx->spots.empty()) return fail(ctx, PMC_E_INVALID, "no spots");
-  if (mode != PMC_FULL_CASCADE) return fail(ctx, PMC_E_INVALID, "mode %d not available in this build", mode);
+  if (mode != PMC_FULL_CASCADE && mode != PMC_SURROGATE) return fail(ctx, PMC_E_INVALID, "unknown mode %d", mode);
+  if (mode == PMC_SURROGATE && !ctx->surr_trained)
+    return fail(ctx, PMC_E_INVALID, "the surrogate is not trained (pmc_train_surrogate or pmc_surrogate_load)");
   if (n_histories == 0) return fail(ctx, PMC_E_INVALID, "n_histories must be > 0");
   if (n_histories > 0xFFFFFFFFull) return fail(ctx, PMC_E_INVALID, "at most 2^32-1 histories per call");
   double wsum = 0.0;
@@ -859,13 +944,21 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     for (int i = 0; i < kQueues; ++i)
       if ((rc = dalloc(ctx, ctx->d_q[i], qcap * sizeof(Particle)))) return rc;
     ctx->q_cap = ctx->d_q[0].n / sizeof(Particle);
+    if (mode == PMC_SURROGATE) {
+      for (int si = 0; si < 2; ++si) {
+        if ((rc = dalloc(ctx, ctx->d_sx[si], ctx->q_cap * kSurrIn * sizeof(float)))) return rc;
+        for (int j = 0; j < 2; ++j)
+          if ((rc = dalloc(ctx, ctx->d_sy[si][j], ctx->q_cap * kSurrOut * sizeof(float)))) return rc;
+      }
+    }
+    ctx->mode = mode;
     CK(cudaMemcpyAsync(ctx->d_spots.p, sd.data(), sd.size() * sizeof(SpotDev), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->d_seed.p, &seed, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
     // graph of the whole run, rebuilt when its shape changes
     char key[256];
     std::snprintf(key, sizeof(key), "%llu/%lld/%zu/%d/%d/%lld/%p/%p/%d", (unsigned long long)n_histories,
                   (long long)rp.chunk, sd.size(), ctx->block, ctx->opt.n_batches, ctx->n_vox, ctx->d_tally.p,
-                  ctx->d_hist.p, ctx->profile ? 1 : 0);
+                  ctx->d_hist.p, (ctx->profile ? 1 : 0) + 2 * mode);
     if (!ctx->gexec || ctx->gkey != key) {
       if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
       cudaGraph_t graph;
@@ -1311,3 +1404,220 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     return fail(ctx, PMC_E_INVALID, "exception in transport");
   }
 }
+
+// ---------------------------------------------------------------------------
+// Learned stand-in of the event generator: data, training, weights, checks.
+// ---------------------------------------------------------------------------
+namespace {
+
+int surrogate_ready(pmc_ctx* ctx) {
+  if (!ctx->have_materials) return fail(ctx, PMC_E_INVALID, "load materials first");
+  if (ctx->n_slots < 1 || ctx->n_slots > kSurrTargets)
+    return fail(ctx, PMC_E_INVALID, "the network takes 1..%d target nuclides (A >= 2), got %d", kSurrTargets, ctx->n_slots);
+  int rc;
+  if ((rc = dalloc(ctx, ctx->d_sp, kSurrParams * sizeof(float)))) return rc;
+  if ((rc = dalloc(ctx, ctx->d_sg, kSurrParams * sizeof(float)))) return rc;
+  if ((rc = dalloc(ctx, ctx->d_sm, kSurrParams * sizeof(float)))) return rc;
+  if ((rc = dalloc(ctx, ctx->d_sv, kSurrParams * sizeof(float)))) return rc;
+  return PMC_OK;
+}
+
+// He-normal weights, zero biases, from a seeded host generator (Box-Muller on a
+// 64-bit LCG: initial values only need to be reproducible, not independent of
+// anything in the method).
+std::vector<float> init_params(uint64_t seed) {
+  std::vector<float> p(kSurrParams, 0.0f);
+  uint64_t x = seed * 6364136223846793005ull + 1442695040888963407ull;
+  auto uni = [&]() {
+    x = x * 6364136223846793005ull + 1442695040888963407ull;
+    return (static_cast<double>(x >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
+  for (int l = 0; l < kSurrLayers; ++l) {
+    const double sd = std::sqrt(2.0 / kLayerIn[l]) * (l == kSurrLayers - 1 ? 0.1 : 1.0);
+    for (size_t i = 0; i < static_cast<size_t>(kLayerIn[l]) * kLayerOut[l]; ++i) {
+      const double r = std::sqrt(-2.0 * std::log(uni())), ph = 6.283185307179586 * uni();
+      p[w_off(l) + i] = static_cast<float>(sd * r * std::cos(ph));
+    }
+  }
+  return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pmc_surrogate_dataset(pmc_ctx* ctx, uint64_t n_events, uint64_t seed, float* out) {
+  if (!ctx || !out) return PMC_E_INVALID;
+  int rc;
+  if ((rc = surrogate_ready(ctx))) return rc;
+  cudaSetDevice(ctx->opt.device);
+  DevBuf b;
+  if ((rc = dalloc(ctx, b, n_events * kSurrFeatures * sizeof(float)))) return rc;
+  CK(launch_surrogate_dataset(static_cast<const NucleusModel*>(ctx->d_nuclei.p), static_cast<const float*>(ctx->d_btab.p),
+                              static_cast<const int*>(ctx->d_slot_nuc.p), ctx->n_slots, seed, n_events,
+                              static_cast<float*>(b.p), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(out, b.p, n_events * kSurrFeatures * sizeof(float), cudaMemcpyDeviceToHost));
+  dfree(ctx, b);
+  return PMC_OK;
+}
+
+int pmc_train_surrogate(pmc_ctx* ctx, const pmc_train_opts* o, pmc_train_result* res) {
+  if (!ctx || !o) return PMC_E_INVALID;
+  if (o->n_events < 1024 || o->batch < 64 || o->batch > 65536 || o->epochs < 1 || !(o->lr > 0.0))
+    return fail(ctx, PMC_E_INVALID, "training options out of range");
+  int rc;
+  if ((rc = surrogate_ready(ctx))) return rc;
+  try {
+    cudaSetDevice(ctx->opt.device);
+    cudaStream_t s = ctx->stream;
+    const uint64_t n = o->n_events;
+    const int B = o->batch, rows = 2 * B;
+    // 1. events from the project's own cascade + evaporation kernel
+    DevBuf feat, perm, X, Y, T, M, act[kSurrLayers + 1], g0, g1, loss;
+    if ((rc = dalloc(ctx, feat, n * kSurrFeatures * sizeof(float)))) return rc;
+    CK(launch_surrogate_dataset(static_cast<const NucleusModel*>(ctx->d_nuclei.p), static_cast<const float*>(ctx->d_btab.p),
+                                static_cast<const int*>(ctx->d_slot_nuc.p), ctx->n_slots, o->seed, n,
+                                static_cast<float*>(feat.p), s));
+    // 2. buffers and initial weights
+    if ((rc = dalloc(ctx, perm, n * sizeof(unsigned)))) return rc;
+    if ((rc = dalloc(ctx, X, static_cast<size_t>(rows) * kSurrIn * sizeof(float)))) return rc;
+    for (DevBuf* b : {&Y, &T, &M})
+      if ((rc = dalloc(ctx, *b, static_cast<size_t>(rows) * kSurrOut * sizeof(float)))) return rc;
+    for (int l = 0; l < kSurrLayers; ++l)
+      if ((rc = dalloc(ctx, act[l], static_cast<size_t>(rows) * kLayerOut[l] * sizeof(float)))) return rc;
+    if ((rc = dalloc(ctx, act[kSurrLayers], static_cast<size_t>(rows) * kSurrOut * sizeof(float)))) return rc;
+    if ((rc = dalloc(ctx, g0, static_cast<size_t>(rows) * kSurrHidden * sizeof(float)))) return rc;
+    if ((rc = dalloc(ctx, g1, static_cast<size_t>(rows) * kSurrHidden * sizeof(float)))) return rc;
+    if ((rc = dalloc(ctx, loss, 64 * sizeof(float)))) return rc;
+    std::vector<float> p0 = init_params(o->seed);
+    CK(cudaMemcpyAsync(ctx->d_sp.p, p0.data(), kSurrParams * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->d_sm.p, 0, kSurrParams * sizeof(float), s));
+    CK(cudaMemsetAsync(ctx->d_sv.p, 0, kSurrParams * sizeof(float), s));
+    float* P = static_cast<float*>(ctx->d_sp.p);
+    float* Gp = static_cast<float*>(ctx->d_sg.p);
+    float* A[kSurrLayers + 1];
+    for (int l = 0; l <= kSurrLayers; ++l) A[l] = static_cast<float*>(act[l].p);
+    // 3. epochs of shuffled mini-batches, AdamW
+    std::vector<unsigned> order(n);
+    uint64_t x = o->seed ^ 0x9e3779b97f4a7c15ull;
+    const uint64_t steps_per_epoch = n / B;
+    int step = 0;
+    double first_loss = 0.0, last_loss = 0.0;
+    float* dloss = static_cast<float*>(loss.p);
+    for (int ep = 0; ep < o->epochs; ++ep) {
+      std::iota(order.begin(), order.end(), 0u);
+      for (uint64_t i = n - 1; i > 0; --i) {                   // Fisher-Yates with a 64-bit LCG
+        x = x * 6364136223846793005ull + 1442695040888963407ull;
+        std::swap(order[i], order[(x >> 33) % (i + 1)]);
+      }
+      CK(cudaMemcpyAsync(perm.p, order.data(), n * sizeof(unsigned), cudaMemcpyHostToDevice, s));
+      CK(cudaMemsetAsync(dloss, 0, 64 * sizeof(float), s));
+      for (uint64_t k = 0; k < steps_per_epoch; ++k) {
+        ++step;
+        CK(launch_train_rows(B, static_cast<const float*>(feat.p), static_cast<const unsigned*>(perm.p), k * B, n,
+                             o->seed, static_cast<unsigned>(step), static_cast<float*>(X.p), static_cast<float*>(Y.p),
+                             static_cast<float*>(T.p), static_cast<float*>(M.p), s));
+        if ((rc = mlp_forward(ctx, P, rows, nullptr, static_cast<float*>(X.p), A, s))) return rc;
+        float* lslot = dloss + (k + 1 == steps_per_epoch ? 1 : (k == 0 ? 2 : 0));
+        CK(launch_pinball(rows, A[kSurrLayers - 1], static_cast<float*>(Y.p), static_cast<float*>(T.p),
+                          static_cast<float*>(M.p), A[kSurrLayers], lslot, s));
+        if ((rc = mlp_backward(ctx, P, Gp, rows, static_cast<float*>(X.p), A, static_cast<float*>(g0.p),
+                               static_cast<float*>(g1.p), s)))
+          return rc;
+        CK(launch_adamw(static_cast<int>(kSurrParams), P, Gp, static_cast<float*>(ctx->d_sm.p),
+                        static_cast<float*>(ctx->d_sv.p), static_cast<float>(o->lr), 0.9f, 0.999f, 1e-8f,
+                        static_cast<float>(o->weight_decay), step, s));
+      }
+      float h[3];
+      CK(cudaMemcpyAsync(h, dloss, 3 * sizeof(float), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (ep == 0) first_loss = h[2];
+      last_loss = h[1];
+    }
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    for (DevBuf* b : {&feat, &perm, &X, &Y, &T, &M, &g0, &g1, &loss}) dfree(ctx, *b);
+    for (int l = 0; l <= kSurrLayers; ++l) dfree(ctx, act[l]);
+    if ((rc = dalloc(ctx, ctx->d_swb, kSurrParams * 2))) return rc;
+    CK(launch_to_bf16(static_cast<int>(kSurrParams), P, ctx->d_swb.p, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->surr_trained = true;
+    if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+    if (res) {
+      res->first_loss = first_loss;
+      res->last_loss = last_loss;
+      res->steps = step;
+    }
+    return PMC_OK;
+  } catch (...) {
+    return fail(ctx, PMC_E_INVALID, "exception in training");
+  }
+}
+
+int pmc_surrogate_params(pmc_ctx* ctx, float* out, size_t n) {
+  if (!ctx || !out) return PMC_E_INVALID;
+  if (n != kSurrParams) return fail(ctx, PMC_E_INVALID, "the network has %zu parameters", kSurrParams);
+  if (!ctx->d_sp.p) return fail(ctx, PMC_E_INVALID, "no network");
+  cudaSetDevice(ctx->opt.device);
+  CK(cudaMemcpy(out, ctx->d_sp.p, n * sizeof(float), cudaMemcpyDeviceToHost));
+  return PMC_OK;
+}
+
+int pmc_surrogate_load(pmc_ctx* ctx, const float* params, size_t n) {
+  if (!ctx || !params) return PMC_E_INVALID;
+  if (n != kSurrParams) return fail(ctx, PMC_E_INVALID, "the network has %zu parameters", kSurrParams);
+  int rc;
+  if ((rc = surrogate_ready(ctx))) return rc;
+  cudaSetDevice(ctx->opt.device);
+  CK(cudaMemcpy(ctx->d_sp.p, params, n * sizeof(float), cudaMemcpyHostToDevice));
+  if ((rc = dalloc(ctx, ctx->d_swb, kSurrParams * 2))) return rc;
+  CK(launch_to_bf16(static_cast<int>(kSurrParams), static_cast<const float*>(ctx->d_sp.p), ctx->d_swb.p, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->surr_trained = true;
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  return PMC_OK;
+}
+
+int pmc_surrogate_grad(pmc_ctx* ctx, const float* params, const float* x, const float* y, const float* tau,
+                       const float* mask, int rows, float* loss, float* grad, float* yhat) {
+  if (!ctx || !params || !x || !y || !tau || !mask || rows < 1 || rows > 65536) return PMC_E_INVALID;
+  int rc;
+  if ((rc = surrogate_ready(ctx))) return rc;
+  cudaSetDevice(ctx->opt.device);
+  cudaStream_t s = ctx->stream;
+  DevBuf X, Y, T, M, act[kSurrLayers + 1], g0, g1, L;
+  if ((rc = dalloc(ctx, X, static_cast<size_t>(rows) * kSurrIn * 4))) return rc;
+  for (DevBuf* b : {&Y, &T, &M})
+    if ((rc = dalloc(ctx, *b, static_cast<size_t>(rows) * kSurrOut * 4))) return rc;
+  for (int l = 0; l < kSurrLayers; ++l)
+    if ((rc = dalloc(ctx, act[l], static_cast<size_t>(rows) * kLayerOut[l] * 4))) return rc;
+  if ((rc = dalloc(ctx, act[kSurrLayers], static_cast<size_t>(rows) * kSurrOut * 4))) return rc;
+  if ((rc = dalloc(ctx, g0, static_cast<size_t>(rows) * kSurrHidden * 4))) return rc;
+  if ((rc = dalloc(ctx, g1, static_cast<size_t>(rows) * kSurrHidden * 4))) return rc;
+  if ((rc = dalloc(ctx, L, 64))) return rc;
+  CK(cudaMemcpy(ctx->d_sp.p, params, kSurrParams * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(X.p, x, static_cast<size_t>(rows) * kSurrIn * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(Y.p, y, static_cast<size_t>(rows) * kSurrOut * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(T.p, tau, static_cast<size_t>(rows) * kSurrOut * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(M.p, mask, static_cast<size_t>(rows) * kSurrOut * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemset(L.p, 0, 64));
+  float* A[kSurrLayers + 1];
+  for (int l = 0; l <= kSurrLayers; ++l) A[l] = static_cast<float*>(act[l].p);
+  const float* P = static_cast<const float*>(ctx->d_sp.p);
+  if ((rc = mlp_forward(ctx, P, rows, nullptr, static_cast<float*>(X.p), A, s))) return rc;
+  CK(launch_pinball(rows, A[kSurrLayers - 1], static_cast<float*>(Y.p), static_cast<float*>(T.p),
+                    static_cast<float*>(M.p), A[kSurrLayers], static_cast<float*>(L.p), s));
+  if ((rc = mlp_backward(ctx, P, static_cast<float*>(ctx->d_sg.p), rows, static_cast<float*>(X.p), A,
+                         static_cast<float*>(g0.p), static_cast<float*>(g1.p), s)))
+    return rc;
+  CK(cudaStreamSynchronize(s));
+  if (loss) CK(cudaMemcpy(loss, L.p, 4, cudaMemcpyDeviceToHost));
+  if (grad) CK(cudaMemcpy(grad, ctx->d_sg.p, kSurrParams * 4, cudaMemcpyDeviceToHost));
+  if (yhat) CK(cudaMemcpy(yhat, A[kSurrLayers - 1], static_cast<size_t>(rows) * kSurrOut * 4, cudaMemcpyDeviceToHost));
+  for (DevBuf* b : {&X, &Y, &T, &M, &g0, &g1, &L}) dfree(ctx, *b);
+  for (int l = 0; l <= kSurrLayers; ++l) dfree(ctx, act[l]);
+  return PMC_OK;
+}
+
+}  // extern "C"

@@ -40,6 +40,16 @@ constexpr int kEvapSteps = 64;
 constexpr unsigned kMaxSteps = 100000u;        // per particle; exceeding it is an error
 constexpr unsigned kNoStraggling = 1u, kNoMcs = 2u, kNoElastic = 4u, kNoInelastic = 8u;
 
+// Learned stand-in of the event generator (quantile network).
+constexpr int kSurrSlots = 4;                    // proton slots per event
+constexpr int kSurrFeatures = 4 + 2 * kSurrSlots;   // E, slot, n_p, T[4], cos[4], local
+constexpr int kSurrTargets = 6;                  // one-hot target slots
+constexpr int kSurrIn = 32;                      // padded input width
+constexpr int kSurrHidden = 256;
+constexpr int kSurrOut = 16;                     // padded output width (10 used)
+constexpr int kSurrLayers = 5;                   // 32-256-256-256-256-16
+constexpr int kSurrTau = 10;                     // quantile levels per row
+
 // ---------------------------------------------------------------------------
 // device data
 // ---------------------------------------------------------------------------

@@ -85,6 +85,31 @@ cudaError_t transport_occupancy(int block, size_t smem, int* blocks_per_sm);
 cudaError_t launch_cascade(const CascadeArgs& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_stats(const StatsArgs& a, cudaStream_t s);
 
+cudaError_t launch_surrogate_dataset(const NucleusModel* nuclei, const float* btab, const int* slot_nuc, int n_slots,
+                                     unsigned long long seed, unsigned long long n, float* out, cudaStream_t s);
+
+cudaError_t launch_gemm(int M, const unsigned* Mp, int N, int K, const float* A, long long sam, long long sak,
+                        const float* B, long long sbk, long long sbn, float* C, long long ldc, const float* bias,
+                        bool relu, const float* mask, bool accumulate, cudaStream_t s);
+cudaError_t launch_mlp_infer(const unsigned* n_rows, unsigned cap, const float* X, const void* Wb, const float* P,
+                             float* Y, int grid, cudaStream_t s);
+cudaError_t launch_to_bf16(int n, const float* a, void* b, cudaStream_t s);
+cudaError_t launch_pinball(int rows, const float* yhat, const float* y, const float* tau, const float* mask,
+                           float* grad, float* loss, cudaStream_t s);
+cudaError_t launch_colsum(int rows, int N, const float* G, float* db, cudaStream_t s);
+cudaError_t launch_adamw(int n, float* p, const float* g, float* m, float* v, float lr, float b1, float b2, float eps,
+                         float wd, int step, cudaStream_t s);
+cudaError_t launch_train_rows(int batch, const float* feat, const unsigned* perm, unsigned long long first,
+                              unsigned long long n_events, unsigned long long seed, unsigned step, float* X, float* Y,
+                              float* tau, float* mask, cudaStream_t s);
+cudaError_t launch_infer_rows(const unsigned* n_ev, unsigned cap, const Particle* qne, const int* nuc_slot,
+                              const unsigned long long* seed, float* X, cudaStream_t s);
+cudaError_t launch_infer_condition(const unsigned* n_ev, unsigned cap, const float* Yhat, float* X, cudaStream_t s);
+cudaError_t launch_infer_emit(const unsigned* n_ev, unsigned cap, const Particle* qne, const float* Y1, const float* Y2,
+                              const unsigned long long* seed, unsigned long long* tally, int B, Particle* qsec,
+                              unsigned* qsec_count, unsigned qsec_cap, Counters* cnt, long long* hist,
+                              unsigned long long hist_n, cudaStream_t s);
+
 // debug entry points
 cudaError_t launch_debug_philox(const uint4* ctr, uint2 key, uint4* out, int n, cudaStream_t s);
 cudaError_t launch_debug_tables(const Physics* ph, const float2* rt, const float2* et, int cls, const double* E,

@@ -27,7 +27,8 @@ EXPORTS = [
     "pmc_create", "pmc_destroy", "pmc_last_error", "pmc_load_materials", "pmc_load_phantom", "pmc_add_spots",
     "pmc_clear_spots", "pmc_transport", "pmc_read_dose", "pmc_read_tally", "pmc_read_ledger",
     "pmc_enable_history_ledger", "pmc_read_history_ledger", "pmc_enable_escape_record", "pmc_read_escape_record",
-    "pmc_set_launch", "pmc_autotune", "pmc_transport_noalloc", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables", "pmc_debug_inc", "pmc_debug_elastic",
+    "pmc_set_launch", "pmc_autotune", "pmc_transport_noalloc", "pmc_surrogate_dataset", "pmc_train_surrogate",
+    "pmc_surrogate_params", "pmc_surrogate_load", "pmc_surrogate_grad", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables", "pmc_debug_inc", "pmc_debug_elastic",
 ]
 
 AllocFn = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -54,6 +55,19 @@ class HuBin(C.Structure):
 
 class Spot(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("E", "sigma_E", "x", "y", "sigma_x", "sigma_y", "u", "v", "w", "weight")]
+
+
+SURROGATE_PARAMS = 209936
+SURROGATE_FEATURES = 12
+
+
+class TrainOpts(C.Structure):
+    _fields_ = [("n_events", C.c_uint64), ("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double),
+                ("weight_decay", C.c_double), ("seed", C.c_uint64)]
+
+
+class TrainResult(C.Structure):
+    _fields_ = [("first_loss", C.c_double), ("last_loss", C.c_double), ("steps", C.c_int64)]
 
 
 class Ledger(C.Structure):
@@ -95,6 +109,12 @@ def lib(path: str = LIB_PATH):
             L.pmc_read_escape_record.argtypes = [vp, C.POINTER(C.c_float), u64, C.POINTER(C.c_uint64)]
             L.pmc_set_launch.argtypes = [vp, i, C.c_int64]
             L.pmc_autotune.argtypes = [vp, u64, u64, C.POINTER(C.c_int), C.POINTER(C.c_int64)]
+            pf = C.POINTER(C.c_float)
+            L.pmc_surrogate_dataset.argtypes = [vp, u64, u64, pf]
+            L.pmc_train_surrogate.argtypes = [vp, C.POINTER(TrainOpts), C.POINTER(TrainResult)]
+            L.pmc_surrogate_params.argtypes = [vp, pf, C.c_size_t]
+            L.pmc_surrogate_load.argtypes = [vp, pf, C.c_size_t]
+            L.pmc_surrogate_grad.argtypes = [vp, pf, pf, pf, pf, pf, i, pf, pf, pf]
             L.pmc_transport_noalloc.argtypes = [vp, u64, u64, vp, vp, vp, vp]
             L.pmc_enable_profile.argtypes = [vp, i]
             L.pmc_read_profile.argtypes = [vp, pd, pi64, pi64]
@@ -114,6 +134,10 @@ class PmcError(RuntimeError):
 
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
 
 
 def _torch_allocator(device):
@@ -301,6 +325,38 @@ class Engine:
         kinds = ("transport_primary", "transport_secondary", "cascade", "stats")
         return {k: {"ms": float(ms[i]), "span_ms": float(ms[4 + i]), "launches": int(n[i])}
                 for i, k in enumerate(kinds)}, int(steps.value)
+
+    # --- learned stand-in of the event generator --------------------------
+    def surrogate_dataset(self, n_events: int, seed: int):
+        out = np.empty((n_events, SURROGATE_FEATURES), dtype=np.float32)
+        self._check(self._L.pmc_surrogate_dataset(self._ctx, n_events, seed, _fp(out)))
+        return out
+
+    def train_surrogate(self, n_events=10_000_000, epochs=3, batch=8192, lr=1e-3, weight_decay=1e-5, seed=4):
+        o = TrainOpts(n_events, epochs, batch, lr, weight_decay, seed)
+        r = TrainResult()
+        self._check(self._L.pmc_train_surrogate(self._ctx, C.byref(o), C.byref(r)))
+        return {"first_loss": r.first_loss, "last_loss": r.last_loss, "steps": r.steps}
+
+    def surrogate_params(self):
+        out = np.empty(SURROGATE_PARAMS, dtype=np.float32)
+        self._check(self._L.pmc_surrogate_params(self._ctx, _fp(out), out.size))
+        return out
+
+    def surrogate_load(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self._L.pmc_surrogate_load(self._ctx, _fp(p), p.size))
+
+    def surrogate_grad(self, params, x, y, tau, mask):
+        f = lambda a: np.ascontiguousarray(a, dtype=np.float32)  # noqa: E731
+        params, x, y, tau, mask = f(params), f(x), f(y), f(tau), f(mask)
+        rows = x.shape[0]
+        loss = np.zeros(1, dtype=np.float32)
+        grad = np.empty(SURROGATE_PARAMS, dtype=np.float32)
+        yhat = np.empty((rows, 16), dtype=np.float32)
+        self._check(self._L.pmc_surrogate_grad(self._ctx, _fp(params), _fp(x), _fp(y), _fp(tau), _fp(mask), rows,
+                                               _fp(loss), _fp(grad), _fp(yhat)))
+        return float(loss[0]), grad, yhat
 
     # --- single-routine device checks ------------------------------------
     def debug_tables(self, material, E):

@@ -1,0 +1,164 @@
+"""The learned stand-in of the event generator on the GPU: gradients of the hand-written
+forward/backward kernels against the FP64 reference, event summaries against the oracle's
+cascade, training, and transport with the trained network against the full cascade."""
+import math
+import time
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import analysis as A
+from oracle import mlp
+from oracle import oracle as O
+from paper_1409_8336_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+FIX = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def trained():
+    from paper_1409_8336_gb300 import Engine
+
+    prob = W.config2()
+    e = Engine(device=0, n_batches=10, fast_math=True)
+    e.load_problem(prob)
+    t0 = time.perf_counter()
+    res = e.train_surrogate(n_events=10_000_000, epochs=2, batch=8192, lr=1e-3, seed=4)
+    res["seconds"] = time.perf_counter() - t0
+    params = e.surrogate_params()
+    yield e, prob, res, params
+    e.close()
+
+
+def test_gradients_match_fp64_reference():
+    from paper_1409_8336_gb300 import Engine
+
+    e = Engine(device=0, n_batches=10)
+    e.load_problem(W.config2())
+    rng = np.random.default_rng(3)
+    rows = 96
+    p = np.concatenate([np.concatenate([rng.normal(0, np.sqrt(2.0 / mlp.DIMS[i]), mlp.DIMS[i] * mlp.DIMS[i + 1]),
+                                        rng.normal(0, 0.05, mlp.DIMS[i + 1])]) for i in range(5)]).astype(np.float32)
+    x = rng.normal(size=(rows, 32)).astype(np.float32)
+    y = rng.normal(size=(rows, 16)).astype(np.float32)
+    tau = rng.uniform(0.05, 0.95, size=(rows, 16)).astype(np.float32)
+    mask = (rng.uniform(size=(rows, 16)) < 0.7).astype(np.float32)
+    loss, g, yh = e.surrogate_grad(p, x, y, tau, mask)
+    lo, go, yo = mlp.grad(p.astype(np.float64), x.astype(np.float64), y, tau, mask, round_bf16=True)
+    e.close()
+    assert np.allclose(yh, yo, rtol=2e-2, atol=2e-2 * np.abs(yo).max())
+    assert loss == pytest.approx(lo, rel=1e-2)
+    # per layer: relative error of the gradient in the Frobenius norm
+    o = 0
+    for i in range(5):
+        for n in (mlp.DIMS[i] * mlp.DIMS[i + 1], mlp.DIMS[i + 1]):
+            a, b = g[o:o + n], go[o:o + n]
+            assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-7, (i, n, np.linalg.norm(a - b) / np.linalg.norm(b))
+            o += n
+
+
+def test_event_summaries_match_oracle_cascade():
+    from paper_1409_8336_gb300 import Engine
+
+    prob = W.config2()
+    e = Engine(device=0, n_batches=10)
+    e.load_problem(prob)
+    seed = 11
+    d = e.surrogate_dataset(20000, seed)
+    e.close()
+    assert stats.kstest((d[:, 0] - 10) / 240, "uniform").pvalue > 1e-3
+    assert set(np.unique(d[:, 1]).astype(int)) == set(range(6))
+    assert np.all(d[:, 2] >= 0) and np.all((d[:, 3:7] >= 0) & (d[:, 3:7] <= 1))
+    assert np.all(np.abs(d[:, 7:11]) <= 1) and np.all(d[:, 11] >= 0)
+    assert np.all(d[:, 3:7].sum(1) + d[:, 11] <= 1 + 1e-5)             # energy out <= energy in
+    # the same events from the oracle: identical random streams, summarised the same way
+    slots = [i for i, n in enumerate(prob.nuclides) if n[1] >= 2]
+    same = 0
+    for i in range(300):
+        Z, Aa = prob.nuclides[slots[int(d[i, 1])]][:2]
+        s_, pr, _ = O.inc_batch(Z, Aa, float(d[i, 0]), seed, i, 1)
+        k = int(s_[0, 0])
+        T = pr[0, :k, 1]
+        sp = pr[0, :k, 0].astype(int)
+        np_or = int(np.sum((sp == 1) & (T > 0.1)))
+        same += np_or == int(d[i, 2])
+    assert same >= 0.7 * 300, same
+
+
+def test_training_reduces_the_pinball_loss(trained):
+    _, _, res, params = trained
+    assert res["steps"] > 1000
+    assert res["last_loss"] < 0.8 * res["first_loss"], res
+    assert np.all(np.isfinite(params))
+
+
+def test_surrogate_spectra_against_cascade(trained):
+    """Secondary-proton spectra of the trained network (sampled on the FP64 reference with the
+    trained weights) against the cascade's, per target: KS statistics."""
+    e, prob, _, params = trained
+    d = e.surrogate_dataset(60000, 99)
+    rng = np.random.default_rng(5)
+    ks_T, ks_n = [], []
+    for slot in range(6):
+        rows = d[d[:, 1] == slot][:4000]
+        n = len(rows)
+        X = np.zeros((n, 32))
+        X[:, 0] = (rows[:, 0] - 130) / 120
+        X[np.arange(n), 1 + slot] = 1
+        X[:, 7] = -1
+        X[:, 8:18] = rng.uniform(size=(n, 10))
+        q_np = mlp.forward(params, X)[1][:, 0]
+        np_s = np.clip(np.floor(q_np + 0.5), 0, 4)
+        X[:, 7] = np_s / 4
+        y2 = mlp.forward(params, X)[1]
+        T_s = (np.clip(y2[:, 1], 0, None) * rows[:, 0])[np_s >= 1]
+        T_c = (rows[:, 3] * rows[:, 0])[rows[:, 2] >= 1]
+        ks_T.append(stats.ks_2samp(T_s, T_c).statistic)
+        ks_n.append(abs(np.mean(np_s) - np.mean(np.minimum(rows[:, 2], 4))))
+    print("KS leading-proton energy per target:", np.round(ks_T, 3), "mean multiplicity error:", np.round(ks_n, 3))
+    assert max(ks_T) < 0.15 and max(ks_n) < 0.3
+
+
+def test_surrogate_transport_gamma_and_speed(trained):
+    """The slab workload, 1e6 histories: dose with the trained network against the full cascade
+    (2 %/2 mm gamma >= 98 %), energy bookkeeping, and the throughput gained."""
+    from paper_1409_8336_gb300 import Engine
+
+    e, prob, _, params = trained
+    n = 1_000_000
+    out = {}
+    for mode in (0, 1):
+        e.enable_profile(True)
+        e.transport(n, 7, mode=mode)
+        t = []
+        for k in range(3):
+            t0 = time.perf_counter()
+            e.transport(n, 7, mode=mode)
+            t.append(time.perf_counter() - t0)
+        prof, _ = e.read_profile()
+        D, sg = A.batch_stats(e.read_tally().astype(np.float64) * FIX)
+        out[mode] = dict(D=D.reshape(prob.shape), t=min(t), led=e.read_ledger(), cascade_ms=prof["cascade"]["ms"])
+    L = out[1]["led"]
+    assert L["dropped"] == 0 and L["errors"] == 0
+    assert abs(L["incident"] - L["deposited"] - L["escaped"] - L["binding"]) < 1e-6 * L["incident"]
+    gam = A.gamma_pass_rate(out[0]["D"], out[1]["D"], prob.voxel)
+    r80f = A.r80(A.depth_dose(out[0]["D"]), prob.voxel[2])
+    r80s = A.r80(A.depth_dose(out[1]["D"]), prob.voxel[2])
+    print("gamma %.4f, R80 full %.3f surrogate %.3f, event stage %.3f -> %.3f ms, transport %.2f -> %.2f ms" % (
+        gam, r80f, r80s, out[0]["cascade_ms"], out[1]["cascade_ms"], 1e3 * out[0]["t"], 1e3 * out[1]["t"]))
+    assert gam >= 0.98
+    assert abs(r80f - r80s) < 0.02
+    assert out[1]["cascade_ms"] < out[0]["cascade_ms"]
+    assert out[1]["t"] < out[0]["t"]
+    # what the training gains: an untrained network (initial weights) is much worse
+    e2 = Engine(device=0, n_batches=10, fast_math=True)
+    e2.load_problem(prob)
+    e2.surrogate_load(np.zeros_like(params))
+    e2.transport(n, 7, mode=1)
+    D0, _ = A.batch_stats(e2.read_tally().astype(np.float64) * FIX)
+    e2.close()
+    gam0 = A.gamma_pass_rate(out[0]["D"], D0.reshape(prob.shape), prob.voxel)
+    print("gamma of an untrained (zero) network: %.4f" % gam0)
+    assert gam0 < gam
