@@ -141,14 +141,34 @@ def oracle_rate(prob, n_total, seconds, seed=1):
     return done / dt, done, dt
 
 
+def config_block(prob, n):
+    """The workload description shared by both arms."""
+    return {"workload": prob.name, "histories_per_step": n, "spots": "70/150/230 MeV, sigma 4 mm",
+            "batches": prob.n_batches, "physics": "full cascade", "l2": "flushed between steps"}
+
+
+def max_over_ranks(value, dist=None):
+    """The slowest rank's time (the whole job ends with it); a no-op on one process."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     prob = workload()
     times, dones = [], []
+    # each step is a bounded sample, sized so the whole run ends within about two minutes
+    per_step = min(max(args.cpu_seconds / 3, 0.5), 120.0 / max(1, args.steps + args.warmup))
     for i in range(args.warmup + args.steps):
-        rate, done, dt = oracle_rate(prob, args.histories, max(2.0, args.cpu_seconds / 3), seed=1 + i)
+        rate, done, dt = oracle_rate(prob, args.histories, per_step, seed=1 + i)
         if i >= args.warmup:
             times.append(dt)
             dones.append(done)
@@ -156,7 +176,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.histories / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": prob.name, "histories": args.histories, "spots": "70/150/230 MeV"},
+            "config": config_block(prob, args.histories),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d histories per step, even over the three spots" % (sum(dones) // len(dones))},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -251,11 +271,7 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    total_ms = sum(ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms), dist)
     value = world * n * args.steps / (total_ms / 1e3)
 
     # end to end through the public API with host buffers (pinned): H2D of the phantom and spots,
@@ -336,10 +352,9 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": prob.name, "histories_per_step": n, "spots": "70/150/230 MeV, sigma 4 mm",
-                       "batches": prob.n_batches, "physics": "full cascade", "l2": "flushed between steps",
-                       "launch": {"block": tuned_block, "histories_per_subgroup": tuned_chunk, "autotuned": True},
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": dict(config_block(prob, n),
+                           launch={"block": tuned_block, "histories_per_subgroup": tuned_chunk, "autotuned": True},
+                           parallelism="replicas" if world > 1 else "single GPU"),
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "kernel": "transport_kernel (primaries)", "achieved": achieved,
