@@ -32,7 +32,6 @@ import numpy as np  # noqa: E402
 METRIC = "proton histories/s on 1 GB300, full cascade (learned surrogate reported beside it)"
 UNIT = "histories/s"
 N_HISTORIES = 1_000_000
-FIX = 2.0 ** -24
 # Scalar arithmetic operations one condensed-history step needs, counted from its
 # formulas (two Philox4x32-10 blocks 200, uniforms 32, range and inverse-range
 # splines 38, cross-section table 9, two voxel-boundary distances 42, Highland
@@ -54,6 +53,8 @@ def parse():
     ap.add_argument("--math", default="fast", choices=["fast", "ieee"], help="headline build")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--train-events", type=int, default=10_000_000)
+    ap.add_argument("--no-gamma", action="store_true")
+    ap.add_argument("--gamma-histories", type=int, default=10_000_000)
     return ap.parse_args()
 
 
@@ -183,6 +184,73 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def gamma_leg(args, device, stream, flush, with_cpu):
+    """The 3-D gamma index (2 %/2 mm, global, 10 % threshold) between two dose maps of the
+    256 x 256 x 160 CT phantom at 1 mm from the engine at two seeds, inside the body (air
+    voxels, HU < -950, set to zero as a body contour would: their dose per mass is not
+    clinical): the device entry point timed with CUDA events on doses already in HBM, the
+    host-array entry point end to end, and the oracle's gamma on a slab of the same maps
+    as the CPU baseline."""
+    import torch
+
+    from paper_1409_8336_gb300 import Engine, GammaIndex, gamma_index
+    from paper_1409_8336_gb300 import workloads as W
+
+    prob = W.config3()
+    eng = Engine(device=device, n_batches=prob.n_batches, fast_math=(args.math == "fast"))
+    eng.load_problem(prob)
+    maps = []
+    body = prob.hu >= -950
+    for seed in (11, 12):
+        eng.transport(args.gamma_histories, seed, stream=stream)
+        maps.append(np.where(body, eng.read_dose()[0].reshape(prob.shape), 0.0))
+    eng.close()
+    ref = torch.from_numpy(maps[0]).to("cuda")
+    ev = torch.from_numpy(maps[1]).to("cuda")
+    g = torch.empty(prob.shape, dtype=torch.float32, device="cuda")
+    gi = GammaIndex(prob.voxel)
+    for _ in range(3):
+        gi(ref, ev, g, stream=stream)
+    ms = []
+    for i in range(10):
+        flush.fill_(float(i))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        gi(ref, ev, g, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    n_eval, n_pass = gi.counts()
+    e2e = []
+    for i in range(4):
+        t0 = time.perf_counter()
+        gamma_index(maps[0], maps[1], prob.voxel)
+        e2e.append(time.perf_counter() - t0)
+    nv = prob.n_voxels
+    out = {"workload": "%s phantom %dx%dx%d at %g mm, %d histories per map, seeds 11 and 12" % (
+               prob.name, *prob.shape[::-1], prob.voxel[0] * 10, args.gamma_histories),
+           "criteria": "2 %/2 mm global, 10 % threshold, search 3 mm, on the grid", "voxels": nv,
+           "evaluated": n_eval, "pass_rate": n_pass / max(n_eval, 1),
+           "ms": statistics.median(ms), "voxels_per_s": nv / (statistics.median(ms) * 1e-3),
+           "e2e_ms": statistics.median(e2e[1:]) * 1e3, "e2e_h2d_bytes": 16 * nv, "e2e_d2h_bytes": 4 * nv + 16,
+           "kernel_bytes": 20 * nv + 8 * n_eval,
+           "kernel_bytes_note": "max pass 8 B/voxel, comparison 8 B/voxel read + 4 B/voxel gamma written + "
+                                "8 B per evaluated voxel of the evaluated grid"}
+    out["achieved_gbs"] = out["kernel_bytes"] / (out["ms"] * 1e-3) / 1e9
+    if with_cpu:
+        from oracle import analysis as A
+
+        sl = slice(prob.shape[0] // 2 - 8, prob.shape[0] // 2 + 8)
+        t0 = time.perf_counter()
+        A.gamma_index(maps[0][sl], maps[1][sl], prob.voxel)
+        dt = time.perf_counter() - t0
+        nsub = maps[0][sl].size
+        out["cpu_baseline"] = {"value": nsub / dt, "unit": "voxels/s", "cores": 1, "kind": "oracle",
+                               "sample": "16 central z-slices (%d voxels) of the same maps in %.2f s" % (nsub, dt)}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -302,7 +370,7 @@ def main():
     # cascade's at the same seed (2 %/2 mm gamma)
     surrogate = None
     if not args.no_surrogate:
-        from oracle import analysis as A
+        from paper_1409_8336_gb300 import gamma_index
 
         t0 = time.perf_counter()
         tr = eng.train_surrogate(n_events=args.train_events, epochs=2, batch=8192, lr=1e-3, seed=4)
@@ -321,15 +389,19 @@ def main():
             b.synchronize()
             sm.append(a.elapsed_time(b))
         eng.transport(n, 77, mode=0, stream=stream)
-        Df, _ = A.batch_stats(eng.read_tally().astype(np.float64) * FIX)
+        Df, _ = eng.read_dose()
         eng.transport(n, 77, mode=1, stream=stream)
-        Ds, _ = A.batch_stats(eng.read_tally().astype(np.float64) * FIX)
-        gam = A.gamma_pass_rate(Df.reshape(prob.shape), Ds.reshape(prob.shape), prob.voxel)
+        Ds, _ = eng.read_dose()
+        _, gam = gamma_index(Df.reshape(prob.shape), Ds.reshape(prob.shape), prob.voxel, want_map=False)
         sval = world * n * args.steps / (sum(sm) / 1e3)
         surrogate = {"value": sval, "unit": UNIT, "ms_per_step": sum(sm) / args.steps, "speedup_vs_full": sval / value,
                      "gamma_2pct_2mm_vs_full": gam, "train_events": args.train_events, "train_seconds": train_s,
                      "train_loss_first_last": [tr["first_loss"], tr["last_loss"]],
                      "network": "MLP 32-256-256-256-256-16, BF16 tensor cores (mma.sync), FP32 accumulate"}
+
+    gamma = None
+    if not args.no_gamma:
+        gamma = gamma_leg(args, local, stream, flush, rank == 0 and world == 1 and not args.no_cpu_baseline)
 
     pk, src = peaks()
     led = ledgers[-1]
@@ -368,6 +440,7 @@ def main():
             "kernels_note": "ms = summed launch durations (the two sub-groups' launches overlap)",
             "math": args.math,
             "surrogate": surrogate,
+            "gamma": gamma,
             "other_build": {"math": "ieee" if args.math == "fast" else "fast",
                             "value": world * n * args.steps / (sum(other_ms) / 1e3),
                             "ms_per_step": sum(other_ms) / args.steps},

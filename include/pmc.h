@@ -236,6 +236,40 @@ int pmc_surrogate_load(pmc_ctx* ctx, const float* params, size_t n);
 int pmc_surrogate_grad(pmc_ctx* ctx, const float* params, const float* x, const float* y, const float* tau,
                        const float* mask, int rows, float* loss, float* grad, float* yhat);
 
+/* ---- 3-D gamma index -------------------------------------------------------
+ * The dose-comparison metric of Sec. II.D (Low et al.), which the paper also
+ * computes on the GPU.  For every reference voxel whose dose exceeds
+ * threshold x max(ref):
+ *   gamma^2 = min over evaluated voxels within search_mm of
+ *             r^2 / dta_mm^2 + (eval - ref)^2 / tol^2,   tol = dose_pct/100 x max(ref)
+ * (global dose criterion, on the grid, no interpolation; FP64).  Doses are
+ * [nz][ny][nx], x fastest, in any unit (both grids the same); voxel sizes in cm.
+ * search_mm <= 0 means 1.5 x dta_mm.  gamma[v] = sqrt(gamma^2) as float, -1 for
+ * voxels not evaluated.  Pass: gamma^2 <= 1 + 1e-12.
+ *
+ * pmc_gamma_plan_bytes: device bytes of a plan for these voxel sizes and distance
+ *   criteria (independent of the grid size).  PMC_E_INVALID if an argument is out
+ *   of range or the search sphere holds more than PMC_GAMMA_MAX_OFFSETS voxels.
+ * pmc_gamma_plan: writes the plan (the search sphere's offsets, sorted) into
+ *   `plan`, caller-owned device memory, 256-byte aligned, plan_bytes long;
+ *   asynchronous on `stream` (cudaStream_t; NULL = legacy default stream).
+ * pmc_gamma_device: compares device-resident grids with a plan, asynchronous on
+ *   `stream`; ref, eval and gamma (may be NULL) are caller-owned device pointers.
+ *   When the stream reaches completion the plan's first 16 bytes hold two uint64:
+ *   voxels evaluated and voxels passing.  Allocates nothing.  A plan serves one
+ *   comparison at a time (order them on one stream).
+ * pmc_gamma_index: the same from host arrays (gamma may be NULL), synchronous,
+ *   with device memory of its own; pass_rate = passed / evaluated (NaN if none). */
+#define PMC_GAMMA_MAX_OFFSETS 65536
+int pmc_gamma_plan_bytes(double dx, double dy, double dz, double dta_mm, double search_mm, size_t* bytes);
+int pmc_gamma_plan(double dx, double dy, double dz, double dta_mm, double search_mm, void* plan, size_t plan_bytes,
+                   void* stream);
+int pmc_gamma_device(void* plan, const double* ref, const double* eval, int nx, int ny, int nz, double dose_pct,
+                     double threshold, float* gamma, void* stream);
+int pmc_gamma_index(const double* ref, const double* eval, int nx, int ny, int nz, double dx, double dy, double dz,
+                    double dose_pct, double dta_mm, double threshold, double search_mm, float* gamma,
+                    double* pass_rate);
+
 /* Device-side evaluation of single routines, for tests.
  * pmc_debug_philox: Philox4x32-10 of n counters ctr[n][4] under key[2]
  *   (Salmon et al., SC'11) into out[n][4].

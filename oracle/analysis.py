@@ -56,19 +56,26 @@ def zscores(Da, sa, Db, sb, frac_of_max=0.1):
     return (Da[m] - Db[m]) / den
 
 
-def gamma_pass_rate(D_ref, D_eval, voxel, dose_pct=2.0, dta_mm=2.0, threshold=0.1, search_mm=None):
-    """Fraction of reference voxels above threshold * max(D_ref) with gamma <= 1.
+def gamma_index(D_ref, D_eval, voxel, dose_pct=2.0, dta_mm=2.0, threshold=0.1, search_mm=None):
+    """3-D gamma index of D_eval against D_ref (Low et al.), the comparison of Sec. II.D.
 
-    D_ref, D_eval: [nz, ny, nx]; voxel: (dx, dy, dz) in cm.  Global criterion:
-    dose tolerance = dose_pct % of max(D_ref).  Gamma^2 = min over evaluated voxels within
-    the search radius of (r^2 / dta^2 + dD^2 / tol^2)."""
+    D_ref, D_eval: [nz, ny, nx]; voxel: (dx, dy, dz) in cm.  Global criterion: the dose
+    tolerance is dose_pct % of max(D_ref).  For every reference voxel above
+    threshold * max(D_ref), gamma^2 = min over evaluated voxels within the search radius
+    (default 1.5 dta) of r^2 / dta^2 + (D_eval - D_ref)^2 / tol^2, on the grid without
+    interpolation.  Returns (gamma^2 per voxel, inf where not evaluated; the mask of
+    evaluated voxels)."""
     D_ref = np.asarray(D_ref, dtype=np.float64)
     D_eval = np.asarray(D_eval, dtype=np.float64)
     dx, dy, dz = (v * 10.0 for v in voxel)  # mm
     tol = dose_pct / 100.0 * D_ref.max()
     search = 1.5 * dta_mm if search_mm is None else search_mm
-    nx_, ny_, nz_ = int(search // dx), int(search // dy), int(search // dz)
+    # every voxel within the search sphere lies inside this box
+    nx_, ny_, nz_ = (int(search // d) + 1 for d in (dx, dy, dz))
     g2 = np.full(D_ref.shape, np.inf)
+    m = D_ref > threshold * D_ref.max()
+    if not m.any():
+        return g2, m
     nz, ny, nx = D_ref.shape
     for kz in range(-nz_, nz_ + 1):
         for ky in range(-ny_, ny_ + 1):
@@ -79,10 +86,25 @@ def gamma_pass_rate(D_ref, D_eval, voxel, dose_pct=2.0, dta_mm=2.0, threshold=0.
                 zs, ze = max(0, -kz), min(nz, nz - kz)
                 ys, ye = max(0, -ky), min(ny, ny - ky)
                 xs, xe = max(0, -kx), min(nx, nx - kx)
+                if zs >= ze or ys >= ye or xs >= xe:
+                    continue
                 ref = D_ref[zs:ze, ys:ye, xs:xe]
                 ev = D_eval[zs + kz:ze + kz, ys + ky:ye + ky, xs + kx:xe + kx]
                 val = r2 / dta_mm ** 2 + (ev - ref) ** 2 / tol ** 2
                 sub = g2[zs:ze, ys:ye, xs:xe]
                 np.minimum(sub, val, out=sub)
-    m = D_ref > threshold * D_ref.max()
-    return float(np.mean(g2[m] <= 1.0 + 1e-12))
+    g2[~m] = np.inf
+    return g2, m
+
+
+def gamma_passes(g2):
+    """The pass decision gamma <= 1, with the 1e-12 allowance both implementations use."""
+    return g2 <= 1.0 + 1e-12
+
+
+def gamma_pass_rate(D_ref, D_eval, voxel, dose_pct=2.0, dta_mm=2.0, threshold=0.1, search_mm=None):
+    """Fraction of evaluated reference voxels with gamma <= 1 (NaN if none is evaluated)."""
+    g2, m = gamma_index(D_ref, D_eval, voxel, dose_pct, dta_mm, threshold, search_mm)
+    if not m.any():
+        return float("nan")
+    return float(np.mean(gamma_passes(g2[m])))

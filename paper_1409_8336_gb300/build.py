@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libpmc.so")
 # -use_fast_math (hardware approximations of division, sqrt, log, exp, sin/cos),
 # the build option the method's authors timed and verified equivalent.
 VARIANTS = {"libpmc.so": [], "libpmc_fast.so": ["-use_fast_math"]}
-SOURCES = ["transport.cu", "cascade.cu", "stats.cu", "surrogate.cu", "host.cu"]
+SOURCES = ["transport.cu", "cascade.cu", "stats.cu", "surrogate.cu", "gamma.cu", "host.cu"]
 HEADERS = ["pmc_device.cuh", "pmc_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -32,8 +32,10 @@ def nvcc() -> str:
 
 
 def flags(extra=()):
-    return [*ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-            *extra]
+    # host FP64 (physics tables, gamma offsets) must not be contracted into FMAs: the
+    # aarch64 and x86-64 builds then give identical tables
+    return [*ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I",
+            os.path.join(ROOT, "include"), *extra]
 
 
 def _stale(obj: str, src: str) -> bool:

@@ -263,7 +263,7 @@ struct pmc_ctx {
   DevBuf d_sp, d_sg, d_sm, d_sv;        // parameters, gradients, Adam moments
   DevBuf d_swb;                         // BF16 copy of the parameters for inference
   DevBuf d_slot_nuc, d_nuc_slot;        // slot -> nuclide, nuclide -> slot
-  DevBuf d_sx[2], d_sh[2][2], d_sy[2][2];   // inference rows and activations, per stream
+  DevBuf d_sx[2], d_sy[2][2];   // inference rows and outputs, per stream
   size_t surr_cap = 0;
   int mode = PMC_FULL_CASCADE;          // mode of the captured graph
   // graph
@@ -395,8 +395,8 @@ void pmc_destroy(pmc_ctx* ctx) {
                     &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_hist, &ctx->d_esc};
   for (DevBuf* b : bufs) dfree(ctx, *b);
   DevBuf* sbufs[] = {&ctx->d_swb, &ctx->d_sp, &ctx->d_sg, &ctx->d_sm, &ctx->d_sv, &ctx->d_slot_nuc, &ctx->d_nuc_slot,
-                     &ctx->d_sx[0], &ctx->d_sx[1], &ctx->d_sh[0][0], &ctx->d_sh[0][1], &ctx->d_sh[1][0],
-                     &ctx->d_sh[1][1], &ctx->d_sy[0][0], &ctx->d_sy[0][1], &ctx->d_sy[1][0], &ctx->d_sy[1][1]};
+                     &ctx->d_sx[0], &ctx->d_sx[1], &ctx->d_sy[0][0], &ctx->d_sy[0][1], &ctx->d_sy[1][0],
+                     &ctx->d_sy[1][1]};
   for (DevBuf* b : sbufs) dfree(ctx, *b);
   cudaStreamDestroy(ctx->stream);
   cudaStreamDestroy(ctx->stream2);
@@ -776,12 +776,10 @@ int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int sour
   if (ctx->mode == PMC_SURROGATE) {
     const int si = (qne == static_cast<Particle*>(ctx->d_q[5].p)) ? 1 : 0;   // which stream's buffers
     float* X = static_cast<float*>(ctx->d_sx[si].p);
-    float* H[2] = {static_cast<float*>(ctx->d_sh[si][0].p), static_cast<float*>(ctx->d_sh[si][1].p)};
     float* Y1 = static_cast<float*>(ctx->d_sy[si][0].p);
     float* Y2 = static_cast<float*>(ctx->d_sy[si][1].p);
     const float* P = static_cast<const float*>(ctx->d_sp.p);
     const unsigned cap = static_cast<unsigned>(ctx->q_cap);
-    (void)H;
     const int grid = ctx->n_sm * 2;
     if ((rc = mark(ctx, s, 2))) return rc;
     CK(launch_infer_rows(qne_count, cap, qne, static_cast<const int*>(ctx->d_nuc_slot.p), a.seed, X, s));
@@ -1621,3 +1619,122 @@ int pmc_surrogate_grad(pmc_ctx* ctx, const float* params, const float* x, const 
 }
 
 }  // extern "C"
+
+// ---- 3-D gamma index (Sec. II.D; Low et al.) --------------------------------
+namespace {
+
+bool gamma_args_ok(double dx, double dy, double dz, double dta_mm, double search_mm) {
+  return dx > 0 && dy > 0 && dz > 0 && dta_mm > 0 && std::isfinite(dx) && std::isfinite(dy) && std::isfinite(dz) &&
+         std::isfinite(dta_mm) && std::isfinite(search_mm);
+}
+
+// Offsets of the search sphere (voxel sizes in cm, radii in mm), sorted by their
+// distance term so that a voxel's scan can stop early.
+int gamma_offsets(double dx_cm, double dy_cm, double dz_cm, double dta_mm, double search_mm,
+                  std::vector<GammaOffset>* out) {
+  if (!gamma_args_ok(dx_cm, dy_cm, dz_cm, dta_mm, search_mm)) return PMC_E_INVALID;
+  const double dx = dx_cm * 10.0, dy = dy_cm * 10.0, dz = dz_cm * 10.0;
+  const double search = search_mm > 0 ? search_mm : 1.5 * dta_mm;
+  const double kxm = std::floor(search / dx) + 1, kym = std::floor(search / dy) + 1, kzm = std::floor(search / dz) + 1;
+  if (kxm * kym * kzm > 8.0 * PMC_GAMMA_MAX_OFFSETS) return PMC_E_INVALID;
+  const int mx = static_cast<int>(kxm), my = static_cast<int>(kym), mz = static_cast<int>(kzm);
+  out->clear();
+  for (int kz = -mz; kz <= mz; ++kz)
+    for (int ky = -my; ky <= my; ++ky)
+      for (int kx = -mx; kx <= mx; ++kx) {
+        const double ax = kx * dx, ay = ky * dy, az = kz * dz;
+        const double r2 = ax * ax + ay * ay + az * az;
+        if (r2 > search * search) continue;
+        if (out->size() >= static_cast<size_t>(PMC_GAMMA_MAX_OFFSETS)) return PMC_E_INVALID;
+        GammaOffset o{};
+        o.kx = static_cast<int16_t>(kx);
+        o.ky = static_cast<int16_t>(ky);
+        o.kz = static_cast<int16_t>(kz);
+        o.r_term = r2 / (dta_mm * dta_mm);
+        out->push_back(o);
+      }
+  std::stable_sort(out->begin(), out->end(),
+                   [](const GammaOffset& a, const GammaOffset& b) { return a.r_term < b.r_term; });
+  return PMC_OK;
+}
+
+}  // namespace
+
+extern "C" int pmc_gamma_plan_bytes(double dx, double dy, double dz, double dta_mm, double search_mm, size_t* bytes) {
+  if (!bytes) return PMC_E_INVALID;
+  std::vector<GammaOffset> off;
+  const int rc = gamma_offsets(dx, dy, dz, dta_mm, search_mm, &off);
+  if (rc != PMC_OK) return rc;
+  *bytes = kGammaHeadBytes + off.size() * sizeof(GammaOffset);
+  return PMC_OK;
+}
+
+extern "C" int pmc_gamma_plan(double dx, double dy, double dz, double dta_mm, double search_mm, void* plan,
+                              size_t plan_bytes, void* stream) {
+  if (!plan || (reinterpret_cast<uintptr_t>(plan) & 255u) != 0) return PMC_E_INVALID;
+  std::vector<GammaOffset> off;
+  const int rc = gamma_offsets(dx, dy, dz, dta_mm, search_mm, &off);
+  if (rc != PMC_OK) return rc;
+  const size_t bytes = kGammaHeadBytes + off.size() * sizeof(GammaOffset);
+  if (plan_bytes < bytes) return PMC_E_INVALID;
+  std::vector<unsigned char> host(bytes, 0);
+  GammaHead head{};
+  head.n_off = static_cast<int>(off.size());
+  head.dx = dx * 10.0;
+  head.dy = dy * 10.0;
+  head.dz = dz * 10.0;
+  head.dta = dta_mm;
+  head.search = search_mm > 0 ? search_mm : 1.5 * dta_mm;
+  std::memcpy(host.data(), &head, sizeof(head));
+  std::memcpy(host.data() + kGammaHeadBytes, off.data(), off.size() * sizeof(GammaOffset));
+  // pageable source: the copy is staged before the call returns, so `host` may go
+  if (cudaMemcpyAsync(plan, host.data(), bytes, cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return PMC_E_CUDA;
+  return PMC_OK;
+}
+
+extern "C" int pmc_gamma_device(void* plan, const double* ref, const double* eval, int nx, int ny, int nz,
+                                double dose_pct, double threshold, float* gamma, void* stream) {
+  if (!plan || !ref || !eval || nx < 1 || ny < 1 || nz < 1 || !(dose_pct > 0) || !(threshold >= 0) ||
+      !std::isfinite(dose_pct) || !std::isfinite(threshold) || (reinterpret_cast<uintptr_t>(plan) & 255u) != 0 ||
+      static_cast<double>(nx) * ny * nz > 9.0e18)
+    return PMC_E_INVALID;
+  if (launch_gamma(ref, eval, nx, ny, nz, plan, dose_pct, threshold, gamma, static_cast<cudaStream_t>(stream)) !=
+      cudaSuccess)
+    return PMC_E_CUDA;
+  return PMC_OK;
+}
+
+extern "C" int pmc_gamma_index(const double* ref, const double* eval, int nx, int ny, int nz, double dx, double dy,
+                               double dz, double dose_pct, double dta_mm, double threshold, double search_mm,
+                               float* gamma, double* pass_rate) {
+  if (!ref || !eval || nx < 1 || ny < 1 || nz < 1) return PMC_E_INVALID;
+  size_t pb = 0;
+  int rc = pmc_gamma_plan_bytes(dx, dy, dz, dta_mm, search_mm, &pb);
+  if (rc != PMC_OK) return rc;
+  const size_t n = static_cast<size_t>(nx) * ny * nz;
+  void *dr = nullptr, *de = nullptr, *dg = nullptr, *dp = nullptr;
+  if (cudaMalloc(&dr, n * 8) != cudaSuccess || cudaMalloc(&de, n * 8) != cudaSuccess ||
+      (gamma && cudaMalloc(&dg, n * 4) != cudaSuccess) || cudaMalloc(&dp, pb) != cudaSuccess) {
+    rc = PMC_E_OOM;
+  } else if (cudaMemcpy(dr, ref, n * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(de, eval, n * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+    rc = PMC_E_CUDA;
+  } else {
+    rc = pmc_gamma_plan(dx, dy, dz, dta_mm, search_mm, dp, pb, nullptr);
+    if (rc == PMC_OK)
+      rc = pmc_gamma_device(dp, static_cast<const double*>(dr), static_cast<const double*>(de), nx, ny, nz, dose_pct,
+                            threshold, static_cast<float*>(dg), nullptr);
+    unsigned long long c[2] = {0, 0};
+    if (rc == PMC_OK && (cudaStreamSynchronize(nullptr) != cudaSuccess ||
+                         cudaMemcpy(c, dp, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                         (gamma && cudaMemcpy(gamma, dg, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess)))
+      rc = PMC_E_CUDA;
+    if (rc == PMC_OK && pass_rate) *pass_rate = c[0] ? static_cast<double>(c[1]) / static_cast<double>(c[0]) : NAN;
+  }
+  cudaFree(dr);
+  cudaFree(de);
+  cudaFree(dg);
+  cudaFree(dp);
+  return rc;
+}

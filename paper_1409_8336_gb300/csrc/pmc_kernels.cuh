@@ -110,6 +110,30 @@ cudaError_t launch_infer_emit(const unsigned* n_ev, unsigned cap, const Particle
                               unsigned* qsec_count, unsigned qsec_cap, Counters* cnt, long long* hist,
                               unsigned long long hist_n, cudaStream_t s);
 
+// Gamma plan in device memory: this head, then at kGammaHeadBytes the offsets of the
+// search sphere sorted by their distance term.
+struct GammaHead {
+  unsigned long long n_eval, n_pass;  // written by each comparison
+  unsigned long long max_key;         // max(ref) as an order-preserving integer
+  unsigned long long work;            // next chunk of voxels to claim
+  int n_off;                          // written by the plan
+  int pad;
+  double dx, dy, dz, dta, search;     // what the plan was made for (mm)
+};
+constexpr size_t kGammaHeadBytes = 256;
+static_assert(sizeof(GammaHead) <= kGammaHeadBytes, "gamma head fits");
+
+// One neighbour offset of the gamma search sphere: voxel steps and the distance
+// term |r|^2 / dta^2 (FP64), 16 bytes.
+struct alignas(16) GammaOffset {
+  int16_t kx, ky, kz, pad;
+  double r_term;
+};
+static_assert(sizeof(GammaOffset) == 16, "gamma offset layout");
+
+cudaError_t launch_gamma(const double* ref, const double* ev, int nx, int ny, int nz, void* plan, double dose_pct,
+                         double threshold, float* gamma, cudaStream_t s);
+
 // debug entry points
 cudaError_t launch_debug_philox(const uint4* ctr, uint2 key, uint4* out, int n, cudaStream_t s);
 cudaError_t launch_debug_tables(const Physics* ph, const float2* rt, const float2* et, int cls, const double* E,

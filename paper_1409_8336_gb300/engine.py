@@ -28,7 +28,9 @@ EXPORTS = [
     "pmc_clear_spots", "pmc_transport", "pmc_read_dose", "pmc_read_tally", "pmc_read_ledger",
     "pmc_enable_history_ledger", "pmc_read_history_ledger", "pmc_enable_escape_record", "pmc_read_escape_record",
     "pmc_set_launch", "pmc_autotune", "pmc_transport_noalloc", "pmc_surrogate_dataset", "pmc_train_surrogate",
-    "pmc_surrogate_params", "pmc_surrogate_load", "pmc_surrogate_grad", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables", "pmc_debug_inc", "pmc_debug_elastic",
+    "pmc_surrogate_params", "pmc_surrogate_load", "pmc_surrogate_grad", "pmc_gamma_plan_bytes", "pmc_gamma_plan", "pmc_gamma_device",
+    "pmc_gamma_index", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables",
+    "pmc_debug_inc", "pmc_debug_elastic",
 ]
 
 AllocFn = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -115,6 +117,10 @@ def lib(path: str = LIB_PATH):
             L.pmc_surrogate_params.argtypes = [vp, pf, C.c_size_t]
             L.pmc_surrogate_load.argtypes = [vp, pf, C.c_size_t]
             L.pmc_surrogate_grad.argtypes = [vp, pf, pf, pf, pf, pf, i, pf, pf, pf]
+            L.pmc_gamma_plan_bytes.argtypes = [d, d, d, d, d, C.POINTER(C.c_size_t)]
+            L.pmc_gamma_plan.argtypes = [d, d, d, d, d, vp, C.c_size_t, vp]
+            L.pmc_gamma_device.argtypes = [vp, vp, vp, i, i, i, d, d, vp, vp]
+            L.pmc_gamma_index.argtypes = [pd, pd, i, i, i, d, d, d, d, d, d, d, pf, pd]
             L.pmc_transport_noalloc.argtypes = [vp, u64, u64, vp, vp, vp, vp]
             L.pmc_enable_profile.argtypes = [vp, i]
             L.pmc_read_profile.argtypes = [vp, pd, pi64, pi64]
@@ -376,6 +382,75 @@ class Engine:
         out = np.empty((len(u), 5))
         self._check(self._L.pmc_debug_elastic(self._ctx, nuclide, E, _dp(u), _dp(out), len(u)))
         return out
+
+
+def gamma_index(ref, ev, voxel, dose_pct=2.0, dta_mm=2.0, threshold=0.1, search_mm=0.0, fast_math=False,
+                want_map=True):
+    """3-D gamma index on the GPU from host arrays (global criterion, on the grid).
+    ref, ev: [nz, ny, nx] doses; voxel (dx, dy, dz) in cm; search_mm 0 means 1.5 dta.
+    Returns (gamma per voxel as float32, -1 where not evaluated, or None; pass rate)."""
+    ref = np.ascontiguousarray(ref, dtype=np.float64)
+    ev = np.ascontiguousarray(ev, dtype=np.float64)
+    if ref.ndim != 3 or ev.shape != ref.shape:
+        raise ValueError("ref and ev must be [nz, ny, nx] arrays of one shape")
+    nz, ny, nx = ref.shape
+    g = np.empty(ref.shape, dtype=np.float32) if want_map else None
+    rate = C.c_double(0.0)
+    rc = lib(LIB_FAST_PATH if fast_math else LIB_PATH).pmc_gamma_index(
+        _dp(ref), _dp(ev), nx, ny, nz, voxel[0], voxel[1], voxel[2], dose_pct, dta_mm, threshold, search_mm,
+        _fp(g) if want_map else None, C.byref(rate))
+    if rc != PMC_OK:
+        raise PmcError(rc, "pmc_gamma_index failed")
+    return g, rate.value
+
+
+class GammaIndex:
+    """3-D gamma index of device-resident doses (torch CUDA tensors of float64, [nz, ny, nx]),
+    asynchronous on a stream.  The plan (the sorted search sphere) is made once per voxel
+    size and distance criteria."""
+
+    def __init__(self, voxel, dose_pct=2.0, dta_mm=2.0, threshold=0.1, search_mm=0.0, fast_math=False,
+                 stream=None):
+        import torch
+
+        self.L = lib(LIB_FAST_PATH if fast_math else LIB_PATH)
+        self.voxel = tuple(float(v) for v in voxel)
+        self.dose_pct, self.threshold = dose_pct, threshold
+        nb = C.c_size_t(0)
+        rc = self.L.pmc_gamma_plan_bytes(*self.voxel, dta_mm, search_mm, C.byref(nb))
+        if rc != PMC_OK:
+            raise PmcError(rc, "pmc_gamma_plan_bytes failed")
+        self.plan_bytes = nb.value
+        self.buf = torch.empty((nb.value + 255) // 8 + 32, dtype=torch.float64, device="cuda")
+        self.plan = (self.buf.data_ptr() + 255) // 256 * 256
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc = self.L.pmc_gamma_plan(*self.voxel, dta_mm, search_mm, self.plan, self.plan_bytes, s.cuda_stream)
+        if rc != PMC_OK:
+            raise PmcError(rc, "pmc_gamma_plan failed")
+
+    def __call__(self, ref, ev, gamma=None, stream=None):
+        """Launches on `stream` (torch stream or None for the current one).  counts() then
+        gives (evaluated, passed) once the stream has reached it."""
+        import torch
+
+        assert ref.is_cuda and ev.is_cuda and ref.dtype == torch.float64 and ev.dtype == torch.float64
+        assert ref.is_contiguous() and ev.is_contiguous() and ref.shape == ev.shape and ref.dim() == 3
+        if gamma is not None:
+            assert gamma.is_cuda and gamma.dtype == torch.float32 and gamma.is_contiguous()
+            assert gamma.shape == ref.shape
+        nz, ny, nx = ref.shape
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc = self.L.pmc_gamma_device(self.plan, ref.data_ptr(), ev.data_ptr(), nx, ny, nz, self.dose_pct,
+                                     self.threshold, gamma.data_ptr() if gamma is not None else None, s.cuda_stream)
+        if rc != PMC_OK:
+            raise PmcError(rc, "pmc_gamma_device failed")
+
+    def counts(self):
+        import torch
+
+        off = (self.plan - self.buf.data_ptr()) // 8
+        c = self.buf[off:off + 2].view(torch.int64).cpu().numpy()
+        return int(c[0]), int(c[1])
 
 
 def debug_philox(ctr, key, fast_math=False):

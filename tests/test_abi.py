@@ -61,3 +61,36 @@ def test_oracle_and_engine_share_no_code():
     for f in ("oracle.c", "oracle.py"):
         text = open(os.path.join(ROOT, "oracle", f)).read()
         assert "paper_1409_8336_gb300" not in text and "pmc_device" not in text
+
+
+def test_gamma_plan_counts_the_search_sphere(libpmc):
+    """Host logic of the gamma entry points (no device call): a plan holds a 256-byte head
+    and 16 bytes per voxel offset within the search sphere; bad arguments are refused."""
+    d = ctypes.c_double
+    libpmc.pmc_gamma_plan_bytes.argtypes = [d, d, d, d, d, ctypes.POINTER(ctypes.c_size_t)]
+    nb = ctypes.c_size_t(0)
+    for voxel, dta, search in (((0.1, 0.1, 0.1), 2.0, 0.0), ((0.125, 0.125, 0.25), 2.0, 0.0),
+                               ((0.05, 0.1, 0.2), 3.0, 5.0)):
+        assert libpmc.pmc_gamma_plan_bytes(*voxel, dta, search, ctypes.byref(nb)) == 0
+        r = search if search > 0 else 1.5 * dta
+        h = [v * 10.0 for v in voxel]
+        m = [int(r // x) + 1 for x in h]
+        count = sum(1 for i in range(-m[0], m[0] + 1) for j in range(-m[1], m[1] + 1) for k in range(-m[2], m[2] + 1)
+                    if (i * h[0]) ** 2 + (j * h[1]) ** 2 + (k * h[2]) ** 2 <= r * r)
+        assert nb.value == 256 + 16 * count
+    assert libpmc.pmc_gamma_plan_bytes(0.1, 0.1, 0.1, 2.0, 0.0, None) == -1
+    assert libpmc.pmc_gamma_plan_bytes(0.1, -0.1, 0.1, 2.0, 0.0, ctypes.byref(nb)) == -1
+    assert libpmc.pmc_gamma_plan_bytes(0.1, 0.1, 0.1, 0.0, 0.0, ctypes.byref(nb)) == -1
+    assert libpmc.pmc_gamma_plan_bytes(0.001, 0.001, 0.001, 2.0, 30.0, ctypes.byref(nb)) == -1   # sphere too large
+    vp, i = ctypes.c_void_p, ctypes.c_int
+    libpmc.pmc_gamma_plan.argtypes = [d, d, d, d, d, vp, ctypes.c_size_t, vp]
+    libpmc.pmc_gamma_device.argtypes = [vp, vp, vp, i, i, i, d, d, vp, vp]
+    # refused before any device call: no plan memory, a misaligned or short plan, NULL doses,
+    # an empty grid, a non-positive dose criterion
+    assert libpmc.pmc_gamma_plan(0.1, 0.1, 0.1, 2.0, 0.0, None, 4096, None) == -1
+    assert libpmc.pmc_gamma_plan(0.1, 0.1, 0.1, 2.0, 0.0, 260, 4096, None) == -1
+    assert libpmc.pmc_gamma_plan(0.1, 0.1, 0.1, 2.0, 0.0, 256, 512, None) == -1
+    assert libpmc.pmc_gamma_device(256, None, None, 4, 4, 4, 2.0, 0.1, None, None) == -1
+    assert libpmc.pmc_gamma_device(256, 512, 1024, 0, 4, 4, 2.0, 0.1, None, None) == -1
+    assert libpmc.pmc_gamma_device(260, 512, 1024, 4, 4, 4, 2.0, 0.1, None, None) == -1
+    assert libpmc.pmc_gamma_device(256, 512, 1024, 4, 4, 4, 0.0, 0.1, None, None) == -1
