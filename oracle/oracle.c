@@ -31,6 +31,9 @@
  *   Sec. II.A.5  coherent nuclear elastic scattering, Ranft dsigma/dOmega (Eq. 3),
  *                relativistic two-body kinematics
  *   Sec. II.B.2  ten groups of N/10 protons for the statistical error
+ *   Sec. IV      dose-averaged LET scored beside the dose (proton energy losses
+ *                weighted by the mean stopping power of the local medium over
+ *                the path of each loss; recoil nuclei and fragments excluded)
  *
  * Parity status: every routine here is pinned by the CPU tests (closed forms,
  * conservation laws, brute-force tallies, published reference values).
@@ -827,6 +830,8 @@ typedef struct {
     or_totals* tot;
     double* esc;                     /* escaping protons [cap][8]: E, x, y, z, u, v, w, root */
     long esc_cap, esc_n;
+    double* let_num;                 /* [V][B] sum of e * L (MeV keV/um) over proton energy losses, or NULL */
+    double* let_den;                 /* [V][B] sum of e (MeV) over the same deposits */
 } or_ctx;
 
 typedef struct { double x[3], d[3], E, nmfp; int iv[3]; uint64_t pid; uint64_t root; } or_particle;
@@ -862,6 +867,18 @@ static void deposit(or_ctx* c, const int iv[3], uint64_t root, double e)
     c->tally[v * P->n_batches + (long)(root % (uint64_t)P->n_batches)] += e;
     c->tot->deposited += e;
     if (c->hl) c->hl[root * 4 + 1] += e;
+}
+/* Dose-averaged LET (Sec. IV): each energy loss e of a transported proton, with the
+ * mean CSDA stopping power L of the local medium over the path that lost it (MeV/cm,
+ * scored in keV/um = 0.1 MeV/cm).  Recoil nuclei and fragments do not score. */
+static void score_let(or_ctx* c, const int iv[3], uint64_t root, double e, double L_mev_cm)
+{
+    if (!c->let_num) return;
+    const or_problem* P = c->P;
+    long v = ((long)iv[2] * P->ny + iv[1]) * P->nx + iv[0];
+    long i = v * P->n_batches + (long)(root % (uint64_t)P->n_batches);
+    c->let_num[i] += e * (0.1 * L_mev_cm);
+    c->let_den[i] += e;
 }
 static void escape(or_ctx* c, uint64_t root, double e)
 {
@@ -956,7 +973,17 @@ static void transport_one(or_ctx* c, or_particle* p, or_pstack* st)
     const int dims[3] = {P->nx, P->ny, P->nz};
     uint32_t k = 0;
     for (;;) {
-        if (p->E <= E_CUT) { deposit(c, p->iv, p->root, p->E); return; }
+        if (p->E <= E_CUT) {
+            deposit(c, p->iv, p->root, p->E);
+            if (c->let_num && p->E > 0.0) {   /* absorbed over its residual range */
+                int m0; double rho0;
+                voxel_props(c, p->iv, &m0, &rho0);
+                const or_matinfo* m0i = &c->mi[m0];
+                double R0 = range_of_energy(&c->tables[m0i->cls], p->E) / (rho0 * m0i->f);
+                if (R0 > 0.0) score_let(c, p->iv, p->root, p->E, p->E / R0);
+            }
+            return;
+        }
         if (k >= 100000u) { deposit(c, p->iv, p->root, p->E); c->tot->errors += 1.0; return; }
         int m; double rho;
         voxel_props(c, p->iv, &m, &rho);
@@ -973,7 +1000,11 @@ static void transport_one(or_ctx* c, or_particle* p, or_pstack* st)
         int axis;
         double d = voxel_exit(P, p->x, p->d, p->iv, &axis);
         c->tot->steps += 1.0;
-        if (Rcm <= lam && Rcm <= d) { deposit(c, p->iv, p->root, E0); return; }
+        if (Rcm <= lam && Rcm <= d) {
+            deposit(c, p->iv, p->root, E0);
+            if (Rcm > 0.0) score_let(c, p->iv, p->root, E0, E0 / Rcm);
+            return;
+        }
         int nuclear = (lam <= d);
         double dx = nuclear ? lam : d;
         double ua[5];
@@ -997,6 +1028,7 @@ static void transport_one(or_ctx* c, or_particle* p, or_pstack* st)
         for (int a = 0; a < 3; ++a) p->x[a] = x1[a] + L2 * p->d[a];
         double Rleft = Rm - s * rf;
         double dE = (Rleft > 0.0) ? E0 - energy_of_range(rt, Rleft) : E0;
+        const double L_step = s > 0.0 ? dE / s : 0.0;     /* mean CSDA stopping power over the path */
         if (!(P->flags & OR_NO_STRAGGLING)) {
             double var = or_bohr_variance(E0, rho, mi->ZA, s);
             dE += sqrt(var) * sqrt(-2.0 * log(ua[2])) * cos(TWO_PI * ua[3]);
@@ -1004,6 +1036,7 @@ static void transport_one(or_ctx* c, or_particle* p, or_pstack* st)
         if (dE < 0.0) dE = 0.0;
         if (dE > E0) dE = E0;
         deposit(c, p->iv, p->root, dE);
+        score_let(c, p->iv, p->root, dE, L_step);
         p->E = E0 - dE;
         p->nmfp -= sig * s;
         ++k;
@@ -1116,15 +1149,18 @@ int or_material_info(const or_problem* P, int m, double* out /* ZA, I, f, X0mass
 }
 
 /* Runs histories [h_begin, h_end) of an n_hist-history simulation. */
-int or_run_esc(const or_problem* P, uint64_t n_hist, uint64_t h_begin, uint64_t h_end, uint64_t seed,
-               double* tally, double* hist_ledger, or_totals* tot, double* esc, long esc_cap, long* esc_n)
+int or_run_full(const or_problem* P, uint64_t n_hist, uint64_t h_begin, uint64_t h_end, uint64_t seed,
+                double* tally, double* hist_ledger, or_totals* tot, double* esc, long esc_cap, long* esc_n,
+                double* let_num, double* let_den)
 {
     if (!P || P->n_mat < 1 || P->n_spots < 1 || P->n_batches < 1) return -1;
+    if ((let_num == NULL) != (let_den == NULL)) return -1;
     or_ctx c;
     memset(&c, 0, sizeof(c));
     memset(tot, 0, sizeof(*tot));
     c.P = P; c.seed = seed; c.tally = tally; c.hl = hist_ledger; c.tot = tot;
     c.esc = esc; c.esc_cap = esc_cap; c.esc_n = 0;
+    c.let_num = let_num; c.let_den = let_den;
     c.mi = (or_matinfo*)calloc(P->n_mat, sizeof(or_matinfo));
     c.tables = (or_range_table*)calloc(P->n_mat + 1, sizeof(or_range_table));
     int ncls = 1;
@@ -1183,6 +1219,12 @@ int or_run_esc(const or_problem* P, uint64_t n_hist, uint64_t h_begin, uint64_t 
     free(st.a); free(cnt); free(c.nuclei); free(c.tables); free(c.mi);
     if (esc_n) *esc_n = c.esc_n;
     return 0;
+}
+
+int or_run_esc(const or_problem* P, uint64_t n_hist, uint64_t h_begin, uint64_t h_end, uint64_t seed,
+               double* tally, double* hist_ledger, or_totals* tot, double* esc, long esc_cap, long* esc_n)
+{
+    return or_run_full(P, n_hist, h_begin, h_end, seed, tally, hist_ledger, tot, esc, esc_cap, esc_n, NULL, NULL);
 }
 
 int or_run(const or_problem* P, uint64_t n_hist, uint64_t h_begin, uint64_t h_end, uint64_t seed,

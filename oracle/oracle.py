@@ -108,6 +108,8 @@ def lib():
             L.or_run.argtypes = [C.POINTER(OrProblem), u64, u64, u64, u64, pd, pd, C.POINTER(OrTotals)]
             L.or_run_esc.argtypes = [C.POINTER(OrProblem), u64, u64, u64, u64, pd, pd, C.POINTER(OrTotals),
                                      pd, C.c_long, C.POINTER(C.c_long)]
+            L.or_run_full.argtypes = [C.POINTER(OrProblem), u64, u64, u64, u64, pd, pd, C.POINTER(OrTotals),
+                                      pd, C.c_long, C.POINTER(C.c_long), pd, pd]
             L.or_evap_batch.argtypes = [i, i, d, u64, u64, i, pd]
             L.or_inc_batch.argtypes = [i, i, d, u64, u64, i, i, pd, pd, pd]
             L.or_nucleus_info.argtypes = [i, i, pd]
@@ -189,36 +191,64 @@ _PROBLEM_FIELDS = ("nuclides", "materials", "hu_bins", "spots", "shape", "voxel"
                    "n_batches", "flags")
 
 
+def run_let(prob, n_hist: int, seed: int, h_begin: int = 0, h_end: int | None = None):
+    """Runs the oracle with dose-averaged LET scoring.  Returns (tally[V, B] MeV,
+    let_num[V, B] MeV keV/um, let_den[V, B] MeV, totals dict): LET_d = sum num / sum den."""
+    L = lib()
+    m = _Marshalled(prob)
+    nv = int(np.prod(prob.shape))
+    tally = np.zeros((nv, prob.n_batches), dtype=np.float64)
+    num = np.zeros_like(tally)
+    den = np.zeros_like(tally)
+    tot = OrTotals()
+    h_end = n_hist if h_end is None else h_end
+    rc = L.or_run_full(C.byref(m.P), n_hist, h_begin, h_end, seed, _dp(tally), None, C.byref(tot), None, 0, None,
+                       _dp(num), _dp(den))
+    if rc != 0:
+        raise RuntimeError("oracle run failed (%d)" % rc)
+    return tally, num, den, {k: getattr(tot, k) for k, _ in OrTotals._fields_}
+
+
 def _run_range(job):
     import types
 
-    fields, n_hist, seed, h0, h1 = job
-    tally, tot, _ = run(types.SimpleNamespace(**fields), n_hist, seed, h_begin=h0, h_end=h1)
+    fields, n_hist, seed, h0, h1, let = job
+    prob = types.SimpleNamespace(**fields)
+    if let:
+        tally, num, den, tot = run_let(prob, n_hist, seed, h_begin=h0, h_end=h1)
+        return tally, tot, num, den
+    tally, tot, _ = run(prob, n_hist, seed, h_begin=h0, h_end=h1)
     return tally, tot
 
 
-def run_parallel(prob, n_hist: int, seed: int, procs: int | None = None):
-    """The same computation as run(), split over history ranges in spawned worker processes
-    (each range is an independent set of histories; tallies are summed in range order)."""
+def run_parallel(prob, n_hist: int, seed: int, procs: int | None = None, let: bool = False):
+    """The same computation as run() (run_let() with let=True), split over history ranges in
+    spawned worker processes (each range is an independent set of histories; tallies are
+    summed in range order).  Returns (tally, totals) or (tally, totals, let_num, let_den)."""
     import multiprocessing as mp
 
     procs = procs or os.cpu_count() or 1
     procs = max(1, min(procs, n_hist // 200 or 1))
     fields = {k: getattr(prob, k) for k in _PROBLEM_FIELDS}
     cuts = [n_hist * i // procs for i in range(procs + 1)]
-    jobs = [(fields, n_hist, seed, cuts[i], cuts[i + 1]) for i in range(procs)]
+    jobs = [(fields, n_hist, seed, cuts[i], cuts[i + 1], let) for i in range(procs)]
     if procs == 1:
         parts = [_run_range(jobs[0])]
     else:
         with mp.get_context("spawn").Pool(procs) as pool:
             parts = pool.map(_run_range, jobs)
-    tally = np.zeros_like(parts[0][0])
+    sums = [np.zeros_like(parts[0][0]) for _ in range(3 if let else 1)]
     totals = {k: 0.0 for k in parts[0][1]}
-    for t, tot in parts:
-        tally += t
+    for part in parts:
+        sums[0] += part[0]
+        if let:
+            sums[1] += part[2]
+            sums[2] += part[3]
         for k in totals:
-            totals[k] += tot[k]
-    return tally, totals
+            totals[k] += part[1][k]
+    if let:
+        return sums[0], totals, sums[1], sums[2]
+    return sums[0], totals
 
 
 def material_info(prob, m: int):

@@ -149,3 +149,46 @@ def test_parallel_runner_equals_serial():
     b, tb, _ = O.run(p, 3000, 13)
     assert np.allclose(a, b, rtol=1e-12, atol=1e-9)
     assert ta["inelastic"] == tb["inelastic"] and ta["steps"] == tb["steps"]
+
+
+def test_let_d_in_csda_is_the_voxel_energy_loss_per_length():
+    """Straggling, MCS and nuclear off: each voxel is crossed by one step of length dz, so
+    LET_d there is the CSDA energy lost in the voxel over dz (and E/R_left in the voxel
+    where the proton stops), from the independent range quadrature.  The LET weights are
+    the dose deposits themselves."""
+    E0, dz = 150.0, 0.1
+    p = W.water_box((200, 3, 3), dz, np.array([W.spot_row(E0, sigma=0.0)]), n_batches=2, flags=ALL_OFF)
+    tally, num, den, tot = O.run_let(p, 4, 1)
+    assert np.allclose(den, tally, rtol=1e-14, atol=0)
+    let = num.sum(1).reshape(p.shape).sum((1, 2)) / np.maximum(den.sum(1).reshape(p.shape).sum((1, 2)), 1e-300)
+    R0 = _R(E0)
+    k_stop = int(R0 // dz)
+    for k in range(k_stop):
+        dE = _E_of_R(R0 - k * dz) - _E_of_R(R0 - (k + 1) * dz)
+        assert let[k] == pytest.approx(0.1 * dE / dz, rel=1e-7), k
+    Ek = _E_of_R(R0 - k_stop * dz)
+    assert let[k_stop] == pytest.approx(0.1 * Ek / (R0 - k_stop * dz), rel=1e-6)
+    assert np.all(let[k_stop + 1:] == 0)
+    # entrance LET against the tabulated stopping power of water (keV/um = 0.1 MeV cm^2/g at 1 g/cm^3)
+    assert let[0] == pytest.approx(0.1 * _S(E0), rel=2e-3)
+
+
+def test_let_d_weights_only_proton_energy_losses():
+    """With nuclear interactions the dose also holds recoil and fragment deposits, which carry
+    no LET: the LET weights stay below the dose tally, and the dose-averaged LET rises towards
+    the Bragg peak.  At the entrance it is the primaries' stopping power without nuclear
+    interactions and above it with them: slow secondary protons raise it."""
+    p = W.water_box((60, 1, 1), 0.25, np.array([W.spot_row(120.0, sigma=0.0)]), n_batches=2)
+    p = p.with_(voxel=(1000.0, 1000.0, 0.25), origin=(-500.0, -500.0, 0.0))
+    tally, num, den, tot = O.run_let(p, 3000, 2)
+    assert tot["inelastic"] > 0 and tot["elastic"] > 0
+    assert np.all(den <= tally * (1 + 1e-12) + 1e-12)
+    assert den.sum() < tally.sum()
+    let = num.sum(1) / np.maximum(den.sum(1), 1e-300)
+    peak = int(np.argmax(tally.sum(1)))
+    assert let[peak] > 3 * let[0]
+    _, num0, den0, _ = O.run_let(p.with_(flags=W.NO_ELASTIC | W.NO_INELASTIC), 3000, 2)
+    let0 = num0.sum(1)[0] / den0.sum(1)[0]
+    E_mid = _E_of_R(_R(120.0) - 0.125)                 # mean energy in the first voxel
+    assert let0 == pytest.approx(0.1 * _S(E_mid), rel=0.01)
+    assert let[0] > 1.05 * let0
