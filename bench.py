@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--train-events", type=int, default=10_000_000)
     ap.add_argument("--no-gamma", action="store_true")
+    ap.add_argument("--no-let", action="store_true")
     ap.add_argument("--gamma-histories", type=int, default=10_000_000)
     return ap.parse_args()
 
@@ -365,6 +366,19 @@ def main():
     h2d = prob.n_voxels * 5 + len(prob.spots) * 80
     d2h = prob.n_voxels * 16
 
+    # dose-averaged LET scored beside the dose (two more tallies), timed the same way
+    let_leg = None
+    if not args.no_let:
+        eng.enable_let(True)
+        timed_steps(eng, 3, 7000)
+        lm = timed_steps(eng, min(args.steps, 20), 7100)
+        let_d, _ = eng.read_let()
+        eng.enable_let(False)
+        lval = world * n * len(lm) / (sum(lm) / 1e3)
+        let_leg = {"value": lval, "unit": UNIT, "ms_per_step": sum(lm) / len(lm), "steps": len(lm),
+                   "time_vs_dose_only": (sum(lm) / len(lm)) / (total_ms / args.steps),
+                   "max_let_d_kev_um": float(let_d.max())}
+
     # the learned stand-in of the event generator: trained outside the timed region on events
     # from the engine's own cascade, then timed the same way, with its dose against the full
     # cascade's at the same seed (2 %/2 mm gamma)
@@ -441,6 +455,7 @@ def main():
             "math": args.math,
             "surrogate": surrogate,
             "gamma": gamma,
+            "let": let_leg,
             "other_build": {"math": "ieee" if args.math == "fast" else "fast",
                             "value": world * n * args.steps / (sum(other_ms) / 1e3),
                             "ms_per_step": sum(other_ms) / args.steps},

@@ -154,6 +154,26 @@ int pmc_read_history_ledger(pmc_ctx* ctx, int64_t* out, uint64_t n_histories);
 int pmc_enable_escape_record(pmc_ctx* ctx, uint64_t cap);
 int pmc_read_escape_record(pmc_ctx* ctx, float* out, uint64_t cap, uint64_t* n);
 
+/* Dose-averaged LET scored beside the dose (Sec. IV: LET_d computed together with
+ * the physical dose).  Every energy loss q of a transported proton (the steps, and
+ * the remainder of a proton absorbed below E_cut or within its residual range) is
+ * weighted by L, the mean CSDA stopping power of the local medium over the path of
+ * that loss (keV/um): the step's CSDA loss over its length, or E/R for an absorbed
+ * proton.  Recoil nuclei and cascade fragments do not score (as in Sec. IV).
+ * LET_d(v) = sum q L / sum q per voxel, in keV/um, with its standard error from the
+ * group tallies by the ratio estimator:
+ *   var = B/(B-1) sum_b (num_b - LET_d den_b)^2 / den^2.
+ * pmc_enable_let: on != 0 scores LET in the next transports (two more int64
+ *   [n_voxels][n_batches] tallies on the device); 0 frees them.
+ * pmc_read_let: LET_d and its standard error per voxel (host arrays of n_voxels,
+ *   either may be NULL; 0 where no proton lost energy).  PMC_E_INVALID unless the
+ *   last transport scored LET on the current grid.
+ * pmc_read_let_tally: raw group tallies [n_voxels][n_batches] (host arrays):
+ *   num in 2^-24 MeV keV/um, den in 2^-24 MeV. */
+int pmc_enable_let(pmc_ctx* ctx, int on);
+int pmc_read_let(pmc_ctx* ctx, double* let_d, double* sigma, size_t n_voxels);
+int pmc_read_let_tally(pmc_ctx* ctx, int64_t* num, int64_t* den, size_t n);
+
 /* Sets the transport launch shape (block size, histories per sub-group)
  * chosen by the caller; 0 keeps the current value.  A non-zero block size
  * also switches the autotuner off. */

@@ -1,6 +1,7 @@
 """Dose-comparison tools used by the tests (test infrastructure, numpy only).
 
 * batch statistics of Sec. II.B.2 (total and its standard error from B groups)
+* dose-averaged LET and its standard error from group tallies (Sec. IV)
 * R80 of an integrated depth-dose curve
 * per-voxel z-scores between two independent estimates
 * brute-force 3-D gamma index (Low et al.), global dose criterion, on the grid
@@ -22,6 +23,24 @@ def batch_stats(tally: np.ndarray):
         return tot, np.zeros_like(tot)
     dev = t - tot[:, None] / B
     return tot, np.sqrt(B / (B - 1) * (dev * dev).sum(1))
+
+
+def let_stats(num: np.ndarray, den: np.ndarray):
+    """Dose-averaged LET from group tallies num[V, B] (sum of e L) and den[V, B] (sum of e):
+    LET_d = sum num / sum den (0 where den is 0), and its standard error by the ratio
+    estimator over the B groups: var = B/(B-1) sum_b (num_b - LET_d den_b)^2 / den^2."""
+    num = np.asarray(num, dtype=np.float64)
+    den = np.asarray(den, dtype=np.float64)
+    B = num.shape[1]
+    N, D = num.sum(1), den.sum(1)
+    ok = D > 0
+    let = np.zeros_like(N)
+    let[ok] = N[ok] / D[ok]
+    sig = np.zeros_like(N)
+    if B > 1:
+        e = num - let[:, None] * den
+        sig[ok] = np.sqrt(B / (B - 1) * (e[ok] ** 2).sum(1)) / D[ok]
+    return let, sig
 
 
 def to_gray(energy_mev: np.ndarray, rho: np.ndarray, voxel_cm3: float) -> np.ndarray:

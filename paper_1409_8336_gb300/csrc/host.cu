@@ -244,6 +244,8 @@ struct pmc_ctx {
   DevBuf d_tally, d_dose, d_sigma, d_counters, d_counts, d_seed, d_spots, d_q[kQueues];
   DevBuf d_hist, d_esc;
   uint64_t hist_n = 0, esc_cap = 0;
+  bool let_on = false, let_valid = false;
+  DevBuf d_let_num, d_let_den, d_let, d_let_sigma;   // dose-averaged LET tallies and results
   size_t q_cap = 0;
   int block = 0;
   int64_t chunk = 0;
@@ -392,7 +394,8 @@ void pmc_destroy(pmc_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->d_phys, &ctx->d_rt, &ctx->d_et, &ctx->d_st, &ctx->d_nuclei, &ctx->d_btab, &ctx->d_mat,
                     &ctx->d_rho, &ctx->d_hu, &ctx->d_tally, &ctx->d_dose, &ctx->d_sigma, &ctx->d_counters,
                     &ctx->d_counts, &ctx->d_seed, &ctx->d_spots, &ctx->d_q[0], &ctx->d_q[1], &ctx->d_q[2],
-                    &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_hist, &ctx->d_esc};
+                    &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_hist, &ctx->d_esc,
+                    &ctx->d_let_num, &ctx->d_let_den, &ctx->d_let, &ctx->d_let_sigma};
   for (DevBuf* b : bufs) dfree(ctx, *b);
   DevBuf* sbufs[] = {&ctx->d_swb, &ctx->d_sp, &ctx->d_sg, &ctx->d_sm, &ctx->d_sv, &ctx->d_slot_nuc, &ctx->d_nuc_slot,
                      &ctx->d_sx[0], &ctx->d_sx[1], &ctx->d_sy[0][0], &ctx->d_sy[0][1], &ctx->d_sy[1][0],
@@ -572,7 +575,12 @@ int pmc_load_phantom(pmc_ctx* ctx, int nx, int ny, int nz, double dx, double dy,
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->n_vox = n;
   ctx->have_phantom = true;
-  if (shape_changed && ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  if (shape_changed) {
+    // results of an earlier run belong to the old grid (and its buffer sizes)
+    ctx->have_run = false;
+    ctx->let_valid = false;
+    if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  }
   return PMC_OK;
 }
 
@@ -629,6 +637,21 @@ int pmc_enable_history_ledger(pmc_ctx* ctx, uint64_t max_histories) {
     if (rc) return rc;
     ctx->hist_n = max_histories;
   }
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  return PMC_OK;
+}
+
+int pmc_enable_let(pmc_ctx* ctx, int on) {
+  if (!ctx) return PMC_E_INVALID;
+  cudaSetDevice(ctx->opt.device);
+  ctx->let_on = on != 0;
+  if (!ctx->let_on) {
+    dfree(ctx, ctx->d_let_num);
+    dfree(ctx, ctx->d_let_den);
+    dfree(ctx, ctx->d_let);
+    dfree(ctx, ctx->d_let_sigma);
+  }
+  ctx->let_valid = false;
   if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
   return PMC_OK;
 }
@@ -733,6 +756,10 @@ TransportArgs transport_args(pmc_ctx* ctx) {
   a.hist_n = ctx->hist_n;
   a.esc = static_cast<float*>(ctx->d_esc.p);
   a.esc_cap = ctx->esc_cap;
+  if (ctx->let_on) {
+    a.let_num = static_cast<unsigned long long*>(ctx->d_let_num.p);
+    a.let_den = static_cast<unsigned long long*>(ctx->d_let_den.p);
+  }
   return a;
 }
 
@@ -813,6 +840,12 @@ StatsArgs stats_args(pmc_ctx* ctx) {
   sa.phys = static_cast<const Physics*>(ctx->d_phys.p);
   sa.dose = static_cast<double*>(ctx->d_dose.p);
   sa.sigma = static_cast<double*>(ctx->d_sigma.p);
+  if (ctx->let_on) {
+    sa.let_num = static_cast<const unsigned long long*>(ctx->d_let_num.p);
+    sa.let_den = static_cast<const unsigned long long*>(ctx->d_let_den.p);
+    sa.let = static_cast<double*>(ctx->d_let.p);
+    sa.let_sigma = static_cast<double*>(ctx->d_let_sigma.p);
+  }
   return sa;
 }
 
@@ -828,6 +861,10 @@ int enqueue_run(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s) {
   CK(cudaMemsetAsync(ctx->d_counters.p, 0, sizeof(Counters), s));
   CK(cudaMemsetAsync(ctx->d_counts.p, 0, (static_cast<size_t>(rp.n_chunks) * kSlots + 1) * sizeof(unsigned), s));
   if (ctx->d_hist.p) CK(cudaMemsetAsync(ctx->d_hist.p, 0, ctx->hist_n * 4 * sizeof(long long), s));
+  if (ctx->let_on) {
+    CK(cudaMemsetAsync(ctx->d_let_num.p, 0, static_cast<size_t>(ctx->n_vox) * ctx->opt.n_batches * 8, s));
+    CK(cudaMemsetAsync(ctx->d_let_den.p, 0, static_cast<size_t>(ctx->n_vox) * ctx->opt.n_batches * 8, s));
+  }
   unsigned* counts = static_cast<unsigned*>(ctx->d_counts.p);
   unsigned* carry_count = counts + static_cast<size_t>(rp.n_chunks) * kSlots;
   Particle* q[kQueues];
@@ -934,6 +971,12 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     if ((rc = dalloc(ctx, ctx->d_tally, static_cast<size_t>(ctx->n_vox) * B * 8))) return rc;
     if ((rc = dalloc(ctx, ctx->d_dose, static_cast<size_t>(ctx->n_vox) * 8))) return rc;
     if ((rc = dalloc(ctx, ctx->d_sigma, static_cast<size_t>(ctx->n_vox) * 8))) return rc;
+    if (ctx->let_on) {
+      if ((rc = dalloc(ctx, ctx->d_let_num, static_cast<size_t>(ctx->n_vox) * B * 8))) return rc;
+      if ((rc = dalloc(ctx, ctx->d_let_den, static_cast<size_t>(ctx->n_vox) * B * 8))) return rc;
+      if ((rc = dalloc(ctx, ctx->d_let, static_cast<size_t>(ctx->n_vox) * 8))) return rc;
+      if ((rc = dalloc(ctx, ctx->d_let_sigma, static_cast<size_t>(ctx->n_vox) * 8))) return rc;
+    }
     if ((rc = dalloc(ctx, ctx->d_counters, sizeof(Counters)))) return rc;
     if ((rc = dalloc(ctx, ctx->d_counts, (static_cast<size_t>(rp.n_chunks) * kSlots + 1) * sizeof(unsigned)))) return rc;
     if ((rc = dalloc(ctx, ctx->d_seed, sizeof(uint64_t)))) return rc;
@@ -954,9 +997,9 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     CK(cudaMemcpyAsync(ctx->d_seed.p, &seed, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
     // graph of the whole run, rebuilt when its shape changes
     char key[256];
-    std::snprintf(key, sizeof(key), "%llu/%lld/%zu/%d/%d/%lld/%p/%p/%d", (unsigned long long)n_histories,
+    std::snprintf(key, sizeof(key), "%llu/%lld/%zu/%d/%d/%lld/%p/%p/%p/%d", (unsigned long long)n_histories,
                   (long long)rp.chunk, sd.size(), ctx->block, ctx->opt.n_batches, ctx->n_vox, ctx->d_tally.p,
-                  ctx->d_hist.p, (ctx->profile ? 1 : 0) + 2 * mode);
+                  ctx->d_hist.p, ctx->let_on ? ctx->d_let_num.p : nullptr, (ctx->profile ? 1 : 0) + 2 * mode);
     if (!ctx->gexec || ctx->gkey != key) {
       if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
       cudaGraph_t graph;
@@ -1038,6 +1081,7 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     L.errors = static_cast<int64_t>(hc.errors);
     ctx->steps_primary = static_cast<int64_t>(hc.steps_primary);
     ctx->have_run = true;
+    ctx->let_valid = ctx->let_on;
     if (hc.dropped) return fail(ctx, PMC_E_QUEUE_OVERFLOW, "%llu particles did not fit a queue", (unsigned long long)hc.dropped);
     if (hc.errors) return fail(ctx, PMC_E_TIMEOUT, "%llu particles exceeded the step limit", (unsigned long long)hc.errors);
     return PMC_OK;
@@ -1086,6 +1130,29 @@ int pmc_read_dose(pmc_ctx* ctx, double* dose, double* sigma, size_t n) {
   cudaSetDevice(ctx->opt.device);
   if (dose) CK(cudaMemcpyAsync(dose, ctx->d_dose.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
   if (sigma) CK(cudaMemcpyAsync(sigma, ctx->d_sigma.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PMC_OK;
+}
+
+int pmc_read_let(pmc_ctx* ctx, double* let_d, double* sigma, size_t n) {
+  if (!ctx) return PMC_E_INVALID;
+  if (!ctx->let_valid) return fail(ctx, PMC_E_INVALID, "no transport with LET scoring has run (pmc_enable_let)");
+  if (n != static_cast<size_t>(ctx->n_vox)) return fail(ctx, PMC_E_INVALID, "n_voxels %zu != %lld", n, ctx->n_vox);
+  cudaSetDevice(ctx->opt.device);
+  if (let_d) CK(cudaMemcpyAsync(let_d, ctx->d_let.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (sigma) CK(cudaMemcpyAsync(sigma, ctx->d_let_sigma.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PMC_OK;
+}
+
+int pmc_read_let_tally(pmc_ctx* ctx, int64_t* num, int64_t* den, size_t n) {
+  if (!ctx) return PMC_E_INVALID;
+  if (!ctx->let_valid) return fail(ctx, PMC_E_INVALID, "no transport with LET scoring has run (pmc_enable_let)");
+  const size_t need = static_cast<size_t>(ctx->n_vox) * ctx->opt.n_batches;
+  if (n != need) return fail(ctx, PMC_E_INVALID, "LET tallies have %zu entries", need);
+  cudaSetDevice(ctx->opt.device);
+  if (num) CK(cudaMemcpyAsync(num, ctx->d_let_num.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (den) CK(cudaMemcpyAsync(den, ctx->d_let_den.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return PMC_OK;
 }

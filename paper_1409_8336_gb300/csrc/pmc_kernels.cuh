@@ -48,6 +48,8 @@ struct TransportArgs {
   unsigned long long hist_n;
   float* esc;                      // escape record [esc_cap][8] or NULL
   unsigned long long esc_cap;
+  unsigned long long* let_num;     // [n_voxels][B] sum of q * LET (2^-24 MeV keV/um), or NULL
+  unsigned long long* let_den;     // [n_voxels][B] sum of q over the same deposits (2^-24 MeV)
 };
 
 struct CascadeArgs {
@@ -77,6 +79,10 @@ struct StatsArgs {
   const Physics* phys;
   double* dose;
   double* sigma;
+  const unsigned long long* let_num;  // LET tallies or NULL
+  const unsigned long long* let_den;
+  double* let;                        // dose-averaged LET (keV/um) and its standard error
+  double* let_sigma;
 };
 
 size_t transport_smem_bytes(int n_cls, int n_mat);

@@ -42,6 +42,31 @@ __global__ void __launch_bounds__(256) stats_kernel(const StatsArgs a) {
     const double scale = rho > 0.0f ? (1.602176634e-10 / (static_cast<double>(rho) * vol)) / kFixD : 0.0;
     a.dose[v] = static_cast<double>(sum) * scale;
     a.sigma[v] = static_cast<double>(sqrtf(corr * ss)) * scale;
+    if (a.let_num) {
+      // LET_d = sum num / sum den; its standard error by the ratio estimator over the
+      // groups: var = B/(B-1) sum_b (num_b - LET_d den_b)^2 / den^2
+      const long long* tn = reinterpret_cast<const long long*>(a.let_num) + v * a.B;
+      const long long* td = reinterpret_cast<const long long*>(a.let_den) + v * a.B;
+      long long sn = 0, sd = 0;
+      for (int b = 0; b < a.B; ++b) {
+        sn += tn[b];
+        sd += td[b];
+      }
+      if (sd > 0) {
+        const double let = static_cast<double>(sn) / static_cast<double>(sd);
+        const float lf = static_cast<float>(let);
+        float e2 = 0.0f;
+        for (int b = 0; b < a.B; ++b) {
+          const float e = ll2f(tn[b]) - lf * ll2f(td[b]);
+          e2 = fmaf(e, e, e2);
+        }
+        a.let[v] = let;
+        a.let_sigma[v] = static_cast<double>(sqrtf(corr * e2) / ll2f(sd));
+      } else {
+        a.let[v] = 0.0;
+        a.let_sigma[v] = 0.0;
+      }
+    }
   }
 }
 

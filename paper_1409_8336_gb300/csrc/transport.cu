@@ -63,6 +63,14 @@ __device__ __forceinline__ void deposit(const TransportArgs& a, int v, const PSt
                                              static_cast<unsigned long long>(q));
 }
 
+// Dose-averaged LET (Sec. IV): an energy loss q of the transported proton, weighted by
+// L, the mean stopping power of the local medium over the path that lost it (keV/um).
+__device__ __forceinline__ void score_let(const TransportArgs& a, int v, const PState& p, long long q, float L) {
+  const size_t i = static_cast<size_t>(v) * a.B + p.b;
+  atomicAdd(a.let_den + i, static_cast<unsigned long long>(q));
+  atomicAdd(a.let_num + i, static_cast<unsigned long long>(__float2ll_rn(static_cast<float>(q) * L)));
+}
+
 __device__ __forceinline__ void escape(const TransportArgs& a, const PState& p, long long q, Acc& acc) {
   acc.esc += q;
   if (a.hist && p.root < a.hist_n) atomicAdd(reinterpret_cast<unsigned long long*>(a.hist + 4ull * p.root + 2),
@@ -139,7 +147,19 @@ __device__ __forceinline__ Particle make_record(const PState& p, float E, float 
 __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt, const float2* et,
                      const float* st, uint2 key, PState& p, Acc& acc) {
   const int v = vindex(a.g, p.ix, p.iy, p.iz);
-  if (p.E <= kEcut) { deposit(a, v, p, fix(p.E), acc); return false; }
+  if (p.E <= kEcut) {
+    const long long q = fix(p.E);
+    deposit(a, v, p, q, acc);
+    if (a.let_num && p.E > 0.0f) {   // absorbed over its residual range: L = E / R
+      int m0;
+      float rho0;
+      voxel_props(ph, a.g, v, m0, rho0);
+      const MatConst& m0c = ph.mat[m0];
+      const float R0 = range_mass(ph, rt, m0c.cls, p.E, logf(p.E)) / (rho0 * m0c.f);
+      if (R0 > 0.0f) score_let(a, v, p, q, 0.1f * p.E / R0);
+    }
+    return false;
+  }
   if (p.k >= kMaxSteps) { deposit(a, v, p, fix(p.E), acc); acc.errors++; return false; }
   int m;
   float rho;
@@ -155,7 +175,12 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   int axis;
   const float d = voxel_exit(a.g, p.x, p.y, p.z, p.u, p.v, p.w, p.ix, p.iy, p.iz, axis);
   acc.steps++;
-  if (Rcm <= lam && Rcm <= d) { deposit(a, v, p, fix(E0), acc); return false; }
+  if (Rcm <= lam && Rcm <= d) {
+    const long long q = fix(E0);
+    deposit(a, v, p, q, acc);
+    if (a.let_num && Rcm > 0.0f) score_let(a, v, p, q, 0.1f * E0 / Rcm);
+    return false;
+  }
   bool nuclear = lam <= d;
   const float dx = nuclear ? lam : d;
   const StepUniforms ua = step_uniforms(key, p.pid, p.k);
@@ -189,7 +214,8 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   const float s = tau * dx + L2;
   p.x = x1 + L2 * p.u; p.y = y1 + L2 * p.v; p.z = z1 + L2 * p.w;
   const float Rleft = Rm - s * rf;
-  float dE = Rleft > 0.0f ? E0 - energy_of_range(ph, et, mc.cls, Rleft) : E0;
+  const float E_left = Rleft > 0.0f ? energy_of_range(ph, et, mc.cls, Rleft) : 0.0f;
+  float dE = E0 - E_left;
   if (!(ph.flags & kNoStraggling)) {
     const float g = 1.0f + E0 / kMp;
     const float b2 = 1.0f - 1.0f / (g * g);
@@ -198,7 +224,18 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   }
   dE = fminf(fmaxf(dE, 0.0f), E0);
   const float E1 = E0 - dE;
-  deposit(a, v, p, fix(E0) - fix(E1), acc);
+  {
+    const long long q = fix(E0) - fix(E1);
+    deposit(a, v, p, q, acc);
+    if (a.let_num) {
+      // mean stopping power over the path: the CSDA loss over s, taken as a difference
+      // of two values of the inverse range table (free of the E -> R -> E round trip,
+      // whose few-ulp error would dominate the loss over the short steps that end at
+      // a voxel face)
+      const float L = s > 0.0f ? 0.1f * (energy_of_range(ph, et, mc.cls, Rm) - E_left) / s : 0.0f;
+      score_let(a, v, p, q, fmaxf(L, 0.0f));
+    }
+  }
   p.E = E1;
   p.nmfp -= sig * s;
   const unsigned kstep = p.k++;

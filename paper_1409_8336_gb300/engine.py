@@ -27,6 +27,7 @@ EXPORTS = [
     "pmc_create", "pmc_destroy", "pmc_last_error", "pmc_load_materials", "pmc_load_phantom", "pmc_add_spots",
     "pmc_clear_spots", "pmc_transport", "pmc_read_dose", "pmc_read_tally", "pmc_read_ledger",
     "pmc_enable_history_ledger", "pmc_read_history_ledger", "pmc_enable_escape_record", "pmc_read_escape_record",
+    "pmc_enable_let", "pmc_read_let", "pmc_read_let_tally",
     "pmc_set_launch", "pmc_autotune", "pmc_transport_noalloc", "pmc_surrogate_dataset", "pmc_train_surrogate",
     "pmc_surrogate_params", "pmc_surrogate_load", "pmc_surrogate_grad", "pmc_gamma_plan_bytes", "pmc_gamma_plan", "pmc_gamma_device",
     "pmc_gamma_index", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables",
@@ -109,6 +110,9 @@ def lib(path: str = LIB_PATH):
             L.pmc_read_history_ledger.argtypes = [vp, pi64, u64]
             L.pmc_enable_escape_record.argtypes = [vp, u64]
             L.pmc_read_escape_record.argtypes = [vp, C.POINTER(C.c_float), u64, C.POINTER(C.c_uint64)]
+            L.pmc_enable_let.argtypes = [vp, i]
+            L.pmc_read_let.argtypes = [vp, vp, vp, C.c_size_t]
+            L.pmc_read_let_tally.argtypes = [vp, pi64, pi64, C.c_size_t]
             L.pmc_set_launch.argtypes = [vp, i, C.c_int64]
             L.pmc_autotune.argtypes = [vp, u64, u64, C.POINTER(C.c_int), C.POINTER(C.c_int64)]
             pf = C.POINTER(C.c_float)
@@ -316,6 +320,25 @@ class Engine:
         self._check(self._L.pmc_read_escape_record(self._ctx, out.ctypes.data_as(C.POINTER(C.c_float)), cap,
                                                    C.byref(n)))
         return out[: n.value]
+
+    def enable_let(self, on=True):
+        """Scores the dose-averaged LET beside the dose in the next transports."""
+        self._check(self._L.pmc_enable_let(self._ctx, 1 if on else 0))
+
+    def read_let(self):
+        """(LET_d, its standard error) per voxel in keV/um."""
+        n = self.n_voxels
+        let, sig = np.empty(n), np.empty(n)
+        self._check(self._L.pmc_read_let(self._ctx, let.ctypes.data, sig.ctypes.data, n))
+        return let, sig
+
+    def read_let_tally(self):
+        """Raw LET group tallies [V, B]: numerator (2^-24 MeV keV/um), weights (2^-24 MeV)."""
+        num = np.empty((self.n_voxels, self.n_batches), dtype=np.int64)
+        den = np.empty_like(num)
+        p = C.POINTER(C.c_int64)
+        self._check(self._L.pmc_read_let_tally(self._ctx, num.ctypes.data_as(p), den.ctypes.data_as(p), num.size))
+        return num, den
 
     def enable_profile(self, on=True):
         self._check(self._L.pmc_enable_profile(self._ctx, 1 if on else 0))

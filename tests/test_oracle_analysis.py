@@ -129,3 +129,25 @@ def test_zscores_select_and_scale():
     sb = np.array([0.4, 0.2, 0.1, 0.8])
     z = A.zscores(Da, sa, Db, sb, frac_of_max=0.1)
     assert np.allclose(z, [-0.5 / 0.5, 0.0, 1.0 / 1.0])
+
+
+def test_let_stats_ratio_estimator():
+    """LET_d = sum num / sum den; a constant ratio across groups has zero spread; and the
+    ratio estimator's error matches the spread of LET_d over many independent repeats."""
+    den = np.array([[1.0, 2.0, 3.0, 4.0], [0.0, 0.0, 0.0, 0.0]])
+    num = 2.5 * den
+    let, sig = A.let_stats(num, den)
+    assert let[0] == 2.5 and sig[0] == 0.0 and let[1] == 0.0 and sig[1] == 0.0
+    # a hand-worked case: num (3, 5), den (1, 1): LET 4, deviations (-1, +1): var = 2 * 2 / 4
+    let, sig = A.let_stats(np.array([[3.0, 5.0]]), np.array([[1.0, 1.0]]))
+    assert let[0] == 4.0 and sig[0] == pytest.approx(1.0)
+    rng = np.random.default_rng(3)
+    reps, B, n = 4000, 20, 50
+    lets, sigs = [], []
+    for _ in range(reps):
+        e = rng.exponential(1.0, (B, n))                  # deposits
+        L = 2.0 + rng.exponential(3.0, (B, n))            # their LET
+        l, s = A.let_stats((e * L).sum(1)[None, :], e.sum(1)[None, :])
+        lets.append(l[0])
+        sigs.append(s[0])
+    assert np.mean(sigs) == pytest.approx(np.std(lets), rel=0.05)
