@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--train-events", type=int, default=10_000_000)
     ap.add_argument("--no-gamma", action="store_true")
     ap.add_argument("--no-let", action="store_true")
+    ap.add_argument("--no-inc", action="store_true")
+    ap.add_argument("--inc-events", type=int, default=2_600_000)
     ap.add_argument("--gamma-histories", type=int, default=10_000_000)
     return ap.parse_args()
 
@@ -183,6 +185,54 @@ def run_reference(args):
                              "sample": "%d histories per step, even over the three spots" % (sum(dones) // len(dones))},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+# Table I of the paper: seconds for 2.6e6 non-elastic interactions at 200 MeV on a GTX680
+TABLE1_GTX680_S = {"O16": {"ieee": 8.39, "fast": 6.61}, "Ca40": {"ieee": 15.56, "fast": 9.77}}
+
+
+def inc_leg(args, device, with_cpu):
+    """The paper's INC benchmark (Table I): 2.6e6 proton-16O and proton-40Ca non-elastic
+    interactions at 200 MeV through the event-generator entry point (cascade and
+    evaporation on the device), device time per batch, both builds; the oracle's event
+    generator on a bounded sample as the CPU baseline."""
+    from paper_1409_8336_gb300 import Engine
+    from paper_1409_8336_gb300 import workloads as W
+
+    prob = W.config2()
+    idx = {"O16": None, "Ca40": None}
+    for i, nu in enumerate(prob.nuclides):
+        name = {(8, 16): "O16", (20, 40): "Ca40"}.get((int(nu[0]), int(nu[1])))
+        if name:
+            idx[name] = i
+    n = args.inc_events
+    out = {"events": n, "energy_mev": 200.0, "paper": "Table I, GTX680 seconds", "targets": {}}
+    for math in ("fast", "ieee"):
+        eng = Engine(device=device, n_batches=prob.n_batches, fast_math=(math == "fast"))
+        eng.load_problem(prob)
+        for name, i in idx.items():
+            eng.nonelastic_events(i, 200.0, n // 10, 99)
+            ms = [eng.nonelastic_events(i, 200.0, n, 100 + r)["ms"] for r in range(3)]
+            y = eng.nonelastic_events(i, 200.0, n, 100)
+            t = statistics.median(ms) / 1e3
+            row = out["targets"].setdefault(name, {})
+            row[math] = {"seconds": t, "events_per_s": n / t, "paper_s": TABLE1_GTX680_S[name][math],
+                         "speedup_vs_paper": TABLE1_GTX680_S[name][math] / t,
+                         "protons_per_event": y["count"]["p"] / y["events"],
+                         "neutrons_per_event": y["count"]["n"] / y["events"]}
+        eng.close()
+    if with_cpu:
+        from oracle import oracle as O
+
+        for name, (Z, A) in (("O16", (8, 16)), ("Ca40", (20, 40))):
+            k = 2000
+            t0 = time.perf_counter()
+            O.inc_batch(Z, A, 200.0, 7, 0, k)
+            dt = time.perf_counter() - t0
+            out["targets"][name]["cpu_baseline"] = {
+                "value": k / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+                "sample": "%d events in %.2f s" % (k, dt), "seconds_for_batch": n * dt / k}
+    return out
 
 
 def gamma_leg(args, device, stream, flush, with_cpu):
@@ -413,6 +463,10 @@ def main():
                      "train_loss_first_last": [tr["first_loss"], tr["last_loss"]],
                      "network": "MLP 32-256-256-256-256-16, BF16 tensor cores (mma.sync), FP32 accumulate"}
 
+    inc = None
+    if not args.no_inc:
+        inc = inc_leg(args, local, rank == 0 and world == 1 and not args.no_cpu_baseline)
+
     gamma = None
     if not args.no_gamma:
         gamma = gamma_leg(args, local, stream, flush, rank == 0 and world == 1 and not args.no_cpu_baseline)
@@ -455,6 +509,7 @@ def main():
             "math": args.math,
             "surrogate": surrogate,
             "gamma": gamma,
+            "inc_table1": inc,
             "let": let_leg,
             "other_build": {"math": "ieee" if args.math == "fast" else "fast",
                             "value": world * n * args.steps / (sum(other_ms) / 1e3),

@@ -256,6 +256,23 @@ int pmc_surrogate_load(pmc_ctx* ctx, const float* params, size_t n);
 int pmc_surrogate_grad(pmc_ctx* ctx, const float* params, const float* x, const float* y, const float* tau,
                        const float* mask, int rows, float* loss, float* grad, float* yhat);
 
+/* ---- non-elastic event generator -------------------------------------------
+ * n non-elastic interactions of a proton of kinetic energy E (MeV) with the
+ * loaded nuclide index `nuclide` (A >= 2): intranuclear cascade and evaporation
+ * (Sec. II.A.4), the same device code and random streams (key seed, particle
+ * pid0 + i for event i) as inside the transport.  The workload of Table I.
+ * Synchronous on the context's stream; `out` receives the totals over the events
+ * and the device time of the event kernel.  Energies in MeV. */
+typedef struct {
+    uint64_t events, transparent, retries;
+    uint64_t count[6];                  /* emitted n, p, d, t, 3He, alpha */
+    double energy[6];                   /* their summed kinetic energies */
+    double residual_T, excitation_left, binding;   /* summed over the events */
+    double ms;                          /* device time of the event kernel */
+} pmc_event_yields;
+int pmc_nonelastic_events(pmc_ctx* ctx, int nuclide, double E, uint64_t n, uint64_t seed, uint64_t pid0,
+                          pmc_event_yields* out);
+
 /* ---- 3-D gamma index -------------------------------------------------------
  * The dose-comparison metric of Sec. II.D (Low et al.), which the paper also
  * computes on the GPU.  For every reference voxel whose dose exceeds

@@ -519,7 +519,97 @@ __global__ void debug_inc_kernel(const NucleusModel* nu, const float* bt, float 
                    pid0 + i, P, sk);
 }
 
+// Sink of the event-generator entry point: per-thread yields of the events it runs.
+struct YieldSink {
+  unsigned long long n_transparent, retries, count[6];
+  long long energy[6], res, ex, bind;
+  __device__ void product(int, int species, double T, float, float, float) {
+    ++count[species];
+    energy[species] += fixd(T);
+  }
+  __device__ void residual(int, int, double Tres, double Ex, double b, int r) {
+    res += fixd(Tres);
+    ex += fixd(Ex);
+    bind += fixd(b);
+    retries += r;
+  }
+  __device__ void transparent(int r) {
+    retries += r;
+    ++n_transparent;
+  }
+};
+
+// n non-elastic events of a proton of energy E on one nucleus (Sec. II.A.4), one
+// event per thread, event i with the random stream of particle pid0 + i.  Yields are
+// reduced per warp and added to `out` as integers (energies in 2^-24 MeV), so the
+// totals do not depend on the order of the events.
+__global__ void __launch_bounds__(128) inc_yield_kernel(const NucleusModel* __restrict__ nu,
+                                                        const float* __restrict__ btab, float E,
+                                                        unsigned long long seed, unsigned long long pid0,
+                                                        unsigned long long n, EventYields* out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  NucleusModel* nuc = reinterpret_cast<NucleusModel*>(smem);
+  float* bt = reinterpret_cast<float*>(nuc + 1);
+  {
+    const float* src = reinterpret_cast<const float*>(nu);
+    float* dst = reinterpret_cast<float*>(nuc);
+    for (int i = threadIdx.x; i < static_cast<int>(sizeof(NucleusModel) / 4); i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < kMaxZ * kMaxA; i += blockDim.x) bt[i] = btab[i];
+  }
+  __syncthreads();
+  const uint2 key = make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32));
+  YieldSink sk{};
+  unsigned long long events = 0;
+  IncP P[kIncStack];
+  for (unsigned long long i = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<unsigned long long>(gridDim.x) * blockDim.x) {
+    nonelastic_event(*nuc, bt, E, key, pid0 + i, P, sk);
+    ++events;
+  }
+  auto wsum = [](unsigned long long x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+  };
+  auto add = [&](unsigned long long* dst, unsigned long long x) {
+    x = wsum(x);
+    if ((threadIdx.x & 31u) == 0 && x) atomicAdd(dst, x);
+  };
+  add(&out->events, events);
+  add(&out->transparent, sk.n_transparent);
+  add(&out->retries, sk.retries);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    add(&out->count[k], sk.count[k]);
+    add(reinterpret_cast<unsigned long long*>(&out->energy[k]), static_cast<unsigned long long>(sk.energy[k]));
+  }
+  add(reinterpret_cast<unsigned long long*>(&out->residual), static_cast<unsigned long long>(sk.res));
+  add(reinterpret_cast<unsigned long long*>(&out->excitation), static_cast<unsigned long long>(sk.ex));
+  add(reinterpret_cast<unsigned long long*>(&out->binding), static_cast<unsigned long long>(sk.bind));
+}
+
 }  // namespace
+
+cudaError_t launch_inc_yields(const NucleusModel* nu, const float* btab, float E, unsigned long long seed,
+                              unsigned long long pid0, unsigned long long n, EventYields* out, cudaStream_t s) {
+  static int blocks_per_sm = 0, n_sm = 0;
+  const size_t smem = sizeof(NucleusModel) + kMaxZ * kMaxA * sizeof(float);
+  if (n_sm == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, inc_yield_kernel, 128, smem);
+    if (e != cudaSuccess) {
+      n_sm = 0;
+      return e;
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(EventYields), s);
+  if (e != cudaSuccess || n == 0) return e;
+  const unsigned long long want = (n + 127) / 128;
+  const unsigned long long cap = static_cast<unsigned long long>(n_sm) * (blocks_per_sm > 0 ? blocks_per_sm : 1);
+  inc_yield_kernel<<<static_cast<unsigned>(want < cap ? want : cap), 128, smem, s>>>(nu, btab, E, seed, pid0, n, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cascade(const CascadeArgs& a, int grid, int block, cudaStream_t s) {
   const size_t smem = a.n_nuc * sizeof(NucleusModel) + kMaxZ * kMaxA * sizeof(float);

@@ -245,6 +245,8 @@ struct pmc_ctx {
   DevBuf d_hist, d_esc;
   uint64_t hist_n = 0, esc_cap = 0;
   bool let_on = false, let_valid = false;
+  DevBuf d_yields;                      // event-generator totals
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   DevBuf d_let_num, d_let_den, d_let, d_let_sigma;   // dose-averaged LET tallies and results
   size_t q_cap = 0;
   int block = 0;
@@ -395,7 +397,9 @@ void pmc_destroy(pmc_ctx* ctx) {
                     &ctx->d_rho, &ctx->d_hu, &ctx->d_tally, &ctx->d_dose, &ctx->d_sigma, &ctx->d_counters,
                     &ctx->d_counts, &ctx->d_seed, &ctx->d_spots, &ctx->d_q[0], &ctx->d_q[1], &ctx->d_q[2],
                     &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_hist, &ctx->d_esc,
-                    &ctx->d_let_num, &ctx->d_let_den, &ctx->d_let, &ctx->d_let_sigma};
+                    &ctx->d_let_num, &ctx->d_let_den, &ctx->d_let, &ctx->d_let_sigma, &ctx->d_yields};
+  if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
+  if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
   for (DevBuf* b : bufs) dfree(ctx, *b);
   DevBuf* sbufs[] = {&ctx->d_swb, &ctx->d_sp, &ctx->d_sg, &ctx->d_sm, &ctx->d_sv, &ctx->d_slot_nuc, &ctx->d_nuc_slot,
                      &ctx->d_sx[0], &ctx->d_sx[1], &ctx->d_sy[0][0], &ctx->d_sy[0][1], &ctx->d_sy[1][0],
@@ -1252,6 +1256,43 @@ int pmc_debug_inc(pmc_ctx* ctx, int nuclide, double E, uint64_t seed, uint64_t p
   CK(cudaMemcpy(summary, d, ns * 8, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(products, d + ns, np * 8, cudaMemcpyDeviceToHost));
   dfree(ctx, b);
+  return PMC_OK;
+}
+
+int pmc_nonelastic_events(pmc_ctx* ctx, int nuclide, double E, uint64_t n, uint64_t seed, uint64_t pid0,
+                          pmc_event_yields* out) {
+  if (!ctx || !out || !(E > 0.0) || !(E < 1.0e4)) return PMC_E_INVALID;
+  if (!ctx->have_materials || nuclide < 0 || nuclide >= ctx->phys.n_nuc || ctx->nucs[nuclide].A < 2)
+    return fail(ctx, PMC_E_INVALID, "bad nuclide (a loaded nuclide with A >= 2)");
+  cudaSetDevice(ctx->opt.device);
+  int rc;
+  if ((rc = dalloc(ctx, ctx->d_yields, sizeof(EventYields)))) return rc;
+  if (!ctx->ev_a) {
+    CK(cudaEventCreate(&ctx->ev_a));
+    CK(cudaEventCreate(&ctx->ev_b));
+  }
+  EventYields* d = static_cast<EventYields*>(ctx->d_yields.p);
+  CK(cudaEventRecord(ctx->ev_a, ctx->stream));
+  CK(launch_inc_yields(static_cast<const NucleusModel*>(ctx->d_nuclei.p) + nuclide,
+                       static_cast<const float*>(ctx->d_btab.p), static_cast<float>(E), seed, pid0, n, d, ctx->stream));
+  CK(cudaEventRecord(ctx->ev_b, ctx->stream));
+  EventYields h{};
+  CK(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b));
+  *out = pmc_event_yields{};
+  out->events = h.events;
+  out->transparent = h.transparent;
+  out->retries = h.retries;
+  for (int k = 0; k < 6; ++k) {
+    out->count[k] = h.count[k];
+    out->energy[k] = static_cast<double>(h.energy[k]) * (1.0 / kFixD);
+  }
+  out->residual_T = static_cast<double>(h.residual) * (1.0 / kFixD);
+  out->excitation_left = static_cast<double>(h.excitation) * (1.0 / kFixD);
+  out->binding = static_cast<double>(h.binding) * (1.0 / kFixD);
+  out->ms = ms;
   return PMC_OK;
 }
 

@@ -116,6 +116,17 @@ cudaError_t launch_infer_emit(const unsigned* n_ev, unsigned cap, const Particle
                               unsigned* qsec_count, unsigned qsec_cap, Counters* cnt, long long* hist,
                               unsigned long long hist_n, cudaStream_t s);
 
+// Yields of a batch of non-elastic events (energies in 2^-24 MeV).
+struct EventYields {
+  unsigned long long events, transparent, retries;
+  unsigned long long count[6];          // n, p, d, t, 3He, alpha emitted
+  long long energy[6];                  // their kinetic energies
+  long long residual, excitation, binding;
+};
+
+cudaError_t launch_inc_yields(const NucleusModel* nu, const float* btab, float E, unsigned long long seed,
+                              unsigned long long pid0, unsigned long long n, EventYields* out, cudaStream_t s);
+
 // Gamma plan in device memory: this head, then at kGammaHeadBytes the offsets of the
 // search sphere sorted by their distance term.
 struct GammaHead {

@@ -27,7 +27,7 @@ EXPORTS = [
     "pmc_create", "pmc_destroy", "pmc_last_error", "pmc_load_materials", "pmc_load_phantom", "pmc_add_spots",
     "pmc_clear_spots", "pmc_transport", "pmc_read_dose", "pmc_read_tally", "pmc_read_ledger",
     "pmc_enable_history_ledger", "pmc_read_history_ledger", "pmc_enable_escape_record", "pmc_read_escape_record",
-    "pmc_enable_let", "pmc_read_let", "pmc_read_let_tally",
+    "pmc_enable_let", "pmc_read_let", "pmc_read_let_tally", "pmc_nonelastic_events",
     "pmc_set_launch", "pmc_autotune", "pmc_transport_noalloc", "pmc_surrogate_dataset", "pmc_train_surrogate",
     "pmc_surrogate_params", "pmc_surrogate_load", "pmc_surrogate_grad", "pmc_gamma_plan_bytes", "pmc_gamma_plan", "pmc_gamma_device",
     "pmc_gamma_index", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables",
@@ -79,6 +79,14 @@ class Ledger(C.Structure):
                                          "queue_high_water", "generations", "dropped", "errors")]
 
 
+class EventYields(C.Structure):
+    _fields_ = [("events", C.c_uint64), ("transparent", C.c_uint64), ("retries", C.c_uint64),
+                ("count", C.c_uint64 * 6), ("energy", C.c_double * 6), ("residual_T", C.c_double),
+                ("excitation_left", C.c_double), ("binding", C.c_double), ("ms", C.c_double)]
+
+
+SPECIES = ("n", "p", "d", "t", "He3", "alpha")
+
 _libs = {}
 _lock = threading.Lock()
 
@@ -111,6 +119,7 @@ def lib(path: str = LIB_PATH):
             L.pmc_enable_escape_record.argtypes = [vp, u64]
             L.pmc_read_escape_record.argtypes = [vp, C.POINTER(C.c_float), u64, C.POINTER(C.c_uint64)]
             L.pmc_enable_let.argtypes = [vp, i]
+            L.pmc_nonelastic_events.argtypes = [vp, i, d, u64, u64, u64, C.POINTER(EventYields)]
             L.pmc_read_let.argtypes = [vp, vp, vp, C.c_size_t]
             L.pmc_read_let_tally.argtypes = [vp, pi64, pi64, C.c_size_t]
             L.pmc_set_launch.argtypes = [vp, i, C.c_int64]
@@ -393,6 +402,17 @@ class Engine:
         r, e = np.empty_like(E), np.empty_like(E)
         self._check(self._L.pmc_debug_tables(self._ctx, material, _dp(E), _dp(r), _dp(e), len(E)))
         return r, e
+
+    def nonelastic_events(self, nuclide, E, n, seed, pid0=0):
+        """n non-elastic events of a proton of energy E (MeV) on the loaded nuclide index
+        `nuclide`, on the device.  Returns the totals: events, transparent, retries,
+        count[species], energy[species] (MeV), residual_T, excitation_left, binding, ms."""
+        y = EventYields()
+        self._check(self._L.pmc_nonelastic_events(self._ctx, nuclide, E, n, seed, pid0, C.byref(y)))
+        out = {k: getattr(y, k) for k, _ in EventYields._fields_ if k not in ("count", "energy")}
+        out["count"] = dict(zip(SPECIES, list(y.count)))
+        out["energy"] = dict(zip(SPECIES, list(y.energy)))
+        return out
 
     def debug_inc(self, nuclide, E, seed, pid0, n, cap=160):
         summ = np.zeros((n, 8))

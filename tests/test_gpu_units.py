@@ -94,3 +94,45 @@ def test_cascade_events_match_oracle(eng, nuc, E):
         assert sum(spec[s][0] for s in sps) + ds[i, 1] == Z + 1
         assert sum(spec[s][1] for s in sps) + ds[i, 2] == A + 1
         assert dp[i, :k, 1].sum() + ds[i, 3] + ds[i, 4] + ds[i, 5] == pytest.approx(E, abs=2e-4)
+
+
+def test_event_generator_totals_equal_the_events_it_runs(eng):
+    """The event-generator entry point runs the transport's event code with the same random
+    streams: its totals equal the sums over the same events run one by one."""
+    e, p = eng
+    n, seed, pid0, E = 3000, 17, 1000, 200.0
+    y = e.nonelastic_events(3, E, n, seed, pid0)
+    ds, dp = e.debug_inc(3, E, seed, pid0, n)
+    assert y["events"] == n
+    assert y["transparent"] == int(ds[:, 7].sum())
+    assert y["retries"] == int(ds[:, 6].sum())
+    live = np.arange(dp.shape[1])[None, :] < ds[:, :1]
+    for k, name in enumerate(("n", "p", "d", "t", "He3", "alpha")):
+        sel = live & (dp[:, :, 0] == k)
+        assert y["count"][name] == int(sel.sum()), name
+        assert y["energy"][name] == pytest.approx(dp[:, :, 1][sel].sum(), abs=n * 2.0 ** -24)
+    ok = ds[:, 7] == 0
+    assert y["residual_T"] == pytest.approx(ds[ok, 3].sum(), abs=n * 2.0 ** -24)
+    assert y["excitation_left"] == pytest.approx(ds[ok, 4].sum(), abs=n * 2.0 ** -24)
+    assert y["ms"] > 0
+
+
+@pytest.mark.parametrize("nuc", [3, 5], ids=["O16", "Ca40"])
+def test_event_generator_yields_match_oracle(eng, nuc):
+    """Table I's reactions (p-16O and p-40Ca at 200 MeV): mean multiplicities and emitted
+    energies per event from 2e5 device events against 2e4 oracle events, within 5 standard
+    errors."""
+    e, p = eng
+    Z, A = p.nuclides[nuc][0], p.nuclides[nuc][1]
+    E = 200.0
+    y = e.nonelastic_events(nuc, E, 200_000, 23)
+    os_, op, _ = O.inc_batch(Z, A, E, 29, 0, 20_000)
+    live = np.arange(op.shape[1])[None, :] < os_[:, :1]
+    ng = y["events"]
+    for k, name in ((0, "n"), (1, "p"), (5, "alpha")):
+        sel = live & (op[:, :, 0] == k)
+        per_ev_n = sel.sum(1)
+        per_ev_T = np.where(sel, op[:, :, 1], 0.0).sum(1)
+        for gv, ov in ((y["count"][name] / ng, per_ev_n), (y["energy"][name] / ng, per_ev_T)):
+            se = ov.std() * np.sqrt(1 / len(ov) + 1 / ng)
+            assert abs(gv - ov.mean()) < 5 * se + 1e-9, (name, gv, ov.mean(), se)
