@@ -32,13 +32,22 @@ import numpy as np  # noqa: E402
 METRIC = "proton histories/s on 1 GB300, full cascade (learned surrogate reported beside it)"
 UNIT = "histories/s"
 N_HISTORIES = 1_000_000
-# Scalar arithmetic operations one condensed-history step needs, counted from its
-# formulas (two Philox4x32-10 blocks 200, uniforms 32, range and inverse-range
-# splines 38, cross-section table 9, two voxel-boundary distances 42, Highland
-# width 18, deflection 40, Bohr straggling 20, deposit and bookkeeping 42): the
-# itemised count is in the design doc.  Peak = FP32/INT32 lanes x SM clock.
-OPS_PER_STEP = 441
+# Scalar operations one condensed-history step needs (the common step: a voxel crossing
+# with multiple scattering and straggling), counted from its formulas with every add,
+# multiply, fused multiply-add, compare, select, conversion, integer and special-function
+# instruction as one (a division as reciprocal + multiply, a square root or logarithm as
+# two): Philox4x32-10 block 99, five uniforms 26, two boundary distances 78, multiple
+# scattering with the direction rotation 73, straggling 25, inverse-range spline 24,
+# range spline 16, fixed-point deposit 23, cross-section table and lambda 13, and the
+# rest of the step logic 53.  Peak = FP32/INT32 lanes x SM clock.
+OPS_PER_STEP = 430
 L2_BYTES = 129 * 2 ** 20
+# DRAM bytes (read + write) of the primary-transport launch per primary history, from a
+# 1-pass ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on this workload
+# (1e6 histories in one launch: 47.8 MB), valid only for the kernel sources it was taken
+# on (their SHA-256 below); otherwise the roofline's traffic is reported as null.
+TRAFFIC = {"bytes_per_history": 47.8, "sources": ("transport.cu", "pmc_device.cuh", "pmc_kernels.cuh"),
+           "sha256": "200bd93a40ca4f560783b85c8423bca57b8ce1a9ae34546fe7f4479863ccf680"}
 
 
 def parse():
@@ -59,6 +68,18 @@ def parse():
     ap.add_argument("--inc-events", type=int, default=2_600_000)
     ap.add_argument("--gamma-histories", type=int, default=10_000_000)
     return ap.parse_args()
+
+
+def traffic_per_launch(histories_per_launch):
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_1409_8336_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != TRAFFIC["sha256"]:
+        return None
+    return TRAFFIC["bytes_per_history"] * histories_per_launch
 
 
 def workload():
@@ -498,7 +519,8 @@ def main():
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "kernel": "transport_kernel (primaries)", "achieved": achieved,
-                         "peak": alu_peak, "unit": "TOP/s", "frac": achieved / alu_peak, "traffic": None,
+                         "peak": alu_peak, "unit": "TOP/s", "frac": achieved / alu_peak,
+                         "traffic": traffic_per_launch(n / max(prof_n / args.steps, 1)),
                          "peak_source": "%s sm_max_mhz x 152 SMs x 128 FP32 lanes" % src,
                          "ops_per_step": OPS_PER_STEP, "steps_per_launch": steps_per_launch,
                          "launch_ms": launch_ms, "primary_span_ms": span_ms,
