@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--no-gamma", action="store_true")
     ap.add_argument("--no-let", action="store_true")
     ap.add_argument("--no-inc", action="store_true")
+    ap.add_argument("--no-plans", action="store_true")
+    ap.add_argument("--plans-scale", type=float, default=1.0, help="histories per plan x this")
+    ap.add_argument("--plans-slots", type=int, default=4)
+    ap.add_argument("--plans-budget-gb", type=float, default=64.0)
     ap.add_argument("--inc-events", type=int, default=2_600_000)
     ap.add_argument("--gamma-histories", type=int, default=10_000_000)
     return ap.parse_args()
@@ -253,6 +257,47 @@ def inc_leg(args, device, with_cpu):
             out["targets"][name]["cpu_baseline"] = {
                 "value": k / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
                 "sample": "%d events in %.2f s" % (k, dt), "seconds_for_batch": n * dt / k}
+    return out
+
+
+def plans_leg(args, device, params):
+    """The multi-plan stream: 64 synthetic CT plans (50-3000 spots, 70-230 MeV, phantoms
+    128x128x96 to 320x320x200 at 1 mm, 1e6-1e7 histories each) through one GPU, several at
+    a time within a device-memory budget; each plan's dose copied to the host when it
+    completes.  Full cascade with the concurrency slots, the same with one slot (plans
+    strictly one after another), and the surrogate form when a trained network is given."""
+    from paper_1409_8336_gb300 import PlanStream
+    from paper_1409_8336_gb300 import workloads as W
+
+    plans = W.config5(scale=args.plans_scale)
+    total = sum(n for _, n, _ in plans)
+    p0 = plans[0][0]
+    out = {"plans": len(plans), "histories": total, "budget_gb": args.plans_budget_gb,
+           "phantoms": sorted({"%dx%dx%d" % p.shape[::-1] for p, _, _ in plans}),
+           "spots_min_max": [min(len(p.spots) for p, _, _ in plans), max(len(p.spots) for p, _, _ in plans)]}
+    forms = [("full_cascade", 0, args.plans_slots), ("full_cascade_one_slot", 0, 1)]
+    if params is not None:
+        forms.append(("surrogate", 1, args.plans_slots))
+    for name, mode, slots in forms:
+        s = PlanStream(device=device, slots=slots, budget_bytes=int(args.plans_budget_gb * 2 ** 30),
+                       fast_math=(args.math == "fast"))
+        s.load_materials(p0.nuclides, p0.materials, p0.hu_bins)
+        if mode == 1:
+            s.load_surrogate(params)
+        s.run(plans[:2], mode, outputs=False)                 # warm-up: modules, pool
+        t0 = time.perf_counter()
+        rc, res = s.run(plans, mode, outputs="dose")
+        wall = time.perf_counter() - t0
+        s.close()
+        ends = np.array([r["t_end_ms"] for r in res])
+        lat = np.array([r["t_end_ms"] - r["t_admit_ms"] for r in res])
+        ok = [r for r in res if r["status"] == 0]
+        out[name] = {"status": rc, "slots": slots, "value": total / wall, "unit": UNIT, "seconds": wall,
+                     "completion_ms_p50": float(np.percentile(ends, 50)),
+                     "completion_ms_p99": float(np.percentile(ends, 99)),
+                     "plan_ms_p50": float(np.percentile(lat, 50)), "plan_ms_p99": float(np.percentile(lat, 99)),
+                     "plans_ok": len(ok), "max_plan_gb": max(r["device_bytes"] for r in res) / 2 ** 30}
+        del res
     return out
 
 
@@ -492,6 +537,10 @@ def main():
     if not args.no_gamma:
         gamma = gamma_leg(args, local, stream, flush, rank == 0 and world == 1 and not args.no_cpu_baseline)
 
+    plans = None
+    if not args.no_plans:
+        plans = plans_leg(args, local, eng.surrogate_params() if surrogate is not None else None)
+
     pk, src = peaks()
     led = ledgers[-1]
     # the primary-transport launches of the two pipelined sub-groups run concurrently: the
@@ -532,6 +581,7 @@ def main():
             "surrogate": surrogate,
             "gamma": gamma,
             "inc_table1": inc,
+            "plans_stream": plans,
             "let": let_leg,
             "other_build": {"math": "ieee" if args.math == "fast" else "fast",
                             "value": world * n * args.steps / (sum(other_ms) / 1e3),

@@ -273,6 +273,57 @@ typedef struct {
 int pmc_nonelastic_events(pmc_ctx* ctx, int nuclide, double E, uint64_t n, uint64_t seed, uint64_t pid0,
                           pmc_event_yields* out);
 
+/* ---- multi-plan stream ---------------------------------------------------------
+ * Many plans (phantom + spots + histories) through one device, several at a time.
+ * A pool of n_slots concurrency slots, each an engine context with its own CUDA
+ * streams, serves the plans in the order given: a plan is admitted when its device
+ * footprint (pmc_plans_bytes) fits in the memory budget left by the plans running;
+ * its slot uploads the phantom, transports (the same kernels, graph and random
+ * streams as pmc_transport, so the dose is bit-identical to a pmc_transport of the
+ * plan alone), copies dose and error out and releases the plan's buffers.  Kernels
+ * of concurrently admitted plans share the SMs.  Allocation is stream-ordered from
+ * one memory pool, so admitting or retiring a plan never synchronises the device.
+ * The paper runs one plan at a time; this serves the batched multi-plan workload.
+ *
+ * pmc_plans_create: opt as for pmc_create (block_size 0 means 256: slots are not
+ *   autotuned; opt->alloc is ignored); budget_bytes > 0.
+ * pmc_plans_load_materials / pmc_plans_load_surrogate: as pmc_load_materials and
+ *   pmc_surrogate_load, for every slot.
+ * pmc_plans_bytes: the device footprint of a plan in `mode`.
+ * pmc_plans_run: runs plans[0..n) (host arrays that must stay valid during the
+ *   call) and fills results[n]; synchronous.  A plan whose footprint exceeds the
+ *   budget is skipped with status PMC_E_OOM.  Returns PMC_OK when every plan
+ *   succeeded, else the first failing plan's status. */
+typedef struct pmc_plan_stream pmc_plan_stream;
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz, x0, y0, z0;      /* cm, as pmc_load_phantom */
+    const int16_t* hu;                  /* HU volume, or NULL with mat and rho */
+    const uint8_t* mat;
+    const float* rho;
+    const pmc_spot* spots;
+    int n_spots;
+    uint64_t n_histories, seed;
+    double* dose_gy;                    /* outputs: host arrays of nx*ny*nz, or NULL */
+    double* sigma_gy;
+} pmc_plan;
+typedef struct {
+    int status;                         /* PMC_OK or the plan's error */
+    int slot;                           /* slot that ran it (-1: never admitted) */
+    uint64_t device_bytes;              /* admitted footprint */
+    double t_admit_ms, t_end_ms;        /* host clock from the start of pmc_plans_run */
+    double gpu_ms;                      /* device time on its slot's stream, upload to dose */
+    pmc_ledger ledger;
+} pmc_plan_result;
+int pmc_plans_create(pmc_plan_stream** out, const pmc_options* opt, int n_slots, uint64_t budget_bytes);
+void pmc_plans_destroy(pmc_plan_stream* s);
+const char* pmc_plans_last_error(const pmc_plan_stream* s);
+int pmc_plans_load_materials(pmc_plan_stream* s, const pmc_nuclide* nuc, int n_nuc, const pmc_material* mat,
+                             int n_mat, const pmc_hu_bin* hu, int n_hu);
+int pmc_plans_load_surrogate(pmc_plan_stream* s, const float* params, size_t n);
+int pmc_plans_bytes(const pmc_plan_stream* s, const pmc_plan* plan, int mode, uint64_t* bytes);
+int pmc_plans_run(pmc_plan_stream* s, const pmc_plan* plans, int n, int mode, pmc_plan_result* results);
+
 /* ---- 3-D gamma index -------------------------------------------------------
  * The dose-comparison metric of Sec. II.D (Low et al.), which the paper also
  * computes on the GPU.  For every reference voxel whose dose exceeds

@@ -6,7 +6,7 @@ C ABI (include/pmc.h).  `Engine` is the thin Python binding of that ABI;
 `workloads` holds the seeded synthetic inputs.
 """
 from .engine import (FULL_CASCADE, NO_ELASTIC, NO_INELASTIC, NO_MCS, NO_STRAGGLING, SURROGATE, Engine, GammaIndex,
-                     PmcError, debug_philox, gamma_index)
+                     PlanStream, PmcError, debug_philox, gamma_index)
 
-__all__ = ["Engine", "PmcError", "GammaIndex", "gamma_index", "debug_philox", "FULL_CASCADE", "SURROGATE", "NO_STRAGGLING", "NO_MCS",
+__all__ = ["Engine", "PlanStream", "PmcError", "GammaIndex", "gamma_index", "debug_philox", "FULL_CASCADE", "SURROGATE", "NO_STRAGGLING", "NO_MCS",
            "NO_ELASTIC", "NO_INELASTIC"]

@@ -6,12 +6,15 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/pmc.h"
@@ -220,6 +223,7 @@ constexpr int kQueues = 7;
 
 struct pmc_ctx {
   pmc_options opt{};
+  cudaMemPool_t pool = nullptr;          // stream-ordered allocation from this pool when set
   int n_sm = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t stream2 = nullptr;      // second stream of the pipelined sub-groups
@@ -295,15 +299,28 @@ int fail(pmc_ctx* c, int code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(ctx, PMC_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+void release(pmc_ctx* ctx, void* p) {
+  if (ctx->pool) cudaFreeAsync(p, ctx->stream);
+  else if (ctx->opt.free) ctx->opt.free(p, ctx->opt.alloc_user);
+  else cudaFree(p);
+}
+
 int dalloc(pmc_ctx* ctx, DevBuf& b, size_t bytes) {
   if (b.p && b.n >= bytes) return PMC_OK;
   if (b.p) {
-    if (ctx->opt.free) ctx->opt.free(b.p, ctx->opt.alloc_user); else cudaFree(b.p);
+    release(ctx, b.p);
     b.p = nullptr;
     b.n = 0;
   }
   if (bytes == 0) return PMC_OK;
-  if (ctx->opt.alloc) {
+  if (ctx->pool) {
+    // stream-ordered: no device-wide synchronisation, so plans on other streams keep running
+    if (cudaMallocFromPoolAsync(&b.p, bytes, ctx->pool, ctx->stream) != cudaSuccess) {
+      cudaGetLastError();
+      b.p = nullptr;
+      return fail(ctx, PMC_E_OOM, "pool allocation of %zu bytes failed", bytes);
+    }
+  } else if (ctx->opt.alloc) {
     b.p = ctx->opt.alloc(bytes, ctx->opt.alloc_user);
     if (!b.p) return fail(ctx, PMC_E_OOM, "allocator returned NULL for %zu bytes", bytes);
   } else if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
@@ -319,7 +336,7 @@ int dalloc(pmc_ctx* ctx, DevBuf& b, size_t bytes) {
 
 void dfree(pmc_ctx* ctx, DevBuf& b) {
   if (!b.p) return;
-  if (ctx->opt.free) ctx->opt.free(b.p, ctx->opt.alloc_user); else cudaFree(b.p);
+  release(ctx, b.p);
   b.p = nullptr;
   b.n = 0;
 }
@@ -405,6 +422,7 @@ void pmc_destroy(pmc_ctx* ctx) {
                      &ctx->d_sx[0], &ctx->d_sx[1], &ctx->d_sy[0][0], &ctx->d_sy[0][1], &ctx->d_sy[1][0],
                      &ctx->d_sy[1][1]};
   for (DevBuf* b : sbufs) dfree(ctx, *b);
+  if (ctx->pool) cudaStreamSynchronize(ctx->stream);   // the stream-ordered frees have run
   cudaStreamDestroy(ctx->stream);
   cudaStreamDestroy(ctx->stream2);
   cudaEventDestroy(ctx->fork_ev);
@@ -1845,4 +1863,234 @@ extern "C" int pmc_gamma_index(const double* ref, const double* eval, int nx, in
   cudaFree(dg);
   cudaFree(dp);
   return rc;
+}
+
+// ---- multi-plan stream: concurrent plans admitted by device memory ----------
+// A pool of concurrency slots, each an engine context with its own streams,
+// serves a list of plans in order.  A plan is admitted when its device
+// footprint fits in what the budget leaves; its slot then uploads the phantom,
+// transports, copies the dose out and releases the plan's buffers.  The slots'
+// persistent kernels share the SMs, so the tail generations of one plan overlap
+// the full-width launches of another.  All allocation is stream-ordered from
+// one memory pool: a plan starting or ending never synchronises the device.
+struct pmc_plan_stream {
+  pmc_options opt{};
+  uint64_t budget = 0;
+  cudaMemPool_t pool = nullptr;
+  std::vector<pmc_ctx*> slots;
+  bool have_materials = false, have_surrogate = false;
+  std::string err;
+};
+
+namespace {
+
+int sfail(pmc_plan_stream* S, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  S->err = buf;
+  return code;
+}
+
+// Pool allocations are rounded to the pool's 2 MiB granularity.
+uint64_t pool_round(uint64_t b) { return b == 0 ? 0 : (b + (2ull << 20) - 1) / (2ull << 20) * (2ull << 20); }
+
+uint64_t plan_footprint(const pmc_options& opt, const pmc_plan& pl, int mode) {
+  const uint64_t nv = static_cast<uint64_t>(pl.nx) * pl.ny * pl.nz;
+  const uint64_t B = static_cast<uint64_t>(opt.n_batches);
+  const int64_t chunk = opt.chunk > 0 ? opt.chunk : (1ll << 22);
+  const uint64_t qcap = std::max<uint64_t>(std::min<uint64_t>(pl.n_histories, static_cast<uint64_t>(chunk)), 1024);
+  const uint64_t n_chunks = (pl.n_histories + qcap - 1) / qcap;
+  uint64_t b = 0;
+  b += pl.hu ? pool_round(nv * 2) : pool_round(nv) + pool_round(nv * 4);
+  b += pool_round(nv * B * 8) + 2 * pool_round(nv * 8);
+  b += kQueues * pool_round(qcap * sizeof(Particle));
+  b += pool_round((n_chunks * (3 * kGenerations + 1) + 1) * sizeof(unsigned));
+  b += pool_round(sizeof(Counters)) + pool_round(8) + pool_round(static_cast<uint64_t>(pl.n_spots) * sizeof(SpotDev));
+  if (mode == PMC_SURROGATE) b += 2 * (pool_round(qcap * kSurrIn * 4) + 2 * pool_round(qcap * kSurrOut * 4));
+  return b;
+}
+
+// Frees what a plan allocated (phantom, tallies, queues); keeps the tables.
+void release_plan(pmc_ctx* ctx) {
+  DevBuf* bufs[] = {&ctx->d_mat, &ctx->d_rho, &ctx->d_hu, &ctx->d_tally, &ctx->d_dose, &ctx->d_sigma,
+                    &ctx->d_counters, &ctx->d_counts, &ctx->d_seed, &ctx->d_spots, &ctx->d_q[0], &ctx->d_q[1],
+                    &ctx->d_q[2], &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_sx[0],
+                    &ctx->d_sx[1], &ctx->d_sy[0][0], &ctx->d_sy[0][1], &ctx->d_sy[1][0], &ctx->d_sy[1][1]};
+  for (DevBuf* b : bufs) dfree(ctx, *b);
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  ctx->have_phantom = false;
+  ctx->have_run = false;
+  ctx->n_vox = 0;
+  ctx->geo = Geometry{};
+}
+
+int run_plan(pmc_ctx* ctx, const pmc_plan& pl, int mode, pmc_plan_result* r) {
+  int rc = pmc_load_phantom(ctx, pl.nx, pl.ny, pl.nz, pl.dx, pl.dy, pl.dz, pl.x0, pl.y0, pl.z0, pl.hu, pl.mat, pl.rho);
+  if (rc == PMC_OK) rc = pmc_clear_spots(ctx);
+  if (rc == PMC_OK) rc = pmc_add_spots(ctx, pl.spots, pl.n_spots);
+  if (rc == PMC_OK) rc = pmc_transport(ctx, pl.n_histories, pl.seed, mode, nullptr);
+  if (rc == PMC_OK && (pl.dose_gy || pl.sigma_gy))
+    rc = pmc_read_dose(ctx, pl.dose_gy, pl.sigma_gy, static_cast<size_t>(pl.nx) * pl.ny * pl.nz);
+  if (rc == PMC_OK) rc = pmc_read_ledger(ctx, &r->ledger);
+  release_plan(ctx);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && rc == PMC_OK) rc = PMC_E_CUDA;   // frees done
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int pmc_plans_create(pmc_plan_stream** out, const pmc_options* opt, int n_slots, uint64_t budget) {
+  if (!out || n_slots < 1 || n_slots > 64 || budget == 0) return PMC_E_INVALID;
+  *out = nullptr;
+  pmc_plan_stream* S = new (std::nothrow) pmc_plan_stream();
+  if (!S) return PMC_E_OOM;
+  if (opt) S->opt = *opt;
+  if (S->opt.n_batches == 0) S->opt.n_batches = 10;
+  if (S->opt.block_size <= 0) S->opt.block_size = 256;   // fixed launch shape: no per-slot autotuning
+  S->opt.alloc = nullptr;
+  S->opt.free = nullptr;
+  S->budget = budget;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = S->opt.device;
+  if (cudaSetDevice(S->opt.device) != cudaSuccess || cudaMemPoolCreate(&S->pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    delete S;
+    return PMC_E_CUDA;
+  }
+  uint64_t keep = ~0ull;   // keep freed memory in the pool between plans
+  cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  for (int i = 0; i < n_slots; ++i) {
+    pmc_ctx* c = nullptr;
+    const int rc = pmc_create(&c, &S->opt);
+    if (rc != PMC_OK) {
+      pmc_plans_destroy(S);
+      return rc;
+    }
+    c->pool = S->pool;
+    S->slots.push_back(c);
+  }
+  *out = S;
+  return PMC_OK;
+}
+
+extern "C" void pmc_plans_destroy(pmc_plan_stream* S) {
+  if (!S) return;
+  for (pmc_ctx* c : S->slots) pmc_destroy(c);
+  if (S->pool) {
+    cudaSetDevice(S->opt.device);
+    cudaMemPoolDestroy(S->pool);
+  }
+  delete S;
+}
+
+extern "C" const char* pmc_plans_last_error(const pmc_plan_stream* S) { return S ? S->err.c_str() : "null stream"; }
+
+extern "C" int pmc_plans_load_materials(pmc_plan_stream* S, const pmc_nuclide* nuc, int n_nuc,
+                                        const pmc_material* mat, int n_mat, const pmc_hu_bin* hu, int n_hu) {
+  if (!S) return PMC_E_INVALID;
+  for (pmc_ctx* c : S->slots) {
+    const int rc = pmc_load_materials(c, nuc, n_nuc, mat, n_mat, hu, n_hu);
+    if (rc != PMC_OK) return sfail(S, rc, "load materials: %s", c->err.c_str());
+  }
+  S->have_materials = true;
+  S->have_surrogate = false;
+  return PMC_OK;
+}
+
+extern "C" int pmc_plans_load_surrogate(pmc_plan_stream* S, const float* params, size_t n) {
+  if (!S || !params) return PMC_E_INVALID;
+  if (!S->have_materials) return sfail(S, PMC_E_INVALID, "load materials first");
+  for (pmc_ctx* c : S->slots) {
+    const int rc = pmc_surrogate_load(c, params, n);
+    if (rc != PMC_OK) return sfail(S, rc, "load surrogate: %s", c->err.c_str());
+  }
+  S->have_surrogate = true;
+  return PMC_OK;
+}
+
+extern "C" int pmc_plans_bytes(const pmc_plan_stream* S, const pmc_plan* plan, int mode, uint64_t* bytes) {
+  if (!S || !plan || !bytes || plan->nx < 1 || plan->ny < 1 || plan->nz < 1) return PMC_E_INVALID;
+  *bytes = plan_footprint(S->opt, *plan, mode);
+  return PMC_OK;
+}
+
+extern "C" int pmc_plans_run(pmc_plan_stream* S, const pmc_plan* plans, int n, int mode, pmc_plan_result* res) {
+  if (!S || n < 0 || (n > 0 && (!plans || !res))) return PMC_E_INVALID;
+  if (!S->have_materials) return sfail(S, PMC_E_INVALID, "load materials first");
+  if (mode != PMC_FULL_CASCADE && mode != PMC_SURROGATE) return sfail(S, PMC_E_INVALID, "unknown mode %d", mode);
+  if (mode == PMC_SURROGATE && !S->have_surrogate) return sfail(S, PMC_E_INVALID, "load the surrogate first");
+  std::vector<uint64_t> fp(n);
+  for (int i = 0; i < n; ++i) {
+    res[i] = pmc_plan_result{};
+    res[i].status = PMC_E_INVALID;
+    res[i].slot = -1;
+    if (plans[i].nx < 1 || plans[i].ny < 1 || plans[i].nz < 1) return sfail(S, PMC_E_INVALID, "plan %d: bad grid", i);
+    fp[i] = plan_footprint(S->opt, plans[i], mode);
+    res[i].device_bytes = fp[i];
+  }
+  std::mutex m;
+  std::condition_variable cv;
+  int next = 0;
+  uint64_t admitted = 0;
+  const auto t0 = std::chrono::steady_clock::now();
+  auto ms_since = [&]() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  };
+  auto slot_main = [&](int slot) {
+    pmc_ctx* ctx = S->slots[slot];
+    cudaSetDevice(S->opt.device);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (;;) {
+      int i = -1;
+      {
+        std::unique_lock<std::mutex> lk(m);
+        for (;;) {
+          if (next >= n) break;
+          if (fp[next] > S->budget) {   // can never be admitted
+            res[next].status = PMC_E_OOM;
+            ++next;
+            continue;
+          }
+          if (admitted + fp[next] <= S->budget) {
+            i = next++;
+            admitted += fp[i];
+            res[i].t_admit_ms = ms_since();
+            res[i].slot = slot;
+            break;
+          }
+          cv.wait(lk);
+        }
+      }
+      if (i < 0) break;
+      cudaEventRecord(e0, ctx->stream);
+      int rc = run_plan(ctx, plans[i], mode, &res[i]);
+      cudaEventRecord(e1, ctx->stream);
+      float gms = 0.0f;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&gms, e0, e1) == cudaSuccess)
+        res[i].gpu_ms = gms;
+      {
+        std::lock_guard<std::mutex> lk(m);
+        admitted -= fp[i];
+        res[i].status = rc;
+        res[i].t_end_ms = ms_since();
+      }
+      cv.notify_all();
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  };
+  std::vector<std::thread> threads;
+  for (size_t k = 0; k < S->slots.size(); ++k) threads.emplace_back(slot_main, static_cast<int>(k));
+  for (auto& t : threads) t.join();
+  int first_bad = PMC_OK;
+  for (int i = 0; i < n; ++i)
+    if (res[i].status != PMC_OK) { first_bad = res[i].status; break; }
+  return first_bad;
 }

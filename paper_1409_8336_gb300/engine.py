@@ -27,7 +27,9 @@ EXPORTS = [
     "pmc_create", "pmc_destroy", "pmc_last_error", "pmc_load_materials", "pmc_load_phantom", "pmc_add_spots",
     "pmc_clear_spots", "pmc_transport", "pmc_read_dose", "pmc_read_tally", "pmc_read_ledger",
     "pmc_enable_history_ledger", "pmc_read_history_ledger", "pmc_enable_escape_record", "pmc_read_escape_record",
-    "pmc_enable_let", "pmc_read_let", "pmc_read_let_tally", "pmc_nonelastic_events",
+    "pmc_enable_let", "pmc_read_let", "pmc_read_let_tally", "pmc_nonelastic_events", "pmc_plans_create",
+    "pmc_plans_destroy", "pmc_plans_last_error", "pmc_plans_load_materials", "pmc_plans_load_surrogate",
+    "pmc_plans_bytes", "pmc_plans_run",
     "pmc_set_launch", "pmc_autotune", "pmc_transport_noalloc", "pmc_surrogate_dataset", "pmc_train_surrogate",
     "pmc_surrogate_params", "pmc_surrogate_load", "pmc_surrogate_grad", "pmc_gamma_plan_bytes", "pmc_gamma_plan", "pmc_gamma_device",
     "pmc_gamma_index", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables",
@@ -85,6 +87,19 @@ class EventYields(C.Structure):
                 ("excitation_left", C.c_double), ("binding", C.c_double), ("ms", C.c_double)]
 
 
+class Plan(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("dy", C.c_double),
+                ("dz", C.c_double), ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
+                ("hu", C.c_void_p), ("mat", C.c_void_p), ("rho", C.c_void_p), ("spots", C.c_void_p),
+                ("n_spots", C.c_int), ("n_histories", C.c_uint64), ("seed", C.c_uint64),
+                ("dose_gy", C.c_void_p), ("sigma_gy", C.c_void_p)]
+
+
+class PlanResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("slot", C.c_int), ("device_bytes", C.c_uint64), ("t_admit_ms", C.c_double),
+                ("t_end_ms", C.c_double), ("gpu_ms", C.c_double), ("ledger", Ledger)]
+
+
 SPECIES = ("n", "p", "d", "t", "He3", "alpha")
 
 _libs = {}
@@ -100,7 +115,7 @@ def lib(path: str = LIB_PATH):
                                   "(or __graft_entry__.build())" % os.path.basename(path))
             L = C.CDLL(path)
             vp, i, u64, d = C.c_void_p, C.c_int, C.c_uint64, C.c_double
-            pd, pi64 = C.POINTER(C.c_double), C.POINTER(C.c_int64)
+            pd, pi64, pf = C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_float)
             L.pmc_create.argtypes = [C.POINTER(vp), C.POINTER(Options)]
             L.pmc_destroy.argtypes = [vp]
             L.pmc_destroy.restype = None
@@ -120,11 +135,20 @@ def lib(path: str = LIB_PATH):
             L.pmc_read_escape_record.argtypes = [vp, C.POINTER(C.c_float), u64, C.POINTER(C.c_uint64)]
             L.pmc_enable_let.argtypes = [vp, i]
             L.pmc_nonelastic_events.argtypes = [vp, i, d, u64, u64, u64, C.POINTER(EventYields)]
+            L.pmc_plans_create.argtypes = [C.POINTER(vp), C.POINTER(Options), i, u64]
+            L.pmc_plans_destroy.argtypes = [vp]
+            L.pmc_plans_destroy.restype = None
+            L.pmc_plans_last_error.argtypes = [vp]
+            L.pmc_plans_last_error.restype = C.c_char_p
+            L.pmc_plans_load_materials.argtypes = [vp, C.POINTER(Nuclide), i, C.POINTER(Material), i,
+                                                   C.POINTER(HuBin), i]
+            L.pmc_plans_load_surrogate.argtypes = [vp, pf, C.c_size_t]
+            L.pmc_plans_bytes.argtypes = [vp, C.POINTER(Plan), i, C.POINTER(C.c_uint64)]
+            L.pmc_plans_run.argtypes = [vp, C.POINTER(Plan), i, i, C.POINTER(PlanResult)]
             L.pmc_read_let.argtypes = [vp, vp, vp, C.c_size_t]
             L.pmc_read_let_tally.argtypes = [vp, pi64, pi64, C.c_size_t]
             L.pmc_set_launch.argtypes = [vp, i, C.c_int64]
             L.pmc_autotune.argtypes = [vp, u64, u64, C.POINTER(C.c_int), C.POINTER(C.c_int64)]
-            pf = C.POINTER(C.c_float)
             L.pmc_surrogate_dataset.argtypes = [vp, u64, u64, pf]
             L.pmc_train_surrogate.argtypes = [vp, C.POINTER(TrainOpts), C.POINTER(TrainResult)]
             L.pmc_surrogate_params.argtypes = [vp, pf, C.c_size_t]
@@ -174,6 +198,21 @@ def _torch_allocator(device):
     return AllocFn(alloc), FreeFn(free)
 
 
+def _material_args(nuclides, materials, hu_bins):
+    nuc = (Nuclide * len(nuclides))(*[Nuclide(*n) for n in nuclides])
+    mats = []
+    for m in materials:
+        M = Material()
+        M.n = len(m["nuc"])
+        for k, (ni, w) in enumerate(zip(m["nuc"], m["w"])):
+            M.nuc[k], M.w[k] = ni, w
+        M.rho, M.I_eV, M.own_table = m["rho"], m.get("I_eV", 0.0), int(m.get("own_table", 0))
+        mats.append(M)
+    mat = (Material * len(mats))(*mats)
+    hu = (HuBin * max(1, len(hu_bins)))(*[HuBin(*b) for b in hu_bins])
+    return nuc, len(nuclides), mat, len(mats), hu, len(hu_bins)
+
+
 class Engine:
     """One engine context on one GPU.  Method names follow the C ABI."""
 
@@ -212,18 +251,7 @@ class Engine:
 
     # --- inputs ---------------------------------------------------------
     def load_materials(self, nuclides, materials, hu_bins=()):
-        nuc = (Nuclide * len(nuclides))(*[Nuclide(*n) for n in nuclides])
-        mats = []
-        for m in materials:
-            M = Material()
-            M.n = len(m["nuc"])
-            for k, (ni, w) in enumerate(zip(m["nuc"], m["w"])):
-                M.nuc[k], M.w[k] = ni, w
-            M.rho, M.I_eV, M.own_table = m["rho"], m.get("I_eV", 0.0), int(m.get("own_table", 0))
-            mats.append(M)
-        mat = (Material * len(mats))(*mats)
-        hu = (HuBin * max(1, len(hu_bins)))(*[HuBin(*b) for b in hu_bins])
-        self._check(self._L.pmc_load_materials(self._ctx, nuc, len(nuclides), mat, len(mats), hu, len(hu_bins)))
+        self._check(self._L.pmc_load_materials(self._ctx, *_material_args(nuclides, materials, hu_bins)))
 
     def load_phantom(self, shape, voxel, origin, hu=None, mat=None, rho=None):
         """shape (nz, ny, nx); arrays [nz, ny, nx] in host memory (pinned or pageable)."""
@@ -425,6 +453,105 @@ class Engine:
         out = np.empty((len(u), 5))
         self._check(self._L.pmc_debug_elastic(self._ctx, nuclide, E, _dp(u), _dp(out), len(u)))
         return out
+
+
+class PlanStream:
+    """Many plans through one GPU, several at a time, admitted by a device-memory budget
+    (pmc_plans_* of the C ABI).  Plans are workloads.Problem-like objects (shape, voxel,
+    origin, hu or mat/rho, spots) with a history count and a seed."""
+
+    def __init__(self, device=0, slots=4, budget_bytes=64 << 30, n_batches=10, physics_flags=0, block_size=0,
+                 chunk=0, fast_math=False):
+        self._L = lib(LIB_FAST_PATH if fast_math else LIB_PATH)
+        opt = Options()
+        opt.device, opt.n_batches, opt.physics_flags = device, n_batches, physics_flags
+        opt.block_size, opt.chunk = block_size, chunk
+        self._s = C.c_void_p()
+        rc = self._L.pmc_plans_create(C.byref(self._s), C.byref(opt), slots, budget_bytes)
+        if rc != PMC_OK:
+            raise PmcError(rc, "pmc_plans_create failed")
+        self.n_batches = n_batches
+
+    def close(self):
+        if self._s:
+            self._L.pmc_plans_destroy(self._s)
+            self._s = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def _check(self, rc):
+        if rc != PMC_OK:
+            raise PmcError(rc, self._L.pmc_plans_last_error(self._s).decode())
+
+    def load_materials(self, nuclides, materials, hu_bins=()):
+        self._check(self._L.pmc_plans_load_materials(self._s, *_material_args(nuclides, materials, hu_bins)))
+
+    def load_surrogate(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self._L.pmc_plans_load_surrogate(self._s, _fp(p), p.size))
+
+    @staticmethod
+    def _plan(prob, n, seed, keep, outputs=True):
+        nz, ny, nx = prob.shape
+        pl = Plan()
+        pl.nx, pl.ny, pl.nz = nx, ny, nz
+        pl.dx, pl.dy, pl.dz = prob.voxel
+        pl.x0, pl.y0, pl.z0 = prob.origin
+
+        def arr(a, dt):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data
+
+        pl.hu = arr(prob.hu, np.int16)
+        if prob.hu is None:
+            pl.mat, pl.rho = arr(prob.mat, np.uint8), arr(prob.rho, np.float32)
+        pl.spots = arr(prob.spots, np.float64)
+        pl.n_spots = len(prob.spots)
+        pl.n_histories, pl.seed = n, seed
+        dose = sigma = None
+        if outputs:
+            dose = np.empty(nx * ny * nz)
+            keep.append(dose)
+            pl.dose_gy = dose.ctypes.data
+            if outputs != "dose":
+                sigma = np.empty(nx * ny * nz)
+                keep.append(sigma)
+                pl.sigma_gy = sigma.ctypes.data
+        return pl, dose, sigma
+
+    def plan_bytes(self, prob, n, mode=0):
+        keep = []
+        pl, _, _ = self._plan(prob, n, 0, keep, outputs=False)
+        b = C.c_uint64(0)
+        self._check(self._L.pmc_plans_bytes(self._s, C.byref(pl), mode, C.byref(b)))
+        return b.value
+
+    def run(self, plans, mode=0, outputs=True):
+        """plans: list of (problem, n_histories, seed); outputs True (dose and sigma), "dose"
+        or False.  Returns (status, one dict per plan: status, slot, device_bytes,
+        t_admit_ms, t_end_ms, gpu_ms, ledger, dose / sigma in Gy)."""
+        keep, arr, outs = [], (Plan * max(1, len(plans)))(), []
+        for i, (prob, n, seed) in enumerate(plans):
+            pl, dose, sigma = self._plan(prob, n, seed, keep, outputs)
+            arr[i] = pl
+            outs.append((dose, sigma))
+        res = (PlanResult * max(1, len(plans)))()
+        rc = self._L.pmc_plans_run(self._s, arr, len(plans), mode, res)
+        out = []
+        for i in range(len(plans)):
+            r = res[i]
+            out.append({"status": r.status, "slot": r.slot, "device_bytes": r.device_bytes,
+                        "t_admit_ms": r.t_admit_ms, "t_end_ms": r.t_end_ms, "gpu_ms": r.gpu_ms,
+                        "ledger": {k: getattr(r.ledger, k) for k, _ in Ledger._fields_},
+                        "dose": outs[i][0], "sigma": outs[i][1]})
+        return rc, out
 
 
 def gamma_index(ref, ev, voxel, dose_pct=2.0, dta_mm=2.0, threshold=0.1, search_mm=0.0, fast_math=False,

@@ -184,6 +184,47 @@ def config3(n_batches=10, flags=0, shape=(160, 256, 256), voxel=0.1, n_layers=40
                    name="ct-%dx%dx%d-%.0fmm-%dspots" % (nx, ny, nz, voxel * 10, len(rows)))
 
 
+def config5(n_plans=64, n_phantoms=8, n_batches=10, flags=0, seed=5, scale=1.0):
+    """Multi-plan stream: n_plans synthetic CT plans, each on one of n_phantoms seeded CT
+    phantoms of 1 mm voxels from 128x128x96 to 320x320x200 (shared between plans), with
+    50-3000 spots (log-uniform) in energy layers within 70-230 MeV on a 5 mm grid,
+    lognormal(0, 0.5) weights, and 1e6-1e7 histories (log-uniform; times `scale`).
+    Returns [(Problem, n_histories, seed)]."""
+    rng = np.random.default_rng(seed)
+    phantoms = []
+    for k in range(n_phantoms):
+        nxy = int(rng.integers(8, 21)) * 16            # 128 .. 320
+        nz = int(rng.integers(12, 26)) * 8              # 96 .. 200
+        if k == 0:
+            nxy, nz = 128, 96
+        if k == n_phantoms - 1:
+            nxy, nz = 320, 200
+        phantoms.append(ct_phantom((nz, nxy, nxy), 0.1, seed * 1000 + k))
+    mats = [WATER, AIR, LUNG, BONE_LO, CORTICAL_BONE, TITANIUM]
+    plans = []
+    for i in range(n_plans):
+        hu = phantoms[int(rng.integers(n_phantoms))]
+        nz, ny, nx = hu.shape
+        n_spots = int(round(np.exp(rng.uniform(np.log(50), np.log(3000)))))
+        n_layers = int(np.clip(round(n_spots / 50), 1, 60))
+        per_layer = max(1, n_spots // n_layers)
+        e_lo = rng.uniform(70.0, 150.0)
+        e_hi = min(230.0, e_lo + rng.uniform(20.0, 80.0))
+        side = int(np.ceil(np.sqrt(per_layer)))
+        rows = []
+        for E in np.linspace(e_lo, e_hi, n_layers):
+            for j in range(per_layer):
+                iy, ix = divmod(j, side)
+                rows.append(spot_row(float(E), x=(ix - (side - 1) / 2) * 0.5, y=(iy - (side - 1) / 2) * 0.5,
+                                     sigma=0.3, weight=float(rng.lognormal(0.0, 0.5))))
+        n_hist = int(round(np.exp(rng.uniform(np.log(1e6), np.log(1e7))) * scale))
+        prob = Problem(NUCLIDES, mats, hu.shape, (0.1, 0.1, 0.1), (-nx * 0.05, -ny * 0.05, 0.0), np.array(rows),
+                       hu=hu, hu_bins=list(HU_BINS), n_batches=n_batches, flags=flags,
+                       name="plan%02d-ct-%dx%dx%d-%dspots" % (i, nx, ny, nz, len(rows)))
+        plans.append((prob, max(n_hist, 1), seed * 100003 + i))
+    return plans
+
+
 CONFIG_HISTORIES = {1: 20000, 2: 1000000, 3: 10000000}
 
 

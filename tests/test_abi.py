@@ -94,3 +94,15 @@ def test_gamma_plan_counts_the_search_sphere(libpmc):
     assert libpmc.pmc_gamma_device(256, 512, 1024, 0, 4, 4, 2.0, 0.1, None, None) == -1
     assert libpmc.pmc_gamma_device(260, 512, 1024, 4, 4, 4, 2.0, 0.1, None, None) == -1
     assert libpmc.pmc_gamma_device(256, 512, 1024, 4, 4, 4, 0.0, 0.1, None, None) == -1
+
+
+def test_binding_loads_and_declares_every_entry_point():
+    """The Python binding loads both builds and sets the argument types of every export
+    (no device call)."""
+    from paper_1409_8336_gb300 import build, engine
+
+    build.build()
+    for path in (engine.LIB_PATH, engine.LIB_FAST_PATH):
+        L = engine.lib(path)
+        for name in engine.EXPORTS:
+            assert getattr(L, name).argtypes is not None or name in ("pmc_last_error",), name
