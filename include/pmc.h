@@ -203,8 +203,9 @@ int pmc_read_profile(pmc_ctx* ctx, double* ms, int64_t* launches, int64_t* prima
  * callback or real-time loop that must not synchronise or stall on the
  * allocator, or an application that gave its whole device memory to its own
  * pool.  Runs the same kernels and physics as pmc_transport and produces the
- * same tallies for the same seed, with all scratch (particle queues,
- * counters, spot table, seed) in one static device array of
+ * same tallies for the same seed, with all scratch (particle queues, the
+ * residual nuclei between cascade and evaporation, counters, spot table, seed)
+ * in one static device array of
  * PMC_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
  * the process exits.  Inputs are the context's loaded materials, phantom and
  * spots; outputs are caller-owned device arrays: tally [n_voxels][n_batches]
@@ -217,7 +218,8 @@ int pmc_read_profile(pmc_ctx* ctx, double* ms, int64_t* launches, int64_t* prima
  * Blocks until done; pmc_read_ledger then reports this run. */
 #define PMC_NOALLOC_CHUNK 65536          /* histories per sub-group */
 #define PMC_NOALLOC_MAX_SPOTS 4096
-#define PMC_NOALLOC_SCRATCH_BYTES (4ull * PMC_NOALLOC_CHUNK * 48ull + 768ull + PMC_NOALLOC_MAX_SPOTS * 56ull)
+#define PMC_NOALLOC_SCRATCH_BYTES \
+    (4ull * PMC_NOALLOC_CHUNK * 48ull + PMC_NOALLOC_CHUNK * 128ull + 768ull + PMC_NOALLOC_MAX_SPOTS * 56ull)
 int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int64_t* tally,
                           double* dose_gy, double* sigma_gy, void* stream);
 

@@ -52,19 +52,21 @@ __device__ __forceinline__ float binding(const float* bt, int Z, int A) {
 }
 
 // Width integral int_0^X (X - x) exp(2 sqrt(a x)) dx: closed form
-// (exp(2Y)(Y^2 - 3Y/2 + 3/4) + Y^2/2 - 3/4)/a^2 with Y = sqrt(a X); its power
-// series sum_{n>=4} 2^(n-2)(n-1)(n-3)/n! Y^n / a^2 where the closed form cancels.
+// (exp(2Y)(Y^2 - 3Y/2 + 3/4) + Y^2/2 - 3/4)/a^2 with Y = sqrt(a X); below Y = 1,
+// where the closed form cancels, its power series sum_{n>=4} c_n Y^n / a^2 with
+// c_n = 2^(n-2)(n-1)(n-3)/n!, summed by Horner's rule to n = 18.
 __device__ float width_integral(float X, float a) {
   if (X <= 0.0f) return 0.0f;
   const float Y = sqrtf(a * X);
   if (Y >= 1.0f) return (expf(2.0f * Y) * (Y * Y - 1.5f * Y + 0.75f) + 0.5f * Y * Y - 0.75f) / (a * a);
-  float term = Y * Y * Y * Y * (4.0f / 24.0f);   // 2^(n-2)/n! Y^n at n = 4
-  float sum = 0.0f;
-  for (int n = 4; n <= 18; ++n) {
-    sum += term * static_cast<float>((n - 1) * (n - 3));
-    term *= 2.0f * Y / static_cast<float>(n + 1);
-  }
-  return sum / (a * a);
+  constexpr float c[15] = {5.00000000e-01f, 5.33333333e-01f, 3.33333333e-01f, 1.52380952e-01f, 5.55555556e-02f,
+                           1.69312169e-02f, 4.44444444e-03f, 1.02613436e-03f, 2.11640212e-04f, 3.94667061e-05f,
+                           6.71873688e-06f, 1.05244550e-06f, 1.52698565e-07f, 2.06361862e-08f, 2.61023189e-09f};
+  float h = c[14];
+#pragma unroll
+  for (int k = 13; k >= 0; --k) h = fmaf(h, Y, c[k]);
+  const float Y2 = Y * Y;
+  return h * Y2 * Y2 / (a * a);
 }
 
 // z in [0, X] with density z exp(2 sqrt(a (X - z))), exact rejection.
@@ -166,185 +168,245 @@ __device__ void nn_collide(float3 p1, float E1, float m1, float3 p2, float E2, f
   T2o = (Et - e1o) - m2;
 }
 
-// The event.  Sink receives products (index, species, kinetic energy, direction
-// in the frame where the incident proton moves along +z), then the residual.
+// ---------------------------------------------------------------------------
+// The event, as steps that a driver strings together: attempt setup, one flight
+// of the current nucleon, the residual nucleus of a finished attempt, the
+// emission of the cascade nucleons, and the evaporation chain.  A driver that
+// calls them in order consumes the event's random stream exactly as a single
+// sequential routine would, whatever it interleaves between events.
+// ---------------------------------------------------------------------------
+struct IncState {
+  IncP p;                   // the nucleon in flight (P[ip] is stale while it flies)
+  int ip, n, sea0, sea1, crossings, iters;
+  bool any;
+};
+
+// Residual nucleus after a successful cascade attempt (double precision bookkeeping).
+struct Residual {
+  double Ex, px, py, pz, bind;
+  int Z, A;
+};
+
+// Attempt setup: entry point uniform on the projected disc of the outer sphere,
+// the incident proton refracted into the outer shell.
+__device__ __forceinline__ void inc_setup(const NucleusModel& nu, float E, Stream& st, IncP* P, IncState& s) {
+  s.n = 1;
+  s.ip = 0;
+  s.sea0 = nu.A - nu.Z;
+  s.sea1 = nu.Z;
+  s.any = false;
+  s.crossings = 0;
+  s.iters = 0;
+  const float b = nu.Rout * sqrtf(st.next());
+  float sph, cph;
+  sincospif(2.0f * st.next(), &sph, &cph);
+  IncP& p0 = s.p;
+  p0.q = 1; p0.T = E; p0.done = 0; p0.refl = 0;
+  p0.rx = b * cph; p0.ry = b * sph; p0.rz = -sqrtf(fmaxf(0.0f, nu.Rout * nu.Rout - b * b));
+  p0.dx = 0.0f; p0.dy = 0.0f; p0.dz = 1.0f;
+  const float ir = rsqrtf(p0.rx * p0.rx + p0.ry * p0.ry + p0.rz * p0.rz);
+  cross_boundary(p0, -p0.rx * ir, -p0.ry * ir, -p0.rz * ir, 0.0f, nu.V[1][kShells - 1], kMp);
+  p0.shell = kShells - 1;
+}
+
+// One flight of s.p: to the next shell boundary (refraction or reflection) or to
+// a sampled NN collision (Pauli-blocked or not).  Returns true when the nucleon
+// has finished (escaped: done = 1; captured or trapped: done = 2).
+__device__ __forceinline__ bool inc_flight(const NucleusModel& nu, Stream& st, IncP* P, IncState& s) {
+  IncP& p = s.p;
+  const int q = p.q;
+  const float m = q ? kMp : kMn;
+  const int i = p.shell;
+  if (p.T - nu.V[q][i] <= 0.0f) { p.done = 2; return true; }
+  if (++s.iters > kIncIterations) { p.done = 2; return true; }   // bounded loop: captured
+  const float s_out = dist_out(p, nu.r[i + 1]);
+  const float s_in = i > 0 ? dist_in(p, nu.r[i]) : -1.0f;
+  const bool inner = s_in >= 0.0f && s_in < s_out;
+  const float s_b = inner ? s_in : s_out;
+  const float sl = sigma_nn(p.T, true) * kFm2PerMb, su = sigma_nn(p.T, false) * kFm2PerMb;
+  const float rate_p = s.sea1 > 0 ? nu.rho[1][i] * (q == 1 ? sl : su) : 0.0f;
+  const float rate_n = s.sea0 > 0 ? nu.rho[0][i] * (q == 0 ? sl : su) : 0.0f;
+  const float rate = rate_p + rate_n;
+  const float uc = st.next();
+  const float s_c = rate > 0.0f ? -logf(uc) / rate : 3.0e38f;
+  if (s_c < s_b) {
+    p.rx += s_c * p.dx; p.ry += s_c * p.dy; p.rz += s_c * p.dz;
+    const int q2 = st.next() * rate < rate_p ? 1 : 0;
+    const float m2 = q2 ? kMp : kMn;
+    const float p2m = nu.pF[q2][i] * cbrtf(st.next());
+    const float3 d2 = iso_dir(st);
+    const float3 ns = iso_dir(st);
+    const float p1m = mom(p.T, m);
+    float3 p1o, p2o;
+    float T1o, T2o;
+    nn_collide(make_float3(p1m * p.dx, p1m * p.dy, p1m * p.dz), p.T + m, m,
+               make_float3(p2m * d2.x, p2m * d2.y, p2m * d2.z), sqrtf(p2m * p2m + m2 * m2), m2, ns, p1o, T1o, p2o,
+               T2o);
+    if (T1o < nu.TF[q][i] || T2o < nu.TF[q2][i]) return false;   // Pauli blocked
+    if (s.n >= kIncStack) return false;                           // stack full: treated as blocked
+    const float i1 = rsqrtf(p1o.x * p1o.x + p1o.y * p1o.y + p1o.z * p1o.z);
+    const float i2 = rsqrtf(p2o.x * p2o.x + p2o.y * p2o.y + p2o.z * p2o.z);
+    p.dx = p1o.x * i1; p.dy = p1o.y * i1; p.dz = p1o.z * i1;
+    p.T = T1o;
+    p.refl = 0;
+    IncP c;
+    c.q = q2; c.T = T2o; c.shell = i; c.done = 0; c.refl = 0;
+    c.rx = p.rx; c.ry = p.ry; c.rz = p.rz;
+    c.dx = p2o.x * i2; c.dy = p2o.y * i2; c.dz = p2o.z * i2;
+    P[s.n++] = c;
+    if (q2 == 1) --s.sea1; else --s.sea0;
+    s.any = true;
+    return false;
+  }
+  p.rx += s_b * p.dx; p.ry += s_b * p.dy; p.rz += s_b * p.dz;
+  if (++s.crossings > kIncCrossings) { p.done = 2; return true; }
+  const float ir = rsqrtf(p.rx * p.rx + p.ry * p.ry + p.rz * p.rz);
+  bool crossed;
+  if (inner) {
+    crossed = cross_boundary(p, -p.rx * ir, -p.ry * ir, -p.rz * ir, nu.V[q][i], nu.V[q][i - 1], m);
+    if (crossed) p.shell = i - 1;
+  } else {
+    const float Vb = (i + 1 < kShells) ? nu.V[q][i + 1] : 0.0f;
+    crossed = cross_boundary(p, p.rx * ir, p.ry * ir, p.rz * ir, nu.V[q][i], Vb, m);
+    if (crossed) {
+      if (i + 1 == kShells) { p.done = 1; return true; }
+      p.shell = i + 1;
+    }
+  }
+  if (!crossed && ++p.refl >= 2) { p.done = 2; return true; }
+  return false;
+}
+
+// After the last nucleon of an attempt: the residual nucleus from energy and
+// momentum conservation with the mass table.  False when the attempt must be
+// redrawn (no allowed collision, an impossible residual, or E* < 0).
+__device__ __forceinline__ bool inc_residual(const NucleusModel& nu, const float* bt, float E, const IncP* P,
+                                             const IncState& s, Residual& r) {
+  if (!s.any) return false;
+  int zesc = 0, nesc = 0;
+  double sumT = 0.0, prx = 0.0, pry = 0.0, prz = static_cast<double>(mom(E, kMp));
+  for (int ip = 0; ip < s.n; ++ip) {
+    if (P[ip].done != 1) continue;
+    ++nesc;
+    zesc += P[ip].q;
+    sumT += static_cast<double>(P[ip].T);
+    const double pm = static_cast<double>(mom(P[ip].T, P[ip].q ? kMp : kMn));
+    prx -= pm * P[ip].dx; pry -= pm * P[ip].dy; prz -= pm * P[ip].dz;
+  }
+  const int Zr = nu.Z + 1 - zesc, Ar = nu.A + 1 - nesc;
+  if (Ar < 1 || Zr < 0 || Zr > Ar) return false;
+  const double dM = static_cast<double>(binding(bt, nu.Z, nu.A)) - static_cast<double>(binding(bt, Zr, Ar));
+  const double Trec = (prx * prx + pry * pry + prz * prz) * static_cast<double>(0.5f / (Ar * static_cast<float>(kAmuD)));
+  const double Ex = static_cast<double>(E) - sumT - Trec - dM;
+  if (Ex < 0.0) return false;
+  r.Ex = Ex; r.px = prx; r.py = pry; r.pz = prz; r.bind = dM; r.Z = Zr; r.A = Ar;
+  return true;
+}
+
+// The cascade nucleons that escaped, as products 0..k-1; returns k.
+template <class Sink>
+__device__ __forceinline__ int inc_emit(const IncP* P, int n, Sink& sink) {
+  int k = 0;
+  for (int ip = 0; ip < n; ++ip) {
+    if (P[ip].done != 1) continue;
+    sink.product(k++, P[ip].q, static_cast<double>(P[ip].T), P[ip].dx, P[ip].dy, P[ip].dz);
+  }
+  return k;
+}
+
+// Evaporation chain of the residual (products k, k+1, ...), then the residual's
+// recoil, leftover excitation and binding to the sink.
+template <class Sink>
+__device__ void evaporate(const float* bt, Stream& st, Residual r, int k, int retries, Sink& sink) {
+  double Ex = r.Ex, bind = r.bind;
+  int Zc = r.Z, Ac = r.A;
+  double pcx = r.px, pcy = r.py, pcz = r.pz;
+  for (int stp = 0; stp < kEvapSteps; ++stp) {
+    float G[6], X[6], Vj[6];
+    float Gs = 0.0f;
+    const float Bc = binding(bt, Zc, Ac);
+    const float Exf = static_cast<float>(Ex);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      G[j] = 0.0f;
+      X[j] = 0.0f;
+      Vj[j] = 0.0f;
+      const int Zd = Zc - kEjZ[j], Ad = Ac - kEjA[j];
+      if (Ad < 1 || Zd < 0 || Zd > Ad) continue;
+      // widths in single precision; the chosen channel's energies are redone in double below
+      const float Sf = Bc - binding(bt, Zd, Ad) - binding(bt, kEjZ[j], kEjA[j]);
+      const float rsum = bt[kMaxZ * kMaxA + Ad] + bt[kMaxZ * kMaxA + kEjA[j]];
+      Vj[j] = (kEjZ[j] > 0 && Zd > 0) ? kCoulomb * kEjZ[j] * Zd / (1.5f * rsum) : 0.0f;
+      X[j] = Exf - Sf - Vj[j];
+      if (X[j] <= 0.0f) continue;
+      const float mu = static_cast<float>(kEjA[j] * Ad) / static_cast<float>(kEjA[j] + Ad);
+      G[j] = kEjG[j] * mu * (1.5f * rsum) * (1.5f * rsum) * width_integral(X[j], Ad * 0.125f);
+      Gs += G[j];
+    }
+    if (!(Gs > 0.0f)) break;
+    const float uch = st.next() * Gs;
+    float acc = 0.0f;
+    int j = 5;
+    for (int c = 0; c < 6; ++c) {
+      acc += G[c];
+      if (uch < acc) { j = c; break; }
+    }
+    while (G[j] <= 0.0f) --j;
+    const int Zd = Zc - kEjZ[j], Ad = Ac - kEjA[j];
+    const double Sj = static_cast<double>(Bc) - static_cast<double>(binding(bt, Zd, Ad)) -
+                      static_cast<double>(binding(bt, kEjZ[j], kEjA[j]));
+    const double Xd = Ex - Sj - static_cast<double>(Vj[j]);
+    const float z = fminf(evap_sample(st, X[j], Ad * 0.125f), static_cast<float>(fmax(Xd, 0.0)));
+    const double eps = static_cast<double>(Vj[j]) + z;
+    const double Exd = Xd - z;
+    const float aj = static_cast<float>(kEjA[j]);
+    const float mu = aj * Ad / (aj + Ad) * static_cast<float>(kAmuD);
+    const double ps = static_cast<double>(sqrtf(2.0f * mu * static_cast<float>(eps)));
+    const float3 nd = iso_dir(st);
+    // Galilean split with masses A u: the parent's velocity is shared
+    const double vfac = static_cast<double>(1.0f / (Ac * static_cast<float>(kAmuD)));
+    const double vx = pcx * vfac, vy = pcy * vfac, vz = pcz * vfac;
+    const double mej = aj * kAmuD, md = Ad * kAmuD;
+    const double ex = mej * vx + ps * nd.x, ey = mej * vy + ps * nd.y, ez = mej * vz + ps * nd.z;
+    pcx = md * vx - ps * nd.x;
+    pcy = md * vy - ps * nd.y;
+    pcz = md * vz - ps * nd.z;
+    const double pe2 = ex * ex + ey * ey + ez * ez;
+    const float ipe = rsqrtf(static_cast<float>(pe2));
+    sink.product(k++, j, pe2 * static_cast<double>(0.5f / (aj * static_cast<float>(kAmuD))),
+                 static_cast<float>(ex) * ipe, static_cast<float>(ey) * ipe, static_cast<float>(ez) * ipe);
+    bind += Sj;
+    Zc = Zd;
+    Ac = Ad;
+    Ex = Exd;
+  }
+  const double Tres = (pcx * pcx + pcy * pcy + pcz * pcz) * static_cast<double>(0.5f / (Ac * static_cast<float>(kAmuD)));
+  sink.residual(Zc, Ac, Tres, Ex, bind, retries);
+}
+
+// The whole event in one thread.  Sink receives products (index, species,
+// kinetic energy, direction in the frame where the incident proton moves along
+// +z), then the residual, or `transparent` when no attempt succeeded.
 template <class Sink>
 __device__ void nonelastic_event(const NucleusModel& nu, const float* bt, float E, uint2 key, unsigned long long pid,
                                  IncP* P, Sink& sink) {
   Stream st{key, pid, 0u, 4, make_float4(0.f, 0.f, 0.f, 0.f)};
-  const float mq[2] = {kMn, kMp};
-  const int Z = nu.Z, A = nu.A;
-  const double pin = static_cast<double>(mom(E, kMp));
+  IncState s;
   int retries = 0;
   for (int attempt = 0; attempt < kIncRetries; ++attempt) {
-    int n = 1, sea0 = A - Z, sea1 = Z;
-    bool any = false;
-    const float b = nu.Rout * sqrtf(st.next());
-    float sph, cph;
-    sincospif(2.0f * st.next(), &sph, &cph);
-    IncP& p0 = P[0];
-    p0.q = 1; p0.T = E; p0.done = 0; p0.refl = 0;
-    p0.rx = b * cph; p0.ry = b * sph; p0.rz = -sqrtf(fmaxf(0.0f, nu.Rout * nu.Rout - b * b));
-    p0.dx = 0.0f; p0.dy = 0.0f; p0.dz = 1.0f;
-    {
-      const float ir = rsqrtf(p0.rx * p0.rx + p0.ry * p0.ry + p0.rz * p0.rz);
-      cross_boundary(p0, -p0.rx * ir, -p0.ry * ir, -p0.rz * ir, 0.0f, nu.V[1][kShells - 1], kMp);
-      p0.shell = kShells - 1;
+    inc_setup(nu, E, st, P, s);
+    for (;;) {
+      if (!inc_flight(nu, st, P, s)) continue;
+      P[s.ip] = s.p;
+      if (++s.ip >= s.n) break;
+      s.p = P[s.ip];
+      s.crossings = 0;
+      s.iters = 0;
     }
-    for (int ip = 0; ip < n; ++ip) {
-      IncP p = P[ip];
-      const int q = p.q;
-      const float m = mq[q];
-      int crossings = 0, iters = 0;
-      for (;;) {
-        const int i = p.shell;
-        if (p.T - nu.V[q][i] <= 0.0f) { p.done = 2; break; }
-        if (++iters > kIncIterations) { p.done = 2; break; }   // bounded loop: captured
-        const float s_out = dist_out(p, nu.r[i + 1]);
-        const float s_in = i > 0 ? dist_in(p, nu.r[i]) : -1.0f;
-        const bool inner = s_in >= 0.0f && s_in < s_out;
-        const float s_b = inner ? s_in : s_out;
-        const float sl = sigma_nn(p.T, true) * kFm2PerMb, su = sigma_nn(p.T, false) * kFm2PerMb;
-        const float rate_p = sea1 > 0 ? nu.rho[1][i] * (q == 1 ? sl : su) : 0.0f;
-        const float rate_n = sea0 > 0 ? nu.rho[0][i] * (q == 0 ? sl : su) : 0.0f;
-        const float rate = rate_p + rate_n;
-        const float uc = st.next();
-        const float s_c = rate > 0.0f ? -logf(uc) / rate : 3.0e38f;
-        if (s_c < s_b) {
-          p.rx += s_c * p.dx; p.ry += s_c * p.dy; p.rz += s_c * p.dz;
-          const int q2 = st.next() * rate < rate_p ? 1 : 0;
-          const float m2 = mq[q2];
-          const float p2m = nu.pF[q2][i] * cbrtf(st.next());
-          const float3 d2 = iso_dir(st);
-          const float3 ns = iso_dir(st);
-          const float p1m = mom(p.T, m);
-          float3 p1o, p2o;
-          float T1o, T2o;
-          nn_collide(make_float3(p1m * p.dx, p1m * p.dy, p1m * p.dz), p.T + m, m,
-                     make_float3(p2m * d2.x, p2m * d2.y, p2m * d2.z), sqrtf(p2m * p2m + m2 * m2), m2, ns, p1o, T1o,
-                     p2o, T2o);
-          if (T1o < nu.TF[q][i] || T2o < nu.TF[q2][i]) continue;   // Pauli blocked
-          if (n >= kIncStack) continue;                              // stack full: treated as blocked
-          const float i1 = rsqrtf(p1o.x * p1o.x + p1o.y * p1o.y + p1o.z * p1o.z);
-          const float i2 = rsqrtf(p2o.x * p2o.x + p2o.y * p2o.y + p2o.z * p2o.z);
-          p.dx = p1o.x * i1; p.dy = p1o.y * i1; p.dz = p1o.z * i1;
-          p.T = T1o;
-          p.refl = 0;
-          IncP c;
-          c.q = q2; c.T = T2o; c.shell = i; c.done = 0; c.refl = 0;
-          c.rx = p.rx; c.ry = p.ry; c.rz = p.rz;
-          c.dx = p2o.x * i2; c.dy = p2o.y * i2; c.dz = p2o.z * i2;
-          P[n++] = c;
-          if (q2 == 1) --sea1; else --sea0;
-          any = true;
-        } else {
-          p.rx += s_b * p.dx; p.ry += s_b * p.dy; p.rz += s_b * p.dz;
-          if (++crossings > kIncCrossings) { p.done = 2; break; }
-          const float ir = rsqrtf(p.rx * p.rx + p.ry * p.ry + p.rz * p.rz);
-          bool crossed;
-          if (inner) {
-            crossed = cross_boundary(p, -p.rx * ir, -p.ry * ir, -p.rz * ir, nu.V[q][i], nu.V[q][i - 1], m);
-            if (crossed) p.shell = i - 1;
-          } else {
-            const float Vb = (i + 1 < kShells) ? nu.V[q][i + 1] : 0.0f;
-            crossed = cross_boundary(p, p.rx * ir, p.ry * ir, p.rz * ir, nu.V[q][i], Vb, m);
-            if (crossed) {
-              if (i + 1 == kShells) { p.done = 1; break; }
-              p.shell = i + 1;
-            }
-          }
-          if (!crossed && ++p.refl >= 2) { p.done = 2; break; }
-        }
-      }
-      P[ip] = p;
-    }
-    if (!any) { ++retries; continue; }
-    // residual nucleus and excitation (double precision bookkeeping)
-    int zesc = 0, nesc = 0;
-    double sumT = 0.0, prx = 0.0, pry = 0.0, prz = pin;
-    for (int ip = 0; ip < n; ++ip) {
-      if (P[ip].done != 1) continue;
-      ++nesc;
-      zesc += P[ip].q;
-      const double T = P[ip].T;
-      sumT += T;
-      const double pm = static_cast<double>(mom(P[ip].T, P[ip].q ? kMp : kMn));
-      prx -= pm * P[ip].dx; pry -= pm * P[ip].dy; prz -= pm * P[ip].dz;
-    }
-    const int Zr = Z + 1 - zesc, Ar = A + 1 - nesc;
-    if (Ar < 1 || Zr < 0 || Zr > Ar) { ++retries; continue; }
-    const double dM = static_cast<double>(binding(bt, Z, A)) - static_cast<double>(binding(bt, Zr, Ar));
-    const double Trec = (prx * prx + pry * pry + prz * prz) * static_cast<double>(0.5f / (Ar * static_cast<float>(kAmuD)));
-    double Ex = static_cast<double>(E) - sumT - Trec - dM;
-    if (Ex < 0.0) { ++retries; continue; }
-    int k = 0;
-    for (int ip = 0; ip < n; ++ip) {
-      if (P[ip].done != 1) continue;
-      sink.product(k++, P[ip].q, static_cast<double>(P[ip].T), P[ip].dx, P[ip].dy, P[ip].dz);
-    }
-    // evaporation chain
-    double bind = dM;
-    int Zc = Zr, Ac = Ar;
-    double pcx = prx, pcy = pry, pcz = prz;
-    for (int stp = 0; stp < kEvapSteps; ++stp) {
-      float G[6], X[6], Vj[6];
-      double Sj[6];
-      float Gs = 0.0f;
-      const float Bc = binding(bt, Zc, Ac);
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        G[j] = 0.0f;
-        X[j] = 0.0f;
-        Vj[j] = 0.0f;
-        Sj[j] = 0.0;
-        const int Zd = Zc - kEjZ[j], Ad = Ac - kEjA[j];
-        if (Ad < 1 || Zd < 0 || Zd > Ad) continue;
-        Sj[j] = static_cast<double>(Bc) - static_cast<double>(binding(bt, Zd, Ad)) -
-                static_cast<double>(binding(bt, kEjZ[j], kEjA[j]));
-        const float rsum = cbrtf(static_cast<float>(Ad)) + cbrtf(static_cast<float>(kEjA[j]));
-        Vj[j] = (kEjZ[j] > 0 && Zd > 0) ? kCoulomb * kEjZ[j] * Zd / (1.5f * rsum) : 0.0f;
-        X[j] = static_cast<float>(Ex - Sj[j] - static_cast<double>(Vj[j]));
-        if (X[j] <= 0.0f) continue;
-        const float mu = static_cast<float>(kEjA[j] * Ad) / static_cast<float>(kEjA[j] + Ad);
-        G[j] = kEjG[j] * mu * (1.5f * rsum) * (1.5f * rsum) * width_integral(X[j], Ad * 0.125f);
-        Gs += G[j];
-      }
-      if (!(Gs > 0.0f)) break;
-      const float uch = st.next() * Gs;
-      float acc = 0.0f;
-      int j = 5;
-      for (int c = 0; c < 6; ++c) {
-        acc += G[c];
-        if (uch < acc) { j = c; break; }
-      }
-      while (G[j] <= 0.0f) --j;
-      const int Zd = Zc - kEjZ[j], Ad = Ac - kEjA[j];
-      const float z = evap_sample(st, X[j], Ad * 0.125f);
-      const double eps = static_cast<double>(Vj[j]) + z;
-      const double Exd = (Ex - Sj[j] - static_cast<double>(Vj[j])) - z;
-      const float aj = static_cast<float>(kEjA[j]);
-      const float mu = aj * Ad / (aj + Ad) * static_cast<float>(kAmuD);
-      const double ps = static_cast<double>(sqrtf(2.0f * mu * static_cast<float>(eps)));
-      const float3 nd = iso_dir(st);
-      // Galilean split with masses A u: the parent's velocity is shared
-      const double vfac = static_cast<double>(1.0f / (Ac * static_cast<float>(kAmuD)));
-      const double vx = pcx * vfac, vy = pcy * vfac, vz = pcz * vfac;
-      const double mej = aj * kAmuD, md = Ad * kAmuD;
-      const double ex = mej * vx + ps * nd.x, ey = mej * vy + ps * nd.y, ez = mej * vz + ps * nd.z;
-      pcx = md * vx - ps * nd.x;
-      pcy = md * vy - ps * nd.y;
-      pcz = md * vz - ps * nd.z;
-      const double pe2 = ex * ex + ey * ey + ez * ez;
-      const float ipe = rsqrtf(static_cast<float>(pe2));
-      sink.product(k++, j, pe2 * static_cast<double>(0.5f / (aj * static_cast<float>(kAmuD))),
-                   static_cast<float>(ex) * ipe, static_cast<float>(ey) * ipe, static_cast<float>(ez) * ipe);
-      bind += Sj[j];
-      Zc = Zd;
-      Ac = Ad;
-      Ex = Exd;
-    }
-    const double Tres = (pcx * pcx + pcy * pcy + pcz * pcz) * static_cast<double>(0.5f / (Ac * static_cast<float>(kAmuD)));
-    sink.residual(Zc, Ac, Tres, Ex, bind, retries);
+    Residual r;
+    if (!inc_residual(nu, bt, E, P, s, r)) { ++retries; continue; }
+    const int k = inc_emit(P, s.n, sink);
+    evaporate(bt, st, r, k, retries, sink);
     return;
   }
   sink.transparent(retries);
@@ -412,62 +474,8 @@ struct TransportSink {
   }
 };
 
-__global__ void __launch_bounds__(128) cascade_kernel(const CascadeArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const unsigned n = min(*a.qne_count, a.qne_cap);
-  if (n == 0) return;
-  if (blockIdx.x * blockDim.x >= n) return;
-  NucleusModel* nuc = reinterpret_cast<NucleusModel*>(smem);
-  float* bt = reinterpret_cast<float*>(nuc + a.n_nuc);
-  {
-    const float* src = reinterpret_cast<const float*>(a.nuclei);
-    float* dst = reinterpret_cast<float*>(nuc);
-    const int nw = a.n_nuc * static_cast<int>(sizeof(NucleusModel) / 4);
-    for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
-    for (int i = threadIdx.x; i < kMaxZ * kMaxA; i += blockDim.x) bt[i] = a.btab[i];
-  }
-  __syncthreads();
-  const unsigned long long seed = *a.seed;
-  TransportSink sk;
-  sk.a = &a;
-  sk.key = make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32));
-  sk.dep = sk.esc = sk.bnd = 0;
-  sk.sec = sk.dropped = sk.retries = sk.n_transparent = 0;
-  IncP P[kIncStack];
-  // Each block takes a tile of blockDim events and sorts it by (target, energy) in
-  // shared memory, so that the lanes of a warp run events of similar length.  The
-  // order of processing does not change any result (random numbers follow the
-  // particle's identity).
-  __shared__ unsigned long long keys[128];
-  for (unsigned base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-    const unsigned i = base + threadIdx.x;
-    unsigned long long key = ~0ull;
-    if (i < n) {
-      const Particle& e = a.qne[i];
-      key = (static_cast<unsigned long long>(e.target) << 56) |
-            (static_cast<unsigned long long>(__float_as_uint(e.E)) << 24) | threadIdx.x;
-    }
-    keys[threadIdx.x] = key;
-    __syncthreads();
-    for (unsigned k = 2; k <= 128; k <<= 1) {          // bitonic sort of the tile
-      for (unsigned j = k >> 1; j > 0; j >>= 1) {
-        const unsigned t = threadIdx.x, l = t ^ j;
-        if (l > t) {
-          const unsigned long long x = keys[t], y = keys[l];
-          const bool up = (t & k) == 0;
-          if ((x > y) == up) { keys[t] = y; keys[l] = x; }
-        }
-        __syncthreads();
-      }
-    }
-    const unsigned long long mine = keys[threadIdx.x];
-    __syncthreads();
-    if (mine != ~0ull) {
-      sk.ev = a.qne[base + static_cast<unsigned>(mine & 0xFFu)];
-      sk.b = sk.ev.root % static_cast<unsigned>(a.B);
-      nonelastic_event(nuc[sk.ev.target], bt, sk.ev.E, sk.key, sk.ev.pid, P, sk);
-    }
-  }
+// Reduces a sink's counters over the warp and adds them to the run counters.
+__device__ __forceinline__ void flush_counters(const TransportSink& sk, Counters* c) {
   auto wsum = [](unsigned long long x) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
@@ -477,7 +485,6 @@ __global__ void __launch_bounds__(128) cascade_kernel(const CascadeArgs a) {
   const unsigned long long bnd = wsum(static_cast<unsigned long long>(sk.bnd));
   const unsigned long long sec = wsum(sk.sec), dr = wsum(sk.dropped), rt = wsum(sk.retries), tr = wsum(sk.n_transparent);
   if ((threadIdx.x & 31u) == 0) {
-    Counters* c = a.cnt;
     if (dep) atomicAdd(&c->deposited, dep);
     if (esc) atomicAdd(&c->escaped, esc);
     if (bnd) atomicAdd(&c->binding, bnd);
@@ -486,6 +493,159 @@ __global__ void __launch_bounds__(128) cascade_kernel(const CascadeArgs a) {
     if (rt) atomicAdd(&c->inc_retries, rt);
     if (tr) atomicAdd(&c->transparent, tr);
   }
+}
+
+__device__ __forceinline__ void stage_tables(const CascadeArgs& a, NucleusModel* nuc, float* bt) {
+  const float* src = reinterpret_cast<const float*>(a.nuclei);
+  float* dst = reinterpret_cast<float*>(nuc);
+  const int nw = a.n_nuc * static_cast<int>(sizeof(NucleusModel) / 4);
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+  for (int i = threadIdx.x; i < kBtabFloats; i += blockDim.x) bt[i] = a.btab[i];
+  __syncthreads();
+}
+
+// Cascade stage: persistent; each lane runs one event at a time, one flight per
+// iteration of a single loop, and takes the next event from the queue as soon as
+// its own is done (warp-aggregated claims), so lanes do not wait at loop exits
+// for the longest cascade of the warp.  A finished cascade emits its escaping
+// nucleons and leaves its residual nucleus, with the position of its random
+// stream, for the evaporation kernel.
+__global__ void __launch_bounds__(128) inc_kernel(const CascadeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned n = min(*a.qne_count, a.qne_cap);
+  if (n == 0) return;
+  NucleusModel* nuc = reinterpret_cast<NucleusModel*>(smem);
+  float* bt = reinterpret_cast<float*>(nuc + a.n_nuc);
+  stage_tables(a, nuc, bt);
+  const unsigned long long seed = *a.seed;
+  const uint2 key = make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32));
+  const unsigned lane = threadIdx.x & 31u;
+  TransportSink sk;
+  sk.a = &a;
+  sk.key = key;
+  sk.dep = sk.esc = sk.bnd = 0;
+  sk.sec = sk.dropped = sk.retries = sk.n_transparent = 0;
+  IncP P[kIncStack];
+  IncState s;
+  Stream st{key, 0ull, 0u, 4, make_float4(0.f, 0.f, 0.f, 0.f)};
+  const NucleusModel* nu = nuc;
+  bool have = false, drained = false, setup = false;
+  int attempt = 0, retries = 0;
+  for (;;) {
+    const unsigned need = __ballot_sync(0xffffffffu, !have && !drained);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned base = 0;
+      if (static_cast<int>(lane) == leader) base = atomicAdd(a.work, static_cast<unsigned>(__popc(need)));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (!have && !drained) {
+        const unsigned idx = base + __popc(need & ((1u << lane) - 1u));
+        if (idx < n) {
+          sk.ev = a.qne[idx];
+          sk.b = sk.ev.root % static_cast<unsigned>(a.B);
+          st = Stream{key, sk.ev.pid, 0u, 4, make_float4(0.f, 0.f, 0.f, 0.f)};
+          nu = nuc + sk.ev.target;
+          attempt = 0;
+          retries = 0;
+          setup = true;
+          have = true;
+        } else {
+          drained = true;
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, !have && drained)) break;
+    if (!have) continue;
+    if (setup) {
+      inc_setup(*nu, sk.ev.E, st, P, s);
+      setup = false;
+      continue;
+    }
+    if (!inc_flight(*nu, st, P, s)) continue;
+    P[s.ip] = s.p;
+    if (++s.ip < s.n) {
+      s.p = P[s.ip];
+      s.crossings = 0;
+      s.iters = 0;
+      continue;
+    }
+    Residual r;
+    if (!inc_residual(*nu, bt, sk.ev.E, P, s, r)) {
+      ++retries;
+      if (++attempt < kIncRetries) {
+        setup = true;
+      } else {
+        sk.transparent(retries);
+        have = false;
+      }
+      continue;
+    }
+    const int k = inc_emit(P, s.n, sk);
+    const unsigned ri = atomicAdd(a.rec_count, 1u);
+    if (ri < a.rec_cap) {
+      EvapRecord& e = a.rec[ri];
+      e.ev = sk.ev;
+      e.Ex = r.Ex; e.px = r.px; e.py = r.py; e.pz = r.pz; e.bind = r.bind;
+      e.buf = st.buf; e.draw = st.draw; e.pos = st.pos;
+      e.Z = r.Z; e.A = r.A; e.k = k; e.retries = retries;
+    } else {
+      evaporate(bt, st, r, k, retries, sk);   // no room to hand it on (cannot happen: one record per event)
+    }
+    have = false;
+  }
+  flush_counters(sk, a.cnt);
+}
+
+// Evaporation stage: one residual per thread; each block sorts its tile of 128
+// residuals by (mass number, excitation) so that a warp's chains are alike.
+__global__ void __launch_bounds__(128) evap_kernel(const CascadeArgs a) {
+  __shared__ float bt[kBtabFloats];
+  __shared__ unsigned long long keys[128];
+  const unsigned n = min(*a.rec_count, a.rec_cap);
+  if (n == 0 || blockIdx.x * blockDim.x >= n) return;
+  for (int i = threadIdx.x; i < kBtabFloats; i += blockDim.x) bt[i] = a.btab[i];
+  __syncthreads();
+  const unsigned long long seed = *a.seed;
+  TransportSink sk;
+  sk.a = &a;
+  sk.key = make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32));
+  sk.dep = sk.esc = sk.bnd = 0;
+  sk.sec = sk.dropped = sk.retries = sk.n_transparent = 0;
+  for (unsigned base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const unsigned i = base + threadIdx.x;
+    unsigned long long key = ~0ull;
+    if (i < n) {
+      const EvapRecord& e = a.rec[i];
+      const float ex = static_cast<float>(fmax(e.Ex, 0.0));
+      key = (static_cast<unsigned long long>(e.A) << 56) | (static_cast<unsigned long long>(__float_as_uint(ex)) << 24) |
+            threadIdx.x;
+    }
+    keys[threadIdx.x] = key;
+    __syncthreads();
+    for (unsigned kk = 2; kk <= 128; kk <<= 1) {          // bitonic sort of the tile
+      for (unsigned j = kk >> 1; j > 0; j >>= 1) {
+        const unsigned t = threadIdx.x, l = t ^ j;
+        if (l > t) {
+          const unsigned long long x = keys[t], y = keys[l];
+          const bool up = (t & kk) == 0;
+          if ((x > y) == up) { keys[t] = y; keys[l] = x; }
+        }
+        __syncthreads();
+      }
+    }
+    const unsigned long long mine = keys[threadIdx.x];
+    __syncthreads();
+    if (mine != ~0ull) {
+      const EvapRecord& e = a.rec[base + static_cast<unsigned>(mine & 0xFFu)];
+      sk.ev = e.ev;
+      sk.b = sk.ev.root % static_cast<unsigned>(a.B);
+      Stream st{sk.key, e.ev.pid, e.draw, e.pos, e.buf};
+      Residual r;
+      r.Ex = e.Ex; r.px = e.px; r.py = e.py; r.pz = e.pz; r.bind = e.bind; r.Z = e.Z; r.A = e.A;
+      evaporate(bt, st, r, e.k, e.retries, sk);
+    }
+  }
+  flush_counters(sk, a.cnt);
 }
 
 // Sink of the debug entry point: products written as rows.
@@ -554,7 +714,7 @@ __global__ void __launch_bounds__(128) inc_yield_kernel(const NucleusModel* __re
     const float* src = reinterpret_cast<const float*>(nu);
     float* dst = reinterpret_cast<float*>(nuc);
     for (int i = threadIdx.x; i < static_cast<int>(sizeof(NucleusModel) / 4); i += blockDim.x) dst[i] = src[i];
-    for (int i = threadIdx.x; i < kMaxZ * kMaxA; i += blockDim.x) bt[i] = btab[i];
+    for (int i = threadIdx.x; i < kBtabFloats; i += blockDim.x) bt[i] = btab[i];
   }
   __syncthreads();
   const uint2 key = make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32));
@@ -592,7 +752,7 @@ __global__ void __launch_bounds__(128) inc_yield_kernel(const NucleusModel* __re
 cudaError_t launch_inc_yields(const NucleusModel* nu, const float* btab, float E, unsigned long long seed,
                               unsigned long long pid0, unsigned long long n, EventYields* out, cudaStream_t s) {
   static int blocks_per_sm = 0, n_sm = 0;
-  const size_t smem = sizeof(NucleusModel) + kMaxZ * kMaxA * sizeof(float);
+  const size_t smem = sizeof(NucleusModel) + kBtabFloats * sizeof(float);
   if (n_sm == 0) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -611,9 +771,22 @@ cudaError_t launch_inc_yields(const NucleusModel* nu, const float* btab, float E
   return cudaGetLastError();
 }
 
-cudaError_t launch_cascade(const CascadeArgs& a, int grid, int block, cudaStream_t s) {
-  const size_t smem = a.n_nuc * sizeof(NucleusModel) + kMaxZ * kMaxA * sizeof(float);
-  cascade_kernel<<<grid, block, smem, s>>>(a);
+cudaError_t launch_cascade(const CascadeArgs& a, cudaStream_t s) {
+  static int n_sm = 0, inc_bps = 0;
+  const size_t smem = a.n_nuc * sizeof(NucleusModel) + kBtabFloats * sizeof(float);
+  if (n_sm == 0) {
+    int dev = 0, sm = 0, bps = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, inc_kernel, 128, kMaxNuc * sizeof(NucleusModel) +
+                                                                                kBtabFloats * sizeof(float));
+    if (e != cudaSuccess) return e;
+    inc_bps = bps > 0 ? bps : 1;
+    n_sm = sm;
+  }
+  inc_kernel<<<n_sm * inc_bps, 128, smem, s>>>(a);
+  evap_kernel<<<n_sm * 8, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -272,6 +272,7 @@ struct pmc_ctx {
   DevBuf d_swb;                         // BF16 copy of the parameters for inference
   DevBuf d_slot_nuc, d_nuc_slot;        // slot -> nuclide, nuclide -> slot
   DevBuf d_sx[2], d_sy[2][2];   // inference rows and outputs, per stream
+  DevBuf d_rec[2];               // residual nuclei between cascade and evaporation, per stream
   size_t surr_cap = 0;
   int mode = PMC_FULL_CASCADE;          // mode of the captured graph
   // graph
@@ -534,9 +535,11 @@ int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc, const pm
       if (nuc[i].A >= 2) build_nucleus(nuc[i].Z, nuc[i].A, nm[i]);
       else std::memset(&nm[i], 0, sizeof(NucleusModel));
     }
-    std::vector<float> bt(kMaxZ * kMaxA);
+    // binding energies [Z][A], then the cube roots A^(1/3) of the mass numbers
+    std::vector<float> bt(kBtabFloats);
     for (int z = 0; z < kMaxZ; ++z)
       for (int a = 0; a < kMaxA; ++a) bt[z * kMaxA + a] = static_cast<float>(binding_energy(z, a));
+    for (int a = 0; a < kMaxA; ++a) bt[kMaxZ * kMaxA + a] = static_cast<float>(std::cbrt(static_cast<double>(a)));
     int rc;
     if ((rc = upload(ctx, ctx->d_phys, &ph, sizeof(Physics)))) return rc;
     if ((rc = upload(ctx, ctx->d_rt, rt.data(), rt.size() * sizeof(float2)))) return rc;
@@ -803,7 +806,7 @@ CascadeArgs cascade_args(pmc_ctx* ctx) {
 // Enqueues one transport -> cascade generation.
 int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int source, uint64_t w0, uint64_t w1,
                        Particle* qin, unsigned* qin_count, Particle* qout, unsigned* qout_count, Particle* qne,
-                       unsigned* qne_count, unsigned* work) {
+                       unsigned* qne_count, unsigned* work, unsigned* cwork, unsigned* rcount) {
   TransportArgs a = transport_args(ctx);
   a.source = source;
   a.w_begin = w0;
@@ -847,8 +850,13 @@ int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int sour
   c.qsec = qout;
   c.qsec_count = qout_count;
   c.qsec_cap = static_cast<unsigned>(ctx->q_cap);
+  const int ri = (qne == static_cast<Particle*>(ctx->d_q[5].p)) ? 1 : 0;   // which stream's buffers
+  c.rec = static_cast<EvapRecord*>(ctx->d_rec[ri].p);
+  c.rec_cap = static_cast<unsigned>(ctx->d_rec[ri].n / sizeof(EvapRecord));
+  c.rec_count = rcount;
+  c.work = cwork;
   if ((rc = mark(ctx, s, 2))) return rc;
-  CK(launch_cascade(c, rp.grid_c, 128, s));
+  CK(launch_cascade(c, s));
   if ((rc = mark(ctx, s, -1))) return rc;
   return PMC_OK;
 }
@@ -872,9 +880,9 @@ StatsArgs stats_args(pmc_ctx* ctx) {
 }
 
 // Count slots per sub-group: [0, G]: secondary queue counts; [G+1, 2G]: event
-// queue counts; [2G+1, 3G]: transport work counters.  A final slot holds the
-// carry count.
-constexpr int kSlots = 3 * kGenerations + 1;
+// queue counts; [2G+1, 3G]: transport work counters; [3G+1, 4G]: cascade work
+// counters; [4G+1, 5G]: residual counts.  A final slot holds the carry count.
+constexpr int kSlots = 5 * kGenerations + 1;
 
 int enqueue_run(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s) {
   ctx->n_events_used = 0;
@@ -911,7 +919,8 @@ int enqueue_run(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s) {
       Particle* out = last ? q[6] : qs[(g + 1) & 1];
       unsigned* out_count = last ? carry_count : cs + g + 1;
       int rc = enqueue_generation(ctx, rp, sc, g == 0 ? 0 : 1, w0, w1, qs[g & 1], cs + g, out, out_count, qs[2],
-                                  cs + kGenerations + 1 + g, cs + 2 * kGenerations + 1 + g);
+                                  cs + kGenerations + 1 + g, cs + 2 * kGenerations + 1 + g,
+                                  cs + 3 * kGenerations + 1 + g, cs + 4 * kGenerations + 1 + g);
       if (rc) return rc;
     }
   }
@@ -1014,6 +1023,10 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
           if ((rc = dalloc(ctx, ctx->d_sy[si][j], ctx->q_cap * kSurrOut * sizeof(float)))) return rc;
       }
     }
+    if (mode == PMC_FULL_CASCADE) {
+      for (int si = 0; si < 2; ++si)
+        if ((rc = dalloc(ctx, ctx->d_rec[si], ctx->q_cap * sizeof(EvapRecord)))) return rc;
+    }
     ctx->mode = mode;
     CK(cudaMemcpyAsync(ctx->d_spots.p, sd.data(), sd.size() * sizeof(SpotDev), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->d_seed.p, &seed, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
@@ -1069,10 +1082,9 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
       unsigned n_in = carry;
       while (n_in > 0) {
         if (++extra > 100000) return fail(ctx, PMC_E_TIMEOUT, "secondary generations did not terminate");
-        const unsigned zero3[3] = {0, 0, 0};
         CK(cudaMemcpyAsync(cs, &n_in, sizeof(unsigned), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(cs + 1, zero3, 3 * sizeof(unsigned), cudaMemcpyHostToDevice, s));
-        int r2 = enqueue_generation(ctx, rp, s, 1, 0, 0, q[0], cs, q[1], cs + 1, q[2], cs + 2, cs + 3);
+        CK(cudaMemsetAsync(cs + 1, 0, 5 * sizeof(unsigned), s));
+        int r2 = enqueue_generation(ctx, rp, s, 1, 0, 0, q[0], cs, q[1], cs + 1, q[2], cs + 2, cs + 3, cs + 4, cs + 5);
         if (r2) return r2;
         CK(cudaMemcpyAsync(&n_in, cs + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1354,7 +1366,8 @@ int pmc_debug_elastic(pmc_ctx* ctx, int nuclide, double E, const double* u, doub
 namespace {
 
 constexpr size_t kNaQueue = static_cast<size_t>(PMC_NOALLOC_CHUNK) * sizeof(Particle);
-constexpr size_t kNaCounters = 4 * kNaQueue;
+constexpr size_t kNaRec = 4 * kNaQueue;
+constexpr size_t kNaCounters = kNaRec + static_cast<size_t>(PMC_NOALLOC_CHUNK) * sizeof(EvapRecord);
 constexpr size_t kNaCounts = kNaCounters + 256;
 constexpr size_t kNaSeed = kNaCounts + 256;
 constexpr size_t kNaSpots = kNaSeed + 256;
@@ -1433,7 +1446,7 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     int bps = 0;
     CK(transport_occupancy(ctx->block, smem, &bps));
     if (bps < 1) return fail(ctx, PMC_E_CUDA, "transport kernel does not fit (block %d, smem %zu)", ctx->block, smem);
-    const int grid_t = ctx->n_sm * bps, grid_c = ctx->n_sm * 8;
+    const int grid_t = ctx->n_sm * bps;
     TransportArgs ta{};
     ta.phys = static_cast<const Physics*>(ctx->d_phys.p);
     ta.rtab = static_cast<const float2*>(ctx->d_rt.p);
@@ -1457,8 +1470,11 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     ca.seed = dseed;
     ca.cnt = counters;
     ca.qne_cap = ca.qsec_cap = PMC_NOALLOC_CHUNK;
+    ca.rec = reinterpret_cast<EvapRecord*>(base + kNaRec);
+    ca.rec_cap = PMC_NOALLOC_CHUNK;
     // sub-groups of PMC_NOALLOC_CHUNK primaries; each runs its generations until no
-    // secondary proton is left (counts: [0] input, [1] output, [2] events, [3] work)
+    // secondary proton is left (counts: [0] input, [1] output, [2] events, [3] transport
+    // work, [4] cascade work, [5] residuals)
     for (uint64_t w0 = 0; w0 < n_histories; w0 += PMC_NOALLOC_CHUNK) {
       const uint64_t w1 = std::min<uint64_t>(n_histories, w0 + PMC_NOALLOC_CHUNK);
       unsigned n_in = 0;
@@ -1466,7 +1482,7 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
         if (g > 100000) return fail(ctx, PMC_E_TIMEOUT, "secondary generations did not terminate");
         Particle* qin = q[g & 1];
         Particle* qout = q[(g + 1) & 1];
-        CK(cudaMemsetAsync(counts + 1, 0, 3 * sizeof(unsigned), s));
+        CK(cudaMemsetAsync(counts + 1, 0, 5 * sizeof(unsigned), s));
         CK(cudaMemcpyAsync(counts, &n_in, sizeof(unsigned), cudaMemcpyHostToDevice, s));
         ta.source = g == 0 ? 0 : 1;
         ta.w_begin = w0;
@@ -1483,7 +1499,9 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
         ca.qne_count = counts + 2;
         ca.qsec = qout;
         ca.qsec_count = counts + 1;
-        CK(launch_cascade(ca, grid_c, 128, s));
+        ca.work = counts + 4;
+        ca.rec_count = counts + 5;
+        CK(launch_cascade(ca, s));
         unsigned n_out = 0;
         CK(cudaMemcpyAsync(&n_out, counts + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1910,6 +1928,7 @@ uint64_t plan_footprint(const pmc_options& opt, const pmc_plan& pl, int mode) {
   b += pool_round((n_chunks * (3 * kGenerations + 1) + 1) * sizeof(unsigned));
   b += pool_round(sizeof(Counters)) + pool_round(8) + pool_round(static_cast<uint64_t>(pl.n_spots) * sizeof(SpotDev));
   if (mode == PMC_SURROGATE) b += 2 * (pool_round(qcap * kSurrIn * 4) + 2 * pool_round(qcap * kSurrOut * 4));
+  else b += 2 * pool_round(qcap * sizeof(EvapRecord));
   return b;
 }
 
@@ -1918,7 +1937,8 @@ void release_plan(pmc_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->d_mat, &ctx->d_rho, &ctx->d_hu, &ctx->d_tally, &ctx->d_dose, &ctx->d_sigma,
                     &ctx->d_counters, &ctx->d_counts, &ctx->d_seed, &ctx->d_spots, &ctx->d_q[0], &ctx->d_q[1],
                     &ctx->d_q[2], &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_sx[0],
-                    &ctx->d_sx[1], &ctx->d_sy[0][0], &ctx->d_sy[0][1], &ctx->d_sy[1][0], &ctx->d_sy[1][1]};
+                    &ctx->d_sx[1], &ctx->d_sy[0][0], &ctx->d_sy[0][1], &ctx->d_sy[1][0], &ctx->d_sy[1][1],
+                    &ctx->d_rec[0], &ctx->d_rec[1]};
   for (DevBuf* b : bufs) dfree(ctx, *b);
   if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
   ctx->have_phantom = false;

@@ -32,6 +32,7 @@ constexpr float kLnS0 = -2.3125f;              // floor(64 ln 0.1) / 64
 constexpr int kMaxMat = 16, kMaxNuc = 16, kMaxNucPerMat = 12, kMaxHu = 16, kMaxCls = 4;
 constexpr int kShells = 15;                    // Woods-Saxon shells, Sec. II.A.4
 constexpr int kMaxZ = 24, kMaxA = 52;          // binding-energy table extent
+constexpr int kBtabFloats = kMaxZ * kMaxA + kMaxA;   // binding energies, then A^(1/3)
 constexpr int kIncStack = 32;                  // cascade particles per event
 constexpr int kIncRetries = 1000;
 constexpr int kIncCrossings = 1000;

@@ -52,9 +52,21 @@ struct TransportArgs {
   unsigned long long* let_den;     // [n_voxels][B] sum of q over the same deposits (2^-24 MeV)
 };
 
+// A residual nucleus handed from the cascade kernel to the evaporation kernel:
+// the event, the residual's state, and where the event's random stream stands.
+struct __align__(16) EvapRecord {
+  Particle ev;                     // the event (position, direction, voxel, identity)
+  float4 buf;                      // the stream's buffered uniforms
+  double Ex, px, py, pz, bind;     // excitation, recoil momentum, binding so far (MeV)
+  unsigned draw;                   // the stream's next Philox block
+  int pos;                         // next uniform in buf
+  int Z, A, k, retries;            // residual, products emitted so far, attempts redrawn
+};
+static_assert(sizeof(EvapRecord) == 128, "evaporation record is 128 bytes");
+
 struct CascadeArgs {
   const NucleusModel* nuclei;      // [n_nuc]
-  const float* btab;               // binding energies [kMaxZ][kMaxA]
+  const float* btab;               // binding energies [kMaxZ][kMaxA], then A^(1/3)
   int n_nuc;
   Geometry g;
   unsigned long long* tally;
@@ -69,6 +81,10 @@ struct CascadeArgs {
   Counters* cnt;
   long long* hist;
   unsigned long long hist_n;
+  EvapRecord* rec;                 // residuals for the evaporation kernel [rec_cap]
+  unsigned* rec_count;
+  unsigned rec_cap;
+  unsigned* work;                  // event counter of the cascade kernel
 };
 
 struct StatsArgs {
@@ -88,7 +104,9 @@ struct StatsArgs {
 size_t transport_smem_bytes(int n_cls, int n_mat);
 cudaError_t launch_transport(const TransportArgs& a, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t transport_occupancy(int block, size_t smem, int* blocks_per_sm);
-cudaError_t launch_cascade(const CascadeArgs& a, int grid, int block, cudaStream_t s);
+// The cascade of the events in a.qne (persistent, lanes refilled from a.work) and the
+// evaporation of their residuals (a.rec); a.work and a.rec_count must be zero.
+cudaError_t launch_cascade(const CascadeArgs& a, cudaStream_t s);
 cudaError_t launch_stats(const StatsArgs& a, cudaStream_t s);
 
 cudaError_t launch_surrogate_dataset(const NucleusModel* nuclei, const float* btab, const int* slot_nuc, int n_slots,

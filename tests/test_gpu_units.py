@@ -98,7 +98,9 @@ def test_cascade_events_match_oracle(eng, nuc, E):
 
 def test_event_generator_totals_equal_the_events_it_runs(eng):
     """The event-generator entry point runs the transport's event code with the same random
-    streams: its totals equal the sums over the same events run one by one."""
+    streams: its totals equal the sums over the same events run one by one (counts exactly;
+    energies to 1e-6, since the same inlined event code compiled into two kernels may fuse
+    multiply-adds differently)."""
     e, p = eng
     n, seed, pid0, E = 3000, 17, 1000, 200.0
     y = e.nonelastic_events(3, E, n, seed, pid0)
@@ -110,10 +112,10 @@ def test_event_generator_totals_equal_the_events_it_runs(eng):
     for k, name in enumerate(("n", "p", "d", "t", "He3", "alpha")):
         sel = live & (dp[:, :, 0] == k)
         assert y["count"][name] == int(sel.sum()), name
-        assert y["energy"][name] == pytest.approx(dp[:, :, 1][sel].sum(), abs=n * 2.0 ** -24)
+        assert y["energy"][name] == pytest.approx(dp[:, :, 1][sel].sum(), rel=1e-6, abs=n * 2.0 ** -24)
     ok = ds[:, 7] == 0
-    assert y["residual_T"] == pytest.approx(ds[ok, 3].sum(), abs=n * 2.0 ** -24)
-    assert y["excitation_left"] == pytest.approx(ds[ok, 4].sum(), abs=n * 2.0 ** -24)
+    assert y["residual_T"] == pytest.approx(ds[ok, 3].sum(), rel=1e-6, abs=n * 2.0 ** -24)
+    assert y["excitation_left"] == pytest.approx(ds[ok, 4].sum(), rel=1e-6, abs=n * 2.0 ** -24)
     assert y["ms"] > 0
 
 
