@@ -271,7 +271,6 @@ struct pmc_ctx {
   DevBuf d_sp, d_sg, d_sm, d_sv;        // parameters, gradients, Adam moments
   DevBuf d_swb;                         // BF16 copy of the parameters for inference
   DevBuf d_slot_nuc, d_nuc_slot;        // slot -> nuclide, nuclide -> slot
-  DevBuf d_sx[2], d_sy[2][2];   // inference rows and outputs, per stream
   DevBuf d_rec[2];               // residual nuclei between cascade and evaporation, per stream
   size_t surr_cap = 0;
   int mode = PMC_FULL_CASCADE;          // mode of the captured graph
@@ -420,8 +419,7 @@ void pmc_destroy(pmc_ctx* ctx) {
   if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
   for (DevBuf* b : bufs) dfree(ctx, *b);
   DevBuf* sbufs[] = {&ctx->d_swb, &ctx->d_sp, &ctx->d_sg, &ctx->d_sm, &ctx->d_sv, &ctx->d_slot_nuc, &ctx->d_nuc_slot,
-                     &ctx->d_sx[0], &ctx->d_sx[1], &ctx->d_sy[0][0], &ctx->d_sy[0][1], &ctx->d_sy[1][0],
-                     &ctx->d_sy[1][1]};
+                     &ctx->d_rec[0], &ctx->d_rec[1]};
   for (DevBuf* b : sbufs) dfree(ctx, *b);
   if (ctx->pool) cudaStreamSynchronize(ctx->stream);   // the stream-ordered frees have run
   cudaStreamDestroy(ctx->stream);
@@ -826,20 +824,12 @@ int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int sour
   CK(launch_transport(a, rp.grid_t, ctx->block, rp.smem, s));
   if ((rc = mark(ctx, s, -1))) return rc;
   if (ctx->mode == PMC_SURROGATE) {
-    const int si = (qne == static_cast<Particle*>(ctx->d_q[5].p)) ? 1 : 0;   // which stream's buffers
-    float* X = static_cast<float*>(ctx->d_sx[si].p);
-    float* Y1 = static_cast<float*>(ctx->d_sy[si][0].p);
-    float* Y2 = static_cast<float*>(ctx->d_sy[si][1].p);
     const float* P = static_cast<const float*>(ctx->d_sp.p);
     const unsigned cap = static_cast<unsigned>(ctx->q_cap);
-    const int grid = ctx->n_sm * 2;
+    const int grid = ctx->n_sm * 2;   // two blocks of 100 KB shared memory per SM
     if ((rc = mark(ctx, s, 2))) return rc;
-    CK(launch_infer_rows(qne_count, cap, qne, static_cast<const int*>(ctx->d_nuc_slot.p), a.seed, X, s));
-    CK(launch_mlp_infer(qne_count, cap, X, ctx->d_swb.p, P, Y1, grid, s));
-    CK(launch_infer_condition(qne_count, cap, Y1, X, s));
-    CK(launch_mlp_infer(qne_count, cap, X, ctx->d_swb.p, P, Y2, grid, s));
-    CK(launch_infer_emit(qne_count, cap, qne, Y1, Y2, a.seed, a.tally, a.B, qout, qout_count, cap, a.cnt, a.hist,
-                         a.hist_n, s));
+    CK(launch_surrogate_events(qne_count, cap, qne, static_cast<const int*>(ctx->d_nuc_slot.p), a.seed, ctx->d_swb.p,
+                               P, a.tally, a.B, qout, qout_count, cap, a.cnt, a.hist, a.hist_n, grid, s));
     if ((rc = mark(ctx, s, -1))) return rc;
     return PMC_OK;
   }
@@ -1016,13 +1006,6 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     for (int i = 0; i < kQueues; ++i)
       if ((rc = dalloc(ctx, ctx->d_q[i], qcap * sizeof(Particle)))) return rc;
     ctx->q_cap = ctx->d_q[0].n / sizeof(Particle);
-    if (mode == PMC_SURROGATE) {
-      for (int si = 0; si < 2; ++si) {
-        if ((rc = dalloc(ctx, ctx->d_sx[si], ctx->q_cap * kSurrIn * sizeof(float)))) return rc;
-        for (int j = 0; j < 2; ++j)
-          if ((rc = dalloc(ctx, ctx->d_sy[si][j], ctx->q_cap * kSurrOut * sizeof(float)))) return rc;
-      }
-    }
     if (mode == PMC_FULL_CASCADE) {
       for (int si = 0; si < 2; ++si)
         if ((rc = dalloc(ctx, ctx->d_rec[si], ctx->q_cap * sizeof(EvapRecord)))) return rc;
@@ -1927,8 +1910,7 @@ uint64_t plan_footprint(const pmc_options& opt, const pmc_plan& pl, int mode) {
   b += kQueues * pool_round(qcap * sizeof(Particle));
   b += pool_round((n_chunks * (3 * kGenerations + 1) + 1) * sizeof(unsigned));
   b += pool_round(sizeof(Counters)) + pool_round(8) + pool_round(static_cast<uint64_t>(pl.n_spots) * sizeof(SpotDev));
-  if (mode == PMC_SURROGATE) b += 2 * (pool_round(qcap * kSurrIn * 4) + 2 * pool_round(qcap * kSurrOut * 4));
-  else b += 2 * pool_round(qcap * sizeof(EvapRecord));
+  if (mode != PMC_SURROGATE) b += 2 * pool_round(qcap * sizeof(EvapRecord));
   return b;
 }
 
@@ -1936,9 +1918,8 @@ uint64_t plan_footprint(const pmc_options& opt, const pmc_plan& pl, int mode) {
 void release_plan(pmc_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->d_mat, &ctx->d_rho, &ctx->d_hu, &ctx->d_tally, &ctx->d_dose, &ctx->d_sigma,
                     &ctx->d_counters, &ctx->d_counts, &ctx->d_seed, &ctx->d_spots, &ctx->d_q[0], &ctx->d_q[1],
-                    &ctx->d_q[2], &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_sx[0],
-                    &ctx->d_sx[1], &ctx->d_sy[0][0], &ctx->d_sy[0][1], &ctx->d_sy[1][0], &ctx->d_sy[1][1],
-                    &ctx->d_rec[0], &ctx->d_rec[1]};
+                    &ctx->d_q[2], &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_rec[0],
+                    &ctx->d_rec[1]};
   for (DevBuf* b : bufs) dfree(ctx, *b);
   if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
   ctx->have_phantom = false;

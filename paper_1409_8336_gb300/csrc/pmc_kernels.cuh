@@ -126,13 +126,11 @@ cudaError_t launch_adamw(int n, float* p, const float* g, float* m, float* v, fl
 cudaError_t launch_train_rows(int batch, const float* feat, const unsigned* perm, unsigned long long first,
                               unsigned long long n_events, unsigned long long seed, unsigned step, float* X, float* Y,
                               float* tau, float* mask, cudaStream_t s);
-cudaError_t launch_infer_rows(const unsigned* n_ev, unsigned cap, const Particle* qne, const int* nuc_slot,
-                              const unsigned long long* seed, float* X, cudaStream_t s);
-cudaError_t launch_infer_condition(const unsigned* n_ev, unsigned cap, const float* Yhat, float* X, cudaStream_t s);
-cudaError_t launch_infer_emit(const unsigned* n_ev, unsigned cap, const Particle* qne, const float* Y1, const float* Y2,
-                              const unsigned long long* seed, unsigned long long* tally, int B, Particle* qsec,
-                              unsigned* qsec_count, unsigned qsec_cap, Counters* cnt, long long* hist,
-                              unsigned long long hist_n, cudaStream_t s);
+cudaError_t launch_surrogate_events(const unsigned* n_ev, unsigned cap, const Particle* qne, const int* nuc_slot,
+                                    const unsigned long long* seed, const void* Wb, const float* P,
+                                    unsigned long long* tally, int B, Particle* qsec, unsigned* qsec_count,
+                                    unsigned qsec_cap, Counters* cnt, long long* hist, unsigned long long hist_n,
+                                    int grid, cudaStream_t s);
 
 // Yields of a batch of non-elastic events (energies in 2^-24 MeV).
 struct EventYields {

@@ -209,16 +209,9 @@ __global__ void train_rows_kernel(int batch, const float* feat, const unsigned* 
   }
 }
 
-// Inference rows from queued events: token -1 (pass 1), then the sampled
-// multiplicity (pass 2).  Uniforms from the event's own stream (tag 8).
-__global__ void infer_rows_kernel(const unsigned* n_ev, unsigned cap, const Particle* qne, const int* nuc_slot,
-                                  const unsigned long long* seedp, float* X) {
-  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= min(*n_ev, cap)) return;
-  const Particle ev = qne[i];
-  const unsigned long long seed = *seedp;
-  const uint2 key = make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32));
-  float* x = X + static_cast<long long>(i) * kSurrIn;
+// Inference row of a queued event: energy, target one-hot, multiplicity token
+// (-1 in the first pass) and ten uniforms from the event's own stream (tag 8).
+__device__ void event_row(const Particle& ev, const int* nuc_slot, uint2 key, float* x) {
   for (int j = 0; j < kSurrIn; ++j) x[j] = 0.0f;
   x[0] = (ev.E - 130.0f) / 120.0f;
   x[1 + nuc_slot[ev.target]] = 1.0f;
@@ -232,91 +225,61 @@ __device__ __forceinline__ int multiplicity(float q) {
   return min(max(static_cast<int>(floorf(q + 0.5f)), 0), kSurrSlots);
 }
 
-__global__ void infer_condition_kernel(const unsigned* n_ev, unsigned cap, const float* Yhat, float* X) {
-  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= min(*n_ev, cap)) return;
-  X[static_cast<long long>(i) * kSurrIn + 1 + kSurrTargets] =
-      static_cast<float>(multiplicity(Yhat[static_cast<long long>(i) * kSurrOut])) / kSurrSlots;
-}
-
 // Emits an event from the network's quantiles: protons to the secondary queue,
 // the local deposit to the event voxel, the rest (neutrons, photons, binding)
 // escapes.  Energy is conserved by construction.
-__global__ void infer_emit_kernel(const unsigned* n_ev, unsigned cap, const Particle* qne, const float* Y1,
-                                  const float* Y2, const unsigned long long* seedp, unsigned long long* tally, int B,
-                                  Particle* qsec, unsigned* qsec_count, unsigned qsec_cap, Counters* cnt,
-                                  long long* hist, unsigned long long hist_n) {
-  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
-  long long dep = 0, esc = 0;
-  unsigned long long sec = 0, dropped = 0;
-  if (i < min(*n_ev, cap)) {
-    const Particle ev = qne[i];
-    const unsigned long long seed = *seedp;
-    const uint2 key = make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32));
-    const float* y1 = Y1 + static_cast<long long>(i) * kSurrOut;
-    const float* y2 = Y2 + static_cast<long long>(i) * kSurrOut;
-    const int np = multiplicity(y1[0]);
-    float T[kSurrSlots], c[kSurrSlots];
-    float sum = 0.0f;
-    for (int k = 0; k < kSurrSlots; ++k) {
-      T[k] = k < np ? fmaxf(y2[1 + k], 0.0f) * ev.E : 0.0f;
-      c[k] = fminf(fmaxf(y2[1 + kSurrSlots + k], -1.0f), 1.0f);
-      sum += T[k];
-    }
-    float loc = fmaxf(y2[1 + 2 * kSurrSlots], 0.0f) * ev.E;
-    sum += loc;
-    if (sum > ev.E) {                                // never more energy out than in
-      const float sc = ev.E / sum;
-      for (int k = 0; k < kSurrSlots; ++k) T[k] *= sc;
-      loc *= sc;
-    }
-    const unsigned b = ev.root % static_cast<unsigned>(B);
-    const float4 ua = draw4(key, ev.pid, 3u, 8u);
-    const float uphi[4] = {ua.x, ua.y, ua.z, ua.w};
-    long long handed = 0;
-    for (int k = 0; k < np; ++k) {
-      if (T[k] <= kEcut) { loc += T[k]; continue; }
-      float sp, cp;
-      sincospif(2.0f * uphi[k], &sp, &cp);
-      const float st = sqrtf(fmaxf(0.0f, 1.0f - c[k] * c[k]));
-      const float3 d = frame_to_lab(ev.u, ev.v, ev.w, st * cp, st * sp, c[k]);
-      Particle r;
-      r.x = ev.x; r.y = ev.y; r.z = ev.z; r.u = d.x; r.v = d.y; r.w = d.z; r.E = T[k];
-      r.voxel = ev.voxel; r.pid = child_pid(key, ev.pid, static_cast<unsigned>(k)); r.root = ev.root; r.target = -1;
-      const unsigned slot = atomicAdd(qsec_count, 1u);
-      if (slot < qsec_cap) {
-        qsec[slot] = r;
-        ++sec;
-        handed += fix(T[k]);
-      } else {
-        ++dropped;
-        loc += T[k];
-      }
-    }
-    const long long qE = fix(ev.E), ql = fix(loc);
-    const long long qesc = qE - handed - ql;       // neutrons, photons and binding: leave the grid
-    atomicAdd(tally + static_cast<size_t>(ev.voxel) * B + b, static_cast<unsigned long long>(ql));
-    dep = ql;
-    esc = qesc;
-    if (hist && ev.root < hist_n) {
-      atomicAdd(reinterpret_cast<unsigned long long*>(hist + 4ull * ev.root + 1), static_cast<unsigned long long>(ql));
-      atomicAdd(reinterpret_cast<unsigned long long*>(hist + 4ull * ev.root + 2), static_cast<unsigned long long>(qesc));
+__device__ void emit_event(const Particle& ev, const float* y1, const float* y2, uint2 key, unsigned long long* tally,
+                           int B, Particle* qsec, unsigned* qsec_count, unsigned qsec_cap, long long* hist,
+                           unsigned long long hist_n, long long& dep, long long& esc, unsigned long long& sec,
+                           unsigned long long& dropped) {
+  const int np = multiplicity(y1[0]);
+  float T[kSurrSlots], c[kSurrSlots];
+  float sum = 0.0f;
+  for (int k = 0; k < kSurrSlots; ++k) {
+    T[k] = k < np ? fmaxf(y2[1 + k], 0.0f) * ev.E : 0.0f;
+    c[k] = fminf(fmaxf(y2[1 + kSurrSlots + k], -1.0f), 1.0f);
+    sum += T[k];
+  }
+  float loc = fmaxf(y2[1 + 2 * kSurrSlots], 0.0f) * ev.E;
+  sum += loc;
+  if (sum > ev.E) {                                // never more energy out than in
+    const float sc = ev.E / sum;
+    for (int k = 0; k < kSurrSlots; ++k) T[k] *= sc;
+    loc *= sc;
+  }
+  const unsigned b = ev.root % static_cast<unsigned>(B);
+  const float4 ua = draw4(key, ev.pid, 3u, 8u);
+  const float uphi[4] = {ua.x, ua.y, ua.z, ua.w};
+  long long handed = 0;
+  for (int k = 0; k < np; ++k) {
+    if (T[k] <= kEcut) { loc += T[k]; continue; }
+    float sp, cp;
+    sincospif(2.0f * uphi[k], &sp, &cp);
+    const float st = sqrtf(fmaxf(0.0f, 1.0f - c[k] * c[k]));
+    const float3 d = frame_to_lab(ev.u, ev.v, ev.w, st * cp, st * sp, c[k]);
+    Particle r;
+    r.x = ev.x; r.y = ev.y; r.z = ev.z; r.u = d.x; r.v = d.y; r.w = d.z; r.E = T[k];
+    r.voxel = ev.voxel; r.pid = child_pid(key, ev.pid, static_cast<unsigned>(k)); r.root = ev.root; r.target = -1;
+    const unsigned slot = atomicAdd(qsec_count, 1u);
+    if (slot < qsec_cap) {
+      qsec[slot] = r;
+      ++sec;
+      handed += fix(T[k]);
+    } else {
+      ++dropped;
+      loc += T[k];
     }
   }
-  auto wsum = [](unsigned long long x) {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-  };
-  const unsigned long long d = wsum(static_cast<unsigned long long>(dep)), e = wsum(static_cast<unsigned long long>(esc));
-  const unsigned long long s = wsum(sec), dr = wsum(dropped);
-  if ((threadIdx.x & 31) == 0) {
-    if (d) atomicAdd(&cnt->deposited, d);
-    if (e) atomicAdd(&cnt->escaped, e);
-    if (s) atomicAdd(&cnt->secondaries, s);
-    if (dr) atomicAdd(&cnt->dropped, dr);
+  const long long qE = fix(ev.E), ql = fix(loc);
+  const long long qesc = qE - handed - ql;       // neutrons, photons and binding: leave the grid
+  atomicAdd(tally + static_cast<size_t>(ev.voxel) * B + b, static_cast<unsigned long long>(ql));
+  dep += ql;
+  esc += qesc;
+  if (hist && ev.root < hist_n) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(hist + 4ull * ev.root + 1), static_cast<unsigned long long>(ql));
+    atomicAdd(reinterpret_cast<unsigned long long*>(hist + 4ull * ev.root + 2), static_cast<unsigned long long>(qesc));
   }
 }
-
 
 // Fused inference: one block takes 64 rows at a time (persistent over the
 // device-resident row count), keeps their activations in shared memory as BF16
@@ -330,23 +293,14 @@ constexpr int kChunk = 64;                       // k-chunk of streamed weights
 constexpr int kWLd = kChunk + 8;                 // 144-byte rows, 16-byte aligned
 constexpr int kInferSmem = 2 * 64 * kActLd * 2 + 2 * 64 * kWLd * 2;
 
-__global__ void __launch_bounds__(128) mlp_infer_kernel(const unsigned* n_rows, unsigned cap, const float* __restrict__ X,
-                                                        const __nv_bfloat16* __restrict__ Wb,
-                                                        const float* __restrict__ P, float* __restrict__ Y) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __nv_bfloat16* act[2] = {reinterpret_cast<__nv_bfloat16*>(smem),
-                           reinterpret_cast<__nv_bfloat16*>(smem) + 64 * kActLd};
-  __nv_bfloat16* wbuf[2] = {reinterpret_cast<__nv_bfloat16*>(smem) + 2 * 64 * kActLd,
-                            reinterpret_cast<__nv_bfloat16*>(smem) + 2 * 64 * kActLd + 64 * kWLd};
-  const unsigned rows = min(*n_rows, cap);
+// The five layers on one 64-row tile whose inputs are in act[0] (columns
+// 0..kSurrIn-1); the last layer's outputs for rows < nvalid go to out[r * kSurrOut + n].
+__device__ void mlp_tile(__nv_bfloat16* const (&act)[2], __nv_bfloat16* const (&wbuf)[2],
+                         const __nv_bfloat16* __restrict__ Wb, const float* __restrict__ P, float* out, int nvalid) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, t = lane & 3;
   const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  for (unsigned r0 = blockIdx.x * 64u; r0 < rows; r0 += gridDim.x * 64u) {
-    for (int e = tid; e < 64 * kSurrIn; e += 128) {
-      const int r = e / kSurrIn, c = e % kSurrIn;
-      act[0][r * kActLd + c] = __float2bfloat16_rn(r0 + r < rows ? X[static_cast<size_t>(r0 + r) * kSurrIn + c] : 0.0f);
-    }
+  {
     size_t off = 0;
     int cur = 0;
 #pragma unroll 1
@@ -432,8 +386,8 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(const unsigned* n_rows, 
                 const float v = acc[i][j][q] + bias[n];
                 if (l < kSurrLayers - 1) {
                   aout[r * kActLd + n] = __float2bfloat16_rn(fmaxf(v, 0.0f));
-                } else if (r0 + r < rows) {
-                  Y[static_cast<size_t>(r0 + r) * kSurrOut + n] = v;
+                } else if (r < nvalid) {
+                  out[r * kSurrOut + n] = v;
                 }
               }
         }
@@ -442,6 +396,101 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(const unsigned* n_rows, 
       off += static_cast<size_t>(din) * dout + dout;
       cur ^= 1;
     }
+  }
+}
+
+__device__ __forceinline__ void tile_buffers(unsigned char* smem, __nv_bfloat16* (&act)[2], __nv_bfloat16* (&wbuf)[2]) {
+  act[0] = reinterpret_cast<__nv_bfloat16*>(smem);
+  act[1] = act[0] + 64 * kActLd;
+  wbuf[0] = act[0] + 2 * 64 * kActLd;
+  wbuf[1] = wbuf[0] + 64 * kWLd;
+}
+
+// Rows X[n][kSurrIn] -> outputs Y[n][kSurrOut] (persistent over 64-row tiles).
+__global__ void __launch_bounds__(128) mlp_infer_kernel(const unsigned* n_rows, unsigned cap, const float* __restrict__ X,
+                                                        const __nv_bfloat16* __restrict__ Wb,
+                                                        const float* __restrict__ P, float* __restrict__ Y) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __nv_bfloat16* act[2];
+  __nv_bfloat16* wbuf[2];
+  tile_buffers(smem, act, wbuf);
+  const unsigned rows = min(*n_rows, cap);
+  for (unsigned r0 = blockIdx.x * 64u; r0 < rows; r0 += gridDim.x * 64u) {
+    for (int e = threadIdx.x; e < 64 * kSurrIn; e += 128) {
+      const int r = e / kSurrIn, c = e % kSurrIn;
+      act[0][r * kActLd + c] = __float2bfloat16_rn(r0 + r < rows ? X[static_cast<size_t>(r0 + r) * kSurrIn + c] : 0.0f);
+    }
+    mlp_tile(act, wbuf, Wb, P, Y + static_cast<size_t>(r0) * kSurrOut, static_cast<int>(min(64u, rows - r0)));
+    __syncthreads();
+  }
+}
+
+// The event stage of a generation with the learned stand-in, fused: per tile of 64
+// queued events, build the inference rows, run the network (multiplicity pass),
+// condition on the sampled multiplicity, run it again and emit the events, with rows
+// and outputs in shared memory throughout.
+constexpr int kEventSmem = kInferSmem + 64 * kSurrIn * 4 + 2 * 64 * kSurrOut * 4;
+
+__global__ void __launch_bounds__(128) surrogate_event_kernel(const unsigned* n_ev, unsigned cap,
+                                                              const Particle* __restrict__ qne, const int* nuc_slot,
+                                                              const unsigned long long* seedp,
+                                                              const __nv_bfloat16* __restrict__ Wb,
+                                                              const float* __restrict__ P, unsigned long long* tally,
+                                                              int B, Particle* qsec, unsigned* qsec_count,
+                                                              unsigned qsec_cap, Counters* cnt, long long* hist,
+                                                              unsigned long long hist_n) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __nv_bfloat16* act[2];
+  __nv_bfloat16* wbuf[2];
+  tile_buffers(smem, act, wbuf);
+  float* xin = reinterpret_cast<float*>(smem + kInferSmem);   // [64][kSurrIn]
+  float* y1 = xin + 64 * kSurrIn;                              // [64][kSurrOut]
+  float* y2 = y1 + 64 * kSurrOut;
+  const unsigned rows = min(*n_ev, cap);
+  const unsigned long long seed = *seedp;
+  const uint2 key = make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32));
+  const int tid = threadIdx.x;
+  long long dep = 0, esc = 0;
+  unsigned long long sec = 0, dropped = 0;
+  for (unsigned r0 = blockIdx.x * 64u; r0 < rows; r0 += gridDim.x * 64u) {
+    const int nvalid = static_cast<int>(min(64u, rows - r0));
+    if (tid < 64) {
+      float* x = xin + tid * kSurrIn;
+      if (tid < nvalid) {
+        event_row(qne[r0 + tid], nuc_slot, key, x);
+      } else {
+        for (int j = 0; j < kSurrIn; ++j) x[j] = 0.0f;
+      }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int e = tid; e < 64 * kSurrIn; e += 128) {
+        const int r = e / kSurrIn, c = e % kSurrIn;
+        act[0][r * kActLd + c] = __float2bfloat16_rn(xin[r * kSurrIn + c]);
+      }
+      mlp_tile(act, wbuf, Wb, P, pass == 0 ? y1 : y2, nvalid);
+      __syncthreads();
+      if (pass == 0 && tid < nvalid)
+        xin[tid * kSurrIn + 1 + kSurrTargets] = static_cast<float>(multiplicity(y1[tid * kSurrOut])) / kSurrSlots;
+      __syncthreads();
+    }
+    if (tid < nvalid)
+      emit_event(qne[r0 + tid], y1 + tid * kSurrOut, y2 + tid * kSurrOut, key, tally, B, qsec, qsec_count, qsec_cap,
+                 hist, hist_n, dep, esc, sec, dropped);
+    __syncthreads();
+  }
+  auto wsum = [](unsigned long long x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+  };
+  const unsigned long long d = wsum(static_cast<unsigned long long>(dep)), e = wsum(static_cast<unsigned long long>(esc));
+  const unsigned long long s = wsum(sec), dr = wsum(dropped);
+  if ((threadIdx.x & 31) == 0) {
+    if (d) atomicAdd(&cnt->deposited, d);
+    if (e) atomicAdd(&cnt->escaped, e);
+    if (s) atomicAdd(&cnt->secondaries, s);
+    if (dr) atomicAdd(&cnt->dropped, dr);
   }
 }
 
@@ -505,23 +554,20 @@ cudaError_t launch_train_rows(int batch, const float* feat, const unsigned* perm
   return cudaGetLastError();
 }
 
-cudaError_t launch_infer_rows(const unsigned* n_ev, unsigned cap, const Particle* qne, const int* nuc_slot,
-                              const unsigned long long* seed, float* X, cudaStream_t s) {
-  infer_rows_kernel<<<(cap + 127) / 128, 128, 0, s>>>(n_ev, cap, qne, nuc_slot, seed, X);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_infer_condition(const unsigned* n_ev, unsigned cap, const float* Yhat, float* X, cudaStream_t s) {
-  infer_condition_kernel<<<(cap + 127) / 128, 128, 0, s>>>(n_ev, cap, Yhat, X);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_infer_emit(const unsigned* n_ev, unsigned cap, const Particle* qne, const float* Y1, const float* Y2,
-                              const unsigned long long* seed, unsigned long long* tally, int B, Particle* qsec,
-                              unsigned* qsec_count, unsigned qsec_cap, Counters* cnt, long long* hist,
-                              unsigned long long hist_n, cudaStream_t s) {
-  infer_emit_kernel<<<(cap + 127) / 128, 128, 0, s>>>(n_ev, cap, qne, Y1, Y2, seed, tally, B, qsec, qsec_count,
-                                                       qsec_cap, cnt, hist, hist_n);
+cudaError_t launch_surrogate_events(const unsigned* n_ev, unsigned cap, const Particle* qne, const int* nuc_slot,
+                                    const unsigned long long* seed, const void* Wb, const float* P,
+                                    unsigned long long* tally, int B, Particle* qsec, unsigned* qsec_count,
+                                    unsigned qsec_cap, Counters* cnt, long long* hist, unsigned long long hist_n,
+                                    int grid, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(surrogate_event_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kEventSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  surrogate_event_kernel<<<grid, 128, kEventSmem, s>>>(n_ev, cap, qne, nuc_slot, seed,
+                                                        static_cast<const __nv_bfloat16*>(Wb), P, tally, B, qsec,
+                                                        qsec_count, qsec_cap, cnt, hist, hist_n);
   return cudaGetLastError();
 }
 

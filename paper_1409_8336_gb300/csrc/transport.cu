@@ -161,6 +161,9 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
     return false;
   }
   if (p.k >= kMaxSteps) { deposit(a, v, p, fix(p.E), acc); acc.errors++; return false; }
+  // the step's uniforms depend only on the particle's identity and step count: drawn
+  // first, their Philox rounds interleave with the table lookups below
+  const StepUniforms ua = step_uniforms(key, p.pid, p.k);
   int m;
   float rho;
   voxel_props(ph, a.g, v, m, rho);
@@ -183,7 +186,6 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   }
   bool nuclear = lam <= d;
   const float dx = nuclear ? lam : d;
-  const StepUniforms ua = step_uniforms(key, p.pid, p.k);
   const float tau = ua.u4;
   const float x1 = p.x + tau * dx * p.u, y1 = p.y + tau * dx * p.v, z1 = p.z + tau * dx * p.w;
   if (!(ph.flags & kNoMcs)) {
