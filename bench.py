@@ -47,7 +47,7 @@ L2_BYTES = 129 * 2 ** 20
 # (1e6 histories in one launch: 47.8 MB), valid only for the kernel sources it was taken
 # on (their SHA-256 below); otherwise the roofline's traffic is reported as null.
 TRAFFIC = {"bytes_per_history": 47.8, "sources": ("transport.cu", "pmc_device.cuh", "pmc_kernels.cuh"),
-           "sha256": "200bd93a40ca4f560783b85c8423bca57b8ce1a9ae34546fe7f4479863ccf680"}
+           "sha256": "99a8ef0bd4d6de4fbb7fa0fb2498a4277cce887d17ddad28dad3735db9baaf94"}
 
 
 def parse():
@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-let", action="store_true")
     ap.add_argument("--no-inc", action="store_true")
     ap.add_argument("--no-plans", action="store_true")
+    ap.add_argument("--launch", default=None, help="BLOCK,CHUNK: fixed launch shape instead of autotuning")
     ap.add_argument("--plans-scale", type=float, default=1.0, help="histories per plan x this")
     ap.add_argument("--plans-slots", type=int, default=4)
     ap.add_argument("--plans-budget-gb", type=float, default=64.0)
@@ -409,15 +410,23 @@ def main():
         return out
 
     # the other build, timed beside the headline one
-    other = Engine(device=local, n_batches=prob.n_batches, fast_math=(args.math != "fast"))
+    fixed = args.launch is not None
+    blk, chk = (int(v) for v in args.launch.split(",")) if fixed else (0, 0)
+    other = Engine(device=local, n_batches=prob.n_batches, fast_math=(args.math != "fast"), block_size=blk)
     other.load_problem(prob)
+    if fixed:
+        other.set_launch(blk, chk)
     timed_steps(other, args.warmup, 5000)
     other_ms = timed_steps(other, args.steps, 6000)
     other.close()
 
     eng = Engine(device=local, n_batches=prob.n_batches, fast_math=(args.math == "fast"))
     eng.load_problem(prob)
-    tuned_block, tuned_chunk = eng.autotune(n)
+    if fixed:
+        eng.set_launch(blk, chk)
+        tuned_block, tuned_chunk = blk, chk
+    else:
+        tuned_block, tuned_chunk = eng.autotune(n)
     eng.enable_profile(True)
 
     def one(seed):
@@ -563,7 +572,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(config_block(prob, n),
-                           launch={"block": tuned_block, "histories_per_subgroup": tuned_chunk, "autotuned": True},
+                           launch={"block": tuned_block, "histories_per_subgroup": tuned_chunk or n,
+                                   "autotuned": not fixed},
                            parallelism="replicas" if world > 1 else "single GPU"),
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
