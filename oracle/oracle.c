@@ -31,6 +31,8 @@
  *   Sec. II.A.5  coherent nuclear elastic scattering, Ranft dsigma/dOmega (Eq. 3),
  *                relativistic two-body kinematics
  *   Sec. II.B.2  ten groups of N/10 protons for the statistical error
+ *   Sec. II.A.2  (option) Moliere multiple scattering in Bethe's form instead of
+ *                the Highland width
  *   Sec. IV      dose-averaged LET scored beside the dose (proton energy losses
  *                weighted by the mean stopping power of the local medium over
  *                the path of each loss; recoil nuclei and fragments excluded)
@@ -38,6 +40,7 @@
  * Parity status: every routine here is pinned by the CPU tests (closed forms,
  * conservation laws, brute-force tallies, published reference values).
  */
+#define _DEFAULT_SOURCE   /* j1() of the C library, used for the Moliere tables */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -67,6 +70,7 @@ static const double PI = 3.14159265358979323846264338328;
 #define OR_NO_MCS 2u
 #define OR_NO_ELASTIC 4u
 #define OR_NO_INELASTIC 8u
+#define OR_MOLIERE 16u   /* Moliere multiple scattering instead of Highland */
 
 /* ------------------------------------------------------------------ */
 /* public structures (mirrored by oracle.py with ctypes)               */
@@ -295,6 +299,115 @@ double or_highland_theta0(double E, double x, double X0cm)
     double br = 1.0 + 0.038 * log(x / (X0cm * beta * beta));
     if (br < 0.0) br = 0.0;
     return 1.07 * 13.6 / (beta * pc) * sqrt(x / X0cm) * br;
+}
+
+/* ------------------------------------------------------------------ */
+/* Moliere multiple scattering, in Bethe's (1953) form: an option beside  */
+/* the paper's Highland width (Sec. II.A.2).                              */
+/* ------------------------------------------------------------------ */
+/* The space angle theta = v chi_c sqrt(B) has the density
+ *   [f0(v) + f1(v)/B + f2(v)/B^2] v dv,  f0 = 2 exp(-v^2),
+ *   f_n(v) = (1/n!) int_0^inf u J0(v u) exp(-u^2/4) [(u^2/4) ln(u^2/4)]^n du,
+ * so its distribution function is F0 + F1/B + F2/B^2 with F0 = 1 - exp(-v^2) and,
+ * since int_0^v J0(t u) t dt = v J1(v u)/u,
+ *   F_n(v) = (1/n!) int_0^inf v J1(v u) exp(-u^2/4) [(u^2/4) ln(u^2/4)]^n du.
+ * F1 and F2 are tabulated by Simpson's rule on [0, MOL_VMAX]; beyond it the density is
+ * read as its single-scattering tail, proportional to v^-3.  B solves
+ * B - ln B = ln(chi_c^2 / (1.167 chi_a^2)); the expansion needs B >= 4.5 (Bethe), so
+ * thinner steps take B = 4.5. */
+#define MOL_N 1601
+#define MOL_VMAX 8.0
+#define MOL_BMIN 4.5
+static double mol_F1[MOL_N], mol_F2[MOL_N];
+static int mol_ready = 0;
+
+static void mol_build(void)
+{
+    const int NU = 4000;
+    const double U = 14.0, h = U / NU;
+    for (int i = 0; i < MOL_N; ++i) {
+        double v = MOL_VMAX * i / (MOL_N - 1), s1 = 0.0, s2 = 0.0;
+        for (int k = 1; k <= NU; ++k) {         /* the integrand vanishes at u = 0 */
+            double u = k * h, y = 0.25 * u * u, L = y * log(y);
+            double g = v * j1(v * u) * exp(-y);
+            double wk = (k == NU) ? 1.0 : ((k & 1) ? 4.0 : 2.0);
+            s1 += wk * g * L;
+            s2 += wk * g * L * L;
+        }
+        mol_F1[i] = s1 * h / 3.0;
+        mol_F2[i] = 0.5 * s2 * h / 3.0;
+    }
+    mol_ready = 1;
+}
+
+/* F_n(v) for n = 0, 1, 2 (linear interpolation of the tables for n > 0) */
+double or_moliere_F(double v, int n)
+{
+    if (!mol_ready) mol_build();
+    if (n == 0) return 1.0 - exp(-v * v);
+    double x = v / MOL_VMAX * (MOL_N - 1);
+    if (x < 0.0) x = 0.0;
+    int i = (int)x;
+    if (i > MOL_N - 2) i = MOL_N - 2;
+    double t = x - i;
+    if (t > 1.0) t = 1.0;
+    const double* F = n == 1 ? mol_F1 : mol_F2;
+    return F[i] + t * (F[i + 1] - F[i]);
+}
+
+static double mol_cdf(double v, double B)
+{
+    return or_moliere_F(v, 0) + or_moliere_F(v, 1) / B + or_moliere_F(v, 2) / (B * B);
+}
+
+/* chi_c^2 (rad^2) and B for a proton of kinetic energy E over mass thickness x
+ * (g/cm^2) of material m */
+void or_moliere_params(const or_problem* P, int m, double E, double x, double* chic2, double* B)
+{
+    const or_material* M = &P->mat[m];
+    double pc = sqrt(E * E + 2.0 * E * M_PROTON), beta = pc / (E + M_PROTON);
+    double zz = 0.0, lna = 0.0;
+    for (int k = 0; k < M->n; ++k) {
+        const or_nuclide* nu = &P->nuc[M->nuc[k]];
+        double Z = nu->Z, c = M->w[k] * Z * (Z + 1.0) / nu->mass_u;
+        double chi0 = 197.3269804 / (0.885 * 52917.721090) * cbrt(Z) / pc;   /* hbar c/(0.885 a0) Z^1/3 / pc */
+        double alpha = Z / (137.035999 * beta);
+        zz += c;
+        lna += c * log(chi0 * chi0 * (1.13 + 3.76 * alpha * alpha));
+    }
+    lna /= zz;
+    *chic2 = K_BETHE * M_ELECTRON * x * zz / (pc * beta * pc * beta);
+    double b = log(*chic2) - lna - (2.0 * 0.5772156649015329 - 1.0);
+    double Bv = MOL_BMIN;
+    if (b > MOL_BMIN - log(MOL_BMIN)) {
+        Bv = b + log(b);
+        for (int it = 0; it < 100; ++it) {
+            double d = (Bv - log(Bv) - b) / (1.0 - 1.0 / Bv);
+            Bv -= d;
+            if (fabs(d) < 1e-13 * Bv) break;
+        }
+        if (Bv < MOL_BMIN) Bv = MOL_BMIN;
+    }
+    *B = Bv;
+}
+
+/* The space angle for the uniform u: the distribution function inverted by bisection,
+ * the tail beyond MOL_VMAX as v^-3, theta capped at pi. */
+double or_moliere_theta(double u, double chic2, double B)
+{
+    double Fmax = mol_cdf(MOL_VMAX, B), v;
+    if (u >= Fmax) {
+        v = MOL_VMAX * sqrt((1.0 - Fmax) / (1.0 - u));
+    } else {
+        double lo = 0.0, hi = MOL_VMAX;
+        for (int it = 0; it < 80; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (mol_cdf(mid, B) < u) lo = mid; else hi = mid;
+        }
+        v = 0.5 * (lo + hi);
+    }
+    double th = v * sqrt(chic2 * B);
+    return th < 0.5 * TWO_PI ? th : 0.5 * TWO_PI;
 }
 
 /* Bohr energy-loss straggling variance (MeV^2) over path x (cm). */
@@ -1012,7 +1125,12 @@ static void transport_one(or_ctx* c, or_particle* p, or_pstack* st)
         double tau = ua[4];
         double x1[3];
         for (int a = 0; a < 3; ++a) x1[a] = p->x[a] + tau * dx * p->d[a];
-        if (!(P->flags & OR_NO_MCS)) {
+        if (!(P->flags & OR_NO_MCS) && (P->flags & OR_MOLIERE)) {
+            double chic2, B;
+            or_moliere_params(P, m, E0, dx * rho, &chic2, &B);
+            double th = or_moliere_theta(ua[0], chic2, B);
+            if (th > 0.0) rotate_dir(p->d, cos(th), sin(th), cos(TWO_PI * ua[1]), sin(TWO_PI * ua[1]));
+        } else if (!(P->flags & OR_NO_MCS)) {
             double th0 = or_highland_theta0(E0, dx, mi->X0mass / rho);
             double r = sqrt(-2.0 * log(ua[0]));
             double tx = th0 * r * cos(TWO_PI * ua[1]), ty = th0 * r * sin(TWO_PI * ua[1]);

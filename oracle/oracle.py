@@ -101,6 +101,11 @@ def lib():
             L.or_evap_integral.restype = d
             L.or_evap_sample_batch.argtypes = [d, d, u64, u64, i, pd]
             L.or_range_roundtrip.argtypes = [d, d, i, pd, pd, pd]
+            L.or_moliere_F.argtypes = [d, i]
+            L.or_moliere_F.restype = d
+            L.or_moliere_params.argtypes = [C.POINTER(OrProblem), i, d, d, pd, pd]
+            L.or_moliere_theta.argtypes = [d, d, d]
+            L.or_moliere_theta.restype = d
             L.or_range_csda.argtypes = [C.POINTER(OrProblem), i, d]
             L.or_range_csda.restype = d
             L.or_material_info.argtypes = [C.POINTER(OrProblem), i, pd]
@@ -249,6 +254,15 @@ def run_parallel(prob, n_hist: int, seed: int, procs: int | None = None, let: bo
     if let:
         return sums[0], totals, sums[1], sums[2]
     return sums[0], totals
+
+
+def moliere_params(prob, m: int, E: float, x: float):
+    """(chi_c^2, B) of a proton of energy E (MeV) over x g/cm^2 of material m."""
+    L = lib()
+    mm = _Marshalled(prob)
+    c2, B = C.c_double(0), C.c_double(0)
+    L.or_moliere_params(C.byref(mm.P), m, E, x, C.byref(c2), C.byref(B))
+    return c2.value, B.value
 
 
 def material_info(prob, m: int):
