@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--train-events", type=int, default=10_000_000)
     ap.add_argument("--no-gamma", action="store_true")
     ap.add_argument("--no-let", action="store_true")
+    ap.add_argument("--no-moliere", action="store_true")
     ap.add_argument("--no-inc", action="store_true")
     ap.add_argument("--no-plans", action="store_true")
     ap.add_argument("--launch", default=None, help="BLOCK,CHUNK: fixed launch shape instead of autotuning")
@@ -504,6 +505,22 @@ def main():
                    "time_vs_dose_only": (sum(lm) / len(lm)) / (total_ms / args.steps),
                    "max_let_d_kev_um": float(let_d.max())}
 
+    # Moliere multiple scattering instead of Highland, the same workload and launch shape
+    moliere = None
+    if not args.no_moliere:
+        from paper_1409_8336_gb300 import workloads as W
+
+        pm = prob.with_(flags=prob.flags | W.MOLIERE)
+        em = Engine(device=local, n_batches=pm.n_batches, physics_flags=pm.flags, fast_math=(args.math == "fast"),
+                    block_size=tuned_block)
+        em.load_problem(pm)
+        em.set_launch(tuned_block, tuned_chunk)
+        timed_steps(em, 3, 8000)
+        mm = timed_steps(em, min(args.steps, 20), 8100)
+        em.close()
+        moliere = {"value": world * n * len(mm) / (sum(mm) / 1e3), "unit": UNIT, "ms_per_step": sum(mm) / len(mm),
+                   "steps": len(mm), "time_vs_highland": (sum(mm) / len(mm)) / (total_ms / args.steps)}
+
     # the learned stand-in of the event generator: trained outside the timed region on events
     # from the engine's own cascade, then timed the same way, with its dose against the full
     # cascade's at the same seed (2 %/2 mm gamma)
@@ -593,6 +610,7 @@ def main():
             "inc_table1": inc,
             "plans_stream": plans,
             "let": let_leg,
+            "moliere": moliere,
             "other_build": {"math": "ieee" if args.math == "fast" else "fast",
                             "value": world * n * args.steps / (sum(other_ms) / 1e3),
                             "ms_per_step": sum(other_ms) / args.steps},

@@ -43,6 +43,11 @@ extern "C" {
 #define PMC_NO_MCS 2u
 #define PMC_NO_ELASTIC 4u
 #define PMC_NO_INELASTIC 8u
+/* Moliere multiple scattering (Bethe's form of Moliere's theory: characteristic and
+ * screening angles, B from B - ln B = ln(chi_c^2 / 1.167 chi_a^2) with the validity floor
+ * B = 4.5, space angle from F0 + F1/B + F2/B^2) instead of the paper's Highland width
+ * (Sec. II.A.2), at the step-start energy over the planned step. */
+#define PMC_MOLIERE 16u
 
 /* transport modes */
 #define PMC_FULL_CASCADE 0        /* non-elastic events by cascade + evaporation */

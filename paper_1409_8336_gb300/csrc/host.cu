@@ -92,6 +92,33 @@ double sigma_el_h(int A, double E) {
 const double GL8X[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
 const double GL8W[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
 
+// Moliere distribution functions (Bethe's form) at kMolN nodes v = i * kMolVmax/(kMolN-1):
+// F0 = 1 - exp(-v^2) and, for n = 1, 2,
+//   F_n(v) = (1/n!) int_0^inf v J1(v u) exp(-u^2/4) [(u^2/4) ln(u^2/4)]^n du,
+// by 8-point Gauss-Legendre on 896 panels of [0, 14].
+std::vector<float4> moliere_table() {
+  std::vector<float4> t(kMolN);
+  const int panels = 896;
+  const double U = 14.0, h = U / panels;
+  for (int i = 0; i < kMolN; ++i) {
+    const double v = static_cast<double>(kMolVmax) * i / (kMolN - 1);
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = 0; k < panels; ++k) {
+      const double c = (k + 0.5) * h, r = 0.5 * h;
+      for (int q = 0; q < 8; ++q) {
+        const double u = c + (q < 4 ? -1.0 : 1.0) * r * GL8X[q & 3], w = r * GL8W[q & 3];
+        const double y = 0.25 * u * u, L = y * std::log(y);
+        const double g = v * ::j1(v * u) * std::exp(-y);
+        s1 += w * g * L;
+        s2 += w * g * L * L;
+      }
+    }
+    t[i] = make_float4(static_cast<float>(1.0 - std::exp(-v * v)), static_cast<float>(s1),
+                       static_cast<float>(0.5 * s2), 0.0f);
+  }
+  return t;
+}
+
 double integrate_inv_s(double a, double b, double ZA, double I) {
   const double m = 0.5 * (a + b), h = 0.5 * (b - a);
   double s = 0.0;
@@ -235,7 +262,7 @@ struct pmc_ctx {
   std::vector<pmc_material> mats;
   std::vector<pmc_nuclide> nucs;
   std::vector<pmc_hu_bin> hus;
-  DevBuf d_phys, d_rt, d_et, d_st, d_nuclei, d_btab;
+  DevBuf d_phys, d_rt, d_et, d_st, d_nuclei, d_btab, d_mol;
   // geometry
   bool have_phantom = false;
   Geometry geo{};
@@ -410,7 +437,7 @@ void pmc_destroy(pmc_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
-  DevBuf* bufs[] = {&ctx->d_phys, &ctx->d_rt, &ctx->d_et, &ctx->d_st, &ctx->d_nuclei, &ctx->d_btab, &ctx->d_mat,
+  DevBuf* bufs[] = {&ctx->d_phys, &ctx->d_rt, &ctx->d_et, &ctx->d_st, &ctx->d_nuclei, &ctx->d_btab, &ctx->d_mol, &ctx->d_mat,
                     &ctx->d_rho, &ctx->d_hu, &ctx->d_tally, &ctx->d_dose, &ctx->d_sigma, &ctx->d_counters,
                     &ctx->d_counts, &ctx->d_seed, &ctx->d_spots, &ctx->d_q[0], &ctx->d_q[1], &ctx->d_q[2],
                     &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_hist, &ctx->d_esc,
@@ -483,6 +510,25 @@ int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc, const pm
         mc.nuc[k] = M.nuc[k];
         mc.n_per_g[k] = static_cast<float>(M.w[k] * kNA / nuc[M.nuc[k]].mass_u * 1e-27);
       }
+      // Moliere: chi_c^2 = K m_e c^2 x sum w Z(Z+1)/A / (p beta)^2; screening angle
+      // chi_a^2 = chi_0^2 (1.13 + 3.76 alpha^2), chi_0 = hbar c Z^(1/3) / (0.885 a0 p),
+      // alpha = Z / (137.036 beta), log-averaged over the elements with weights w Z(Z+1)/A
+      double zz = 0.0;
+      for (int k = 0; k < M.n; ++k) {
+        const double Z = nuc[M.nuc[k]].Z;
+        zz += M.w[k] * Z * (Z + 1.0) / nuc[M.nuc[k]].mass_u;
+      }
+      const double q0 = 197.3269804 / (0.885 * 52917.721090);   // hbar c / (0.885 a0), MeV
+      double lnq = 0.0;
+      for (int k = 0; k < M.n; ++k) {
+        const double Z = nuc[M.nuc[k]].Z;
+        const double c = M.w[k] * Z * (Z + 1.0) / nuc[M.nuc[k]].mass_u / zz;
+        lnq += c * std::log(q0 * q0 * std::pow(Z, 2.0 / 3.0));
+        mc.mol_c[k] = static_cast<float>(c);
+        mc.mol_k[k] = static_cast<float>(3.76 * Z * Z / (137.035999 * 137.035999));
+      }
+      mc.mol_K = static_cast<float>(0.307075 * 0.51099895 * zz);
+      mc.mol_lnq = static_cast<float>(lnq);
     }
     int ncls = 1;
     for (int m = 0; m < n_mat; ++m) {
@@ -545,6 +591,12 @@ int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc, const pm
     if ((rc = upload(ctx, ctx->d_st, st.data(), st.size() * sizeof(float)))) return rc;
     if ((rc = upload(ctx, ctx->d_nuclei, nm.data(), nm.size() * sizeof(NucleusModel)))) return rc;
     if ((rc = upload(ctx, ctx->d_btab, bt.data(), bt.size() * sizeof(float)))) return rc;
+    if (ph.flags & kMoliere) {
+      const std::vector<float4> mt = moliere_table();
+      if ((rc = upload(ctx, ctx->d_mol, mt.data(), mt.size() * sizeof(float4)))) return rc;
+    } else {
+      dfree(ctx, ctx->d_mol);
+    }
     std::vector<int> slot_nuc, nuc_slot(n_nuc, -1);
     for (int i = 0; i < n_nuc; ++i)
       if (nuc[i].A >= 2) { nuc_slot[i] = static_cast<int>(slot_nuc.size()); slot_nuc.push_back(i); }
@@ -768,6 +820,7 @@ TransportArgs transport_args(pmc_ctx* ctx) {
   a.rtab = static_cast<const float2*>(ctx->d_rt.p);
   a.etab = static_cast<const float2*>(ctx->d_et.p);
   a.stab = static_cast<const float*>(ctx->d_st.p);
+  a.mol = static_cast<const float4*>(ctx->d_mol.p);
   a.g = ctx->geo;
   a.tally = static_cast<unsigned long long*>(ctx->d_tally.p);
   a.B = ctx->opt.n_batches;
@@ -980,7 +1033,7 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     int64_t chunk = ctx->chunk > 0 ? ctx->chunk : (1ll << 22);
     rp.chunk = std::min<int64_t>(chunk, static_cast<int64_t>(n_histories));
     rp.n_chunks = static_cast<int>((n_histories + rp.chunk - 1) / rp.chunk);
-    rp.smem = transport_smem_bytes(ctx->phys.n_cls, ctx->phys.n_mat);
+    rp.smem = transport_smem_bytes(ctx->phys.n_cls, ctx->phys.n_mat, ctx->d_mol.p != nullptr);
     int bps = 0;
     CK(transport_occupancy(ctx->block, rp.smem, &bps));
     if (bps < 1) return fail(ctx, PMC_E_CUDA, "transport kernel does not fit (block %d, smem %zu)", ctx->block, rp.smem);
@@ -1425,7 +1478,7 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     CK(cudaMemcpyAsync(dseed, &seed, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(tally, 0, static_cast<size_t>(ctx->n_vox) * B * 8, s));
     CK(cudaMemsetAsync(counters, 0, sizeof(Counters), s));
-    const size_t smem = transport_smem_bytes(ctx->phys.n_cls, ctx->phys.n_mat);
+    const size_t smem = transport_smem_bytes(ctx->phys.n_cls, ctx->phys.n_mat, ctx->d_mol.p != nullptr);
     int bps = 0;
     CK(transport_occupancy(ctx->block, smem, &bps));
     if (bps < 1) return fail(ctx, PMC_E_CUDA, "transport kernel does not fit (block %d, smem %zu)", ctx->block, smem);
@@ -1435,6 +1488,7 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     ta.rtab = static_cast<const float2*>(ctx->d_rt.p);
     ta.etab = static_cast<const float2*>(ctx->d_et.p);
     ta.stab = static_cast<const float*>(ctx->d_st.p);
+    ta.mol = static_cast<const float4*>(ctx->d_mol.p);
     ta.g = ctx->geo;
     ta.tally = reinterpret_cast<unsigned long long*>(tally);
     ta.B = ctx->opt.n_batches;

@@ -39,7 +39,10 @@ constexpr int kIncCrossings = 1000;
 constexpr int kIncIterations = 100000;          // flights per nucleon
 constexpr int kEvapSteps = 64;
 constexpr unsigned kMaxSteps = 100000u;        // per particle; exceeding it is an error
-constexpr unsigned kNoStraggling = 1u, kNoMcs = 2u, kNoElastic = 4u, kNoInelastic = 8u;
+constexpr unsigned kNoStraggling = 1u, kNoMcs = 2u, kNoElastic = 4u, kNoInelastic = 8u, kMoliere = 16u;
+constexpr int kMolN = 1025;                    // Moliere distribution-function nodes on v in [0, kMolVmax]
+constexpr float kMolVmax = 8.0f;
+constexpr float kMolBmin = 4.5f;               // validity floor of the expansion (Bethe)
 
 // Learned stand-in of the event generator (quantile network).
 constexpr int kSurrSlots = 4;                    // proton slots per event
@@ -63,6 +66,10 @@ struct MatConst {
   int n;
   int nuc[kMaxNucPerMat];
   float n_per_g[kMaxNucPerMat];    // atoms per gram x 1e-27 (so that n * sigma[mb] is cm^2/g)
+  // Moliere: chi_c^2 = mol_K x / (p beta)^2 (x in g/cm^2); ln chi_a^2 = mol_lnq - 2 ln p
+  // + sum_j mol_c[j] ln(1.13 + mol_k[j] / beta^2), weights Z(Z+1)/A by mass
+  float mol_K, mol_lnq;
+  float mol_c[kMaxNucPerMat], mol_k[kMaxNucPerMat];
 };
 
 struct NucConst {
@@ -230,6 +237,33 @@ __device__ __forceinline__ float sigma_el(const NucConst& n, float E) {
   if (E <= 0.0f) return 0.0f;
   if (n.A == 1) return sigma_nn(E, true);
   return n.el * (1.0f + 20.0f / (E + 10.0f));
+}
+
+// Moliere space angle for the uniform u (Bethe's form): the distribution function
+// F0 + F1/B + F2/B^2 (nodes T[i] = (F0, F1, F2) at v = i h) inverted by bisection over
+// the nodes and linear interpolation; beyond kMolVmax the single-scattering tail
+// (density ~ v^-3); theta = v chi_c sqrt(B), at most pi.
+__device__ __forceinline__ float moliere_theta(const float4* T, float u, float chic2, float B) {
+  const float iB = 1.0f / B, iB2 = iB * iB;
+  auto F = [&](int i) {
+    const float4 t = T[i];
+    return t.x + t.y * iB + t.z * iB2;
+  };
+  const float Fmax = F(kMolN - 1);
+  float v;
+  if (u >= Fmax) {
+    v = kMolVmax * sqrtf((1.0f - Fmax) / (1.0f - u));
+  } else {
+    int lo = 0, hi = kMolN - 1;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (F(mid) <= u) lo = mid; else hi = mid;
+    }
+    const float f0 = F(lo), f1 = F(hi);
+    const float t = f1 > f0 ? (u - f0) / (f1 - f0) : 0.0f;
+    v = (static_cast<float>(lo) + t) * (kMolVmax / static_cast<float>(kMolN - 1));
+  }
+  return fminf(v * sqrtf(chic2 * B), 3.14159265f);
 }
 
 // ---------------------------------------------------------------------------

@@ -25,6 +25,7 @@ struct TransportArgs {
   const float2* rtab;              // [n_cls][kNE] range splines
   const float2* etab;              // [n_cls][kNR] inverse splines
   const float* stab;               // [n_mat][kNS] total cross-section per unit density
+  const float4* mol;               // [kMolN] Moliere distribution functions, or NULL (Highland)
   Geometry g;
   unsigned long long* tally;       // [n_voxels][B]
   int B;
@@ -101,7 +102,7 @@ struct StatsArgs {
   double* let_sigma;
 };
 
-size_t transport_smem_bytes(int n_cls, int n_mat);
+size_t transport_smem_bytes(int n_cls, int n_mat, bool moliere);
 cudaError_t launch_transport(const TransportArgs& a, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t transport_occupancy(int block, size_t smem, int* blocks_per_sm);
 // The cascade of the events in a.qne (persistent, lanes refilled from a.work) and the

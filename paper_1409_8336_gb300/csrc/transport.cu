@@ -145,7 +145,7 @@ __device__ __forceinline__ Particle make_record(const PState& p, float E, float 
 
 // One condensed-history step (Sec. II.A.3).  Returns false when the particle ends.
 __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt, const float2* et,
-                     const float* st, uint2 key, PState& p, Acc& acc) {
+                     const float* st, const float4* mol, uint2 key, PState& p, Acc& acc) {
   const int v = vindex(a.g, p.ix, p.iy, p.iz);
   if (p.E <= kEcut) {
     const long long q = fix(p.E);
@@ -188,7 +188,31 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   const float dx = nuclear ? lam : d;
   const float tau = ua.u4;
   const float x1 = p.x + tau * dx * p.u, y1 = p.y + tau * dx * p.v, z1 = p.z + tau * dx * p.w;
-  if (!(ph.flags & kNoMcs)) {
+  if (!(ph.flags & kNoMcs) && mol) {
+    // Moliere (Bethe's form), at the step-start energy over the planned step
+    const float pc = sqrtf(E0 * E0 + 2.0f * E0 * kMp);
+    const float beta = pc / (E0 + kMp);
+    const float pb = pc * beta;
+    const float chic2 = mc.mol_K * dx * rho / (pb * pb);
+    const float ib2 = 1.0f / (beta * beta);
+    float lna = mc.mol_lnq - 2.0f * logf(pc);
+    for (int j = 0; j < mc.n; ++j) lna += mc.mol_c[j] * logf(1.13f + mc.mol_k[j] * ib2);
+    const float b = logf(chic2) - lna - 0.15443133f;   // ln 1.167 = 2 Euler's constant - 1
+    float B = kMolBmin;
+    if (b > kMolBmin - 1.50407740f) {                   // B - ln B = b has B > 4.5
+      B = b + logf(b);
+#pragma unroll
+      for (int it = 0; it < 4; ++it) B -= (B - logf(B) - b) / (1.0f - 1.0f / B);
+      B = fmaxf(B, kMolBmin);
+    }
+    const float th = moliere_theta(mol, ua.u0, chic2, B);
+    if (th > 0.0f) {
+      float s_, c_, sp, cp;
+      sincosf(th, &s_, &c_);
+      sincospif(2.0f * ua.u1, &sp, &cp);
+      rotate(p.u, p.v, p.w, c_, s_, cp, sp);
+    }
+  } else if (!(ph.flags & kNoMcs)) {
     // Highland x 1.07 at the step-start energy, over the planned step
     const float pc = sqrtf(E0 * E0 + 2.0f * E0 * kMp);
     const float beta = pc / (E0 + kMp);
@@ -349,6 +373,12 @@ __global__ void __launch_bounds__(256, PMC_TRANSPORT_MIN_BLOCKS) transport_kerne
   for (int i = threadIdx.x; i < ncls * kNE; i += blockDim.x) rt[i] = a.rtab[i];
   for (int i = threadIdx.x; i < ncls * kNR; i += blockDim.x) et[i] = a.etab[i];
   for (int i = threadIdx.x; i < nmat * kNS; i += blockDim.x) st[i] = a.stab[i];
+  float4* mol = nullptr;
+  if (a.mol) {
+    const size_t off_mol = ((reinterpret_cast<unsigned char*>(st + nmat * kNS) - smem) + 15) / 16 * 16;
+    mol = reinterpret_cast<float4*>(smem + off_mol);
+    for (int i = threadIdx.x; i < kMolN; i += blockDim.x) mol[i] = a.mol[i];
+  }
   __syncthreads();
   const Physics& ph = *php;
 
@@ -380,7 +410,7 @@ __global__ void __launch_bounds__(256, PMC_TRANSPORT_MIN_BLOCKS) transport_kerne
       }
     }
     if (__all_sync(0xffffffffu, !alive && drained)) break;
-    if (alive) alive = step(a, ph, rt, et, st, key, p, acc);
+    if (alive) alive = step(a, ph, rt, et, st, mol, key, p, acc);
   }
 
   // flush the lane counters (warp reduction, one atomic per warp and counter)
@@ -410,9 +440,10 @@ __global__ void __launch_bounds__(256, PMC_TRANSPORT_MIN_BLOCKS) transport_kerne
 
 }  // namespace
 
-size_t transport_smem_bytes(int n_cls, int n_mat) {
-  return (sizeof(Physics) + 15) / 16 * 16 + 1ull * n_cls * (kNE + kNR) * sizeof(float2) +
-         1ull * n_mat * kNS * sizeof(float);
+size_t transport_smem_bytes(int n_cls, int n_mat, bool moliere) {
+  const size_t b = (sizeof(Physics) + 15) / 16 * 16 + 1ull * n_cls * (kNE + kNR) * sizeof(float2) +
+                   1ull * n_mat * kNS * sizeof(float);
+  return moliere ? (b + 15) / 16 * 16 + kMolN * sizeof(float4) : b;
 }
 
 cudaError_t transport_occupancy(int block, size_t smem, int* blocks_per_sm) {
