@@ -143,14 +143,17 @@ __device__ __forceinline__ Particle make_record(const PState& p, float E, float 
   return r;
 }
 
-// One condensed-history step (Sec. II.A.3).  Returns false when the particle ends.
+// One condensed-history step (Sec. II.A.3).  Returns false when the particle ends.  kLet and
+// kMol compile the LET scoring and the Moliere option in; without them the step carries no
+// test for either.
+template <bool kLet, bool kMol>
 __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt, const float2* et,
                      const float* st, const float4* mol, uint2 key, PState& p, Acc& acc) {
   const int v = vindex(a.g, p.ix, p.iy, p.iz);
   if (p.E <= kEcut) {
     const long long q = fix(p.E);
     deposit(a, v, p, q, acc);
-    if (a.let_num && p.E > 0.0f) {   // absorbed over its residual range: L = E / R
+    if (kLet && p.E > 0.0f) {   // absorbed over its residual range: L = E / R
       int m0;
       float rho0;
       voxel_props(ph, a.g, v, m0, rho0);
@@ -181,14 +184,14 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   if (Rcm <= lam && Rcm <= d) {
     const long long q = fix(E0);
     deposit(a, v, p, q, acc);
-    if (a.let_num && Rcm > 0.0f) score_let(a, v, p, q, 0.1f * E0 / Rcm);
+    if (kLet && Rcm > 0.0f) score_let(a, v, p, q, 0.1f * E0 / Rcm);
     return false;
   }
   bool nuclear = lam <= d;
   const float dx = nuclear ? lam : d;
   const float tau = ua.u4;
   const float x1 = p.x + tau * dx * p.u, y1 = p.y + tau * dx * p.v, z1 = p.z + tau * dx * p.w;
-  if (!(ph.flags & kNoMcs) && mol) {
+  if (kMol && !(ph.flags & kNoMcs)) {
     // Moliere (Bethe's form), at the step-start energy over the planned step
     const float pc = sqrtf(E0 * E0 + 2.0f * E0 * kMp);
     const float beta = pc / (E0 + kMp);
@@ -253,7 +256,7 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   {
     const long long q = fix(E0) - fix(E1);
     deposit(a, v, p, q, acc);
-    if (a.let_num) {
+    if (kLet) {
       // mean stopping power over the path: the CSDA loss over s, taken as a difference
       // of two values of the inverse range table (free of the E -> R -> E round trip,
       // whose few-ulp error would dominate the loss over the short steps that end at
@@ -350,6 +353,7 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
 #define PMC_TRANSPORT_MIN_BLOCKS 3   // measured best on GB300: 3 resident blocks of 256 per SM
 #endif
 
+template <bool kLet, bool kMol>
 __global__ void __launch_bounds__(256, PMC_TRANSPORT_MIN_BLOCKS) transport_kernel(const TransportArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned long long n_items =
@@ -374,7 +378,7 @@ __global__ void __launch_bounds__(256, PMC_TRANSPORT_MIN_BLOCKS) transport_kerne
   for (int i = threadIdx.x; i < ncls * kNR; i += blockDim.x) et[i] = a.etab[i];
   for (int i = threadIdx.x; i < nmat * kNS; i += blockDim.x) st[i] = a.stab[i];
   float4* mol = nullptr;
-  if (a.mol) {
+  if (kMol) {
     const size_t off_mol = ((reinterpret_cast<unsigned char*>(st + nmat * kNS) - smem) + 15) / 16 * 16;
     mol = reinterpret_cast<float4*>(smem + off_mol);
     for (int i = threadIdx.x; i < kMolN; i += blockDim.x) mol[i] = a.mol[i];
@@ -410,7 +414,7 @@ __global__ void __launch_bounds__(256, PMC_TRANSPORT_MIN_BLOCKS) transport_kerne
       }
     }
     if (__all_sync(0xffffffffu, !alive && drained)) break;
-    if (alive) alive = step(a, ph, rt, et, st, mol, key, p, acc);
+    if (alive) alive = step<kLet, kMol>(a, ph, rt, et, st, mol, key, p, acc);
   }
 
   // flush the lane counters (warp reduction, one atomic per warp and counter)
@@ -446,15 +450,29 @@ size_t transport_smem_bytes(int n_cls, int n_mat, bool moliere) {
   return moliere ? (b + 15) / 16 * 16 + kMolN * sizeof(float4) : b;
 }
 
+namespace {
+// the four specialisations, indexed by (LET scored) + 2 (Moliere scattering)
+void (*const kTransportKernels[4])(const TransportArgs) = {
+    transport_kernel<false, false>, transport_kernel<true, false>, transport_kernel<false, true>,
+    transport_kernel<true, true>};
+}  // namespace
+
 cudaError_t transport_occupancy(int block, size_t smem, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(transport_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel, block, smem);
+  int lo = 1 << 30;
+  for (auto k : kTransportKernels) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, block, smem);
+    if (e != cudaSuccess) return e;
+    lo = b < lo ? b : lo;
+  }
+  *blocks_per_sm = lo;
+  return cudaSuccess;
 }
 
 cudaError_t launch_transport(const TransportArgs& a, int grid, int block, size_t smem, cudaStream_t s) {
-  transport_kernel<<<grid, block, smem, s>>>(a);
+  kTransportKernels[(a.let_num ? 1 : 0) + (a.mol ? 2 : 0)]<<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
 }
 
