@@ -41,13 +41,19 @@ N_HISTORIES = 1_000_000
 # range spline 16, fixed-point deposit 23, cross-section table and lambda 13, and the
 # rest of the step logic 53.  Peak = FP32/INT32 lanes x SM clock.
 OPS_PER_STEP = 430
+# Algorithmic bytes of a step at L2 on the slab workload: material id 1 B + density 4 B +
+# the tally's 64-bit read-modify-write 16 B.
+BYTES_PER_STEP = 21
+# The learned stand-in's two network passes per event (multiplicity, then the products), each
+# 2 x (32*256 + 3*256*256 + 256*16) multiply-add FLOPs.
+SURROGATE_FLOPS_PER_EVENT = 2 * 2 * (32 * 256 + 3 * 256 * 256 + 256 * 16)
 L2_BYTES = 129 * 2 ** 20
 # DRAM bytes (read + write) of the primary-transport launch per primary history, from a
 # 1-pass ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on this workload
-# (1e6 histories in one launch: 47.8 MB), valid only for the kernel sources it was taken
+# (1e6 histories in one launch: 47.9 MB), valid only for the kernel sources it was taken
 # on (their SHA-256 below); otherwise the roofline's traffic is reported as null.
-TRAFFIC = {"bytes_per_history": 47.9, "sources": ("transport.cu", "pmc_device.cuh", "pmc_kernels.cuh"),
-           "sha256": "458881de9da7f3d538b477672a59c2dbd5cf3c4d9c582937d88a0514211de36a"}
+TRAFFIC = {"bytes_per_history": 47.8, "sources": ("transport.cu", "pmc_device.cuh", "pmc_kernels.cuh"),
+           "sha256": "585fe3af68dc987691929e0c14b4a0cb9682327054b3955456a33e938940c6bc"}
 
 
 def parse():
@@ -86,6 +92,19 @@ def traffic_per_launch(histories_per_launch):
     if h.hexdigest() != TRAFFIC["sha256"]:
         return None
     return TRAFFIC["bytes_per_history"] * histories_per_launch
+
+
+def memory_fractions(pk, steps_per_step, span_ms, traffic, launches_per_step):
+    """The transport's memory side beside its ALU roofline: the algorithmic bytes of its steps
+    (served mostly by L2) and the DRAM bytes ncu measured, both against the measured HBM peak."""
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    alg = BYTES_PER_STEP * steps_per_step / (span_ms * 1e-3) / 1e9
+    out = {"peak_gbs": hbm, "algorithmic_bytes_per_step": BYTES_PER_STEP, "algorithmic_gbs": alg,
+           "algorithmic_frac": alg / hbm, "dram_gbs": None, "dram_frac": None}
+    if traffic is not None:
+        d = traffic * launches_per_step / (span_ms * 1e-3) / 1e9
+        out["dram_gbs"], out["dram_frac"] = d, d / hbm
+    return out
 
 
 def workload():
@@ -172,6 +191,67 @@ def oracle_rate(prob, n_total, seconds, seed=1):
     return done / dt, done, dt
 
 
+_ORACLE_FIELDS = None
+
+
+def _oracle_init(fields):
+    global _ORACLE_FIELDS
+    _ORACLE_FIELDS = fields
+
+
+def _oracle_range(job):
+    """One worker's share: histories [h0, h1) of the workload through the oracle (totals only;
+    the tally stays in the worker)."""
+    from oracle import oracle as O
+
+    n_total, seed, h0, h1 = job
+    return O._run_range((_ORACLE_FIELDS, n_total, seed, h0, h1, False))[1]
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """The CPU oracle over all host cores: spawned worker processes (safe after CUDA has been
+    initialised in this process) holding the workload, each running history ranges."""
+
+    def __init__(self, prob, n_total, procs=None):
+        import multiprocessing as mp
+        from oracle import oracle as O
+
+        self.procs = procs or host_cores()
+        self.n_total = n_total
+        self.cnt = O.allocate_histories(prob, n_total)
+        self.first = np.concatenate([[0], np.cumsum(self.cnt)[:-1]])
+        fields = {k: getattr(prob, k) for k in O._PROBLEM_FIELDS}
+        self.pool = mp.get_context("spawn").Pool(self.procs, initializer=_oracle_init, initargs=(fields,))
+        f0 = int(self.first[0])
+        self.pool.map(_oracle_range, [(n_total, 1, f0, f0 + 1)] * self.procs, chunksize=1)   # load the oracle
+
+    def rate(self, seconds, rate1, seed=1):
+        """Histories/s over an even sample of the spots, sized from the single-thread rate
+        rate1 to take about `seconds` on all workers."""
+        per = max(self.procs, int(rate1 * seconds * self.procs / len(self.cnt)))
+        jobs = []
+        for s in range(len(self.cnt)):
+            k = min(per, int(self.cnt[s]))
+            cuts = [int(self.first[s]) + k * i // self.procs for i in range(self.procs + 1)]
+            jobs += [(self.n_total, seed, cuts[i], cuts[i + 1]) for i in range(self.procs) if cuts[i + 1] > cuts[i]]
+        done = sum(j[3] - j[2] for j in jobs)
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_range, jobs, chunksize=1)
+        dt = time.perf_counter() - t0
+        return done / dt, done, dt
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def config_block(prob, n):
     """The workload description shared by both arms."""
     return {"workload": prob.name, "histories_per_step": n, "spots": "70/150/230 MeV, sigma 4 mm",
@@ -196,20 +276,25 @@ def run_reference(args):
         return
     prob = workload()
     times, dones = [], []
-    # each step is a bounded sample, sized so the whole run ends within about two minutes
+    # the oracle on all host cores; each step is a bounded sample, sized so the whole run
+    # ends within about two minutes
+    rate1, _, _ = oracle_rate(prob, args.histories, 1.0)
+    pool = OraclePool(prob, args.histories)
     per_step = min(max(args.cpu_seconds / 3, 0.5), 120.0 / max(1, args.steps + args.warmup))
     for i in range(args.warmup + args.steps):
-        rate, done, dt = oracle_rate(prob, args.histories, per_step, seed=1 + i)
+        rate, done, dt = pool.rate(per_step, rate1, seed=1 + i)
         if i >= args.warmup:
             times.append(dt)
             dones.append(done)
+    pool.close()
     value = sum(dones) / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.histories / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_block(prob, args.histories),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d histories per step, even over the three spots" % (sum(dones) // len(dones))},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
+                             "sample": "%d histories per step, even over the three spots, on %d worker processes" %
+                                       (sum(dones) // len(dones), pool.procs)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -428,7 +513,10 @@ def main():
         tuned_block, tuned_chunk = blk, chk
     else:
         tuned_block, tuned_chunk = eng.autotune(n)
-    eng.enable_profile(True)
+    # the timed steps record events around the primary-transport launches only (the
+    # roofline's kernel); events around every launch cost ~3 % of a step, so the per-kind
+    # breakdown comes from profiled steps after the timed region
+    eng.enable_profile(True, primary_only=True)
 
     def one(seed):
         flush.fill_(float(seed))                           # evict L2 between steps
@@ -446,9 +534,8 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ms, prof_ms, prof_n, steps_primary, ledgers, launches = [], 0.0, 0, 0, [], 0
+    ms, prof_ms, prof_n, steps_primary, ledgers = [], 0.0, 0, 0, []
     prof_span = 0.0
-    kinds = {}
     with Clocks(local) as clk:
         for i in range(args.steps):
             t, prof, s0, led = one(rank * 100003 + i + 1)
@@ -458,15 +545,23 @@ def main():
             prof_n += prof["transport_primary"]["launches"]
             steps_primary += s0
             ledgers.append(led)
-            launches += sum(p["launches"] for p in prof.values())
-            for k, v in prof.items():
-                kinds.setdefault(k, [0.0, 0])
-                kinds[k][0] += v["ms"] / args.steps
-                kinds[k][1] = v["launches"]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     total_ms = max_over_ranks(sum(ms), dist)
+    # every launch timed, on steps after the timed region (the same graph: its launch count
+    # per step is the timed steps' too)
+    eng.enable_profile(True)
+    kinds, n_kind_steps, per_step_launches = {}, min(args.steps, 10), 0
+    for i in range(n_kind_steps):
+        _, prof, _, _ = one(rank * 100003 + 50000 + i)
+        per_step_launches = sum(p["launches"] for p in prof.values())
+        for k, v in prof.items():
+            kinds.setdefault(k, [0.0, 0])
+            kinds[k][0] += v["ms"] / n_kind_steps
+            kinds[k][1] = v["launches"]
+    eng.enable_profile(False)
+    launches = per_step_launches * args.steps
     value = world * n * args.steps / (total_ms / 1e3)
 
     # end to end through the public API with host buffers (pinned): H2D of the phantom and spots,
@@ -544,16 +639,35 @@ def main():
             b.record(stream)
             b.synchronize()
             sm.append(a.elapsed_time(b))
+        # the fused event stage, timed on profiled steps after the timed ones
+        eng.enable_profile(True)
+        ev_ms, n_ev, n_prof = 0.0, 0, min(args.steps, 10)
+        for i in range(n_prof):
+            flush.fill_(float(i))
+            eng.transport(n, 3500 + i, mode=1, stream=stream)
+            torch.cuda.synchronize()
+            ev_ms += eng.read_profile()[0]["cascade"]["ms"]
+            n_ev += eng.read_ledger()["inelastic"]
+        eng.enable_profile(False)
         eng.transport(n, 77, mode=0, stream=stream)
         Df, _ = eng.read_dose()
         eng.transport(n, 77, mode=1, stream=stream)
         Ds, _ = eng.read_dose()
         _, gam = gamma_index(Df.reshape(prob.shape), Ds.reshape(prob.shape), prob.voxel, want_map=False)
         sval = world * n * args.steps / (sum(sm) / 1e3)
+        pk_s, src_s = peaks()
+        tflops = SURROGATE_FLOPS_PER_EVENT * n_ev / (ev_ms * 1e-3) / 1e12
+        tpeak = float(pk_s.get("bf16_tflops_sustained", 1700.0))
         surrogate = {"value": sval, "unit": UNIT, "ms_per_step": sum(sm) / args.steps, "speedup_vs_full": sval / value,
                      "gamma_2pct_2mm_vs_full": gam, "train_events": args.train_events, "train_seconds": train_s,
                      "train_loss_first_last": [tr["first_loss"], tr["last_loss"]],
-                     "network": "MLP 32-256-256-256-256-16, BF16 tensor cores (mma.sync), FP32 accumulate"}
+                     "network": "MLP 32-256-256-256-256-16, BF16 tensor cores (mma.sync), FP32 accumulate",
+                     "event_stage": {"bound": "tensor", "kernel": "surrogate_event_kernel", "events_per_step": n_ev / n_prof,
+                                     "ms_per_step": ev_ms / n_prof, "flops_per_event": SURROGATE_FLOPS_PER_EVENT,
+                                     "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak,
+                                     "peak_source": "%s bf16 sustained" % src_s,
+                                     "note": "two network passes per event; the stage also builds the inputs, "
+                                             "conditions the outputs and emits the products"}}
 
     inc = None
     if not args.no_inc:
@@ -580,13 +694,20 @@ def main():
     alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12       # FP32 lanes x clock, TOP/s
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, done, dt = oracle_rate(prob, n, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d histories (equal thirds of the 70/150/230 MeV spots) in %.1f s" % (done, dt)}
+        rate1, done1, dt1 = oracle_rate(prob, n, args.cpu_seconds)
+        pool = OraclePool(prob, n)
+        rate, done, dt = pool.rate(args.cpu_seconds * 2 / 3, rate1)
+        pool.close()
+        cpu = {"value": rate, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
+               "sample": "%d histories (equal thirds of the 70/150/230 MeV spots) in %.1f s on %d worker processes"
+                         % (done, dt, pool.procs),
+               "single_core": {"value": rate1, "cores": 1,
+                               "sample": "%d histories (equal thirds of the spots) in %.1f s" % (done1, dt1)}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "ms_per_step_best": min(ms), "ms_per_step_median": statistics.median(ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(config_block(prob, n),
                            launch={"block": tuned_block, "histories_per_subgroup": tuned_chunk or n,
@@ -600,10 +721,15 @@ def main():
                          "peak_source": "%s sm_max_mhz x 152 SMs x 128 FP32 lanes" % src,
                          "ops_per_step": OPS_PER_STEP, "steps_per_launch": steps_per_launch,
                          "launch_ms": launch_ms, "primary_span_ms": span_ms,
-                         "primary_launches_per_step": prof_n / args.steps},
+                         "primary_launches_per_step": prof_n / args.steps,
+                         "memory": memory_fractions(pk, steps_per_step, span_ms,
+                                                    traffic_per_launch(n / max(prof_n / args.steps, 1)),
+                                                    prof_n / args.steps)},
             "clocks": clk.summary(),
             "kernels_ms_per_step": {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in kinds.items()},
-            "kernels_note": "ms = summed launch durations (the two sub-groups' launches overlap)",
+            "kernels_note": "ms = summed launch durations (the two sub-groups' launches overlap), from %d steps "
+                            "after the timed region with events around every launch; the timed steps carry "
+                            "events around the primary-transport launches only" % n_kind_steps,
             "math": args.math,
             "surrogate": surrogate,
             "gamma": gamma,

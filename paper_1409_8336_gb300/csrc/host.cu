@@ -95,7 +95,8 @@ const double GL8W[4] = {0.3626837833783620, 0.3137066458778873, 0.22238103445337
 // Moliere distribution functions (Bethe's form) at kMolN nodes v = i * kMolVmax/(kMolN-1):
 // F0 = 1 - exp(-v^2) and, for n = 1, 2,
 //   F_n(v) = (1/n!) int_0^inf v J1(v u) exp(-u^2/4) [(u^2/4) ln(u^2/4)]^n du,
-// by 8-point Gauss-Legendre on 896 panels of [0, 14].
+// by 8-point Gauss-Legendre on 896 panels of [0, 14].  The fourth component of node i holds
+// B(b_i), the root of B - ln B = b_i at b_i = kMolB0 + i / kMolBScale (Newton in double).
 std::vector<float4> moliere_table() {
   std::vector<float4> t(kMolN);
   const int panels = 896;
@@ -113,8 +114,15 @@ std::vector<float4> moliere_table() {
         s2 += w * g * L * L;
       }
     }
+    const double b = static_cast<double>(kMolB0) + i / static_cast<double>(kMolBScale);
+    double B = std::max(4.5, b + std::log(b));
+    for (int it = 0; it < 40; ++it) {
+      const double d = (B - std::log(B) - b) / (1.0 - 1.0 / B);
+      B -= d;
+      if (std::fabs(d) < 1e-15 * B) break;
+    }
     t[i] = make_float4(static_cast<float>(1.0 - std::exp(-v * v)), static_cast<float>(s1),
-                       static_cast<float>(0.5 * s2), 0.0f);
+                       static_cast<float>(0.5 * s2), static_cast<float>(i == 0 ? 4.5 : B));
   }
   return t;
 }
@@ -284,7 +292,7 @@ struct pmc_ctx {
   int64_t chunk = 0;
   bool tuned = false;                  // launch shape fixed (by the caller or the autotuner)
   // kernel timing
-  bool profile = false;
+  int profile = 0;                  // 0 off, 1 every launch, 2 primary-transport launches only
   std::vector<cudaEvent_t> events;      // pairs around launches
   std::vector<int> event_kind;          // kind per pair
   size_t n_events_used = 0;
@@ -485,7 +493,7 @@ int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc, const pm
       c.mass = static_cast<float>(nuclear_mass(q.Z, q.A));
     }
     // materials: Z/A, mean excitation energy, Eq. 1 factor, radiation length, classes
-    std::vector<double> ZA(n_mat), Iv(n_mat);
+    std::vector<double> ZA(n_mat), Iv(n_mat), mol_zz(n_mat, 0.0);
     for (int m = 0; m < n_mat; ++m) {
       const pmc_material& M = mat[m];
       if (M.n < 1 || M.n > PMC_MAX_NUC_PER_MAT || M.rho <= 0.0) return fail(ctx, PMC_E_INVALID, "material %d invalid", m);
@@ -518,17 +526,8 @@ int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc, const pm
         const double Z = nuc[M.nuc[k]].Z;
         zz += M.w[k] * Z * (Z + 1.0) / nuc[M.nuc[k]].mass_u;
       }
-      const double q0 = 197.3269804 / (0.885 * 52917.721090);   // hbar c / (0.885 a0), MeV
-      double lnq = 0.0;
-      for (int k = 0; k < M.n; ++k) {
-        const double Z = nuc[M.nuc[k]].Z;
-        const double c = M.w[k] * Z * (Z + 1.0) / nuc[M.nuc[k]].mass_u / zz;
-        lnq += c * std::log(q0 * q0 * std::pow(Z, 2.0 / 3.0));
-        mc.mol_c[k] = static_cast<float>(c);
-        mc.mol_k[k] = static_cast<float>(3.76 * Z * Z / (137.035999 * 137.035999));
-      }
       mc.mol_K = static_cast<float>(0.307075 * 0.51099895 * zz);
-      mc.mol_lnq = static_cast<float>(lnq);
+      mol_zz[m] = zz;
     }
     int ncls = 1;
     for (int m = 0; m < n_mat; ++m) {
@@ -592,8 +591,33 @@ int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc, const pm
     if ((rc = upload(ctx, ctx->d_nuclei, nm.data(), nm.size() * sizeof(NucleusModel)))) return rc;
     if ((rc = upload(ctx, ctx->d_btab, bt.data(), bt.size() * sizeof(float)))) return rc;
     if (ph.flags & kMoliere) {
+      // the distribution table, then per material G_m(E) = ln chi_c^2 - ln x - ln(1.167 chi_a^2)
+      // on the cross-section grid: chi_c^2 = K x / (p beta)^2, and the screening angle
+      // chi_a^2 = chi_0^2 (1.13 + 3.76 alpha^2), chi_0 = hbar c Z^(1/3) / (0.885 a0 p),
+      // alpha = Z / (137.036 beta), log-averaged over the elements with weights w Z(Z+1)/A
       const std::vector<float4> mt = moliere_table();
-      if ((rc = upload(ctx, ctx->d_mol, mt.data(), mt.size() * sizeof(float4)))) return rc;
+      std::vector<float> tab(moliere_table_bytes(n_mat) / sizeof(float));
+      std::memcpy(tab.data(), mt.data(), mt.size() * sizeof(float4));
+      const double q0 = 197.3269804 / (0.885 * 52917.721090);   // hbar c / (0.885 a0), MeV
+      const double mp = 938.272088;
+      for (int m = 0; m < n_mat; ++m) {
+        const pmc_material& M = mat[m];
+        for (int j = 0; j < kNS; ++j) {
+          const double E = std::exp(static_cast<double>(kLnS0) + j / 64.0);
+          const double pc = std::sqrt(E * E + 2.0 * E * mp), beta = pc / (E + mp);
+          double lna = -2.0 * std::log(pc);
+          for (int k = 0; k < M.n; ++k) {
+            const double Z = nuc[M.nuc[k]].Z;
+            const double c = M.w[k] * Z * (Z + 1.0) / nuc[M.nuc[k]].mass_u / mol_zz[m];
+            const double al = Z / (137.035999 * beta);
+            lna += c * std::log(q0 * q0 * std::pow(Z, 2.0 / 3.0) * (1.13 + 3.76 * al * al));
+          }
+          const double lnK = std::log(0.307075 * 0.51099895 * mol_zz[m]);
+          tab[kMolN * 4 + m * kNS + j] =
+              static_cast<float>(lnK - 2.0 * std::log(pc * beta) - lna - (2.0 * 0.57721566490153286 - 1.0));
+        }
+      }
+      if ((rc = upload(ctx, ctx->d_mol, tab.data(), tab.size() * sizeof(float)))) return rc;
     } else {
       dfree(ctx, ctx->d_mol);
     }
@@ -689,7 +713,8 @@ int pmc_set_launch(pmc_ctx* ctx, int block_size, int64_t chunk) {
 
 int pmc_enable_profile(pmc_ctx* ctx, int on) {
   if (!ctx) return PMC_E_INVALID;
-  ctx->profile = on != 0;
+  if (on < 0 || on > 2) return fail(ctx, PMC_E_INVALID, "profile mode must be 0, 1 or 2");
+  ctx->profile = on;
   return PMC_OK;
 }
 
@@ -756,16 +781,17 @@ struct RunPlan {
   size_t smem;
 };
 
-// Records a timing event (kind >= 0 opens a pair, -1 closes it) when profiling.
-int mark(pmc_ctx* ctx, cudaStream_t s, int kind) {
-  if (!ctx->profile) return PMC_OK;
+// Records a timing event opening (open) or closing a pair around a launch of the given kind,
+// when that kind is profiled.
+int mark(pmc_ctx* ctx, cudaStream_t s, int kind, bool open) {
+  if (!ctx->profile || (ctx->profile == 2 && kind != 0)) return PMC_OK;
   if (ctx->n_events_used == ctx->events.size()) {
     cudaEvent_t e;
     CK(cudaEventCreate(&e));
     ctx->events.push_back(e);
   }
   cudaEvent_t e = ctx->events[ctx->n_events_used++];
-  if (kind >= 0) ctx->event_kind.push_back(kind);
+  if (open) ctx->event_kind.push_back(kind);
   CK(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
   return PMC_OK;
 }
@@ -873,17 +899,18 @@ int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int sour
   a.qne_cap = static_cast<unsigned>(ctx->q_cap);
   a.work = work;
   int rc;
-  if ((rc = mark(ctx, s, source == 0 ? 0 : 1))) return rc;
+  const int kind = source == 0 ? 0 : 1;
+  if ((rc = mark(ctx, s, kind, true))) return rc;
   CK(launch_transport(a, rp.grid_t, ctx->block, rp.smem, s));
-  if ((rc = mark(ctx, s, -1))) return rc;
+  if ((rc = mark(ctx, s, kind, false))) return rc;
   if (ctx->mode == PMC_SURROGATE) {
     const float* P = static_cast<const float*>(ctx->d_sp.p);
     const unsigned cap = static_cast<unsigned>(ctx->q_cap);
     const int grid = ctx->n_sm * 2;   // two blocks of 100 KB shared memory per SM
-    if ((rc = mark(ctx, s, 2))) return rc;
+    if ((rc = mark(ctx, s, 2, true))) return rc;
     CK(launch_surrogate_events(qne_count, cap, qne, static_cast<const int*>(ctx->d_nuc_slot.p), a.seed, ctx->d_swb.p,
                                P, a.tally, a.B, qout, qout_count, cap, a.cnt, a.hist, a.hist_n, grid, s));
-    if ((rc = mark(ctx, s, -1))) return rc;
+    if ((rc = mark(ctx, s, 2, false))) return rc;
     return PMC_OK;
   }
   CascadeArgs c = cascade_args(ctx);
@@ -898,9 +925,9 @@ int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int sour
   c.rec_cap = static_cast<unsigned>(ctx->d_rec[ri].n / sizeof(EvapRecord));
   c.rec_count = rcount;
   c.work = cwork;
-  if ((rc = mark(ctx, s, 2))) return rc;
+  if ((rc = mark(ctx, s, 2, true))) return rc;
   CK(launch_cascade(c, s));
-  if ((rc = mark(ctx, s, -1))) return rc;
+  if ((rc = mark(ctx, s, 2, false))) return rc;
   return PMC_OK;
 }
 
@@ -972,9 +999,9 @@ int enqueue_run(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s) {
     CK(cudaStreamWaitEvent(s, ctx->join_ev, 0));
   }
   int rc;
-  if ((rc = mark(ctx, s, 3))) return rc;
+  if ((rc = mark(ctx, s, 3, true))) return rc;
   CK(launch_stats(stats_args(ctx), s));
-  if ((rc = mark(ctx, s, -1))) return rc;
+  if ((rc = mark(ctx, s, 3, false))) return rc;
   return PMC_OK;
 }
 
@@ -1070,7 +1097,7 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     char key[256];
     std::snprintf(key, sizeof(key), "%llu/%lld/%zu/%d/%d/%lld/%p/%p/%p/%d", (unsigned long long)n_histories,
                   (long long)rp.chunk, sd.size(), ctx->block, ctx->opt.n_batches, ctx->n_vox, ctx->d_tally.p,
-                  ctx->d_hist.p, ctx->let_on ? ctx->d_let_num.p : nullptr, (ctx->profile ? 1 : 0) + 2 * mode);
+                  ctx->d_hist.p, ctx->let_on ? ctx->d_let_num.p : nullptr, ctx->profile + 3 * mode);
     if (!ctx->gexec || ctx->gkey != key) {
       if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
       cudaGraph_t graph;

@@ -43,6 +43,14 @@ constexpr unsigned kNoStraggling = 1u, kNoMcs = 2u, kNoElastic = 4u, kNoInelasti
 constexpr int kMolN = 1025;                    // Moliere distribution-function nodes on v in [0, kMolVmax]
 constexpr float kMolVmax = 8.0f;
 constexpr float kMolBmin = 4.5f;               // validity floor of the expansion (Bethe)
+// B(b), the root of B - ln B = b, tabulated in the fourth component of the distribution
+// table's nodes: node i at b = kMolB0 + i / kMolBScale (kMolB0 = 4.5 - ln 4.5, B = 4.5)
+constexpr float kMolB0 = 2.99592471f;
+constexpr float kMolBScale = 32.0f;
+// Device bytes of the Moliere tables: kMolN float4 nodes, then n_mat x kNS floats of G_m.
+__host__ __device__ constexpr size_t moliere_table_bytes(int n_mat) {
+  return kMolN * sizeof(float4) + static_cast<size_t>(n_mat) * kNS * sizeof(float);
+}
 
 // Learned stand-in of the event generator (quantile network).
 constexpr int kSurrSlots = 4;                    // proton slots per event
@@ -66,10 +74,9 @@ struct MatConst {
   int n;
   int nuc[kMaxNucPerMat];
   float n_per_g[kMaxNucPerMat];    // atoms per gram x 1e-27 (so that n * sigma[mb] is cm^2/g)
-  // Moliere: chi_c^2 = mol_K x / (p beta)^2 (x in g/cm^2); ln chi_a^2 = mol_lnq - 2 ln p
-  // + sum_j mol_c[j] ln(1.13 + mol_k[j] / beta^2), weights Z(Z+1)/A by mass
-  float mol_K, mol_lnq;
-  float mol_c[kMaxNucPerMat], mol_k[kMaxNucPerMat];
+  // Moliere: chi_c^2 = mol_K x / (p beta)^2 (x in g/cm^2); the rest of the B equation is
+  // tabulated per material (moliere_b below)
+  float mol_K;
 };
 
 struct NucConst {
@@ -264,6 +271,30 @@ __device__ __forceinline__ float moliere_theta(const float4* T, float u, float c
     v = (static_cast<float>(lo) + t) * (kMolVmax / static_cast<float>(kMolN - 1));
   }
   return fminf(v * sqrtf(chic2 * B), 3.14159265f);
+}
+
+// Moliere's B for a step of x = rho dx g/cm^2 of material m at ln E: b = ln chi_c^2 -
+// ln(1.167 chi_a^2) = ln x + G_m(E), with G_m tabulated on the cross-section grid after the
+// distribution table; B from the tabulated root of B - ln B = b (Newton beyond its end), and
+// the expansion's floor 4.5 below b(4.5).
+__device__ __forceinline__ float moliere_b(const float4* T, int m, float lnE, float x) {
+  const float* G = reinterpret_cast<const float*>(T + kMolN);
+  float s = (lnE - kLnS0) * kTabScale;
+  s = fminf(fmaxf(s, 0.0f), static_cast<float>(kNS - 1) - 1e-3f);
+  const int j = static_cast<int>(s);
+  const float* g = G + m * kNS + j;
+  const float b = logf(x) + (g[0] + (s - static_cast<float>(j)) * (g[1] - g[0]));
+  if (!(b > kMolB0)) return kMolBmin;
+  const float sb = (b - kMolB0) * kMolBScale;
+  if (sb < static_cast<float>(kMolN - 1)) {
+    const int i = static_cast<int>(sb);
+    const float w0 = T[i].w, w1 = T[i + 1].w;
+    return w0 + (sb - static_cast<float>(i)) * (w1 - w0);
+  }
+  float B = b + logf(b);
+#pragma unroll
+  for (int it = 0; it < 4; ++it) B -= (B - logf(B) - b) / (1.0f - 1.0f / B);
+  return B;
 }
 
 // ---------------------------------------------------------------------------

@@ -194,20 +194,9 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   if (kMol && !(ph.flags & kNoMcs)) {
     // Moliere (Bethe's form), at the step-start energy over the planned step
     const float pc = sqrtf(E0 * E0 + 2.0f * E0 * kMp);
-    const float beta = pc / (E0 + kMp);
-    const float pb = pc * beta;
+    const float pb = pc * pc / (E0 + kMp);
     const float chic2 = mc.mol_K * dx * rho / (pb * pb);
-    const float ib2 = 1.0f / (beta * beta);
-    float lna = mc.mol_lnq - 2.0f * logf(pc);
-    for (int j = 0; j < mc.n; ++j) lna += mc.mol_c[j] * logf(1.13f + mc.mol_k[j] * ib2);
-    const float b = logf(chic2) - lna - 0.15443133f;   // ln 1.167 = 2 Euler's constant - 1
-    float B = kMolBmin;
-    if (b > kMolBmin - 1.50407740f) {                   // B - ln B = b has B > 4.5
-      B = b + logf(b);
-#pragma unroll
-      for (int it = 0; it < 4; ++it) B -= (B - logf(B) - b) / (1.0f - 1.0f / B);
-      B = fmaxf(B, kMolBmin);
-    }
+    const float B = moliere_b(mol, m, lnE, dx * rho);
     const float th = moliere_theta(mol, ua.u0, chic2, B);
     if (th > 0.0f) {
       float s_, c_, sp, cp;
@@ -381,7 +370,9 @@ __global__ void __launch_bounds__(256, PMC_TRANSPORT_MIN_BLOCKS) transport_kerne
   if (kMol) {
     const size_t off_mol = ((reinterpret_cast<unsigned char*>(st + nmat * kNS) - smem) + 15) / 16 * 16;
     mol = reinterpret_cast<float4*>(smem + off_mol);
-    for (int i = threadIdx.x; i < kMolN; i += blockDim.x) mol[i] = a.mol[i];
+    const float4* src = a.mol;
+    const int n4 = static_cast<int>(moliere_table_bytes(nmat) / sizeof(float4));
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) mol[i] = src[i];
   }
   __syncthreads();
   const Physics& ph = *php;
@@ -447,7 +438,7 @@ __global__ void __launch_bounds__(256, PMC_TRANSPORT_MIN_BLOCKS) transport_kerne
 size_t transport_smem_bytes(int n_cls, int n_mat, bool moliere) {
   const size_t b = (sizeof(Physics) + 15) / 16 * 16 + 1ull * n_cls * (kNE + kNR) * sizeof(float2) +
                    1ull * n_mat * kNS * sizeof(float);
-  return moliere ? (b + 15) / 16 * 16 + kMolN * sizeof(float4) : b;
+  return moliere ? (b + 15) / 16 * 16 + moliere_table_bytes(n_mat) : b;
 }
 
 namespace {

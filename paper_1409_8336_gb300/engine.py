@@ -377,8 +377,10 @@ class Engine:
         self._check(self._L.pmc_read_let_tally(self._ctx, num.ctypes.data_as(p), den.ctypes.data_as(p), num.size))
         return num, den
 
-    def enable_profile(self, on=True):
-        self._check(self._L.pmc_enable_profile(self._ctx, 1 if on else 0))
+    def enable_profile(self, on=True, primary_only=False):
+        """Kernel timing events inside the run's graph: around every launch, or around the
+        primary-transport launches only (primary_only, the lightest)."""
+        self._check(self._L.pmc_enable_profile(self._ctx, (2 if primary_only else 1) if on else 0))
 
     def read_profile(self):
         """Per kernel kind (primary transport, secondary transport, cascade, statistics):

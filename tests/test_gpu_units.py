@@ -138,3 +138,31 @@ def test_event_generator_yields_match_oracle(eng, nuc):
         for gv, ov in ((y["count"][name] / ng, per_ev_n), (y["energy"][name] / ng, per_ev_T)):
             se = ov.std() * np.sqrt(1 / len(ov) + 1 / ng)
             assert abs(gv - ov.mean()) < 5 * se + 1e-9, (name, gv, ov.mean(), se)
+
+
+def test_profile_modes_time_what_they_say_and_leave_the_dose_alone():
+    """Timing events around every launch, around the primary-transport launches only, or
+    none: the same run gives the same tallies; the light mode times the primary launches
+    and nothing else; an unknown mode is refused."""
+    from paper_1409_8336_gb300 import Engine, PmcError
+
+    p = W.config2()
+    e = Engine(device=0, n_batches=10, fast_math=True, block_size=192)
+    e.load_problem(p)
+    doses, profs = [], []
+    for mode in ("all", "primary", "off"):
+        e.enable_profile(mode != "off", primary_only=(mode == "primary"))
+        e.transport(50_000, 21)
+        profs.append(e.read_profile()[0])
+        doses.append(e.read_dose())
+    full, light, off = profs
+    assert all(full[k]["launches"] > 0 for k in full)
+    assert light["transport_primary"]["launches"] == full["transport_primary"]["launches"]
+    assert light["transport_primary"]["ms"] > 0.0
+    assert all(light[k]["launches"] == 0 for k in light if k != "transport_primary")
+    assert all(off[k]["launches"] == 0 for k in off)
+    for d, s in doses[1:]:
+        assert np.array_equal(d, doses[0][0]) and np.array_equal(s, doses[0][1])
+    with pytest.raises(PmcError):
+        e._check(e._L.pmc_enable_profile(e._ctx, 3))
+    e.close()
