@@ -283,144 +283,170 @@ __device__ void emit_event(const Particle& ev, const float* y1, const float* y2,
 
 // Fused inference: one block takes 64 rows at a time (persistent over the
 // device-resident row count), keeps their activations in shared memory as BF16
-// through all five layers, and streams each layer's BF16 weights in 64x64
-// chunks with 16-byte loads, double-buffered: the next chunk's loads are in
-// flight while the tensor cores consume the current one (FP32 accumulation).
+// through all five layers, and streams the layers' BF16 weights in 64x64
+// chunks by cp.async (global -> shared, bypassing L1) through three buffers:
+// the copies of the next two chunks, across layer boundaries, are in flight
+// while the tensor cores consume the current one (FP32 accumulation).
 // Two launches per generation replace ten layer GEMMs and their activations in
 // global memory.
 constexpr int kActLd = kSurrHidden + 8;          // padded row (conflict-free fragment loads)
 constexpr int kChunk = 64;                       // k-chunk of streamed weights
 constexpr int kWLd = kChunk + 8;                 // 144-byte rows, 16-byte aligned
-constexpr int kInferSmem = 2 * 64 * kActLd * 2 + 2 * 64 * kWLd * 2;
+constexpr int kWStages = 3;                      // weight-chunk buffers
+constexpr int kInferSmem = 2 * 64 * kActLd * 2 + kWStages * 64 * kWLd * 2;
 
-// The five layers on one 64-row tile whose inputs are in act[0] (columns
-// 0..kSurrIn-1); the last layer's outputs for rows < nvalid go to out[r * kSurrOut + n].
-__device__ void mlp_tile(__nv_bfloat16* const (&act)[2], __nv_bfloat16* const (&wbuf)[2],
-                         const __nv_bfloat16* __restrict__ Wb, const float* __restrict__ P, float* out, int nvalid) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  {
-    size_t off = 0;
-    int cur = 0;
-#pragma unroll 1
-    for (int l = 0; l < kSurrLayers; ++l) {
-      const int din = l == 0 ? kSurrIn : kSurrHidden;
-      const int dout = l == kSurrLayers - 1 ? kSurrOut : kSurrHidden;
-      const int kc = din < kChunk ? din : kChunk;          // chunk width (32 for the first layer)
-      const int vec_per_row = kc / 8;                      // 16-byte vectors per weight row
-      const __nv_bfloat16* W = Wb + off;
-      const float* bias = P + off + static_cast<size_t>(din) * dout;
-      const __nv_bfloat16* ain = act[cur];
-      __nv_bfloat16* aout = act[cur ^ 1];
-      const int n_chunks = (dout + 63) / 64 * (din / kc);
-      // chunk c: n-tile c / (din / kc), k-chunk c % (din / kc)
-      uint4 pf[4];
-      auto fetch = [&](int c) {
-        const int n0 = (c / (din / kc)) * 64, k0 = (c % (din / kc)) * kc;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int v = tid + 128 * i, nn = v / vec_per_row, kv = (v % vec_per_row) * 8;
-          pf[i] = (nn < 64 && n0 + nn < dout)
-                      ? *reinterpret_cast<const uint4*>(W + static_cast<size_t>(n0 + nn) * din + k0 + kv)
-                      : make_uint4(0u, 0u, 0u, 0u);
-        }
-      };
-      auto stash = [&](int buf) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int v = tid + 128 * i, nn = v / vec_per_row, kv = (v % vec_per_row) * 8;
-          if (nn < 64) *reinterpret_cast<uint4*>(wbuf[buf] + nn * kWLd + kv) = pf[i];
-        }
-      };
-      fetch(0);
-      stash(0);
-      __syncthreads();
-      float acc[2][4][4];
-#pragma unroll 1
-      for (int c = 0; c < n_chunks; ++c) {
-        const int kpn = din / kc;
-        const int n0 = (c / kpn) * 64, k0 = (c % kpn) * kc;
-        if (c % kpn == 0) {
-#pragma unroll
-          for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-              for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-        }
-        if (c + 1 < n_chunks) fetch(c + 1);                  // loads in flight during the MMAs
-        const __nv_bfloat16* Ws = wbuf[c & 1];
-        for (int kk = 0; kk < kc; kk += 16) {
-          unsigned af[2][4], bfr[4][2];
-#pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            const __nv_bfloat16* a0 = ain + (wm + 16 * i + g) * kActLd + k0 + kk + 2 * t;
-            af[i][0] = *reinterpret_cast<const unsigned*>(a0);
-            af[i][1] = *reinterpret_cast<const unsigned*>(a0 + 8 * kActLd);
-            af[i][2] = *reinterpret_cast<const unsigned*>(a0 + 8);
-            af[i][3] = *reinterpret_cast<const unsigned*>(a0 + 8 * kActLd + 8);
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const __nv_bfloat16* b0 = Ws + (wn + 8 * j + g) * kWLd + kk + 2 * t;
-            bfr[j][0] = *reinterpret_cast<const unsigned*>(b0);
-            bfr[j][1] = *reinterpret_cast<const unsigned*>(b0 + 8);
-          }
-#pragma unroll
-          for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
-        }
-        if (c + 1 < n_chunks) stash((c + 1) & 1);
-        if (c % kpn == kpn - 1) {                            // n-tile complete: epilogue
-#pragma unroll
-          for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const int r = wm + 16 * i + g + (q >= 2 ? 8 : 0);
-                const int n = n0 + wn + 8 * j + 2 * t + (q & 1);
-                if (n >= dout) continue;
-                const float v = acc[i][j][q] + bias[n];
-                if (l < kSurrLayers - 1) {
-                  aout[r * kActLd + n] = __float2bfloat16_rn(fmaxf(v, 0.0f));
-                } else if (r < nvalid) {
-                  out[r * kSurrOut + n] = v;
-                }
-              }
-        }
-        __syncthreads();
-      }
-      off += static_cast<size_t>(din) * dout + dout;
-      cur ^= 1;
-    }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_newest_pending() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+// Position of the weight-chunk stream: layer l, chunk c of that layer (n-tile c / kpn,
+// k-chunk c % kpn), and the layer's offset in the parameter vector.
+struct ChunkCursor {
+  int l = 0, c = 0;
+  size_t off = 0;
+};
+__device__ __forceinline__ int layer_in(int l) { return l == 0 ? kSurrIn : kSurrHidden; }
+__device__ __forceinline__ int layer_out(int l) { return l == kSurrLayers - 1 ? kSurrOut : kSurrHidden; }
+__device__ __forceinline__ int layer_kc(int l) { return layer_in(l) < kChunk ? layer_in(l) : kChunk; }
+__device__ __forceinline__ int layer_chunks(int l) { return (layer_out(l) + 63) / 64 * (layer_in(l) / layer_kc(l)); }
+
+// Starts the copies of the cursor's chunk into buf (nothing past the last layer); rows of a
+// chunk beyond the layer's outputs are zero-filled.
+__device__ __forceinline__ void issue_chunk(const ChunkCursor& f, const __nv_bfloat16* __restrict__ Wb,
+                                            __nv_bfloat16* buf) {
+  if (f.l >= kSurrLayers) return;
+  const int din = layer_in(f.l), dout = layer_out(f.l), kc = layer_kc(f.l), kpn = din / kc;
+  const int n0 = (f.c / kpn) * 64, k0 = (f.c % kpn) * kc, vpr = kc / 8;
+  const __nv_bfloat16* W = Wb + f.off;
+  for (int v = threadIdx.x; v < 64 * vpr; v += blockDim.x) {
+    const int nn = v / vpr, kv = (v % vpr) * 8;
+    __nv_bfloat16* dst = buf + nn * kWLd + kv;
+    if (n0 + nn < dout) cp_async16(dst, W + static_cast<size_t>(n0 + nn) * din + k0 + kv);
+    else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
-__device__ __forceinline__ void tile_buffers(unsigned char* smem, __nv_bfloat16* (&act)[2], __nv_bfloat16* (&wbuf)[2]) {
-  act[0] = reinterpret_cast<__nv_bfloat16*>(smem);
-  act[1] = act[0] + 64 * kActLd;
-  wbuf[0] = act[0] + 2 * 64 * kActLd;
-  wbuf[1] = wbuf[0] + 64 * kWLd;
+__device__ __forceinline__ void advance_chunk(ChunkCursor& f) {
+  if (f.l >= kSurrLayers) return;
+  if (++f.c == layer_chunks(f.l)) {
+    f.off += static_cast<size_t>(layer_in(f.l)) * layer_out(f.l) + layer_out(f.l);
+    ++f.l;
+    f.c = 0;
+  }
 }
 
+// The five layers on one 64-row tile whose inputs are in the first activation buffer (columns
+// 0..kSurrIn-1); the last layer's outputs for rows < nvalid go to out[r * kSurrOut + n].
+__device__ __forceinline__ void mlp_tile(__nv_bfloat16* const tile, const __nv_bfloat16* __restrict__ Wb,
+                         const float* __restrict__ P, float* out, int nvalid) {
+  // shared memory of the tile: two activation buffers [64][kActLd], then kWStages weight
+  // buffers [64][kWLd] (addressed arithmetically: no local-memory pointer arrays)
+  __nv_bfloat16* const wbuf0 = tile + 2 * 64 * kActLd;
+  auto wbuf = [&](int i) { return wbuf0 + i * (64 * kWLd); };
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  // prologue: the first two chunks in flight (one commit group per chunk, empty past the end)
+  ChunkCursor f;
+  issue_chunk(f, Wb, wbuf(0));
+  cp_async_commit();
+  advance_chunk(f);
+  issue_chunk(f, Wb, wbuf(1));
+  cp_async_commit();
+  advance_chunk(f);
+  size_t off = 0;
+  int cur = 0, q = 0;
+#pragma unroll 1
+  for (int l = 0; l < kSurrLayers; ++l) {
+    const int din = layer_in(l), dout = layer_out(l), kc = layer_kc(l), kpn = din / kc;
+    const float* bias = P + off + static_cast<size_t>(din) * dout;
+    const __nv_bfloat16* ain = tile + cur * (64 * kActLd);
+    __nv_bfloat16* aout = tile + (cur ^ 1) * (64 * kActLd);
+    const int n_chunks = layer_chunks(l);
+    float acc[2][4][4];
+#pragma unroll 1
+    for (int c = 0; c < n_chunks; ++c, ++q) {
+      const int n0 = (c / kpn) * 64, k0 = (c % kpn) * kc;
+      cp_async_wait_newest_pending();   // this thread's copies of chunk q have landed
+      __syncthreads();                  // everyone's have; chunk q-1 and the last epilogue are done
+      issue_chunk(f, Wb, wbuf((q + 2) % kWStages));
+      cp_async_commit();
+      advance_chunk(f);
+      if (c % kpn == 0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+      }
+      const __nv_bfloat16* Ws = wbuf(q % kWStages);
+      for (int kk = 0; kk < kc; kk += 16) {
+        unsigned af[2][4], bfr[4][2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const __nv_bfloat16* a0 = ain + (wm + 16 * i + g) * kActLd + k0 + kk + 2 * t;
+          af[i][0] = *reinterpret_cast<const unsigned*>(a0);
+          af[i][1] = *reinterpret_cast<const unsigned*>(a0 + 8 * kActLd);
+          af[i][2] = *reinterpret_cast<const unsigned*>(a0 + 8);
+          af[i][3] = *reinterpret_cast<const unsigned*>(a0 + 8 * kActLd + 8);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const __nv_bfloat16* b0 = Ws + (wn + 8 * j + g) * kWLd + kk + 2 * t;
+          bfr[j][0] = *reinterpret_cast<const unsigned*>(b0);
+          bfr[j][1] = *reinterpret_cast<const unsigned*>(b0 + 8);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
+      }
+      if (c % kpn == kpn - 1) {                            // n-tile complete: epilogue
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r4 = 0; r4 < 4; ++r4) {
+              const int r = wm + 16 * i + g + (r4 >= 2 ? 8 : 0);
+              const int n = n0 + wn + 8 * j + 2 * t + (r4 & 1);
+              if (n >= dout) continue;
+              const float v = acc[i][j][r4] + bias[n];
+              if (l < kSurrLayers - 1) {
+                aout[r * kActLd + n] = __float2bfloat16_rn(fmaxf(v, 0.0f));
+              } else if (r < nvalid) {
+                out[r * kSurrOut + n] = v;
+              }
+            }
+      }
+    }
+    off += static_cast<size_t>(din) * dout + dout;
+    cur ^= 1;
+  }
+  __syncthreads();
+}
+
+
+
 // Rows X[n][kSurrIn] -> outputs Y[n][kSurrOut] (persistent over 64-row tiles).
-__global__ void __launch_bounds__(128) mlp_infer_kernel(const unsigned* n_rows, unsigned cap, const float* __restrict__ X,
+__global__ void __launch_bounds__(128, 2) mlp_infer_kernel(const unsigned* n_rows, unsigned cap, const float* __restrict__ X,
                                                         const __nv_bfloat16* __restrict__ Wb,
                                                         const float* __restrict__ P, float* __restrict__ Y) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __nv_bfloat16* act[2];
-  __nv_bfloat16* wbuf[2];
-  tile_buffers(smem, act, wbuf);
+  __nv_bfloat16* const tile = reinterpret_cast<__nv_bfloat16*>(smem);   // act[0] = tile
   const unsigned rows = min(*n_rows, cap);
   for (unsigned r0 = blockIdx.x * 64u; r0 < rows; r0 += gridDim.x * 64u) {
     for (int e = threadIdx.x; e < 64 * kSurrIn; e += 128) {
       const int r = e / kSurrIn, c = e % kSurrIn;
-      act[0][r * kActLd + c] = __float2bfloat16_rn(r0 + r < rows ? X[static_cast<size_t>(r0 + r) * kSurrIn + c] : 0.0f);
+      tile[r * kActLd + c] = __float2bfloat16_rn(r0 + r < rows ? X[static_cast<size_t>(r0 + r) * kSurrIn + c] : 0.0f);
     }
-    mlp_tile(act, wbuf, Wb, P, Y + static_cast<size_t>(r0) * kSurrOut, static_cast<int>(min(64u, rows - r0)));
+    mlp_tile(tile, Wb, P, Y + static_cast<size_t>(r0) * kSurrOut, static_cast<int>(min(64u, rows - r0)));
     __syncthreads();
   }
 }
@@ -431,7 +457,7 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(const unsigned* n_rows, 
 // and outputs in shared memory throughout.
 constexpr int kEventSmem = kInferSmem + 64 * kSurrIn * 4 + 2 * 64 * kSurrOut * 4;
 
-__global__ void __launch_bounds__(128) surrogate_event_kernel(const unsigned* n_ev, unsigned cap,
+__global__ void __launch_bounds__(128, 2) surrogate_event_kernel(const unsigned* n_ev, unsigned cap,
                                                               const Particle* __restrict__ qne, const int* nuc_slot,
                                                               const unsigned long long* seedp,
                                                               const __nv_bfloat16* __restrict__ Wb,
@@ -440,9 +466,7 @@ __global__ void __launch_bounds__(128) surrogate_event_kernel(const unsigned* n_
                                                               unsigned qsec_cap, Counters* cnt, long long* hist,
                                                               unsigned long long hist_n) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __nv_bfloat16* act[2];
-  __nv_bfloat16* wbuf[2];
-  tile_buffers(smem, act, wbuf);
+  __nv_bfloat16* const tile = reinterpret_cast<__nv_bfloat16*>(smem);   // act[0] = tile
   float* xin = reinterpret_cast<float*>(smem + kInferSmem);   // [64][kSurrIn]
   float* y1 = xin + 64 * kSurrIn;                              // [64][kSurrOut]
   float* y2 = y1 + 64 * kSurrOut;
@@ -467,9 +491,9 @@ __global__ void __launch_bounds__(128) surrogate_event_kernel(const unsigned* n_
     for (int pass = 0; pass < 2; ++pass) {
       for (int e = tid; e < 64 * kSurrIn; e += 128) {
         const int r = e / kSurrIn, c = e % kSurrIn;
-        act[0][r * kActLd + c] = __float2bfloat16_rn(xin[r * kSurrIn + c]);
+        tile[r * kActLd + c] = __float2bfloat16_rn(xin[r * kSurrIn + c]);
       }
-      mlp_tile(act, wbuf, Wb, P, pass == 0 ? y1 : y2, nvalid);
+      mlp_tile(tile, Wb, P, pass == 0 ? y1 : y2, nvalid);
       __syncthreads();
       if (pass == 0 && tid < nvalid)
         xin[tid * kSurrIn + 1 + kSurrTargets] = static_cast<float>(multiplicity(y1[tid * kSurrOut])) / kSurrSlots;
