@@ -127,6 +127,43 @@ std::vector<float4> moliere_table() {
   return t;
 }
 
+// Brackets for inverting F = F0 + x F1 + x^2 F2, x = 1/B in (0, 1/4.5]: per node the least
+// and greatest F over x (F is quadratic in x), both increasing along the nodes as F is for
+// each B; for u in [u_k, u_k+1) the node below u lies at or above the last node whose
+// greatest F is <= u_k, and at or below the last node whose least F is <= u_k+1.  Two
+// nodes of margin each side cover single-precision evaluation on the device.
+std::vector<unsigned> moliere_guide(const std::vector<float4>& t) {
+  std::vector<double> flo(kMolN), fhi(kMolN);
+  const double xm = 1.0 / 4.5;
+  for (int i = 0; i < kMolN; ++i) {
+    const double a = t[i].x, b = t[i].y, c = t[i].z;
+    auto F = [&](double x) { return a + x * (b + x * c); };
+    double lo = std::min(F(0.0), F(xm)), hi = std::max(F(0.0), F(xm));
+    if (c != 0.0) {
+      const double xs = -b / (2.0 * c);
+      if (xs > 0.0 && xs < xm) { lo = std::min(lo, F(xs)); hi = std::max(hi, F(xs)); }
+    }
+    flo[i] = lo;
+    fhi[i] = hi;
+  }
+  for (int i = 1; i < kMolN; ++i) {        // enforce monotone bounds (conservative)
+    flo[i] = std::max(flo[i], flo[i - 1]);
+  }
+  for (int i = kMolN - 2; i >= 0; --i) fhi[i] = std::min(fhi[i], fhi[i + 1]);
+  std::vector<unsigned> g(kMolGuide);
+  for (int k = 0; k < kMolGuide; ++k) {
+    const double ua = static_cast<double>(k) / kMolGuide, ub = static_cast<double>(k + 1) / kMolGuide;
+    int llo = 0, lhi = 0;
+    for (int i = 0; i < kMolN; ++i) {
+      if (fhi[i] <= ua) llo = i;
+      if (flo[i] <= ub) lhi = i;
+    }
+    const int lo = std::max(0, llo - 2), hi = std::min(kMolN - 1, lhi + 3);
+    g[k] = static_cast<unsigned>(lo) | (static_cast<unsigned>(hi) << 16);
+  }
+  return g;
+}
+
 double integrate_inv_s(double a, double b, double ZA, double I) {
   const double m = 0.5 * (a + b), h = 0.5 * (b - a);
   double s = 0.0;
@@ -598,6 +635,8 @@ int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc, const pm
       const std::vector<float4> mt = moliere_table();
       std::vector<float> tab(moliere_table_bytes(n_mat) / sizeof(float));
       std::memcpy(tab.data(), mt.data(), mt.size() * sizeof(float4));
+      const std::vector<unsigned> guide = moliere_guide(mt);
+      std::memcpy(tab.data() + kMolN * 4, guide.data(), guide.size() * sizeof(unsigned));
       const double q0 = 197.3269804 / (0.885 * 52917.721090);   // hbar c / (0.885 a0), MeV
       const double mp = 938.272088;
       for (int m = 0; m < n_mat; ++m) {
@@ -613,7 +652,7 @@ int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc, const pm
             lna += c * std::log(q0 * q0 * std::pow(Z, 2.0 / 3.0) * (1.13 + 3.76 * al * al));
           }
           const double lnK = std::log(0.307075 * 0.51099895 * mol_zz[m]);
-          tab[kMolN * 4 + m * kNS + j] =
+          tab[kMolN * 4 + kMolGuide + m * kNS + j] =
               static_cast<float>(lnK - 2.0 * std::log(pc * beta) - lna - (2.0 * 0.57721566490153286 - 1.0));
         }
       }

@@ -47,9 +47,12 @@ constexpr float kMolBmin = 4.5f;               // validity floor of the expansio
 // table's nodes: node i at b = kMolB0 + i / kMolBScale (kMolB0 = 4.5 - ln 4.5, B = 4.5)
 constexpr float kMolB0 = 2.99592471f;
 constexpr float kMolBScale = 32.0f;
-// Device bytes of the Moliere tables: kMolN float4 nodes, then n_mat x kNS floats of G_m.
+// A guide to the distribution table's inversion: for u in [k, k+1) / kMolGuide, node
+// brackets [lo, hi] (16 bits each) with F(lo) <= u < F(hi) for every B >= 4.5.
+constexpr int kMolGuide = 256;
+// Device bytes of the Moliere tables: kMolN float4 nodes, the guide, then n_mat x kNS floats of G_m.
 __host__ __device__ constexpr size_t moliere_table_bytes(int n_mat) {
-  return kMolN * sizeof(float4) + static_cast<size_t>(n_mat) * kNS * sizeof(float);
+  return kMolN * sizeof(float4) + kMolGuide * sizeof(unsigned) + static_cast<size_t>(n_mat) * kNS * sizeof(float);
 }
 
 // Learned stand-in of the event generator (quantile network).
@@ -247,8 +250,8 @@ __device__ __forceinline__ float sigma_el(const NucConst& n, float E) {
 }
 
 // Moliere space angle for the uniform u (Bethe's form): the distribution function
-// F0 + F1/B + F2/B^2 (nodes T[i] = (F0, F1, F2) at v = i h) inverted by bisection over
-// the nodes and linear interpolation; beyond kMolVmax the single-scattering tail
+// F0 + F1/B + F2/B^2 (nodes T[i] = (F0, F1, F2) at v = i h) inverted by bisection within
+// the guide's bracket for u and linear interpolation; beyond kMolVmax the single-scattering tail
 // (density ~ v^-3); theta = v chi_c sqrt(B), at most pi.
 __device__ __forceinline__ float moliere_theta(const float4* T, float u, float chic2, float B) {
   const float iB = 1.0f / B, iB2 = iB * iB;
@@ -261,7 +264,9 @@ __device__ __forceinline__ float moliere_theta(const float4* T, float u, float c
   if (u >= Fmax) {
     v = kMolVmax * sqrtf((1.0f - Fmax) / (1.0f - u));
   } else {
-    int lo = 0, hi = kMolN - 1;
+    const unsigned* guide = reinterpret_cast<const unsigned*>(T + kMolN);
+    const unsigned gw = guide[min(static_cast<int>(u * static_cast<float>(kMolGuide)), kMolGuide - 1)];
+    int lo = static_cast<int>(gw & 0xffffu), hi = static_cast<int>(gw >> 16);
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
       if (F(mid) <= u) lo = mid; else hi = mid;
@@ -278,7 +283,7 @@ __device__ __forceinline__ float moliere_theta(const float4* T, float u, float c
 // distribution table; B from the tabulated root of B - ln B = b (Newton beyond its end), and
 // the expansion's floor 4.5 below b(4.5).
 __device__ __forceinline__ float moliere_b(const float4* T, int m, float lnE, float x) {
-  const float* G = reinterpret_cast<const float*>(T + kMolN);
+  const float* G = reinterpret_cast<const float*>(T + kMolN) + kMolGuide;
   float s = (lnE - kLnS0) * kTabScale;
   s = fminf(fmaxf(s, 0.0f), static_cast<float>(kNS - 1) - 1e-3f);
   const int j = static_cast<int>(s);
