@@ -265,6 +265,12 @@ int pmc_surrogate_load(pmc_ctx* ctx, const float* params, size_t n);
  * the gradient [PMC_SURROGATE_PARAMS] and the outputs yhat [rows][16]. */
 int pmc_surrogate_grad(pmc_ctx* ctx, const float* params, const float* x, const float* y, const float* tau,
                        const float* mask, int rows, float* loss, float* grad, float* yhat);
+/* The loaded network on the tensor cores, as inside the transport's event stage: inputs
+ * x[rows][32] -> outputs y[rows][16] (host arrays, 1 <= rows <= 1048576), BF16 weights and
+ * activations with FP32 accumulation (the network is not part of the paper: it stands in
+ * for Sec. II.A.4's event generator).  PMC_E_INVALID without a network or with bad
+ * arguments, PMC_E_TIMEOUT if a device wait of the tensor-core pipeline timed out. */
+int pmc_surrogate_infer(pmc_ctx* ctx, const float* x, int rows, float* y);
 
 /* ---- non-elastic event generator -------------------------------------------
  * n non-elastic interactions of a proton of kinetic energy E (MeV) with the

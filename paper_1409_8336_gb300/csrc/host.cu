@@ -945,7 +945,7 @@ int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int sour
   if (ctx->mode == PMC_SURROGATE) {
     const float* P = static_cast<const float*>(ctx->d_sp.p);
     const unsigned cap = static_cast<unsigned>(ctx->q_cap);
-    const int grid = ctx->n_sm * 2;   // two blocks of 100 KB shared memory per SM
+    const int grid = ctx->n_sm;       // one block per SM: 132 KB of shared memory, 256 TMEM columns
     if ((rc = mark(ctx, s, 2, true))) return rc;
     CK(launch_surrogate_events(qne_count, cap, qne, static_cast<const int*>(ctx->d_nuc_slot.p), a.seed, ctx->d_swb.p,
                                P, a.tally, a.B, qout, qout_count, cap, a.cnt, a.hist, a.hist_n, grid, s));
@@ -1219,7 +1219,9 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     ctx->have_run = true;
     ctx->let_valid = ctx->let_on;
     if (hc.dropped) return fail(ctx, PMC_E_QUEUE_OVERFLOW, "%llu particles did not fit a queue", (unsigned long long)hc.dropped);
-    if (hc.errors) return fail(ctx, PMC_E_TIMEOUT, "%llu particles exceeded the step limit", (unsigned long long)hc.errors);
+    if (hc.errors)
+      return fail(ctx, PMC_E_TIMEOUT, "%llu particles exceeded the step limit or device waits timed out",
+                  (unsigned long long)hc.errors);
     return PMC_OK;
   } catch (...) {
     return fail(ctx, PMC_E_INVALID, "exception in transport");
@@ -1643,7 +1645,9 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     L.dropped = static_cast<int64_t>(hc.dropped);
     L.errors = static_cast<int64_t>(hc.errors);
     if (hc.dropped) return fail(ctx, PMC_E_QUEUE_OVERFLOW, "%llu particles did not fit a queue", (unsigned long long)hc.dropped);
-    if (hc.errors) return fail(ctx, PMC_E_TIMEOUT, "%llu particles exceeded the step limit", (unsigned long long)hc.errors);
+    if (hc.errors)
+      return fail(ctx, PMC_E_TIMEOUT, "%llu particles exceeded the step limit or device waits timed out",
+                  (unsigned long long)hc.errors);
     return PMC_OK;
   } catch (...) {
     return fail(ctx, PMC_E_INVALID, "exception in transport");
@@ -1862,6 +1866,29 @@ int pmc_surrogate_grad(pmc_ctx* ctx, const float* params, const float* x, const 
   if (yhat) CK(cudaMemcpy(yhat, A[kSurrLayers - 1], static_cast<size_t>(rows) * kSurrOut * 4, cudaMemcpyDeviceToHost));
   for (DevBuf* b : {&X, &Y, &T, &M, &g0, &g1, &L}) dfree(ctx, *b);
   for (int l = 0; l <= kSurrLayers; ++l) dfree(ctx, act[l]);
+  return PMC_OK;
+}
+
+int pmc_surrogate_infer(pmc_ctx* ctx, const float* x, int rows, float* y) {
+  if (!ctx || !x || !y || rows < 1 || rows > (1 << 20)) return PMC_E_INVALID;
+  if (!ctx->surr_trained || !ctx->d_swb.p) return fail(ctx, PMC_E_INVALID, "no network loaded");
+  cudaSetDevice(ctx->opt.device);
+  cudaStream_t s = ctx->stream;
+  DevBuf X, Y, E;
+  int rc;
+  if ((rc = dalloc(ctx, X, static_cast<size_t>(rows) * kSurrIn * 4))) return rc;
+  if ((rc = dalloc(ctx, Y, static_cast<size_t>(rows) * kSurrOut * 4))) return rc;
+  if ((rc = dalloc(ctx, E, sizeof(int)))) return rc;
+  CK(cudaMemcpyAsync(X.p, x, static_cast<size_t>(rows) * kSurrIn * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(E.p, 0, sizeof(int), s));
+  CK(launch_mlp_rows(rows, static_cast<const float*>(X.p), ctx->d_swb.p, static_cast<const float*>(ctx->d_sp.p),
+                     static_cast<float*>(Y.p), static_cast<int*>(E.p), ctx->n_sm, s));
+  int err = 0;
+  CK(cudaMemcpyAsync(y, Y.p, static_cast<size_t>(rows) * kSurrOut * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&err, E.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (DevBuf* b : {&X, &Y, &E}) dfree(ctx, *b);
+  if (err) return fail(ctx, PMC_E_TIMEOUT, "a tensor-core wait timed out");
   return PMC_OK;
 }
 

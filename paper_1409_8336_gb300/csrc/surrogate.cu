@@ -281,183 +281,281 @@ __device__ void emit_event(const Particle& ev, const float* y1, const float* y2,
   }
 }
 
-// Fused inference: one block takes 64 rows at a time (persistent over the
-// device-resident row count), keeps their activations in shared memory as BF16
-// through all five layers, and streams the layers' BF16 weights in 64x64
-// chunks by cp.async (global -> shared, bypassing L1) through three buffers:
-// the copies of the next two chunks, across layer boundaries, are in flight
-// while the tensor cores consume the current one (FP32 accumulation).
-// Two launches per generation replace ten layer GEMMs and their activations in
-// global memory.
-constexpr int kActLd = kSurrHidden + 8;          // padded row (conflict-free fragment loads)
-constexpr int kChunk = 64;                       // k-chunk of streamed weights
-constexpr int kWLd = kChunk + 8;                 // 144-byte rows, 16-byte aligned
-constexpr int kWStages = 3;                      // weight-chunk buffers
-constexpr int kInferSmem = 2 * 64 * kActLd * 2 + kWStages * 64 * kWLd * 2;
+// ---------------------------------------------------------------------------
+// 5th-generation tensor cores (tcgen05): the network of the event stage on 128-row tiles.
+// Operands live in shared memory in the canonical K-major layout without swizzle: "core
+// matrices" of 8 rows x 16 bytes (8 BF16 along K), contiguous (128 B); the two core matrices
+// of a 16-wide K slice sit 128 B apart (leading byte offset) and successive 8-row groups
+// 256 B apart (stride byte offset), so one K slice of 128 rows is 4 KB.  One thread issues
+// the MMAs (D[128 x N] += A[128 x 16] B[16 x N], BF16 in, FP32 accumulate in tensor memory);
+// their completion is signalled on an mbarrier, and the epilogue reads the accumulator back
+// with tcgen05.ld (warp w owns accumulator rows 32w..32w+31).
+// ---------------------------------------------------------------------------
+namespace tc {
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_newest_pending() {
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+__device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// Shared-memory matrix descriptor: start address, leading / stride byte offsets (all >> 4),
+// descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (static_cast<uint64_t>(1) << 46);
 }
 
-// Position of the weight-chunk stream: layer l, chunk c of that layer (n-tile c / kpn,
-// k-chunk c % kpn), and the layer's offset in the parameter vector.
-struct ChunkCursor {
-  int l = 0, c = 0;
-  size_t off = 0;
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N.
+__device__ __forceinline__ uint32_t idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id, bool accumulate) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+               ::"r"(tmem), "l"(a), "l"(b), "r"(id), "r"(accumulate ? 1 : 0));
+}
+
+__device__ __forceinline__ void commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// Waits for the mbarrier phase with the given parity; false after kSpin polls (the caller
+// reports the error and stops issuing work).
+constexpr int kSpin = 1 << 22;
+__device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < kSpin && !done; ++it)
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+  return done != 0;
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's row.
+__device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offsets in the canonical layout: activation (row r, column k) of the 128-row tile, and
+// weight (output n, chunk column kl) of a chunk of kKC columns for N outputs.
+constexpr int kRows = 128, kKC = 32;
+__device__ __forceinline__ uint32_t act_off(int r, int k) {
+  return (k >> 4) * 4096 + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+__device__ __forceinline__ uint32_t w_off(int n, int kl, int N) {
+  return (kl >> 4) * (N * 32) + (n >> 3) * 256 + ((kl >> 3) & 1) * 128 + (n & 7) * 16 + (kl & 7) * 2;
+}
+
+constexpr int kActBytes = 16 * 4096;                 // 128 rows x 256 BF16
+constexpr int kWBytes = kSurrHidden * kKC * 2;       // one weight chunk: 256 outputs x 32 columns
+constexpr int kTmemCols = kSurrHidden;               // the widest accumulator: 128 x 256 FP32
+
+// Starts the copies of weight chunk c (columns c*kKC..) of a layer with din inputs and N outputs.
+__device__ __forceinline__ void load_chunk(const __nv_bfloat16* __restrict__ W, int din, int N, int c,
+                                           unsigned char* dst) {
+  for (int u = threadIdx.x; u < N * (kKC / 8); u += blockDim.x) {
+    const int n = u / (kKC / 8), kl = (u % (kKC / 8)) * 8;
+    const uint32_t d = saddr(dst + w_off(n, kl, N));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(W + static_cast<size_t>(n) * din + c * kKC + kl)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Pipeline state kept across passes: the two mbarriers' phase parities.
+struct Pipe {
+  uint32_t tmem, mbar0, mbar1, phase;   // phase bit b: parity of mbarrier b's next completion
+  bool ok;
+  // Called by every thread in uniform control flow; the outcome is made warp-uniform (the
+  // epilogue's tcgen05.ld is warp-collective), and once a wait has failed no more are made.
+  __device__ __forceinline__ void wait_buf(int b) {
+    const bool r = ok && wait(b ? mbar1 : mbar0, (phase >> b) & 1u);
+    phase ^= 1u << b;
+    ok = __all_sync(0xffffffffu, r);
+  }
 };
-__device__ __forceinline__ int layer_in(int l) { return l == 0 ? kSurrIn : kSurrHidden; }
-__device__ __forceinline__ int layer_out(int l) { return l == kSurrLayers - 1 ? kSurrOut : kSurrHidden; }
-__device__ __forceinline__ int layer_kc(int l) { return layer_in(l) < kChunk ? layer_in(l) : kChunk; }
-__device__ __forceinline__ int layer_chunks(int l) { return (layer_out(l) + 63) / 64 * (layer_in(l) / layer_kc(l)); }
 
-// Starts the copies of the cursor's chunk into buf (nothing past the last layer); rows of a
-// chunk beyond the layer's outputs are zero-filled.
-__device__ __forceinline__ void issue_chunk(const ChunkCursor& f, const __nv_bfloat16* __restrict__ Wb,
-                                            __nv_bfloat16* buf) {
-  if (f.l >= kSurrLayers) return;
-  const int din = layer_in(f.l), dout = layer_out(f.l), kc = layer_kc(f.l), kpn = din / kc;
-  const int n0 = (f.c / kpn) * 64, k0 = (f.c % kpn) * kc, vpr = kc / 8;
-  const __nv_bfloat16* W = Wb + f.off;
-  for (int v = threadIdx.x; v < 64 * vpr; v += blockDim.x) {
-    const int nn = v / vpr, kv = (v % vpr) * 8;
-    __nv_bfloat16* dst = buf + nn * kWLd + kv;
-    if (n0 + nn < dout) cp_async16(dst, W + static_cast<size_t>(n0 + nn) * din + k0 + kv);
-    else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
-  }
-}
-
-__device__ __forceinline__ void advance_chunk(ChunkCursor& f) {
-  if (f.l >= kSurrLayers) return;
-  if (++f.c == layer_chunks(f.l)) {
-    f.off += static_cast<size_t>(layer_in(f.l)) * layer_out(f.l) + layer_out(f.l);
-    ++f.l;
-    f.c = 0;
-  }
-}
-
-// The five layers on one 64-row tile whose inputs are in the first activation buffer (columns
-// 0..kSurrIn-1); the last layer's outputs for rows < nvalid go to out[r * kSurrOut + n].
-__device__ __forceinline__ void mlp_tile(__nv_bfloat16* const tile, const __nv_bfloat16* __restrict__ Wb,
-                         const float* __restrict__ P, float* out, int nvalid) {
-  // shared memory of the tile: two activation buffers [64][kActLd], then kWStages weight
-  // buffers [64][kWLd] (addressed arithmetically: no local-memory pointer arrays)
-  __nv_bfloat16* const wbuf0 = tile + 2 * 64 * kActLd;
-  auto wbuf = [&](int i) { return wbuf0 + i * (64 * kWLd); };
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  // prologue: the first two chunks in flight (one commit group per chunk, empty past the end)
-  ChunkCursor f;
-  issue_chunk(f, Wb, wbuf(0));
-  cp_async_commit();
-  advance_chunk(f);
-  issue_chunk(f, Wb, wbuf(1));
-  cp_async_commit();
-  advance_chunk(f);
+// One pass of the network over the tile: inputs in act columns 0..kSurrIn-1; each thread's
+// row of the last layer (bias added) goes to out[threadIdx.x * kSurrOut + n].  The weight
+// chunks stream through two buffers: chunk q+1 is copied while the MMAs of chunk q run, after
+// the MMAs of chunk q-1 (which read that buffer) have completed.
+__device__ void mlp_pass(unsigned char* act, unsigned char* wb0, unsigned char* wb1, Pipe& pp,
+                         const __nv_bfloat16* __restrict__ Wb, const float* __restrict__ P, float* out) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t trow = pp.tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  load_chunk(Wb, kSurrIn, kSurrHidden, 0, wb0);
   size_t off = 0;
-  int cur = 0, q = 0;
+  int q = 0;
+  bool prev_waited = true;
 #pragma unroll 1
   for (int l = 0; l < kSurrLayers; ++l) {
-    const int din = layer_in(l), dout = layer_out(l), kc = layer_kc(l), kpn = din / kc;
-    const float* bias = P + off + static_cast<size_t>(din) * dout;
-    const __nv_bfloat16* ain = tile + cur * (64 * kActLd);
-    __nv_bfloat16* aout = tile + (cur ^ 1) * (64 * kActLd);
-    const int n_chunks = layer_chunks(l);
-    float acc[2][4][4];
+    const int din = l == 0 ? kSurrIn : kSurrHidden;
+    const int N = l == kSurrLayers - 1 ? kSurrOut : kSurrHidden;
+    const int nc = din / kKC;
+    const uint32_t id = idesc(kRows, N);
+    const float* __restrict__ bias = P + off + static_cast<size_t>(din) * N;
 #pragma unroll 1
-    for (int c = 0; c < n_chunks; ++c, ++q) {
-      const int n0 = (c / kpn) * 64, k0 = (c % kpn) * kc;
-      cp_async_wait_newest_pending();   // this thread's copies of chunk q have landed
-      __syncthreads();                  // everyone's have; chunk q-1 and the last epilogue are done
-      issue_chunk(f, Wb, wbuf((q + 2) % kWStages));
-      cp_async_commit();
-      advance_chunk(f);
-      if (c % kpn == 0) {
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+    for (int c = 0; c < nc; ++c, ++q) {
+      const int b = q & 1;
+      if (!prev_waited) pp.wait_buf(b ^ 1);               // MMAs of chunk q-1 done: its buffer is free
+      asm volatile("cp.async.wait_all;" ::: "memory");    // this thread's copies of chunk q landed
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();                                    // everyone's copies, and the last epilogue
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // the next chunk: of this layer, else the next layer's first
+      if (c + 1 < nc) {
+        load_chunk(Wb + off, din, N, c + 1, b ? wb0 : wb1);
+      } else if (l + 1 < kSurrLayers) {
+        const size_t off2 = off + static_cast<size_t>(din) * N + N;
+        load_chunk(Wb + off2, kSurrHidden, l + 1 == kSurrLayers - 1 ? kSurrOut : kSurrHidden, 0, b ? wb0 : wb1);
       }
-      const __nv_bfloat16* Ws = wbuf(q % kWStages);
-      for (int kk = 0; kk < kc; kk += 16) {
-        unsigned af[2][4], bfr[4][2];
+      const unsigned char* wbuf = b ? wb1 : wb0;
+      if (tid == 0 && pp.ok) {
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const __nv_bfloat16* a0 = ain + (wm + 16 * i + g) * kActLd + k0 + kk + 2 * t;
-          af[i][0] = *reinterpret_cast<const unsigned*>(a0);
-          af[i][1] = *reinterpret_cast<const unsigned*>(a0 + 8 * kActLd);
-          af[i][2] = *reinterpret_cast<const unsigned*>(a0 + 8);
-          af[i][3] = *reinterpret_cast<const unsigned*>(a0 + 8 * kActLd + 8);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const __nv_bfloat16* b0 = Ws + (wn + 8 * j + g) * kWLd + kk + 2 * t;
-          bfr[j][0] = *reinterpret_cast<const unsigned*>(b0);
-          bfr[j][1] = *reinterpret_cast<const unsigned*>(b0 + 8);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
+        for (int s = 0; s < kKC / 16; ++s)
+          mma(pp.tmem, desc(saddr(act + (c * (kKC / 16) + s) * 4096), 128, 256), desc(saddr(wbuf + s * (N * 32)), 128, 256),
+              id, c > 0 || s > 0);
+        commit(b ? pp.mbar1 : pp.mbar0);
       }
-      if (c % kpn == kpn - 1) {                            // n-tile complete: epilogue
+      prev_waited = false;
+      if (c + 1 == nc) {                                  // layer complete: epilogue
+        pp.wait_buf(b);
+        prev_waited = true;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!pp.ok) continue;
+        if (l + 1 < kSurrLayers) {
+#pragma unroll 1
+          for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            ld16(trow + c0, v);
+            uint32_t h[8];
 #pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r4 = 0; r4 < 4; ++r4) {
-              const int r = wm + 16 * i + g + (r4 >= 2 ? 8 : 0);
-              const int n = n0 + wn + 8 * j + 2 * t + (r4 & 1);
-              if (n >= dout) continue;
-              const float v = acc[i][j][r4] + bias[n];
-              if (l < kSurrLayers - 1) {
-                aout[r * kActLd + n] = __float2bfloat16_rn(fmaxf(v, 0.0f));
-              } else if (r < nvalid) {
-                out[r * kSurrOut + n] = v;
-              }
+            for (int i = 0; i < 8; ++i) {
+              const __nv_bfloat162 t2 = __floats2bfloat162_rn(fmaxf(v[2 * i] + __ldg(bias + c0 + 2 * i), 0.0f),
+                                                              fmaxf(v[2 * i + 1] + __ldg(bias + c0 + 2 * i + 1), 0.0f));
+              h[i] = *reinterpret_cast<const uint32_t*>(&t2);
             }
+            *reinterpret_cast<uint4*>(act + act_off(tid, c0)) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(act + act_off(tid, c0 + 8)) = make_uint4(h[4], h[5], h[6], h[7]);
+          }
+        } else {
+          float v[16];
+          ld16(trow, v);
+#pragma unroll
+          for (int i = 0; i < kSurrOut; ++i) out[tid * kSurrOut + i] = v[i] + __ldg(bias + i);
+        }
       }
     }
-    off += static_cast<size_t>(din) * dout + dout;
-    cur ^= 1;
+    off += static_cast<size_t>(din) * N + N;
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
 }
 
+// Setup of a block that runs the network on the tensor cores (every thread calls it): two
+// mbarriers and kTmemCols columns of tensor memory, allocated by warp 0.
+__device__ __forceinline__ Pipe begin(unsigned long long* mbar, uint32_t* tslot, int* fail) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar + 1)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *fail = 0;
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)), "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return Pipe{*tslot, saddr(mbar), saddr(mbar + 1), 0u, true};
+}
 
+// Frees the block's tensor memory (every thread calls it, after its last tcgen05.ld).
+__device__ __forceinline__ void end(const Pipe& pp) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(pp.tmem), "r"(kTmemCols));
+}
 
-// Rows X[n][kSurrIn] -> outputs Y[n][kSurrOut] (persistent over 64-row tiles).
-__global__ void __launch_bounds__(128, 2) mlp_infer_kernel(const unsigned* n_rows, unsigned cap, const float* __restrict__ X,
-                                                        const __nv_bfloat16* __restrict__ Wb,
-                                                        const float* __restrict__ P, float* __restrict__ Y) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __nv_bfloat16* const tile = reinterpret_cast<__nv_bfloat16*>(smem);   // act[0] = tile
-  const unsigned rows = min(*n_rows, cap);
-  for (unsigned r0 = blockIdx.x * 64u; r0 < rows; r0 += gridDim.x * 64u) {
-    for (int e = threadIdx.x; e < 64 * kSurrIn; e += 128) {
-      const int r = e / kSurrIn, c = e % kSurrIn;
-      tile[r * kActLd + c] = __float2bfloat16_rn(r0 + r < rows ? X[static_cast<size_t>(r0 + r) * kSurrIn + c] : 0.0f);
+// This thread's row of the layer-0 operand from FP32 inputs (BF16, canonical layout).
+__device__ __forceinline__ void put_row(unsigned char* act, const float* x) {
+#pragma unroll
+  for (int k0 = 0; k0 < kSurrIn; k0 += 8) {
+    uint32_t h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __nv_bfloat162 t2 = __floats2bfloat162_rn(x[k0 + 2 * i], x[k0 + 2 * i + 1]);
+      h[i] = *reinterpret_cast<const uint32_t*>(&t2);
     }
-    mlp_tile(tile, Wb, P, Y + static_cast<size_t>(r0) * kSurrOut, static_cast<int>(min(64u, rows - r0)));
-    __syncthreads();
+    *reinterpret_cast<uint4*>(act + act_off(threadIdx.x, k0)) = make_uint4(h[0], h[1], h[2], h[3]);
   }
 }
 
-// The event stage of a generation with the learned stand-in, fused: per tile of 64
-// queued events, build the inference rows, run the network (multiplicity pass),
-// condition on the sampled multiplicity, run it again and emit the events, with rows
-// and outputs in shared memory throughout.
-constexpr int kEventSmem = kInferSmem + 64 * kSurrIn * 4 + 2 * 64 * kSurrOut * 4;
+// Shared memory of a network block: operands aligned to 1 KB, then the buffers after them.
+struct Smem {
+  unsigned char *act, *wb0, *wb1;
+  float* rest;
+};
+__device__ __forceinline__ Smem carve(unsigned char* smem) {
+  Smem m;
+  m.act = smem + ((1024u - (saddr(smem) & 1023u)) & 1023u);
+  m.wb0 = m.act + kActBytes;
+  m.wb1 = m.wb0 + kWBytes;
+  m.rest = reinterpret_cast<float*>(m.wb1 + kWBytes);
+  return m;
+}
+constexpr int kBaseSmem = 1024 + kActBytes + 2 * kWBytes;
 
-__global__ void __launch_bounds__(128, 2) surrogate_event_kernel(const unsigned* n_ev, unsigned cap,
+}  // namespace tc
+
+// The network over rows X[n][kSurrIn] -> Y[n][kSurrOut] (persistent over 128-row tiles); a
+// tensor-core wait that timed out raises *err.
+constexpr int kRowsSmem = tc::kBaseSmem + tc::kRows * kSurrOut * 4 + 64;
+__global__ void __launch_bounds__(128, 1) mlp_rows_kernel(int rows, const float* __restrict__ X,
+                                                         const __nv_bfloat16* __restrict__ Wb,
+                                                         const float* __restrict__ P, float* __restrict__ Y, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const tc::Smem m = tc::carve(smem);
+  float* yb = m.rest;                                         // [128][kSurrOut]
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(yb + tc::kRows * kSurrOut);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  int* fail = reinterpret_cast<int*>(tslot + 1);
+  const int tid = threadIdx.x;
+  if (rows <= static_cast<int>(blockIdx.x) * tc::kRows) return;   // uniform: no tensor memory taken
+  tc::Pipe pp = tc::begin(mbar, tslot, fail);
+  for (int r0 = blockIdx.x * tc::kRows; r0 < rows; r0 += gridDim.x * tc::kRows) {
+    const int nvalid = min(tc::kRows, rows - r0);
+    float x[kSurrIn];
+#pragma unroll
+    for (int j = 0; j < kSurrIn; ++j) x[j] = tid < nvalid ? X[static_cast<size_t>(r0 + tid) * kSurrIn + j] : 0.0f;
+    tc::put_row(m.act, x);
+    tc::mlp_pass(m.act, m.wb0, m.wb1, pp, Wb, P, yb);
+    if (!pp.ok) atomicOr(fail, 1);
+    __syncthreads();
+    if (*fail) break;
+    if (tid < nvalid)
+      for (int j = 0; j < kSurrOut; ++j) Y[static_cast<size_t>(r0 + tid) * kSurrOut + j] = yb[tid * kSurrOut + j];
+  }
+  if (tid == 0 && *fail) atomicAdd(err, 1);
+  tc::end(pp);
+}
+
+// The event stage of a generation with the learned stand-in, fused: per tile of 128 queued
+// events (one per thread), build the inference rows, run the network on the tensor cores
+// (multiplicity pass), condition on the sampled multiplicity, run it again and emit the
+// events, with rows, activations and outputs in shared memory throughout.
+constexpr int kEventSmem = tc::kBaseSmem + tc::kRows * kSurrIn * 4 + 2 * tc::kRows * kSurrOut * 4 + 64;
+static_assert(kSurrIn % tc::kKC == 0 && kSurrHidden % tc::kKC == 0, "weight chunks tile the inputs");
+static_assert(tc::kRows * kSurrHidden * 2 == tc::kActBytes, "activation tile");
+
+__global__ void __launch_bounds__(128, 1) surrogate_event_kernel(const unsigned* n_ev, unsigned cap,
                                                               const Particle* __restrict__ qne, const int* nuc_slot,
                                                               const unsigned long long* seedp,
                                                               const __nv_bfloat16* __restrict__ Wb,
@@ -466,56 +564,57 @@ __global__ void __launch_bounds__(128, 2) surrogate_event_kernel(const unsigned*
                                                               unsigned qsec_cap, Counters* cnt, long long* hist,
                                                               unsigned long long hist_n) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __nv_bfloat16* const tile = reinterpret_cast<__nv_bfloat16*>(smem);   // act[0] = tile
-  float* xin = reinterpret_cast<float*>(smem + kInferSmem);   // [64][kSurrIn]
-  float* y1 = xin + 64 * kSurrIn;                              // [64][kSurrOut]
-  float* y2 = y1 + 64 * kSurrOut;
+  const tc::Smem m = tc::carve(smem);
+  float* xin = m.rest;                                        // [128][kSurrIn]
+  float* y1 = xin + tc::kRows * kSurrIn;                      // [128][kSurrOut]
+  float* y2 = y1 + tc::kRows * kSurrOut;
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(y2 + tc::kRows * kSurrOut);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  int* fail = reinterpret_cast<int*>(tslot + 1);
+  const int tid = threadIdx.x;
   const unsigned rows = min(*n_ev, cap);
+  if (rows <= static_cast<unsigned>(blockIdx.x) * tc::kRows) return;   // uniform: no tensor memory taken
+  tc::Pipe pp = tc::begin(mbar, tslot, fail);
   const unsigned long long seed = *seedp;
   const uint2 key = make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32));
-  const int tid = threadIdx.x;
   long long dep = 0, esc = 0;
   unsigned long long sec = 0, dropped = 0;
-  for (unsigned r0 = blockIdx.x * 64u; r0 < rows; r0 += gridDim.x * 64u) {
-    const int nvalid = static_cast<int>(min(64u, rows - r0));
-    if (tid < 64) {
-      float* x = xin + tid * kSurrIn;
-      if (tid < nvalid) {
-        event_row(qne[r0 + tid], nuc_slot, key, x);
-      } else {
-        for (int j = 0; j < kSurrIn; ++j) x[j] = 0.0f;
-      }
+  float* x = xin + tid * kSurrIn;
+  for (unsigned r0 = blockIdx.x * tc::kRows; r0 < rows; r0 += gridDim.x * tc::kRows) {
+    const int nvalid = static_cast<int>(min(static_cast<unsigned>(tc::kRows), rows - r0));
+    if (tid < nvalid) {
+      event_row(qne[r0 + tid], nuc_slot, key, x);
+    } else {
+      for (int j = 0; j < kSurrIn; ++j) x[j] = 0.0f;
     }
-    __syncthreads();
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
-      for (int e = tid; e < 64 * kSurrIn; e += 128) {
-        const int r = e / kSurrIn, c = e % kSurrIn;
-        tile[r * kActLd + c] = __float2bfloat16_rn(xin[r * kSurrIn + c]);
-      }
-      mlp_tile(tile, Wb, P, pass == 0 ? y1 : y2, nvalid);
-      __syncthreads();
+      tc::put_row(m.act, x);
+      tc::mlp_pass(m.act, m.wb0, m.wb1, pp, Wb, P, pass == 0 ? y1 : y2);
       if (pass == 0 && tid < nvalid)
-        xin[tid * kSurrIn + 1 + kSurrTargets] = static_cast<float>(multiplicity(y1[tid * kSurrOut])) / kSurrSlots;
-      __syncthreads();
+        x[1 + kSurrTargets] = static_cast<float>(multiplicity(y1[tid * kSurrOut])) / kSurrSlots;
     }
+    if (!pp.ok) atomicOr(fail, 1);
+    __syncthreads();
+    if (*fail) break;                                   // a tensor-core wait timed out: stop
     if (tid < nvalid)
       emit_event(qne[r0 + tid], y1 + tid * kSurrOut, y2 + tid * kSurrOut, key, tally, B, qsec, qsec_count, qsec_cap,
                  hist, hist_n, dep, esc, sec, dropped);
-    __syncthreads();
   }
-  auto wsum = [](unsigned long long x) {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
+  auto wsum = [](unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
   };
   const unsigned long long d = wsum(static_cast<unsigned long long>(dep)), e = wsum(static_cast<unsigned long long>(esc));
-  const unsigned long long s = wsum(sec), dr = wsum(dropped);
-  if ((threadIdx.x & 31) == 0) {
+  const unsigned long long s2 = wsum(sec), dr = wsum(dropped);
+  if ((tid & 31) == 0) {
     if (d) atomicAdd(&cnt->deposited, d);
     if (e) atomicAdd(&cnt->escaped, e);
-    if (s) atomicAdd(&cnt->secondaries, s);
+    if (s2) atomicAdd(&cnt->secondaries, s2);
     if (dr) atomicAdd(&cnt->dropped, dr);
   }
+  if (tid == 0 && *fail) atomicAdd(&cnt->errors, 1ull);
+  tc::end(pp);
 }
 
 __global__ void to_bf16_kernel(int n, const float* a, __nv_bfloat16* b) {
@@ -525,15 +624,16 @@ __global__ void to_bf16_kernel(int n, const float* a, __nv_bfloat16* b) {
 
 }  // namespace
 
-cudaError_t launch_mlp_infer(const unsigned* n_rows, unsigned cap, const float* X, const void* Wb, const float* P,
-                             float* Y, int grid, cudaStream_t s) {
+cudaError_t launch_mlp_rows(int rows, const float* X, const void* Wb, const float* P, float* Y, int* err, int n_sm,
+                            cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kInferSmem);
+    cudaError_t e = cudaFuncSetAttribute(mlp_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowsSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  mlp_infer_kernel<<<grid, 128, kInferSmem, s>>>(n_rows, cap, X, static_cast<const __nv_bfloat16*>(Wb), P, Y);
+  const int grid = min(n_sm, (rows + tc::kRows - 1) / tc::kRows);
+  mlp_rows_kernel<<<grid, tc::kRows, kRowsSmem, s>>>(rows, X, static_cast<const __nv_bfloat16*>(Wb), P, Y, err);
   return cudaGetLastError();
 }
 
@@ -589,7 +689,7 @@ cudaError_t launch_surrogate_events(const unsigned* n_ev, unsigned cap, const Pa
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  surrogate_event_kernel<<<grid, 128, kEventSmem, s>>>(n_ev, cap, qne, nuc_slot, seed,
+  surrogate_event_kernel<<<grid, tc::kRows, kEventSmem, s>>>(n_ev, cap, qne, nuc_slot, seed,
                                                         static_cast<const __nv_bfloat16*>(Wb), P, tally, B, qsec,
                                                         qsec_count, qsec_cap, cnt, hist, hist_n);
   return cudaGetLastError();

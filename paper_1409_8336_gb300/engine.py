@@ -31,7 +31,7 @@ EXPORTS = [
     "pmc_plans_destroy", "pmc_plans_last_error", "pmc_plans_load_materials", "pmc_plans_load_surrogate",
     "pmc_plans_bytes", "pmc_plans_run",
     "pmc_set_launch", "pmc_autotune", "pmc_transport_noalloc", "pmc_surrogate_dataset", "pmc_train_surrogate",
-    "pmc_surrogate_params", "pmc_surrogate_load", "pmc_surrogate_grad", "pmc_gamma_plan_bytes", "pmc_gamma_plan", "pmc_gamma_device",
+    "pmc_surrogate_params", "pmc_surrogate_load", "pmc_surrogate_grad", "pmc_surrogate_infer", "pmc_gamma_plan_bytes", "pmc_gamma_plan", "pmc_gamma_device",
     "pmc_gamma_index", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables",
     "pmc_debug_inc", "pmc_debug_elastic",
 ]
@@ -154,6 +154,7 @@ def lib(path: str = LIB_PATH):
             L.pmc_surrogate_params.argtypes = [vp, pf, C.c_size_t]
             L.pmc_surrogate_load.argtypes = [vp, pf, C.c_size_t]
             L.pmc_surrogate_grad.argtypes = [vp, pf, pf, pf, pf, pf, i, pf, pf, pf]
+            L.pmc_surrogate_infer.argtypes = [vp, pf, i, pf]
             L.pmc_gamma_plan_bytes.argtypes = [d, d, d, d, d, C.POINTER(C.c_size_t)]
             L.pmc_gamma_plan.argtypes = [d, d, d, d, d, vp, C.c_size_t, vp]
             L.pmc_gamma_device.argtypes = [vp, vp, vp, i, i, i, d, d, vp, vp]
@@ -425,6 +426,14 @@ class Engine:
         self._check(self._L.pmc_surrogate_grad(self._ctx, _fp(params), _fp(x), _fp(y), _fp(tau), _fp(mask), rows,
                                                _fp(loss), _fp(grad), _fp(yhat)))
         return float(loss[0]), grad, yhat
+
+    def surrogate_infer(self, x):
+        """The loaded network on the tensor cores (as in the transport's event stage):
+        rows x[n][32] -> outputs [n][16]."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.empty((x.shape[0], 16), dtype=np.float32)
+        self._check(self._L.pmc_surrogate_infer(self._ctx, _fp(x), x.shape[0], _fp(y)))
+        return y
 
     # --- single-routine device checks ------------------------------------
     def debug_tables(self, material, E):

@@ -59,6 +59,31 @@ def test_gradients_match_fp64_reference():
             o += n
 
 
+@pytest.mark.parametrize("rows", [1, 128, 129, 1000, 40_000])
+def test_tensor_core_network_matches_fp64_reference(rows):
+    """The event stage's network on the 5th-generation tensor cores (tcgen05, 128-row tiles,
+    accumulators in tensor memory) against the FP64 reference with the same BF16 roundings of
+    weights and layer inputs: one partial tile, exactly one, one plus one row, a ragged tail,
+    and more tiles than blocks."""
+    from paper_1409_8336_gb300 import Engine
+
+    e = Engine(device=0, n_batches=10)
+    e.load_problem(W.config2())
+    rng = np.random.default_rng(11)
+    p = np.concatenate([np.concatenate([rng.normal(0, np.sqrt(2.0 / mlp.DIMS[i]), mlp.DIMS[i] * mlp.DIMS[i + 1]),
+                                        rng.normal(0, 0.05, mlp.DIMS[i + 1])]) for i in range(5)]).astype(np.float32)
+    e.surrogate_load(p)
+    x = rng.normal(size=(rows, 32)).astype(np.float32)
+    y = e.surrogate_infer(x)
+    e.close()
+    _, ref = mlp.forward(p.astype(np.float64), x.astype(np.float64), round_bf16=True)
+    scale = np.abs(ref).max()
+    err = np.abs(y - ref)
+    assert np.all(np.isfinite(y))
+    assert err.max() <= 2e-2 * scale, err.max() / scale
+    assert np.median(err) <= 2e-3 * scale
+
+
 def test_event_summaries_match_oracle_cascade():
     from paper_1409_8336_gb300 import Engine
 
