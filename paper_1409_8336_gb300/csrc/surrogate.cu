@@ -352,28 +352,50 @@ __device__ __forceinline__ uint32_t w_off(int n, int kl, int N) {
 
 constexpr int kActBytes = 16 * 4096;                 // 128 rows x 256 BF16
 constexpr int kWBytes = kSurrHidden * kKC * 2;       // one weight chunk: 256 outputs x 32 columns
+constexpr int kStages = 4;                           // weight-chunk buffers (three chunks in flight)
 constexpr int kTmemCols = kSurrHidden;               // the widest accumulator: 128 x 256 FP32
 
-// Starts the copies of weight chunk c (columns c*kKC..) of a layer with din inputs and N outputs.
-__device__ __forceinline__ void load_chunk(const __nv_bfloat16* __restrict__ W, int din, int N, int c,
-                                           unsigned char* dst) {
-  for (int u = threadIdx.x; u < N * (kKC / 8); u += blockDim.x) {
-    const int n = u / (kKC / 8), kl = (u % (kKC / 8)) * 8;
-    const uint32_t d = saddr(dst + w_off(n, kl, N));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(W + static_cast<size_t>(n) * din + c * kKC + kl)
-                 : "memory");
+__device__ __forceinline__ int layer_in(int l) { return l == 0 ? kSurrIn : kSurrHidden; }
+__device__ __forceinline__ int layer_out(int l) { return l == kSurrLayers - 1 ? kSurrOut : kSurrHidden; }
+
+// Position in the weight-chunk stream of one pass: layer l, chunk c of it (columns c*kKC..),
+// and the layer's offset in the parameter vector.
+struct Cursor {
+  int l = 0, c = 0;
+  size_t off = 0;
+};
+
+// Starts the copies of the cursor's chunk into dst and advances the cursor; past the last
+// layer it commits an empty group, so that every pipeline step commits exactly one.
+__device__ __forceinline__ void load_next(Cursor& f, const __nv_bfloat16* __restrict__ Wb, unsigned char* dst) {
+  if (f.l < kSurrLayers) {
+    const int din = layer_in(f.l), N = layer_out(f.l);
+    const __nv_bfloat16* W = Wb + f.off;
+    for (int u = threadIdx.x; u < N * (kKC / 8); u += blockDim.x) {
+      const int n = u / (kKC / 8), kl = (u % (kKC / 8)) * 8;
+      const uint32_t d = saddr(dst + w_off(n, kl, N));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d),
+                   "l"(W + static_cast<size_t>(n) * din + f.c * kKC + kl)
+                   : "memory");
+    }
+    if (++f.c == din / kKC) {
+      f.off += static_cast<size_t>(din) * N + N;
+      ++f.l;
+      f.c = 0;
+    }
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Pipeline state kept across passes: the two mbarriers' phase parities.
+// Pipeline state kept across passes: one mbarrier per weight buffer (at mbar + 8 b) and their
+// phase parities.
 struct Pipe {
-  uint32_t tmem, mbar0, mbar1, phase;   // phase bit b: parity of mbarrier b's next completion
+  uint32_t tmem, mbar, phase;   // phase bit b: parity of mbarrier b's next completion
   bool ok;
   // Called by every thread in uniform control flow; the outcome is made warp-uniform (the
   // epilogue's tcgen05.ld is warp-collective), and once a wait has failed no more are made.
   __device__ __forceinline__ void wait_buf(int b) {
-    const bool r = ok && wait(b ? mbar1 : mbar0, (phase >> b) & 1u);
+    const bool r = ok && wait(mbar + 8u * b, (phase >> b) & 1u);
     phase ^= 1u << b;
     ok = __all_sync(0xffffffffu, r);
   }
@@ -381,13 +403,15 @@ struct Pipe {
 
 // One pass of the network over the tile: inputs in act columns 0..kSurrIn-1; each thread's
 // row of the last layer (bias added) goes to out[threadIdx.x * kSurrOut + n].  The weight
-// chunks stream through two buffers: chunk q+1 is copied while the MMAs of chunk q run, after
-// the MMAs of chunk q-1 (which read that buffer) have completed.
-__device__ void mlp_pass(unsigned char* act, unsigned char* wb0, unsigned char* wb1, Pipe& pp,
-                         const __nv_bfloat16* __restrict__ Wb, const float* __restrict__ P, float* out) {
+// chunks stream through kStages buffers: chunks q+1..q+3 are in flight while the MMAs of chunk
+// q run; chunk q+3 goes into the buffer of chunk q-1 once the MMAs that read it completed.
+__device__ void mlp_pass(unsigned char* act, unsigned char* wb, Pipe& pp, const __nv_bfloat16* __restrict__ Wb,
+                         const float* __restrict__ P, float* out) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t trow = pp.tmem + (static_cast<uint32_t>(warp * 32) << 16);
-  load_chunk(Wb, kSurrIn, kSurrHidden, 0, wb0);
+  Cursor f;
+#pragma unroll
+  for (int i = 0; i < kStages - 1; ++i) load_next(f, Wb, wb + i * kWBytes);
   size_t off = 0;
   int q = 0;
   bool prev_waited = true;
@@ -400,27 +424,21 @@ __device__ void mlp_pass(unsigned char* act, unsigned char* wb0, unsigned char* 
     const float* __restrict__ bias = P + off + static_cast<size_t>(din) * N;
 #pragma unroll 1
     for (int c = 0; c < nc; ++c, ++q) {
-      const int b = q & 1;
-      if (!prev_waited) pp.wait_buf(b ^ 1);               // MMAs of chunk q-1 done: its buffer is free
-      asm volatile("cp.async.wait_all;" ::: "memory");    // this thread's copies of chunk q landed
+      const int b = q % kStages;
+      if (!prev_waited) pp.wait_buf((q + kStages - 1) % kStages);   // MMAs of chunk q-1 done
+      asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 2) : "memory");   // own copies of chunk q landed
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();                                    // everyone's copies, and the last epilogue
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // the next chunk: of this layer, else the next layer's first
-      if (c + 1 < nc) {
-        load_chunk(Wb + off, din, N, c + 1, b ? wb0 : wb1);
-      } else if (l + 1 < kSurrLayers) {
-        const size_t off2 = off + static_cast<size_t>(din) * N + N;
-        load_chunk(Wb + off2, kSurrHidden, l + 1 == kSurrLayers - 1 ? kSurrOut : kSurrHidden, 0, b ? wb0 : wb1);
-      }
-      const unsigned char* wbuf = b ? wb1 : wb0;
+      load_next(f, Wb, wb + ((q + kStages - 1) % kStages) * kWBytes);   // chunk q+3, into chunk q-1's buffer
+      const unsigned char* wbuf = wb + b * kWBytes;
       if (tid == 0 && pp.ok) {
 #pragma unroll
         for (int s = 0; s < kKC / 16; ++s)
           mma(pp.tmem, desc(saddr(act + (c * (kKC / 16) + s) * 4096), 128, 256), desc(saddr(wbuf + s * (N * 32)), 128, 256),
               id, c > 0 || s > 0);
-        commit(b ? pp.mbar1 : pp.mbar0);
+        commit(pp.mbar + 8u * b);
       }
       prev_waited = false;
       if (c + 1 == nc) {                                  // layer complete: epilogue
@@ -457,12 +475,11 @@ __device__ void mlp_pass(unsigned char* act, unsigned char* wb0, unsigned char* 
   __syncthreads();
 }
 
-// Setup of a block that runs the network on the tensor cores (every thread calls it): two
+// Setup of a block that runs the network on the tensor cores (every thread calls it): kStages
 // mbarriers and kTmemCols columns of tensor memory, allocated by warp 0.
 __device__ __forceinline__ Pipe begin(unsigned long long* mbar, uint32_t* tslot, int* fail) {
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar + 1)));
+    for (int b = 0; b < kStages; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar + b)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *fail = 0;
   }
@@ -473,7 +490,7 @@ __device__ __forceinline__ Pipe begin(unsigned long long* mbar, uint32_t* tslot,
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  return Pipe{*tslot, saddr(mbar), saddr(mbar + 1), 0u, true};
+  return Pipe{*tslot, saddr(mbar), 0u, true};
 }
 
 // Frees the block's tensor memory (every thread calls it, after its last tcgen05.ld).
@@ -500,24 +517,23 @@ __device__ __forceinline__ void put_row(unsigned char* act, const float* x) {
 
 // Shared memory of a network block: operands aligned to 1 KB, then the buffers after them.
 struct Smem {
-  unsigned char *act, *wb0, *wb1;
+  unsigned char *act, *wb;
   float* rest;
 };
 __device__ __forceinline__ Smem carve(unsigned char* smem) {
   Smem m;
   m.act = smem + ((1024u - (saddr(smem) & 1023u)) & 1023u);
-  m.wb0 = m.act + kActBytes;
-  m.wb1 = m.wb0 + kWBytes;
-  m.rest = reinterpret_cast<float*>(m.wb1 + kWBytes);
+  m.wb = m.act + kActBytes;
+  m.rest = reinterpret_cast<float*>(m.wb + kStages * kWBytes);
   return m;
 }
-constexpr int kBaseSmem = 1024 + kActBytes + 2 * kWBytes;
+constexpr int kBaseSmem = 1024 + kActBytes + kStages * kWBytes;
 
 }  // namespace tc
 
 // The network over rows X[n][kSurrIn] -> Y[n][kSurrOut] (persistent over 128-row tiles); a
 // tensor-core wait that timed out raises *err.
-constexpr int kRowsSmem = tc::kBaseSmem + tc::kRows * kSurrOut * 4 + 64;
+constexpr int kRowsSmem = tc::kBaseSmem + tc::kRows * kSurrOut * 4 + 8 * tc::kStages + 16;
 __global__ void __launch_bounds__(128, 1) mlp_rows_kernel(int rows, const float* __restrict__ X,
                                                          const __nv_bfloat16* __restrict__ Wb,
                                                          const float* __restrict__ P, float* __restrict__ Y, int* err) {
@@ -525,7 +541,7 @@ __global__ void __launch_bounds__(128, 1) mlp_rows_kernel(int rows, const float*
   const tc::Smem m = tc::carve(smem);
   float* yb = m.rest;                                         // [128][kSurrOut]
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(yb + tc::kRows * kSurrOut);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + tc::kStages);
   int* fail = reinterpret_cast<int*>(tslot + 1);
   const int tid = threadIdx.x;
   if (rows <= static_cast<int>(blockIdx.x) * tc::kRows) return;   // uniform: no tensor memory taken
@@ -536,7 +552,7 @@ __global__ void __launch_bounds__(128, 1) mlp_rows_kernel(int rows, const float*
 #pragma unroll
     for (int j = 0; j < kSurrIn; ++j) x[j] = tid < nvalid ? X[static_cast<size_t>(r0 + tid) * kSurrIn + j] : 0.0f;
     tc::put_row(m.act, x);
-    tc::mlp_pass(m.act, m.wb0, m.wb1, pp, Wb, P, yb);
+    tc::mlp_pass(m.act, m.wb, pp, Wb, P, yb);
     if (!pp.ok) atomicOr(fail, 1);
     __syncthreads();
     if (*fail) break;
@@ -551,7 +567,7 @@ __global__ void __launch_bounds__(128, 1) mlp_rows_kernel(int rows, const float*
 // events (one per thread), build the inference rows, run the network on the tensor cores
 // (multiplicity pass), condition on the sampled multiplicity, run it again and emit the
 // events, with rows, activations and outputs in shared memory throughout.
-constexpr int kEventSmem = tc::kBaseSmem + tc::kRows * kSurrIn * 4 + 2 * tc::kRows * kSurrOut * 4 + 64;
+constexpr int kEventSmem = tc::kBaseSmem + tc::kRows * kSurrIn * 4 + 2 * tc::kRows * kSurrOut * 4 + 8 * tc::kStages + 16;
 static_assert(kSurrIn % tc::kKC == 0 && kSurrHidden % tc::kKC == 0, "weight chunks tile the inputs");
 static_assert(tc::kRows * kSurrHidden * 2 == tc::kActBytes, "activation tile");
 
@@ -569,7 +585,7 @@ __global__ void __launch_bounds__(128, 1) surrogate_event_kernel(const unsigned*
   float* y1 = xin + tc::kRows * kSurrIn;                      // [128][kSurrOut]
   float* y2 = y1 + tc::kRows * kSurrOut;
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(y2 + tc::kRows * kSurrOut);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + tc::kStages);
   int* fail = reinterpret_cast<int*>(tslot + 1);
   const int tid = threadIdx.x;
   const unsigned rows = min(*n_ev, cap);
@@ -590,7 +606,7 @@ __global__ void __launch_bounds__(128, 1) surrogate_event_kernel(const unsigned*
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
       tc::put_row(m.act, x);
-      tc::mlp_pass(m.act, m.wb0, m.wb1, pp, Wb, P, pass == 0 ? y1 : y2);
+      tc::mlp_pass(m.act, m.wb, pp, Wb, P, pass == 0 ? y1 : y2);
       if (pass == 0 && tid < nvalid)
         x[1 + kSurrTargets] = static_cast<float>(multiplicity(y1[tid * kSurrOut])) / kSurrSlots;
     }
