@@ -945,7 +945,7 @@ int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int sour
   if (ctx->mode == PMC_SURROGATE) {
     const float* P = static_cast<const float*>(ctx->d_sp.p);
     const unsigned cap = static_cast<unsigned>(ctx->q_cap);
-    const int grid = ctx->n_sm;       // one block per SM: 132 KB of shared memory, 256 TMEM columns
+    const int grid = ctx->n_sm * 2;   // two blocks per SM: 112 KB of shared memory and 256 TMEM columns each
     if ((rc = mark(ctx, s, 2, true))) return rc;
     CK(launch_surrogate_events(qne_count, cap, qne, static_cast<const int*>(ctx->d_nuc_slot.p), a.seed, ctx->d_swb.p,
                                P, a.tally, a.B, qout, qout_count, cap, a.cnt, a.hist, a.hist_n, grid, s));

@@ -211,13 +211,18 @@ __global__ void train_rows_kernel(int batch, const float* feat, const unsigned* 
 
 // Inference row of a queued event: energy, target one-hot, multiplicity token
 // (-1 in the first pass) and ten uniforms from the event's own stream (tag 8).
-__device__ void event_row(const Particle& ev, const int* nuc_slot, uint2 key, float* x) {
+// (x is the thread's own row, kept in registers: every index below is a compile-time one)
+__device__ __forceinline__ void event_row(const Particle& ev, const int* nuc_slot, uint2 key, float (&x)[kSurrIn]) {
+#pragma unroll
   for (int j = 0; j < kSurrIn; ++j) x[j] = 0.0f;
   x[0] = (ev.E - 130.0f) / 120.0f;
-  x[1 + nuc_slot[ev.target]] = 1.0f;
+  const int slot = nuc_slot[ev.target];
+#pragma unroll
+  for (int j = 0; j < kSurrTargets; ++j) x[1 + j] = j == slot ? 1.0f : 0.0f;
   x[1 + kSurrTargets] = -1.0f;
   const float4 u0 = draw4(key, ev.pid, 0u, 8u), u1 = draw4(key, ev.pid, 1u, 8u), u2 = draw4(key, ev.pid, 2u, 8u);
   const float u[12] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w, u2.x, u2.y, u2.z, u2.w};
+#pragma unroll
   for (int j = 0; j < kSurrTau; ++j) x[2 + kSurrTargets + j] = u[j];
 }
 
@@ -228,7 +233,8 @@ __device__ __forceinline__ int multiplicity(float q) {
 // Emits an event from the network's quantiles: protons to the secondary queue,
 // the local deposit to the event voxel, the rest (neutrons, photons, binding)
 // escapes.  Energy is conserved by construction.
-__device__ void emit_event(const Particle& ev, const float* y1, const float* y2, uint2 key, unsigned long long* tally,
+__device__ void emit_event(const Particle& ev, const float (&y1)[kSurrOut], const float (&y2)[kSurrOut], uint2 key,
+                           unsigned long long* tally,
                            int B, Particle* qsec, unsigned* qsec_count, unsigned qsec_cap, long long* hist,
                            unsigned long long hist_n, long long& dep, long long& esc, unsigned long long& sec,
                            unsigned long long& dropped) {
@@ -352,7 +358,7 @@ __device__ __forceinline__ uint32_t w_off(int n, int kl, int N) {
 
 constexpr int kActBytes = 16 * 4096;                 // 128 rows x 256 BF16
 constexpr int kWBytes = kSurrHidden * kKC * 2;       // one weight chunk: 256 outputs x 32 columns
-constexpr int kStages = 4;                           // weight-chunk buffers (three chunks in flight)
+constexpr int kStages = 3;                           // weight-chunk buffers (two chunks in flight)
 constexpr int kTmemCols = kSurrHidden;               // the widest accumulator: 128 x 256 FP32
 
 __device__ __forceinline__ int layer_in(int l) { return l == 0 ? kSurrIn : kSurrHidden; }
@@ -402,11 +408,13 @@ struct Pipe {
 };
 
 // One pass of the network over the tile: inputs in act columns 0..kSurrIn-1; each thread's
-// row of the last layer (bias added) goes to out[threadIdx.x * kSurrOut + n].  The weight
-// chunks stream through kStages buffers: chunks q+1..q+3 are in flight while the MMAs of chunk
-// q run; chunk q+3 goes into the buffer of chunk q-1 once the MMAs that read it completed.
-__device__ void mlp_pass(unsigned char* act, unsigned char* wb, Pipe& pp, const __nv_bfloat16* __restrict__ Wb,
-                         const float* __restrict__ P, float* out) {
+// row of the last layer (bias added) goes to its registers out[n].  The weight
+// chunks stream through kStages buffers: the next kStages-1 chunks are in flight while the MMAs
+// of chunk q run; chunk q+kStages-1 goes into the buffer of chunk q-1 once the MMAs that read
+// it completed.
+__device__ __forceinline__ void mlp_pass(unsigned char* act, unsigned char* wb, Pipe& pp,
+                                         const __nv_bfloat16* __restrict__ Wb, const float* __restrict__ P,
+                                         float (&out)[kSurrOut]) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t trow = pp.tmem + (static_cast<uint32_t>(warp * 32) << 16);
   Cursor f;
@@ -431,7 +439,7 @@ __device__ void mlp_pass(unsigned char* act, unsigned char* wb, Pipe& pp, const 
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();                                    // everyone's copies, and the last epilogue
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      load_next(f, Wb, wb + ((q + kStages - 1) % kStages) * kWBytes);   // chunk q+3, into chunk q-1's buffer
+      load_next(f, Wb, wb + ((q + kStages - 1) % kStages) * kWBytes);   // into chunk q-1's buffer
       const unsigned char* wbuf = wb + b * kWBytes;
       if (tid == 0 && pp.ok) {
 #pragma unroll
@@ -465,7 +473,7 @@ __device__ void mlp_pass(unsigned char* act, unsigned char* wb, Pipe& pp, const 
           float v[16];
           ld16(trow, v);
 #pragma unroll
-          for (int i = 0; i < kSurrOut; ++i) out[tid * kSurrOut + i] = v[i] + __ldg(bias + i);
+          for (int i = 0; i < kSurrOut; ++i) out[i] = v[i] + __ldg(bias + i);
         }
       }
     }
@@ -502,7 +510,7 @@ __device__ __forceinline__ void end(const Pipe& pp) {
 }
 
 // This thread's row of the layer-0 operand from FP32 inputs (BF16, canonical layout).
-__device__ __forceinline__ void put_row(unsigned char* act, const float* x) {
+__device__ __forceinline__ void put_row(unsigned char* act, const float (&x)[kSurrIn]) {
 #pragma unroll
   for (int k0 = 0; k0 < kSurrIn; k0 += 8) {
     uint32_t h[4];
@@ -515,51 +523,54 @@ __device__ __forceinline__ void put_row(unsigned char* act, const float* x) {
   }
 }
 
-// Shared memory of a network block: operands aligned to 1 KB, then the buffers after them.
+// Shared memory of a network block (the descriptors need 16-byte alignment, which dynamic
+// shared memory has): activations, the weight buffers, kStages mbarriers, the tensor-memory
+// address and a failure flag.  112 KB: two blocks per SM, each with 256 TMEM columns.
 struct Smem {
   unsigned char *act, *wb;
-  float* rest;
+  unsigned long long* mbar;
+  uint32_t* tslot;
+  int* fail;
 };
 __device__ __forceinline__ Smem carve(unsigned char* smem) {
   Smem m;
-  m.act = smem + ((1024u - (saddr(smem) & 1023u)) & 1023u);
+  m.act = smem;
   m.wb = m.act + kActBytes;
-  m.rest = reinterpret_cast<float*>(m.wb + kStages * kWBytes);
+  m.mbar = reinterpret_cast<unsigned long long*>(m.wb + kStages * kWBytes);
+  m.tslot = reinterpret_cast<uint32_t*>(m.mbar + kStages);
+  m.fail = reinterpret_cast<int*>(m.tslot + 1);
   return m;
 }
-constexpr int kBaseSmem = 1024 + kActBytes + kStages * kWBytes;
+constexpr int kSmem = kActBytes + kStages * kWBytes + 8 * kStages + 8;
 
 }  // namespace tc
 
 // The network over rows X[n][kSurrIn] -> Y[n][kSurrOut] (persistent over 128-row tiles); a
 // tensor-core wait that timed out raises *err.
-constexpr int kRowsSmem = tc::kBaseSmem + tc::kRows * kSurrOut * 4 + 8 * tc::kStages + 16;
-__global__ void __launch_bounds__(128, 1) mlp_rows_kernel(int rows, const float* __restrict__ X,
+__global__ void __launch_bounds__(128, 2) mlp_rows_kernel(int rows, const float* __restrict__ X,
                                                          const __nv_bfloat16* __restrict__ Wb,
                                                          const float* __restrict__ P, float* __restrict__ Y, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   const tc::Smem m = tc::carve(smem);
-  float* yb = m.rest;                                         // [128][kSurrOut]
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(yb + tc::kRows * kSurrOut);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + tc::kStages);
-  int* fail = reinterpret_cast<int*>(tslot + 1);
   const int tid = threadIdx.x;
   if (rows <= static_cast<int>(blockIdx.x) * tc::kRows) return;   // uniform: no tensor memory taken
-  tc::Pipe pp = tc::begin(mbar, tslot, fail);
+  tc::Pipe pp = tc::begin(m.mbar, m.tslot, m.fail);
   for (int r0 = blockIdx.x * tc::kRows; r0 < rows; r0 += gridDim.x * tc::kRows) {
     const int nvalid = min(tc::kRows, rows - r0);
-    float x[kSurrIn];
+    float x[kSurrIn], y[kSurrOut];
 #pragma unroll
     for (int j = 0; j < kSurrIn; ++j) x[j] = tid < nvalid ? X[static_cast<size_t>(r0 + tid) * kSurrIn + j] : 0.0f;
     tc::put_row(m.act, x);
-    tc::mlp_pass(m.act, m.wb, pp, Wb, P, yb);
-    if (!pp.ok) atomicOr(fail, 1);
+    tc::mlp_pass(m.act, m.wb, pp, Wb, P, y);
+    if (!pp.ok) atomicOr(m.fail, 1);
     __syncthreads();
-    if (*fail) break;
-    if (tid < nvalid)
-      for (int j = 0; j < kSurrOut; ++j) Y[static_cast<size_t>(r0 + tid) * kSurrOut + j] = yb[tid * kSurrOut + j];
+    if (*m.fail) break;
+    if (tid < nvalid) {
+#pragma unroll
+      for (int j = 0; j < kSurrOut; ++j) Y[static_cast<size_t>(r0 + tid) * kSurrOut + j] = y[j];
+    }
   }
-  if (tid == 0 && *fail) atomicAdd(err, 1);
+  if (tid == 0 && *m.fail) atomicAdd(err, 1);
   tc::end(pp);
 }
 
@@ -567,11 +578,7 @@ __global__ void __launch_bounds__(128, 1) mlp_rows_kernel(int rows, const float*
 // events (one per thread), build the inference rows, run the network on the tensor cores
 // (multiplicity pass), condition on the sampled multiplicity, run it again and emit the
 // events, with rows, activations and outputs in shared memory throughout.
-constexpr int kEventSmem = tc::kBaseSmem + tc::kRows * kSurrIn * 4 + 2 * tc::kRows * kSurrOut * 4 + 8 * tc::kStages + 16;
-static_assert(kSurrIn % tc::kKC == 0 && kSurrHidden % tc::kKC == 0, "weight chunks tile the inputs");
-static_assert(tc::kRows * kSurrHidden * 2 == tc::kActBytes, "activation tile");
-
-__global__ void __launch_bounds__(128, 1) surrogate_event_kernel(const unsigned* n_ev, unsigned cap,
+__global__ void __launch_bounds__(128, 2) surrogate_event_kernel(const unsigned* n_ev, unsigned cap,
                                                               const Particle* __restrict__ qne, const int* nuc_slot,
                                                               const unsigned long long* seedp,
                                                               const __nv_bfloat16* __restrict__ Wb,
@@ -581,41 +588,34 @@ __global__ void __launch_bounds__(128, 1) surrogate_event_kernel(const unsigned*
                                                               unsigned long long hist_n) {
   extern __shared__ __align__(16) unsigned char smem[];
   const tc::Smem m = tc::carve(smem);
-  float* xin = m.rest;                                        // [128][kSurrIn]
-  float* y1 = xin + tc::kRows * kSurrIn;                      // [128][kSurrOut]
-  float* y2 = y1 + tc::kRows * kSurrOut;
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(y2 + tc::kRows * kSurrOut);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + tc::kStages);
-  int* fail = reinterpret_cast<int*>(tslot + 1);
   const int tid = threadIdx.x;
   const unsigned rows = min(*n_ev, cap);
   if (rows <= static_cast<unsigned>(blockIdx.x) * tc::kRows) return;   // uniform: no tensor memory taken
-  tc::Pipe pp = tc::begin(mbar, tslot, fail);
+  tc::Pipe pp = tc::begin(m.mbar, m.tslot, m.fail);
   const unsigned long long seed = *seedp;
   const uint2 key = make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32));
   long long dep = 0, esc = 0;
   unsigned long long sec = 0, dropped = 0;
-  float* x = xin + tid * kSurrIn;
   for (unsigned r0 = blockIdx.x * tc::kRows; r0 < rows; r0 += gridDim.x * tc::kRows) {
     const int nvalid = static_cast<int>(min(static_cast<unsigned>(tc::kRows), rows - r0));
+    float x[kSurrIn], y1[kSurrOut], y2[kSurrOut];
     if (tid < nvalid) {
       event_row(qne[r0 + tid], nuc_slot, key, x);
     } else {
+#pragma unroll
       for (int j = 0; j < kSurrIn; ++j) x[j] = 0.0f;
     }
-#pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
-      tc::put_row(m.act, x);
-      tc::mlp_pass(m.act, m.wb, pp, Wb, P, pass == 0 ? y1 : y2);
-      if (pass == 0 && tid < nvalid)
-        x[1 + kSurrTargets] = static_cast<float>(multiplicity(y1[tid * kSurrOut])) / kSurrSlots;
-    }
-    if (!pp.ok) atomicOr(fail, 1);
+    tc::put_row(m.act, x);
+    tc::mlp_pass(m.act, m.wb, pp, Wb, P, y1);         // multiplicity pass
+    x[1 + kSurrTargets] = static_cast<float>(multiplicity(y1[0])) / kSurrSlots;
+    tc::put_row(m.act, x);
+    tc::mlp_pass(m.act, m.wb, pp, Wb, P, y2);         // conditioned on the sampled multiplicity
+    if (!pp.ok) atomicOr(m.fail, 1);
     __syncthreads();
-    if (*fail) break;                                   // a tensor-core wait timed out: stop
+    if (*m.fail) break;                               // a tensor-core wait timed out: stop
     if (tid < nvalid)
-      emit_event(qne[r0 + tid], y1 + tid * kSurrOut, y2 + tid * kSurrOut, key, tally, B, qsec, qsec_count, qsec_cap,
-                 hist, hist_n, dep, esc, sec, dropped);
+      emit_event(qne[r0 + tid], y1, y2, key, tally, B, qsec, qsec_count, qsec_cap, hist, hist_n, dep, esc, sec,
+                 dropped);
   }
   auto wsum = [](unsigned long long v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(128, 1) surrogate_event_kernel(const unsigned*
     if (s2) atomicAdd(&cnt->secondaries, s2);
     if (dr) atomicAdd(&cnt->dropped, dr);
   }
-  if (tid == 0 && *fail) atomicAdd(&cnt->errors, 1ull);
+  if (tid == 0 && *m.fail) atomicAdd(&cnt->errors, 1ull);
   tc::end(pp);
 }
 
@@ -644,12 +644,12 @@ cudaError_t launch_mlp_rows(int rows, const float* X, const void* Wb, const floa
                             cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowsSmem);
+    cudaError_t e = cudaFuncSetAttribute(mlp_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int grid = min(n_sm, (rows + tc::kRows - 1) / tc::kRows);
-  mlp_rows_kernel<<<grid, tc::kRows, kRowsSmem, s>>>(rows, X, static_cast<const __nv_bfloat16*>(Wb), P, Y, err);
+  const int grid = min(2 * n_sm, (rows + tc::kRows - 1) / tc::kRows);
+  mlp_rows_kernel<<<grid, tc::kRows, tc::kSmem, s>>>(rows, X, static_cast<const __nv_bfloat16*>(Wb), P, Y, err);
   return cudaGetLastError();
 }
 
@@ -701,11 +701,11 @@ cudaError_t launch_surrogate_events(const unsigned* n_ev, unsigned cap, const Pa
                                     int grid, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(surrogate_event_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kEventSmem);
+    cudaError_t e = cudaFuncSetAttribute(surrogate_event_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  surrogate_event_kernel<<<grid, tc::kRows, kEventSmem, s>>>(n_ev, cap, qne, nuc_slot, seed,
+  surrogate_event_kernel<<<grid, tc::kRows, tc::kSmem, s>>>(n_ev, cap, qne, nuc_slot, seed,
                                                         static_cast<const __nv_bfloat16*>(Wb), P, tally, B, qsec,
                                                         qsec_count, qsec_cap, cnt, hist, hist_n);
   return cudaGetLastError();
