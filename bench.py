@@ -53,7 +53,7 @@ L2_BYTES = 129 * 2 ** 20
 # (1e6 histories in one launch: 47.9 MB), valid only for the kernel sources it was taken
 # on (their SHA-256 below); otherwise the roofline's traffic is reported as null.
 TRAFFIC = {"bytes_per_history": 47.8, "sources": ("transport.cu", "pmc_device.cuh", "pmc_kernels.cuh"),
-           "sha256": "335bc99199f9e20732b24dd65a89e1e3d434bf34c5f43aa4b1e6670a70a0e305"}
+           "sha256": "c83c9f581ecfb10a605cc641ce3c7e6beee7ce8da4986707267e3ba02039235e"}
 
 
 def parse():
