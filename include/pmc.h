@@ -392,6 +392,11 @@ int pmc_debug_tables(pmc_ctx* ctx, int material, const double* E, double* r_out,
 int pmc_debug_inc(pmc_ctx* ctx, int nuclide, double E, uint64_t seed, uint64_t pid0, int n,
                   double* summary, double* products, int cap);
 int pmc_debug_elastic(pmc_ctx* ctx, int nuclide, double E, const double* u, double* out, int n);
+/* pmc_debug_surrogate_waits: runs the tensor-core network on one 128-row tile with its MMAs
+ * withheld and short mbarrier waits, so that every wait runs out: returns PMC_E_TIMEOUT
+ * (the block stops, frees its tensor memory and reports), and the context stays usable.
+ * PMC_E_INVALID without a loaded network. */
+int pmc_debug_surrogate_waits(pmc_ctx* ctx);
 
 #ifdef __cplusplus
 }

@@ -1869,8 +1869,8 @@ int pmc_surrogate_grad(pmc_ctx* ctx, const float* params, const float* x, const 
   return PMC_OK;
 }
 
-int pmc_surrogate_infer(pmc_ctx* ctx, const float* x, int rows, float* y) {
-  if (!ctx || !x || !y || rows < 1 || rows > (1 << 20)) return PMC_E_INVALID;
+namespace {
+int surrogate_rows(pmc_ctx* ctx, const float* x, int rows, float* y, bool check_waits) {
   if (!ctx->surr_trained || !ctx->d_swb.p) return fail(ctx, PMC_E_INVALID, "no network loaded");
   cudaSetDevice(ctx->opt.device);
   cudaStream_t s = ctx->stream;
@@ -1882,7 +1882,7 @@ int pmc_surrogate_infer(pmc_ctx* ctx, const float* x, int rows, float* y) {
   CK(cudaMemcpyAsync(X.p, x, static_cast<size_t>(rows) * kSurrIn * 4, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(E.p, 0, sizeof(int), s));
   CK(launch_mlp_rows(rows, static_cast<const float*>(X.p), ctx->d_swb.p, static_cast<const float*>(ctx->d_sp.p),
-                     static_cast<float*>(Y.p), static_cast<int*>(E.p), ctx->n_sm, s));
+                     static_cast<float*>(Y.p), static_cast<int*>(E.p), ctx->n_sm, check_waits, s));
   int err = 0;
   CK(cudaMemcpyAsync(y, Y.p, static_cast<size_t>(rows) * kSurrOut * 4, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&err, E.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1890,6 +1890,18 @@ int pmc_surrogate_infer(pmc_ctx* ctx, const float* x, int rows, float* y) {
   for (DevBuf* b : {&X, &Y, &E}) dfree(ctx, *b);
   if (err) return fail(ctx, PMC_E_TIMEOUT, "a tensor-core wait timed out");
   return PMC_OK;
+}
+}  // namespace
+
+int pmc_surrogate_infer(pmc_ctx* ctx, const float* x, int rows, float* y) {
+  if (!ctx || !x || !y || rows < 1 || rows > (1 << 20)) return PMC_E_INVALID;
+  return surrogate_rows(ctx, x, rows, y, false);
+}
+
+int pmc_debug_surrogate_waits(pmc_ctx* ctx) {
+  if (!ctx) return PMC_E_INVALID;
+  std::vector<float> x(128 * kSurrIn, 0.0f), y(128 * kSurrOut);
+  return surrogate_rows(ctx, x.data(), 128, y.data(), true);
 }
 
 }  // extern "C"

@@ -117,7 +117,7 @@ cudaError_t launch_gemm(int M, const unsigned* Mp, int N, int K, const float* A,
                         const float* B, long long sbk, long long sbn, float* C, long long ldc, const float* bias,
                         bool relu, const float* mask, bool accumulate, cudaStream_t s);
 cudaError_t launch_mlp_rows(int rows, const float* X, const void* Wb, const float* P, float* Y, int* err, int n_sm,
-                            cudaStream_t s);
+                            bool check_waits, cudaStream_t s);
 cudaError_t launch_to_bf16(int n, const float* a, void* b, cudaStream_t s);
 cudaError_t launch_pinball(int rows, const float* yhat, const float* y, const float* tau, const float* mask,
                            float* grad, float* loss, cudaStream_t s);

@@ -323,12 +323,12 @@ __device__ __forceinline__ void commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-// Waits for the mbarrier phase with the given parity; false after kSpin polls (the caller
+// Waits for the mbarrier phase with the given parity; false after `spin` polls (the caller
 // reports the error and stops issuing work).
 constexpr int kSpin = 1 << 22;
-__device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity, int spin) {
   uint32_t done = 0;
-  for (int it = 0; it < kSpin && !done; ++it)
+  for (int it = 0; it < spin && !done; ++it)
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
                  : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
   return done != 0;
@@ -398,10 +398,12 @@ __device__ __forceinline__ void load_next(Cursor& f, const __nv_bfloat16* __rest
 struct Pipe {
   uint32_t tmem, mbar, phase;   // phase bit b: parity of mbarrier b's next completion
   bool ok;
+  bool issue;                   // false only in the wait check: no MMA is issued, so waits run out
+  int spin;                     // polls per wait
   // Called by every thread in uniform control flow; the outcome is made warp-uniform (the
   // epilogue's tcgen05.ld is warp-collective), and once a wait has failed no more are made.
   __device__ __forceinline__ void wait_buf(int b) {
-    const bool r = ok && wait(mbar + 8u * b, (phase >> b) & 1u);
+    const bool r = ok && wait(mbar + 8u * b, (phase >> b) & 1u, spin);
     phase ^= 1u << b;
     ok = __all_sync(0xffffffffu, r);
   }
@@ -441,7 +443,7 @@ __device__ __forceinline__ void mlp_pass(unsigned char* act, unsigned char* wb, 
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       load_next(f, Wb, wb + ((q + kStages - 1) % kStages) * kWBytes);   // into chunk q-1's buffer
       const unsigned char* wbuf = wb + b * kWBytes;
-      if (tid == 0 && pp.ok) {
+      if (tid == 0 && pp.ok && pp.issue) {
 #pragma unroll
         for (int s = 0; s < kKC / 16; ++s)
           mma(pp.tmem, desc(saddr(act + (c * (kKC / 16) + s) * 4096), 128, 256), desc(saddr(wbuf + s * (N * 32)), 128, 256),
@@ -485,7 +487,8 @@ __device__ __forceinline__ void mlp_pass(unsigned char* act, unsigned char* wb, 
 
 // Setup of a block that runs the network on the tensor cores (every thread calls it): kStages
 // mbarriers and kTmemCols columns of tensor memory, allocated by warp 0.
-__device__ __forceinline__ Pipe begin(unsigned long long* mbar, uint32_t* tslot, int* fail) {
+__device__ __forceinline__ Pipe begin(unsigned long long* mbar, uint32_t* tslot, int* fail, bool issue = true,
+                                      int spin = kSpin) {
   if (threadIdx.x == 0) {
     for (int b = 0; b < kStages; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar + b)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -498,11 +501,13 @@ __device__ __forceinline__ Pipe begin(unsigned long long* mbar, uint32_t* tslot,
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  return Pipe{*tslot, saddr(mbar), 0u, true};
+  return Pipe{*tslot, saddr(mbar), 0u, true, issue, spin};
 }
 
-// Frees the block's tensor memory (every thread calls it, after its last tcgen05.ld).
+// Frees the block's tensor memory (every thread calls it, after its last tcgen05.ld), with no
+// copy of its own still in flight.
 __device__ __forceinline__ void end(const Pipe& pp) {
+  asm volatile("cp.async.wait_all;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if ((threadIdx.x >> 5) == 0)
@@ -546,15 +551,17 @@ constexpr int kSmem = kActBytes + kStages * kWBytes + 8 * kStages + 8;
 }  // namespace tc
 
 // The network over rows X[n][kSurrIn] -> Y[n][kSurrOut] (persistent over 128-row tiles); a
-// tensor-core wait that timed out raises *err.
+// tensor-core wait that timed out raises *err.  With check_waits the MMAs are withheld and the
+// waits poll briefly: they run out, which exercises the error path (nothing is in flight).
 __global__ void __launch_bounds__(128, 2) mlp_rows_kernel(int rows, const float* __restrict__ X,
                                                          const __nv_bfloat16* __restrict__ Wb,
-                                                         const float* __restrict__ P, float* __restrict__ Y, int* err) {
+                                                         const float* __restrict__ P, float* __restrict__ Y, int* err,
+                                                         int check_waits) {
   extern __shared__ __align__(16) unsigned char smem[];
   const tc::Smem m = tc::carve(smem);
   const int tid = threadIdx.x;
   if (rows <= static_cast<int>(blockIdx.x) * tc::kRows) return;   // uniform: no tensor memory taken
-  tc::Pipe pp = tc::begin(m.mbar, m.tslot, m.fail);
+  tc::Pipe pp = tc::begin(m.mbar, m.tslot, m.fail, !check_waits, check_waits ? 256 : tc::kSpin);
   for (int r0 = blockIdx.x * tc::kRows; r0 < rows; r0 += gridDim.x * tc::kRows) {
     const int nvalid = min(tc::kRows, rows - r0);
     float x[kSurrIn], y[kSurrOut];
@@ -641,7 +648,7 @@ __global__ void to_bf16_kernel(int n, const float* a, __nv_bfloat16* b) {
 }  // namespace
 
 cudaError_t launch_mlp_rows(int rows, const float* X, const void* Wb, const float* P, float* Y, int* err, int n_sm,
-                            cudaStream_t s) {
+                            bool check_waits, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(mlp_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem);
@@ -649,7 +656,8 @@ cudaError_t launch_mlp_rows(int rows, const float* X, const void* Wb, const floa
     attr = true;
   }
   const int grid = min(2 * n_sm, (rows + tc::kRows - 1) / tc::kRows);
-  mlp_rows_kernel<<<grid, tc::kRows, tc::kSmem, s>>>(rows, X, static_cast<const __nv_bfloat16*>(Wb), P, Y, err);
+  mlp_rows_kernel<<<grid, tc::kRows, tc::kSmem, s>>>(rows, X, static_cast<const __nv_bfloat16*>(Wb), P, Y, err,
+                                                     check_waits ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@ EXPORTS = [
     "pmc_set_launch", "pmc_autotune", "pmc_transport_noalloc", "pmc_surrogate_dataset", "pmc_train_surrogate",
     "pmc_surrogate_params", "pmc_surrogate_load", "pmc_surrogate_grad", "pmc_surrogate_infer", "pmc_gamma_plan_bytes", "pmc_gamma_plan", "pmc_gamma_device",
     "pmc_gamma_index", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables",
-    "pmc_debug_inc", "pmc_debug_elastic",
+    "pmc_debug_inc", "pmc_debug_elastic", "pmc_debug_surrogate_waits",
 ]
 
 AllocFn = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -155,6 +155,7 @@ def lib(path: str = LIB_PATH):
             L.pmc_surrogate_load.argtypes = [vp, pf, C.c_size_t]
             L.pmc_surrogate_grad.argtypes = [vp, pf, pf, pf, pf, pf, i, pf, pf, pf]
             L.pmc_surrogate_infer.argtypes = [vp, pf, i, pf]
+            L.pmc_debug_surrogate_waits.argtypes = [vp]
             L.pmc_gamma_plan_bytes.argtypes = [d, d, d, d, d, C.POINTER(C.c_size_t)]
             L.pmc_gamma_plan.argtypes = [d, d, d, d, d, vp, C.c_size_t, vp]
             L.pmc_gamma_device.argtypes = [vp, vp, vp, i, i, i, d, d, vp, vp]
@@ -436,6 +437,11 @@ class Engine:
         return y
 
     # --- single-routine device checks ------------------------------------
+    def debug_surrogate_waits(self):
+        """Runs the tensor-core network with its MMAs withheld so every wait runs out;
+        returns the library's status (PMC_E_TIMEOUT expected)."""
+        return int(self._L.pmc_debug_surrogate_waits(self._ctx))
+
     def debug_tables(self, material, E):
         E = np.ascontiguousarray(E, dtype=np.float64)
         r, e = np.empty_like(E), np.empty_like(E)

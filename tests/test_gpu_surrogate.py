@@ -84,6 +84,26 @@ def test_tensor_core_network_matches_fp64_reference(rows):
     assert np.median(err) <= 2e-3 * scale
 
 
+def test_tensor_core_waits_are_bounded_and_the_context_recovers():
+    """With the MMAs withheld every mbarrier wait of the pipeline runs out: the call returns
+    PMC_E_TIMEOUT instead of hanging, and the same context then computes correctly."""
+    from paper_1409_8336_gb300 import Engine
+    from paper_1409_8336_gb300.engine import ERRORS
+
+    e = Engine(device=0, n_batches=10)
+    e.load_problem(W.config2())
+    rng = np.random.default_rng(12)
+    p = np.concatenate([np.concatenate([rng.normal(0, np.sqrt(2.0 / mlp.DIMS[i]), mlp.DIMS[i] * mlp.DIMS[i + 1]),
+                                        rng.normal(0, 0.05, mlp.DIMS[i + 1])]) for i in range(5)]).astype(np.float32)
+    e.surrogate_load(p)
+    assert ERRORS[e.debug_surrogate_waits()] == "PMC_E_TIMEOUT"
+    x = rng.normal(size=(300, 32)).astype(np.float32)
+    y = e.surrogate_infer(x)
+    e.close()
+    _, ref = mlp.forward(p.astype(np.float64), x.astype(np.float64), round_bf16=True)
+    assert np.abs(y - ref).max() <= 2e-2 * np.abs(ref).max()
+
+
 def test_event_summaries_match_oracle_cascade():
     from paper_1409_8336_gb300 import Engine
 
