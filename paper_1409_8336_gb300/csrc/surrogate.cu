@@ -10,9 +10,12 @@
 // with the token "unknown" for the multiplicity, then with the sampled
 // multiplicity for the rest.
 //
-// Dense layers run on the tensor cores: BF16 operands (weights and activations
-// rounded from FP32 master copies when a tile is staged in shared memory), FP32
-// accumulation, with the warp-level mma.sync m16n8k16 instruction.
+// Dense layers run on the tensor cores with BF16 operands and FP32 accumulation.
+// Inference (the event stage inside the transport, and pmc_surrogate_infer) uses
+// the 5th-generation tcgen05 MMAs with accumulators in tensor memory (namespace
+// tc below); training uses a generic strided GEMM on the warp-level mma.sync
+// m16n8k16 instruction (weights and activations rounded from FP32 master copies
+// when a tile is staged in shared memory).
 #include <cuda_bf16.h>
 
 #include "pmc_kernels.cuh"
