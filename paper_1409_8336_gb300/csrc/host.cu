@@ -341,7 +341,7 @@ struct pmc_ctx {
   bool surr_trained = false;
   int n_slots = 0;                      // non-elastic target slots (nuclides with A >= 2, in order)
   DevBuf d_sp, d_sg, d_sm, d_sv;        // parameters, gradients, Adam moments
-  DevBuf d_swb;                         // BF16 copy of the parameters for inference
+  DevBuf d_swb;                         // BF16 inference weights, packed in streaming order
   DevBuf d_slot_nuc, d_nuc_slot;        // slot -> nuclide, nuclide -> slot
   DevBuf d_rec[2];               // residual nuclei between cascade and evaporation, per stream
   size_t surr_cap = 0;
@@ -1788,8 +1788,8 @@ int pmc_train_surrogate(pmc_ctx* ctx, const pmc_train_opts* o, pmc_train_result*
     CK(cudaGetLastError());
     for (DevBuf* b : {&feat, &perm, &X, &Y, &T, &M, &g0, &g1, &loss}) dfree(ctx, *b);
     for (int l = 0; l <= kSurrLayers; ++l) dfree(ctx, act[l]);
-    if ((rc = dalloc(ctx, ctx->d_swb, kSurrParams * 2))) return rc;
-    CK(launch_to_bf16(static_cast<int>(kSurrParams), P, ctx->d_swb.p, s));
+    if ((rc = dalloc(ctx, ctx->d_swb, packed_weight_bytes()))) return rc;
+    CK(launch_pack_weights(P, ctx->d_swb.p, s));
     CK(cudaStreamSynchronize(s));
     ctx->surr_trained = true;
     if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
@@ -1820,8 +1820,8 @@ int pmc_surrogate_load(pmc_ctx* ctx, const float* params, size_t n) {
   if ((rc = surrogate_ready(ctx))) return rc;
   cudaSetDevice(ctx->opt.device);
   CK(cudaMemcpy(ctx->d_sp.p, params, n * sizeof(float), cudaMemcpyHostToDevice));
-  if ((rc = dalloc(ctx, ctx->d_swb, kSurrParams * 2))) return rc;
-  CK(launch_to_bf16(static_cast<int>(kSurrParams), static_cast<const float*>(ctx->d_sp.p), ctx->d_swb.p, ctx->stream));
+  if ((rc = dalloc(ctx, ctx->d_swb, packed_weight_bytes()))) return rc;
+  CK(launch_pack_weights(static_cast<const float*>(ctx->d_sp.p), ctx->d_swb.p, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->surr_trained = true;
   if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }

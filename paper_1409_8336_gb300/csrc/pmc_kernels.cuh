@@ -118,7 +118,9 @@ cudaError_t launch_gemm(int M, const unsigned* Mp, int N, int K, const float* A,
                         bool relu, const float* mask, bool accumulate, cudaStream_t s);
 cudaError_t launch_mlp_rows(int rows, const float* X, const void* Wb, const float* P, float* Y, int* err, int n_sm,
                             bool check_waits, cudaStream_t s);
-cudaError_t launch_to_bf16(int n, const float* a, void* b, cudaStream_t s);
+// The inference weights: BF16, each streamed chunk in the byte order of its shared-memory buffer.
+size_t packed_weight_bytes();
+cudaError_t launch_pack_weights(const float* P, void* packed, cudaStream_t s);
 cudaError_t launch_pinball(int rows, const float* yhat, const float* y, const float* tau, const float* mask,
                            float* grad, float* loss, cudaStream_t s);
 cudaError_t launch_colsum(int rows, int N, const float* G, float* db, cudaStream_t s);

@@ -367,133 +367,152 @@ constexpr int kTmemCols = kSurrHidden;               // the widest accumulator: 
 __device__ __forceinline__ int layer_in(int l) { return l == 0 ? kSurrIn : kSurrHidden; }
 __device__ __forceinline__ int layer_out(int l) { return l == kSurrLayers - 1 ? kSurrOut : kSurrHidden; }
 
-// Position in the weight-chunk stream of one pass: layer l, chunk c of it (columns c*kKC..),
-// and the layer's offset in the parameter vector.
-struct Cursor {
-  int l = 0, c = 0;
-  size_t off = 0;
-};
-
-// Starts the copies of the cursor's chunk into dst and advances the cursor; past the last
-// layer it commits an empty group, so that every pipeline step commits exactly one.
-__device__ __forceinline__ void load_next(Cursor& f, const __nv_bfloat16* __restrict__ Wb, unsigned char* dst) {
-  if (f.l < kSurrLayers) {
-    const int din = layer_in(f.l), N = layer_out(f.l);
-    const __nv_bfloat16* W = Wb + f.off;
-    for (int u = threadIdx.x; u < N * (kKC / 8); u += blockDim.x) {
-      const int n = u / (kKC / 8), kl = (u % (kKC / 8)) * 8;
-      const uint32_t d = saddr(dst + w_off(n, kl, N));
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d),
-                   "l"(W + static_cast<size_t>(n) * din + f.c * kKC + kl)
-                   : "memory");
-    }
-    if (++f.c == din / kKC) {
-      f.off += static_cast<size_t>(din) * N + N;
-      ++f.l;
-      f.c = 0;
-    }
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
+// The packed weights: every chunk (layer l, columns c*kKC..c*kKC+kKC-1) stored contiguously in
+// exactly the byte order of its shared-memory buffer (w_off), so that one bulk copy moves it.
+// A pass streams kChunksPerPass chunks: 1 for the first layer, din / kKC for each other.
+constexpr int kChunksPerPass = kSurrIn / kKC + (kSurrLayers - 1) * (kSurrHidden / kKC);
+__host__ __device__ constexpr int layer_in_c(int l) { return l == 0 ? kSurrIn : kSurrHidden; }
+__host__ __device__ constexpr int layer_out_c(int l) { return l == kSurrLayers - 1 ? kSurrOut : kSurrHidden; }
+// Chunk k of the pass -> its layer and column chunk.
+__device__ __forceinline__ void chunk_pos(int k, int& l, int& c) {
+  const int k0 = kSurrIn / kKC;
+  if (k < k0) { l = 0; c = k; return; }
+  l = 1 + (k - k0) / (kSurrHidden / kKC);
+  c = (k - k0) % (kSurrHidden / kKC);
 }
+// Byte offset of chunk (l, c) in the packed weights, and its size.
+__host__ __device__ inline size_t chunk_offset(int l, int c) {
+  size_t o = 0;
+  for (int i = 0; i < l; ++i) o += static_cast<size_t>(layer_in_c(i)) * layer_out_c(i) * 2;
+  return o + static_cast<size_t>(c) * layer_out_c(l) * kKC * 2;
+}
+__host__ __device__ constexpr uint32_t chunk_bytes(int l) { return static_cast<uint32_t>(layer_out_c(l) * kKC * 2); }
 
-// Pipeline state kept across passes: one mbarrier per weight buffer (at mbar + 8 b) and their
-// phase parities.
+// Pipeline state kept across passes.  Barriers at mbar + 8 i: full[b] (i = b: the bulk copy
+// of the chunk in buffer b has landed), empty[b] (i = kStages + b: the MMAs reading buffer b
+// are done), layer (i = 2 kStages: all MMAs of a layer are done).  Thread 0 runs the chunk
+// stream and waits on full and empty; every thread waits on layer.  Each completion of each
+// barrier is waited exactly once, so a parity bit per barrier tracks its phase.
 struct Pipe {
-  uint32_t tmem, mbar, phase;   // phase bit b: parity of mbarrier b's next completion
+  uint32_t tmem, mbar, phase;   // phase bit i: parity of barrier i's next completion
   bool ok;
   bool issue;                   // false only in the wait check: no MMA is issued, so waits run out
   int spin;                     // polls per wait
-  // Called by every thread in uniform control flow; the outcome is made warp-uniform (the
-  // epilogue's tcgen05.ld is warp-collective), and once a wait has failed no more are made.
-  __device__ __forceinline__ void wait_buf(int b) {
-    const bool r = ok && wait(mbar + 8u * b, (phase >> b) & 1u, spin);
-    phase ^= 1u << b;
-    ok = __all_sync(0xffffffffu, r);
+  int issued;                   // thread 0: chunks of the current pass whose copies were started
+  __device__ __forceinline__ uint32_t bar(int i) const { return mbar + 8u * i; }
+  __device__ __forceinline__ bool wait_bar(int i) {
+    const bool r = wait(bar(i), (phase >> i) & 1u, spin);
+    phase ^= 1u << i;
+    return r;
   }
 };
 
-// One pass of the network over the tile: inputs in act columns 0..kSurrIn-1; each thread's
-// row of the last layer (bias added) goes to its registers out[n].  The weight
-// chunks stream through kStages buffers: the next kStages-1 chunks are in flight while the MMAs
-// of chunk q run; chunk q+kStages-1 goes into the buffer of chunk q-1 once the MMAs that read
-// it completed.
+// Thread 0: starts the bulk copy of chunk k of the pass into its buffer.
+__device__ __forceinline__ void issue_copy(Pipe& pp, int k, const unsigned char* __restrict__ packed,
+                                           unsigned char* wb) {
+  int l, c;
+  chunk_pos(k, l, c);
+  const int b = k % kStages;
+  const uint32_t bytes = chunk_bytes(l);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(pp.bar(b)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(saddr(wb + b * kWBytes)), "l"(packed + chunk_offset(l, c)), "r"(bytes), "r"(pp.bar(b))
+               : "memory");
+  pp.issued = k + 1;
+}
+
+// One pass of the network over the tile: inputs in act columns 0..kSurrIn-1 (written by every
+// thread before the call); each thread's row of the last layer (bias added) goes to its
+// registers out[n].  Thread 0 streams the weight chunks by bulk copies kStages deep and issues
+// the MMAs; after issuing chunk q's it refills the buffer of chunk q-1 (whose MMAs have had
+// chunk q's time to finish).  All threads meet at each layer's end for the epilogue.
 __device__ __forceinline__ void mlp_pass(unsigned char* act, unsigned char* wb, Pipe& pp,
-                                         const __nv_bfloat16* __restrict__ Wb, const float* __restrict__ P,
+                                         const unsigned char* __restrict__ packed, const float* __restrict__ P,
                                          float (&out)[kSurrOut]) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t trow = pp.tmem + (static_cast<uint32_t>(warp * 32) << 16);
-  Cursor f;
-#pragma unroll
-  for (int i = 0; i < kStages - 1; ++i) load_next(f, Wb, wb + i * kWBytes);
+  if (tid == 0) {
+    pp.issued = 0;
+    if (pp.ok)
+      for (int k = 0; k < kStages; ++k) issue_copy(pp, k, packed, wb);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the layer-0 operand rows
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   size_t off = 0;
   int q = 0;
-  bool prev_waited = true;
 #pragma unroll 1
   for (int l = 0; l < kSurrLayers; ++l) {
-    const int din = l == 0 ? kSurrIn : kSurrHidden;
-    const int N = l == kSurrLayers - 1 ? kSurrOut : kSurrHidden;
-    const int nc = din / kKC;
-    const uint32_t id = idesc(kRows, N);
+    const int din = layer_in_c(l), N = layer_out_c(l), nc = din / kKC;
     const float* __restrict__ bias = P + off + static_cast<size_t>(din) * N;
+    if (tid == 0) {
+      const uint32_t id = idesc(kRows, N);
 #pragma unroll 1
-    for (int c = 0; c < nc; ++c, ++q) {
-      const int b = q % kStages;
-      if (!prev_waited) pp.wait_buf((q + kStages - 1) % kStages);   // MMAs of chunk q-1 done
-      asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 2) : "memory");   // own copies of chunk q landed
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();                                    // everyone's copies, and the last epilogue
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      load_next(f, Wb, wb + ((q + kStages - 1) % kStages) * kWBytes);   // into chunk q-1's buffer
-      const unsigned char* wbuf = wb + b * kWBytes;
-      if (tid == 0 && pp.ok && pp.issue) {
+      for (int c = 0; c < nc; ++c, ++q) {
+        const int b = q % kStages;
+        if (q < pp.issued) pp.ok = pp.wait_bar(b) && pp.ok;   // the chunk landed (waited even after a failure)
+        if (pp.ok && pp.issue) {
 #pragma unroll
-        for (int s = 0; s < kKC / 16; ++s)
-          mma(pp.tmem, desc(saddr(act + (c * (kKC / 16) + s) * 4096), 128, 256), desc(saddr(wbuf + s * (N * 32)), 128, 256),
-              id, c > 0 || s > 0);
-        commit(pp.mbar + 8u * b);
-      }
-      prev_waited = false;
-      if (c + 1 == nc) {                                  // layer complete: epilogue
-        pp.wait_buf(b);
-        prev_waited = true;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!pp.ok) continue;
-        if (l + 1 < kSurrLayers) {
-#pragma unroll 1
-          for (int c0 = 0; c0 < N; c0 += 16) {
-            float v[16];
-            ld16(trow + c0, v);
-            uint32_t h[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const __nv_bfloat162 t2 = __floats2bfloat162_rn(fmaxf(v[2 * i] + __ldg(bias + c0 + 2 * i), 0.0f),
-                                                              fmaxf(v[2 * i + 1] + __ldg(bias + c0 + 2 * i + 1), 0.0f));
-              h[i] = *reinterpret_cast<const uint32_t*>(&t2);
-            }
-            *reinterpret_cast<uint4*>(act + act_off(tid, c0)) = make_uint4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<uint4*>(act + act_off(tid, c0 + 8)) = make_uint4(h[4], h[5], h[6], h[7]);
-          }
-        } else {
-          float v[16];
-          ld16(trow, v);
-#pragma unroll
-          for (int i = 0; i < kSurrOut; ++i) out[i] = v[i] + __ldg(bias + i);
+          for (int s2 = 0; s2 < kKC / 16; ++s2)
+            mma(pp.tmem, desc(saddr(act + (c * (kKC / 16) + s2) * 4096), 128, 256),
+                desc(saddr(wb + b * kWBytes + s2 * (N * 32)), 128, 256), id, c > 0 || s2 > 0);
+          commit(pp.bar(kStages + b));
+          if (c + 1 == nc) commit(pp.bar(2 * kStages));
+        }
+        // refill the buffer of chunk q-1 with chunk q-1+kStages once its MMAs are done
+        if (pp.ok && q >= 1 && q - 1 + kStages < kChunksPerPass) {
+          pp.ok = pp.wait_bar(kStages + (q - 1) % kStages);
+          if (pp.ok) issue_copy(pp, q - 1 + kStages, packed, wb);
         }
       }
     }
+    // every thread: the layer's MMAs are done (warp-uniform outcome: tcgen05.ld is warp-collective)
+    const bool r = pp.ok && wait(pp.bar(2 * kStages), (pp.phase >> (2 * kStages)) & 1u, pp.spin);
+    pp.phase ^= 1u << (2 * kStages);
+    pp.ok = __all_sync(0xffffffffu, r);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (pp.ok) {
+      if (l + 1 < kSurrLayers) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float v[16];
+          ld16(trow + c0, v);
+          uint32_t h[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const __nv_bfloat162 t2 = __floats2bfloat162_rn(fmaxf(v[2 * i] + __ldg(bias + c0 + 2 * i), 0.0f),
+                                                            fmaxf(v[2 * i + 1] + __ldg(bias + c0 + 2 * i + 1), 0.0f));
+            h[i] = *reinterpret_cast<const uint32_t*>(&t2);
+          }
+          *reinterpret_cast<uint4*>(act + act_off(tid, c0)) = make_uint4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<uint4*>(act + act_off(tid, c0 + 8)) = make_uint4(h[4], h[5], h[6], h[7]);
+        }
+      } else {
+        float v[16];
+        ld16(trow, v);
+#pragma unroll
+        for (int i = 0; i < kSurrOut; ++i) out[i] = v[i] + __ldg(bias + i);
+      }
+    }
     off += static_cast<size_t>(din) * N + N;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the epilogue's operand rows
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
+  // thread 0: the MMA completions of the last chunks, whose buffers were not refilled
+  if (tid == 0 && pp.ok && pp.issue)
+    for (int k = kChunksPerPass - kStages; k < kChunksPerPass; ++k) pp.ok = pp.wait_bar(kStages + k % kStages) && pp.ok;
 }
+static_assert(kChunksPerPass > kStages, "the stream is deeper than the pipeline");
 
-// Setup of a block that runs the network on the tensor cores (every thread calls it): kStages
-// mbarriers and kTmemCols columns of tensor memory, allocated by warp 0.
+// Setup of a block that runs the network on the tensor cores (every thread calls it): 2 kStages
+// + 1 mbarriers and kTmemCols columns of tensor memory, allocated by warp 0.
 __device__ __forceinline__ Pipe begin(unsigned long long* mbar, uint32_t* tslot, int* fail, bool issue = true,
                                       int spin = kSpin) {
   if (threadIdx.x == 0) {
-    for (int b = 0; b < kStages; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar + b)));
+    for (int b = 0; b < 2 * kStages + 1; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar + b)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *fail = 0;
   }
@@ -504,7 +523,7 @@ __device__ __forceinline__ Pipe begin(unsigned long long* mbar, uint32_t* tslot,
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  return Pipe{*tslot, saddr(mbar), 0u, true, issue, spin};
+  return Pipe{*tslot, saddr(mbar), 0u, true, issue, spin, 0};
 }
 
 // Frees the block's tensor memory (every thread calls it, after its last tcgen05.ld), with no
@@ -532,8 +551,9 @@ __device__ __forceinline__ void put_row(unsigned char* act, const float (&x)[kSu
 }
 
 // Shared memory of a network block (the descriptors need 16-byte alignment, which dynamic
-// shared memory has): activations, the weight buffers, kStages mbarriers, the tensor-memory
-// address and a failure flag.  112 KB: two blocks per SM, each with 256 TMEM columns.
+// shared memory has; bulk copies 16-byte addresses and sizes): activations, the weight buffers,
+// 2 kStages + 1 mbarriers, the tensor-memory address and a failure flag.  112 KB: two blocks
+// per SM, each with 256 TMEM columns.
 struct Smem {
   unsigned char *act, *wb;
   unsigned long long* mbar;
@@ -545,11 +565,11 @@ __device__ __forceinline__ Smem carve(unsigned char* smem) {
   m.act = smem;
   m.wb = m.act + kActBytes;
   m.mbar = reinterpret_cast<unsigned long long*>(m.wb + kStages * kWBytes);
-  m.tslot = reinterpret_cast<uint32_t*>(m.mbar + kStages);
+  m.tslot = reinterpret_cast<uint32_t*>(m.mbar + 2 * kStages + 1);
   m.fail = reinterpret_cast<int*>(m.tslot + 1);
   return m;
 }
-constexpr int kSmem = kActBytes + kStages * kWBytes + 8 * kStages + 8;
+constexpr int kSmem = kActBytes + kStages * kWBytes + 8 * (2 * kStages + 1) + 8;
 
 }  // namespace tc
 
@@ -571,7 +591,7 @@ __global__ void __launch_bounds__(128, 2) mlp_rows_kernel(int rows, const float*
 #pragma unroll
     for (int j = 0; j < kSurrIn; ++j) x[j] = tid < nvalid ? X[static_cast<size_t>(r0 + tid) * kSurrIn + j] : 0.0f;
     tc::put_row(m.act, x);
-    tc::mlp_pass(m.act, m.wb, pp, Wb, P, y);
+    tc::mlp_pass(m.act, m.wb, pp, reinterpret_cast<const unsigned char*>(Wb), P, y);
     if (!pp.ok) atomicOr(m.fail, 1);
     __syncthreads();
     if (*m.fail) break;
@@ -616,10 +636,10 @@ __global__ void __launch_bounds__(128, 2) surrogate_event_kernel(const unsigned*
       for (int j = 0; j < kSurrIn; ++j) x[j] = 0.0f;
     }
     tc::put_row(m.act, x);
-    tc::mlp_pass(m.act, m.wb, pp, Wb, P, y1);         // multiplicity pass
+    tc::mlp_pass(m.act, m.wb, pp, reinterpret_cast<const unsigned char*>(Wb), P, y1);   // multiplicity pass
     x[1 + kSurrTargets] = static_cast<float>(multiplicity(y1[0])) / kSurrSlots;
     tc::put_row(m.act, x);
-    tc::mlp_pass(m.act, m.wb, pp, Wb, P, y2);         // conditioned on the sampled multiplicity
+    tc::mlp_pass(m.act, m.wb, pp, reinterpret_cast<const unsigned char*>(Wb), P, y2);   // conditioned on it
     if (!pp.ok) atomicOr(m.fail, 1);
     __syncthreads();
     if (*m.fail) break;                               // a tensor-core wait timed out: stop
@@ -643,9 +663,28 @@ __global__ void __launch_bounds__(128, 2) surrogate_event_kernel(const unsigned*
   tc::end(pp);
 }
 
-__global__ void to_bf16_kernel(int n, const float* a, __nv_bfloat16* b) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = __float2bfloat16_rn(a[i]);
+// The inference weights: BF16 of the FP32 parameters (round to nearest even), each chunk in
+// the byte order of its shared-memory buffer (one 16-byte unit = 8 consecutive columns of one
+// output row per thread).
+__global__ void pack_weights_kernel(const float* __restrict__ P, unsigned char* __restrict__ packed) {
+  int u = blockIdx.x * blockDim.x + threadIdx.x;
+  size_t off = 0;
+  for (int l = 0; l < kSurrLayers; ++l) {
+    const int din = tc::layer_in_c(l), N = tc::layer_out_c(l), units = N * din / 8;
+    if (u < units) {
+      const int n = u / (din / 8), k = (u % (din / 8)) * 8, c = k / tc::kKC, kl = k % tc::kKC;
+      const float* w = P + off + static_cast<size_t>(n) * din + k;
+      uint32_t h[4];
+      for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 t2 = __floats2bfloat162_rn(w[2 * i], w[2 * i + 1]);
+        h[i] = *reinterpret_cast<const uint32_t*>(&t2);
+      }
+      *reinterpret_cast<uint4*>(packed + tc::chunk_offset(l, c) + tc::w_off(n, kl, N)) = make_uint4(h[0], h[1], h[2], h[3]);
+      return;
+    }
+    u -= units;
+    off += static_cast<size_t>(din) * N + N;
+  }
 }
 
 }  // namespace
@@ -664,8 +703,11 @@ cudaError_t launch_mlp_rows(int rows, const float* X, const void* Wb, const floa
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_bf16(int n, const float* a, void* b, cudaStream_t s) {
-  to_bf16_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, a, static_cast<__nv_bfloat16*>(b));
+size_t packed_weight_bytes() { return tc::chunk_offset(kSurrLayers, 0); }
+
+cudaError_t launch_pack_weights(const float* P, void* packed, cudaStream_t s) {
+  const int units = static_cast<int>(packed_weight_bytes() / 16);
+  pack_weights_kernel<<<(units + 255) / 256, 256, 0, s>>>(P, static_cast<unsigned char*>(packed));
   return cudaGetLastError();
 }
 
