@@ -555,7 +555,8 @@ def main():
     kinds, n_kind_steps, per_step_launches = {}, min(args.steps, 10), 0
     for i in range(n_kind_steps):
         _, prof, _, _ = one(rank * 100003 + 50000 + i)
-        per_step_launches = sum(p["launches"] for p in prof.values())
+        # one timing pair spans each cascade launch, which runs two kernels (cascade, evaporation)
+        per_step_launches = sum(p["launches"] * (2 if k == "cascade" else 1) for k, p in prof.items())
         for k, v in prof.items():
             kinds.setdefault(k, [0.0, 0])
             kinds[k][0] += v["ms"] / n_kind_steps
