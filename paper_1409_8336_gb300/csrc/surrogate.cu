@@ -691,12 +691,10 @@ __global__ void pack_weights_kernel(const float* __restrict__ P, unsigned char* 
 
 cudaError_t launch_mlp_rows(int rows, const float* X, const void* Wb, const float* P, float* Y, int* err, int n_sm,
                             bool check_waits, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // set once per process; a function-local static is initialised exactly once even when
+  // several host threads (the multi-plan stream's slots) reach this first
+  static const cudaError_t attr = cudaFuncSetAttribute(mlp_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem);
+  if (attr != cudaSuccess) return attr;
   const int grid = min(2 * n_sm, (rows + tc::kRows - 1) / tc::kRows);
   mlp_rows_kernel<<<grid, tc::kRows, tc::kSmem, s>>>(rows, X, static_cast<const __nv_bfloat16*>(Wb), P, Y, err,
                                                      check_waits ? 1 : 0);
@@ -752,12 +750,10 @@ cudaError_t launch_surrogate_events(const unsigned* n_ev, unsigned cap, const Pa
                                     unsigned long long* tally, int B, Particle* qsec, unsigned* qsec_count,
                                     unsigned qsec_cap, Counters* cnt, long long* hist, unsigned long long hist_n,
                                     int grid, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(surrogate_event_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // set once per process; a function-local static is initialised exactly once even when
+  // several host threads (the multi-plan stream's slots) reach this first
+  static const cudaError_t attr = cudaFuncSetAttribute(surrogate_event_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem);
+  if (attr != cudaSuccess) return attr;
   surrogate_event_kernel<<<grid, tc::kRows, tc::kSmem, s>>>(n_ev, cap, qne, nuc_slot, seed,
                                                         static_cast<const __nv_bfloat16*>(Wb), P, tally, B, qsec,
                                                         qsec_count, qsec_cap, cnt, hist, hist_n);
