@@ -749,44 +749,52 @@ __global__ void __launch_bounds__(128) inc_yield_kernel(const NucleusModel* __re
 
 }  // namespace
 
+// SM count and resident blocks per SM of a persistent launch, with the query's status.
+struct LaunchShape {
+  cudaError_t e;
+  int n_sm, bps;
+};
+
 cudaError_t launch_inc_yields(const NucleusModel* nu, const float* btab, float E, unsigned long long seed,
                               unsigned long long pid0, unsigned long long n, EventYields* out, cudaStream_t s) {
-  static int blocks_per_sm = 0, n_sm = 0;
   const size_t smem = sizeof(NucleusModel) + kBtabFloats * sizeof(float);
-  if (n_sm == 0) {
+  // queried once per process (a function-local static is initialised exactly once, also
+  // when several host threads arrive together)
+  static const LaunchShape sh = [smem] {
+    LaunchShape r{cudaSuccess, 0, 0};
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, inc_yield_kernel, 128, smem);
-    if (e != cudaSuccess) {
-      n_sm = 0;
-      return e;
-    }
-  }
+    r.e = cudaGetDevice(&dev);
+    if (r.e == cudaSuccess) r.e = cudaDeviceGetAttribute(&r.n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (r.e == cudaSuccess) r.e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r.bps, inc_yield_kernel, 128, smem);
+    return r;
+  }();
+  if (sh.e != cudaSuccess) return sh.e;
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(EventYields), s);
   if (e != cudaSuccess || n == 0) return e;
   const unsigned long long want = (n + 127) / 128;
-  const unsigned long long cap = static_cast<unsigned long long>(n_sm) * (blocks_per_sm > 0 ? blocks_per_sm : 1);
+  const unsigned long long cap = static_cast<unsigned long long>(sh.n_sm) * (sh.bps > 0 ? sh.bps : 1);
   inc_yield_kernel<<<static_cast<unsigned>(want < cap ? want : cap), 128, smem, s>>>(nu, btab, E, seed, pid0, n, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cascade(const CascadeArgs& a, cudaStream_t s) {
-  static int n_sm = 0, inc_bps = 0;
   const size_t smem = a.n_nuc * sizeof(NucleusModel) + kBtabFloats * sizeof(float);
-  if (n_sm == 0) {
-    int dev = 0, sm = 0, bps = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, inc_kernel, 128, kMaxNuc * sizeof(NucleusModel) +
-                                                                                kBtabFloats * sizeof(float));
-    if (e != cudaSuccess) return e;
-    inc_bps = bps > 0 ? bps : 1;
-    n_sm = sm;
-  }
-  inc_kernel<<<n_sm * inc_bps, 128, smem, s>>>(a);
-  evap_kernel<<<n_sm * 8, 128, 0, s>>>(a);
+  // queried once per process, for the largest table (the multi-plan stream's slot threads
+  // may arrive together: a function-local static is initialised exactly once)
+  static const LaunchShape sh = [] {
+    LaunchShape r{cudaSuccess, 0, 0};
+    int dev = 0;
+    r.e = cudaGetDevice(&dev);
+    if (r.e == cudaSuccess) r.e = cudaDeviceGetAttribute(&r.n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (r.e == cudaSuccess)
+      r.e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r.bps, inc_kernel, 128,
+                                                          kMaxNuc * sizeof(NucleusModel) + kBtabFloats * sizeof(float));
+    if (r.bps < 1) r.bps = 1;
+    return r;
+  }();
+  if (sh.e != cudaSuccess) return sh.e;
+  inc_kernel<<<sh.n_sm * sh.bps, 128, smem, s>>>(a);
+  evap_kernel<<<sh.n_sm * 8, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -153,19 +153,24 @@ __global__ void __launch_bounds__(256) gamma_kernel(const double* __restrict__ r
 
 cudaError_t launch_gamma(const double* ref, const double* ev, int nx, int ny, int nz, void* plan, double dose_pct,
                          double threshold, float* gamma, cudaStream_t s) {
-  static int occ[2] = {0, 0};
-  static int n_sm = 0;
-  if (n_sm == 0) {
+  // queried once per process (a function-local static is initialised exactly once, also when
+  // several host threads arrive together)
+  struct Shape {
+    cudaError_t e;
+    int n_sm, occ[2];
+  };
+  static const Shape sh = [] {
+    Shape r{cudaSuccess, 0, {0, 0}};
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], dose_max_kernel, 256, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], gamma_kernel, 256, 0);
-    if (e != cudaSuccess) {
-      n_sm = 0;
-      return e;
-    }
-  }
+    r.e = cudaGetDevice(&dev);
+    if (r.e == cudaSuccess) r.e = cudaDeviceGetAttribute(&r.n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (r.e == cudaSuccess) r.e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r.occ[0], dose_max_kernel, 256, 0);
+    if (r.e == cudaSuccess) r.e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r.occ[1], gamma_kernel, 256, 0);
+    return r;
+  }();
+  if (sh.e != cudaSuccess) return sh.e;
+  const int n_sm = sh.n_sm;
+  const int* occ = sh.occ;
   GammaHead* head = static_cast<GammaHead*>(plan);
   const GammaOffset* off = reinterpret_cast<const GammaOffset*>(static_cast<unsigned char*>(plan) + kGammaHeadBytes);
   const long long n = static_cast<long long>(nx) * ny * nz;
