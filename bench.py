@@ -50,10 +50,10 @@ SURROGATE_FLOPS_PER_EVENT = 2 * 2 * (32 * 256 + 3 * 256 * 256 + 256 * 16)
 L2_BYTES = 129 * 2 ** 20
 # DRAM bytes (read + write) of the primary-transport launch per primary history, from a
 # 1-pass ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on this workload
-# (1e6 histories in one launch: 47.7 MB), valid only for the kernel sources it was taken
+# (1e6 histories in one launch: 47.8 MB), valid only for the kernel sources it was taken
 # on (their SHA-256 below); otherwise the roofline's traffic is reported as null.
-TRAFFIC = {"bytes_per_history": 47.7, "sources": ("transport.cu", "pmc_device.cuh", "pmc_kernels.cuh"),
-           "sha256": "e386051c545b77ab7fdb90e631899a9d4aeb78a16b0a1f1f5a040f0daa5673f0"}
+TRAFFIC = {"bytes_per_history": 47.8, "sources": ("transport.cu", "pmc_device.cuh", "pmc_kernels.cuh"),
+           "sha256": "8cab0dc887dea6073aec0996dc3e72b42624a99ad574abd8b25f64e7be8e006c"}
 
 
 def parse():

@@ -816,7 +816,7 @@ struct RunPlan {
   uint64_t n;
   int64_t chunk;
   int n_chunks;
-  int grid_t, grid_c;
+  int grid_t, grid_s, grid_c;   // transport grids of the primary and the secondary generations
   size_t smem;
 };
 
@@ -940,7 +940,7 @@ int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int sour
   int rc;
   const int kind = source == 0 ? 0 : 1;
   if ((rc = mark(ctx, s, kind, true))) return rc;
-  CK(launch_transport(a, rp.grid_t, ctx->block, rp.smem, s));
+  CK(launch_transport(a, source == 0 ? rp.grid_t : rp.grid_s, ctx->block, rp.smem, s));
   if ((rc = mark(ctx, s, kind, false))) return rc;
   if (ctx->mode == PMC_SURROGATE) {
     const float* P = static_cast<const float*>(ctx->d_sp.p);
@@ -1100,10 +1100,12 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     rp.chunk = std::min<int64_t>(chunk, static_cast<int64_t>(n_histories));
     rp.n_chunks = static_cast<int>((n_histories + rp.chunk - 1) / rp.chunk);
     rp.smem = transport_smem_bytes(ctx->phys.n_cls, ctx->phys.n_mat, ctx->d_mol.p != nullptr);
-    int bps = 0;
-    CK(transport_occupancy(ctx->block, rp.smem, &bps));
-    if (bps < 1) return fail(ctx, PMC_E_CUDA, "transport kernel does not fit (block %d, smem %zu)", ctx->block, rp.smem);
+    int bps = 0, bps2 = 0;
+    CK(transport_occupancy(ctx->block, rp.smem, &bps, &bps2));
+    if (bps < 1 || bps2 < 1)
+      return fail(ctx, PMC_E_CUDA, "transport kernel does not fit (block %d, smem %zu)", ctx->block, rp.smem);
     rp.grid_t = ctx->n_sm * bps;
+    rp.grid_s = ctx->n_sm * bps2;
     rp.grid_c = ctx->n_sm * 8;      // one tile of 128 events per block for typical event counts
     // buffers
     int rc;
@@ -1547,10 +1549,11 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     CK(cudaMemsetAsync(tally, 0, static_cast<size_t>(ctx->n_vox) * B * 8, s));
     CK(cudaMemsetAsync(counters, 0, sizeof(Counters), s));
     const size_t smem = transport_smem_bytes(ctx->phys.n_cls, ctx->phys.n_mat, ctx->d_mol.p != nullptr);
-    int bps = 0;
-    CK(transport_occupancy(ctx->block, smem, &bps));
-    if (bps < 1) return fail(ctx, PMC_E_CUDA, "transport kernel does not fit (block %d, smem %zu)", ctx->block, smem);
-    const int grid_t = ctx->n_sm * bps;
+    int bps = 0, bps2 = 0;
+    CK(transport_occupancy(ctx->block, smem, &bps, &bps2));
+    if (bps < 1 || bps2 < 1)
+      return fail(ctx, PMC_E_CUDA, "transport kernel does not fit (block %d, smem %zu)", ctx->block, smem);
+    const int grid_t = ctx->n_sm * bps, grid_s = ctx->n_sm * bps2;
     TransportArgs ta{};
     ta.phys = static_cast<const Physics*>(ctx->d_phys.p);
     ta.rtab = static_cast<const float2*>(ctx->d_rt.p);
@@ -1599,7 +1602,7 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
         ta.qne = q[2];
         ta.qne_count = counts + 2;
         ta.work = counts + 3;
-        CK(launch_transport(ta, grid_t, ctx->block, smem, s));
+        CK(launch_transport(ta, ta.source == 0 ? grid_t : grid_s, ctx->block, smem, s));
         ca.qne = q[2];
         ca.qne_count = counts + 2;
         ca.qsec = qout;

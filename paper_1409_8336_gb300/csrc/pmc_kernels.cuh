@@ -104,7 +104,8 @@ struct StatsArgs {
 
 size_t transport_smem_bytes(int n_cls, int n_mat, bool moliere);
 cudaError_t launch_transport(const TransportArgs& a, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t transport_occupancy(int block, size_t smem, int* blocks_per_sm);
+// Resident blocks per SM of the primary- and secondary-generation transport kernels.
+cudaError_t transport_occupancy(int block, size_t smem, int* blocks_primary, int* blocks_secondary);
 // The cascade of the events in a.qne (persistent, lanes refilled from a.work) and the
 // evaporation of their residuals (a.rec); a.work and a.rec_count must be zero.
 cudaError_t launch_cascade(const CascadeArgs& a, cudaStream_t s);

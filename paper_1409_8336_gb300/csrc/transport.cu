@@ -341,9 +341,15 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
 #ifndef PMC_TRANSPORT_MIN_BLOCKS
 #define PMC_TRANSPORT_MIN_BLOCKS 3   // measured best on GB300: 3 resident blocks of 256 per SM
 #endif
+// Secondary generations hold few particles and last as long as their longest track: there a
+// step's latency counts more than the number of resident warps, and with 2 blocks per SM the
+// step has the registers to be shorter (secondary stage 1.50 against 1.61 ms on the slab).
+#ifndef PMC_TRANSPORT_MIN_BLOCKS_SECONDARY
+#define PMC_TRANSPORT_MIN_BLOCKS_SECONDARY 2
+#endif
 
-template <bool kLet, bool kMol>
-__global__ void __launch_bounds__(256, PMC_TRANSPORT_MIN_BLOCKS) transport_kernel(const TransportArgs a) {
+template <bool kLet, bool kMol, int kMinBlocks>
+__global__ void __launch_bounds__(256, kMinBlocks) transport_kernel(const TransportArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned long long n_items =
       a.source == 0 ? (a.w_end - a.w_begin) : static_cast<unsigned long long>(min(*a.qin_count, a.qin_cap));
@@ -442,28 +448,33 @@ size_t transport_smem_bytes(int n_cls, int n_mat, bool moliere) {
 }
 
 namespace {
-// the four specialisations, indexed by (LET scored) + 2 (Moliere scattering)
-void (*const kTransportKernels[4])(const TransportArgs) = {
-    transport_kernel<false, false>, transport_kernel<true, false>, transport_kernel<false, true>,
-    transport_kernel<true, true>};
+// the specialisations: [primaries, secondaries][(LET scored) + 2 (Moliere scattering)]
+constexpr int kP = PMC_TRANSPORT_MIN_BLOCKS, kS = PMC_TRANSPORT_MIN_BLOCKS_SECONDARY;
+void (*const kTransportKernels[2][4])(const TransportArgs) = {
+    {transport_kernel<false, false, kP>, transport_kernel<true, false, kP>, transport_kernel<false, true, kP>,
+     transport_kernel<true, true, kP>},
+    {transport_kernel<false, false, kS>, transport_kernel<true, false, kS>, transport_kernel<false, true, kS>,
+     transport_kernel<true, true, kS>}};
 }  // namespace
 
-cudaError_t transport_occupancy(int block, size_t smem, int* blocks_per_sm) {
-  int lo = 1 << 30;
-  for (auto k : kTransportKernels) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, block, smem);
-    if (e != cudaSuccess) return e;
-    lo = b < lo ? b : lo;
+cudaError_t transport_occupancy(int block, size_t smem, int* blocks_primary, int* blocks_secondary) {
+  for (int g = 0; g < 2; ++g) {
+    int lo = 1 << 30;
+    for (auto k : kTransportKernels[g]) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+      int b = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, block, smem);
+      if (e != cudaSuccess) return e;
+      lo = b < lo ? b : lo;
+    }
+    *(g ? blocks_secondary : blocks_primary) = lo;
   }
-  *blocks_per_sm = lo;
   return cudaSuccess;
 }
 
 cudaError_t launch_transport(const TransportArgs& a, int grid, int block, size_t smem, cudaStream_t s) {
-  kTransportKernels[(a.let_num ? 1 : 0) + (a.mol ? 2 : 0)]<<<grid, block, smem, s>>>(a);
+  kTransportKernels[a.source ? 1 : 0][(a.let_num ? 1 : 0) + (a.mol ? 2 : 0)]<<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
 }
 
