@@ -47,6 +47,9 @@ def test_invalid_calls_fail_without_a_device(libpmc):
     assert libpmc.pmc_create(None, None) == -1          # PMC_E_INVALID, no context pointer
     libpmc.pmc_transport.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]
     assert libpmc.pmc_transport(None, 10, 1, 0, None) == -1
+    assert libpmc.pmc_surrogate_infer(None, None, 1, None) == -1
+    assert libpmc.pmc_debug_surrogate_waits(None) == -1
+    assert libpmc.pmc_enable_profile(None, 2) == -1
 
 
 def test_oracle_and_engine_share_no_code():
