@@ -71,6 +71,7 @@ static const double PI = 3.14159265358979323846264338328;
 #define OR_NO_ELASTIC 4u
 #define OR_NO_INELASTIC 8u
 #define OR_MOLIERE 16u   /* Moliere multiple scattering instead of Highland */
+#define OR_VAVILOV 32u   /* Vavilov straggling (table set by or_set_vavilov) where kappa <= 10 */
 
 /* ------------------------------------------------------------------ */
 /* public structures (mirrored by oracle.py with ctypes)               */
@@ -408,6 +409,56 @@ double or_moliere_theta(double u, double chic2, double B)
     }
     double th = v * sqrt(chic2 * B);
     return th < 0.5 * TWO_PI ? th : 0.5 * TWO_PI;
+}
+
+/* Vavilov straggling (optional; the paper uses Bohr's Gaussian).  The table, built by the
+ * oracle's Python side from the characteristic function of the Bethe collision spectrum
+ * (oracle/vavilov.py), holds quantiles of z = (loss - mean loss) / xi on OR_VAV_NB values of
+ * beta^2 in [0, 0.5], OR_VAV_NK values of ln kappa in [ln 0.01, ln 10] and OR_VAV_NU values of
+ * u in [1e-4, 1 - 1e-4], each row shifted to mean zero; sampled by trilinear interpolation. */
+#define OR_VAV_NK 31
+#define OR_VAV_NB 6
+#define OR_VAV_NU 513
+static double or_vav_tab[OR_VAV_NB * OR_VAV_NK * OR_VAV_NU];
+static int or_vav_ready = 0;
+
+void or_set_vavilov(const double* tab)
+{
+    memcpy(or_vav_tab, tab, sizeof(or_vav_tab));
+    or_vav_ready = 1;
+}
+
+/* xi = (K/2)(Z/A) rho x / beta^2 (MeV) and kappa = xi / T_max of a proton of energy E over x cm. */
+void or_vavilov_params(double E, double rho, double ZA, double x, double* xi, double* kappa)
+{
+    double g = 1.0 + E / M_PROTON;
+    double b2 = 1.0 - 1.0 / (g * g);
+    double r = M_ELECTRON / M_PROTON;
+    double tmax = 2.0 * M_ELECTRON * b2 * g * g / (1.0 + 2.0 * g * r + r * r);
+    *xi = 0.5 * K_BETHE * ZA * rho * x / b2;
+    *kappa = *xi / tmax;
+}
+
+double or_vavilov_z(double kappa, double b2, double u)
+{
+    double lk = log(kappa < 0.01 ? 0.01 : (kappa > 10.0 ? 10.0 : kappa));
+    double a = (lk - log(0.01)) / (log(10.0) - log(0.01)) * (OR_VAV_NK - 1);
+    double b = (b2 < 0.0 ? 0.0 : (b2 > 0.5 ? 0.5 : b2)) / 0.5 * (OR_VAV_NB - 1);
+    double cc = u * (OR_VAV_NU - 1);
+    int ia = (int)a, ib = (int)b, ic = (int)cc;
+    if (ia > OR_VAV_NK - 2) ia = OR_VAV_NK - 2;
+    if (ib > OR_VAV_NB - 2) ib = OR_VAV_NB - 2;
+    if (ic > OR_VAV_NU - 2) ic = OR_VAV_NU - 2;
+    double fa = a - ia, fb = b - ib, fc = cc - ic;
+    double v[2][2];
+    for (int jb = 0; jb < 2; ++jb)
+        for (int ja = 0; ja < 2; ++ja) {
+            const double* row = or_vav_tab + ((size_t)(ib + jb) * OR_VAV_NK + (ia + ja)) * OR_VAV_NU;
+            v[jb][ja] = row[ic] + fc * (row[ic + 1] - row[ic]);
+        }
+    double lo = v[0][0] + fa * (v[0][1] - v[0][0]);
+    double hi = v[1][0] + fa * (v[1][1] - v[1][0]);
+    return lo + fb * (hi - lo);
 }
 
 /* Bohr energy-loss straggling variance (MeV^2) over path x (cm). */
@@ -1148,8 +1199,15 @@ static void transport_one(or_ctx* c, or_particle* p, or_pstack* st)
         double dE = (Rleft > 0.0) ? E0 - energy_of_range(rt, Rleft) : E0;
         const double L_step = s > 0.0 ? dE / s : 0.0;     /* mean CSDA stopping power over the path */
         if (!(P->flags & OR_NO_STRAGGLING)) {
-            double var = or_bohr_variance(E0, rho, mi->ZA, s);
-            dE += sqrt(var) * sqrt(-2.0 * log(ua[2])) * cos(TWO_PI * ua[3]);
+            double xi = 0.0, kap = 1e300;
+            if ((P->flags & OR_VAVILOV) && or_vav_ready) or_vavilov_params(E0, rho, mi->ZA, s, &xi, &kap);
+            if (kap <= 10.0) {
+                double g = 1.0 + E0 / M_PROTON;
+                dE += xi * or_vavilov_z(kap, 1.0 - 1.0 / (g * g), ua[2]);
+            } else {
+                double var = or_bohr_variance(E0, rho, mi->ZA, s);
+                dE += sqrt(var) * sqrt(-2.0 * log(ua[2])) * cos(TWO_PI * ua[3]);
+            }
         }
         if (dE < 0.0) dE = 0.0;
         if (dE > E0) dE = E0;

@@ -106,6 +106,10 @@ def lib():
             L.or_moliere_params.argtypes = [C.POINTER(OrProblem), i, d, d, pd, pd]
             L.or_moliere_theta.argtypes = [d, d, d]
             L.or_moliere_theta.restype = d
+            L.or_set_vavilov.argtypes = [pd]
+            L.or_vavilov_params.argtypes = [d, d, d, d, pd, pd]
+            L.or_vavilov_z.argtypes = [d, d, d]
+            L.or_vavilov_z.restype = d
             L.or_range_csda.argtypes = [C.POINTER(OrProblem), i, d]
             L.or_range_csda.restype = d
             L.or_material_info.argtypes = [C.POINTER(OrProblem), i, pd]
@@ -127,10 +131,28 @@ def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+VAVILOV = 32
+_vav_ready = False
+
+
+def _ensure_vavilov(L):
+    """Hands the Vavilov table (oracle/vavilov.py) to the C oracle, once per process."""
+    global _vav_ready
+    with _lock:
+        if not _vav_ready:
+            from oracle import vavilov as V
+
+            tab = np.ascontiguousarray(V.table(), dtype=np.float64)
+            L.or_set_vavilov(_dp(tab))
+            _vav_ready = True
+
+
 class _Marshalled:
     """Keeps the ctypes arrays of one problem alive."""
 
     def __init__(self, prob):
+        if int(prob.flags) & VAVILOV:
+            _ensure_vavilov(lib())
         self.nuc = (Nuclide * len(prob.nuclides))(*[Nuclide(*n) for n in prob.nuclides])
         mats = []
         for m in prob.materials:

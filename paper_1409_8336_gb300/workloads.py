@@ -50,6 +50,7 @@ BONE_LO = _material([(H, 0.070), (C, 0.200), (N, 0.040), (O, 0.530), (P, 0.050),
 # Flags switching physics off (used by the pin and parity tests only).
 NO_STRAGGLING, NO_MCS, NO_ELASTIC, NO_INELASTIC = 1, 2, 4, 8
 MOLIERE = 16                      # Moliere multiple scattering instead of Highland
+VAVILOV = 32                      # Vavilov straggling where kappa <= 10 instead of Bohr's Gaussian
 
 
 @dataclass
