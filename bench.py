@@ -50,10 +50,10 @@ SURROGATE_FLOPS_PER_EVENT = 2 * 2 * (32 * 256 + 3 * 256 * 256 + 256 * 16)
 L2_BYTES = 129 * 2 ** 20
 # DRAM bytes (read + write) of the primary-transport launch per primary history, from a
 # 1-pass ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on this workload
-# (1e6 histories in one launch: 47.8 MB), valid only for the kernel sources it was taken
+# (1e6 histories in one launch: 48.0 MB), valid only for the kernel sources it was taken
 # on (their SHA-256 below); otherwise the roofline's traffic is reported as null.
-TRAFFIC = {"bytes_per_history": 47.8, "sources": ("transport.cu", "pmc_device.cuh", "pmc_kernels.cuh"),
-           "sha256": "8cab0dc887dea6073aec0996dc3e72b42624a99ad574abd8b25f64e7be8e006c"}
+TRAFFIC = {"bytes_per_history": 48.0, "sources": ("transport.cu", "pmc_device.cuh", "pmc_kernels.cuh"),
+           "sha256": "f3bbc6d8d302b606c4da958f04760b0fd9045a7499df1364ad1dfcac810383a3"}
 
 
 def parse():
@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-gamma", action="store_true")
     ap.add_argument("--no-let", action="store_true")
     ap.add_argument("--no-moliere", action="store_true")
+    ap.add_argument("--no-vavilov", action="store_true")
     ap.add_argument("--no-inc", action="store_true")
     ap.add_argument("--no-plans", action="store_true")
     ap.add_argument("--launch", default=None, help="BLOCK,CHUNK: fixed launch shape instead of autotuning")
@@ -617,6 +618,22 @@ def main():
         moliere = {"value": world * n * len(mm) / (sum(mm) / 1e3), "unit": UNIT, "ms_per_step": sum(mm) / len(mm),
                    "steps": len(mm), "time_vs_highland": (sum(mm) / len(mm)) / (total_ms / args.steps)}
 
+    # Vavilov straggling instead of Bohr's Gaussian, the same workload and launch shape
+    vavilov = None
+    if not args.no_vavilov:
+        from paper_1409_8336_gb300 import workloads as W
+
+        pv = prob.with_(flags=prob.flags | W.VAVILOV)
+        ev = Engine(device=local, n_batches=pv.n_batches, physics_flags=pv.flags, fast_math=(args.math == "fast"),
+                    block_size=tuned_block)
+        ev.load_problem(pv)
+        ev.set_launch(tuned_block, tuned_chunk)
+        timed_steps(ev, 3, 8500)
+        vm = timed_steps(ev, min(args.steps, 20), 8600)
+        ev.close()
+        vavilov = {"value": world * n * len(vm) / (sum(vm) / 1e3), "unit": UNIT, "ms_per_step": sum(vm) / len(vm),
+                   "steps": len(vm), "time_vs_bohr": (sum(vm) / len(vm)) / (total_ms / args.steps)}
+
     # the learned stand-in of the event generator: trained outside the timed region on events
     # from the engine's own cascade, then timed the same way, with its dose against the full
     # cascade's at the same seed (2 %/2 mm gamma)
@@ -738,6 +755,7 @@ def main():
             "plans_stream": plans,
             "let": let_leg,
             "moliere": moliere,
+            "vavilov": vavilov,
             "other_build": {"math": "ieee" if args.math == "fast" else "fast",
                             "value": world * n * args.steps / (sum(other_ms) / 1e3),
                             "ms_per_step": sum(other_ms) / args.steps},

@@ -48,6 +48,14 @@ extern "C" {
  * B = 4.5, space angle from F0 + F1/B + F2/B^2) instead of the paper's Highland width
  * (Sec. II.A.2), at the step-start energy over the planned step. */
 #define PMC_MOLIERE 16u
+/* physics flag: Vavilov energy-loss straggling (the paper uses Bohr's Gaussian, Sec. II.A.2,
+ * and prints no Vavilov formula).  Where kappa = xi / T_max <= 10 (xi = (K/2)(Z/A) rho s /
+ * beta^2 over the step's path s, T_max the largest transfer to a free electron) the loss
+ * fluctuation about the CSDA mean is drawn from Vavilov's distribution for the Bethe spectrum
+ * of transfers, tabulated from its characteristic function (kappa clamped to [0.01, 10], the
+ * quantile tails cut at 1e-4, each row centred so the mean loss stays the CSDA loss); above
+ * 10, Bohr's Gaussian of the same variance. */
+#define PMC_VAVILOV 32u
 
 /* transport modes */
 #define PMC_FULL_CASCADE 0        /* non-elastic events by cascade + evaporation */
@@ -397,6 +405,11 @@ int pmc_debug_elastic(pmc_ctx* ctx, int nuclide, double E, const double* u, doub
  * (the block stops, frees its tensor memory and reports), and the context stays usable.
  * PMC_E_INVALID without a loaded network. */
 int pmc_debug_surrogate_waits(pmc_ctx* ctx);
+/* pmc_debug_vavilov_table: the Vavilov straggling table the transport samples from, built on
+ * the host (no device needed): quantiles of z = (loss - mean loss) / xi, [6 values of beta^2 in
+ * [0, 0.5]][31 values of ln kappa in [ln 0.01, ln 10]][513 values of u in [1e-4, 1 - 1e-4]],
+ * each row shifted to mean zero.  n must be 6 * 31 * 513; PMC_E_INVALID otherwise. */
+int pmc_debug_vavilov_table(float* out, size_t n);
 
 #ifdef __cplusplus
 }

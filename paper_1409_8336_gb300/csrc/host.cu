@@ -15,6 +15,7 @@
 #include <numeric>
 #include <string>
 #include <thread>
+#include <complex>
 #include <vector>
 
 #include "../../include/pmc.h"
@@ -164,6 +165,133 @@ std::vector<unsigned> moliere_guide(const std::vector<float4>& t) {
   return g;
 }
 
+// ---- Vavilov straggling table -------------------------------------------------
+// The fluctuation of the loss about its mean, for the Bethe spectrum of transfers to free
+// electrons xi (1/eps^2 - beta^2 / (eps eps_max)) on (0, eps_max], has in units of eps_max the
+// characteristic function ln phi(tau) = kappa (I2(tau) - beta^2 I1(tau)) with
+// I1 = -Cin + i (Si - tau), I2 = -(e^{i tau} - 1 - i tau) + i tau (-Cin + i Si) and
+// Cin = gamma + ln tau - Ci.  Its density comes from a discrete Fourier inversion; the table
+// holds quantiles of z = (loss - mean) / xi (see kVav* in pmc_device.cuh).
+
+// Sine and cosine integrals: power series up to 4; beyond, the continued fraction of
+// E1(i x) = -Ci(x) + i (Si(x) - pi/2) evaluated by the modified Lentz method.
+void sine_cosine_integrals(double x, double& si, double& ci) {
+  if (x <= 4.0) {
+    double p = x, s = x;                                  // x^(2k+1) / (2k+1)!
+    for (int k = 1; k < 40; ++k) {
+      p *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+      s += p / (2.0 * k + 1.0);
+    }
+    double q = 1.0, c = 0.0;                              // x^(2k) / (2k)!
+    for (int k = 1; k < 40; ++k) {
+      q *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+      c += q / (2.0 * k);
+    }
+    si = s;
+    ci = 0.57721566490153286 + std::log(x) + c;
+    return;
+  }
+  using cd = std::complex<double>;
+  cd b(1.0, x), c(1e300, 0.0), d = 1.0 / b, h = d;
+  for (int k = 1; k < 100000; ++k) {
+    const double a = -static_cast<double>(k) * k;
+    b += 2.0;
+    d = 1.0 / (a * d + b);
+    c = b + a / c;
+    const cd del = c * d;
+    h *= del;
+    if (std::abs(del - 1.0) < 1e-16) break;
+  }
+  h *= cd(std::cos(x), -std::sin(x));
+  ci = -h.real();
+  si = 1.5707963267948966 + h.imag();
+}
+
+// In-place radix-2 DFT X_j = sum_k x_k exp(-2 pi i j k / n), n a power of two.
+void dft_forward(std::vector<std::complex<double>>& a) {
+  const size_t n = a.size();
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (size_t len = 2; len <= n; len <<= 1) {
+    const double ang = -2.0 * 3.14159265358979323846 / static_cast<double>(len);
+    const std::complex<double> wl(std::cos(ang), std::sin(ang));
+    for (size_t i = 0; i < n; i += len) {
+      std::complex<double> w(1.0, 0.0);
+      for (size_t k = 0; k < len / 2; ++k) {
+        const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+        w *= wl;
+      }
+    }
+  }
+}
+
+// One table row: the kVavNU quantiles of z at (kappa, beta^2), shifted to mean zero.
+std::vector<double> vavilov_row(double kappa, double b2) {
+  const int n = 1 << 14;
+  const double sd = std::sqrt(kappa * (1.0 - 0.5 * b2));
+  const double ylo = -10.0 * sd - 0.05, yhi = 10.0 * sd + 3.0, L = yhi - ylo, dy = L / n;
+  std::vector<std::complex<double>> a(n);
+  for (int k = 0; k < n; ++k) {
+    const int kk = k < n / 2 ? k : k - n;
+    const double tau = 2.0 * 3.14159265358979323846 * kk / L;
+    std::complex<double> lp(0.0, 0.0);
+    if (kk != 0) {
+      const double t = std::fabs(tau);
+      double si, ci;
+      sine_cosine_integrals(t, si, ci);
+      const double cin = 0.57721566490153286 + std::log(t) - ci;
+      const std::complex<double> i1(-cin, si - t);
+      const std::complex<double> i2 = -(std::complex<double>(std::cos(t) - 1.0, std::sin(t) - t)) +
+                                      std::complex<double>(-t * si, -t * cin);
+      lp = kappa * (i2 - b2 * i1);
+      if (tau < 0.0) lp = std::conj(lp);
+    }
+    a[k] = std::exp(lp) * std::polar(1.0, -tau * ylo);
+  }
+  dft_forward(a);
+  std::vector<double> cdf(n + 1, 0.0);
+  for (int j = 0; j < n; ++j) cdf[j + 1] = cdf[j] + std::max(a[j].real() / L, 0.0) * dy;
+  for (int j = 0; j <= n; ++j) cdf[j] /= cdf[n];
+  for (int j = 1; j <= n; ++j) cdf[j] = std::max(cdf[j], cdf[j - 1]);
+  std::vector<double> z(kVavNU);
+  int j = 0;
+  for (int i = 0; i < kVavNU; ++i) {
+    const double u = kVavU0 + i * (1.0 - 2.0 * kVavU0) / (kVavNU - 1);
+    while (j < n - 1 && cdf[j + 1] < u) ++j;
+    const double w = cdf[j + 1] > cdf[j] ? (u - cdf[j]) / (cdf[j + 1] - cdf[j]) : 0.0;
+    z[i] = (ylo - 0.5 * dy + (j + w) * dy) / kappa;
+  }
+  double mean = 0.5 * (z.front() + z.back());
+  for (int i = 1; i < kVavNU - 1; ++i) mean += z[i];
+  mean /= (kVavNU - 1);
+  for (double& v : z) v -= mean;
+  return z;
+}
+
+// The table [kVavNB][kVavNK][kVavNU], built once per process.
+const std::vector<float>& vavilov_table() {
+  static const std::vector<float> tab = [] {
+    std::vector<float> t(static_cast<size_t>(kVavNB) * kVavNK * kVavNU);
+    for (int ib = 0; ib < kVavNB; ++ib)
+      for (int ik = 0; ik < kVavNK; ++ik) {
+        const double b2 = kVavB2Max * ib / (kVavNB - 1);
+        const double kappa =
+            std::exp(std::log(kVavK0) + (std::log(kVavK1) - std::log(kVavK0)) * ik / (kVavNK - 1));
+        const std::vector<double> row = vavilov_row(kappa, b2);
+        for (int i = 0; i < kVavNU; ++i)
+          t[(static_cast<size_t>(ib) * kVavNK + ik) * kVavNU + i] = static_cast<float>(row[i]);
+      }
+    return t;
+  }();
+  return tab;
+}
+
 double integrate_inv_s(double a, double b, double ZA, double I) {
   const double m = 0.5 * (a + b), h = 0.5 * (b - a);
   double s = 0.0;
@@ -307,7 +435,7 @@ struct pmc_ctx {
   std::vector<pmc_material> mats;
   std::vector<pmc_nuclide> nucs;
   std::vector<pmc_hu_bin> hus;
-  DevBuf d_phys, d_rt, d_et, d_st, d_nuclei, d_btab, d_mol;
+  DevBuf d_phys, d_rt, d_et, d_st, d_nuclei, d_btab, d_mol, d_vav;
   // geometry
   bool have_phantom = false;
   Geometry geo{};
@@ -482,7 +610,7 @@ void pmc_destroy(pmc_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
-  DevBuf* bufs[] = {&ctx->d_phys, &ctx->d_rt, &ctx->d_et, &ctx->d_st, &ctx->d_nuclei, &ctx->d_btab, &ctx->d_mol, &ctx->d_mat,
+  DevBuf* bufs[] = {&ctx->d_phys, &ctx->d_rt, &ctx->d_et, &ctx->d_st, &ctx->d_nuclei, &ctx->d_btab, &ctx->d_mol, &ctx->d_vav, &ctx->d_mat,
                     &ctx->d_rho, &ctx->d_hu, &ctx->d_tally, &ctx->d_dose, &ctx->d_sigma, &ctx->d_counters,
                     &ctx->d_counts, &ctx->d_seed, &ctx->d_spots, &ctx->d_q[0], &ctx->d_q[1], &ctx->d_q[2],
                     &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_hist, &ctx->d_esc,
@@ -659,6 +787,12 @@ int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc, const pm
       if ((rc = upload(ctx, ctx->d_mol, tab.data(), tab.size() * sizeof(float)))) return rc;
     } else {
       dfree(ctx, ctx->d_mol);
+    }
+    if (ph.flags & kVavilov) {
+      const std::vector<float>& vt = vavilov_table();
+      if ((rc = upload(ctx, ctx->d_vav, vt.data(), vt.size() * sizeof(float)))) return rc;
+    } else {
+      dfree(ctx, ctx->d_vav);
     }
     std::vector<int> slot_nuc, nuc_slot(n_nuc, -1);
     for (int i = 0; i < n_nuc; ++i)
@@ -886,6 +1020,7 @@ TransportArgs transport_args(pmc_ctx* ctx) {
   a.etab = static_cast<const float2*>(ctx->d_et.p);
   a.stab = static_cast<const float*>(ctx->d_st.p);
   a.mol = static_cast<const float4*>(ctx->d_mol.p);
+  a.vav = static_cast<const float*>(ctx->d_vav.p);
   a.g = ctx->geo;
   a.tally = static_cast<unsigned long long*>(ctx->d_tally.p);
   a.B = ctx->opt.n_batches;
@@ -1560,6 +1695,7 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     ta.etab = static_cast<const float2*>(ctx->d_et.p);
     ta.stab = static_cast<const float*>(ctx->d_st.p);
     ta.mol = static_cast<const float4*>(ctx->d_mol.p);
+    ta.vav = static_cast<const float*>(ctx->d_vav.p);
     ta.g = ctx->geo;
     ta.tally = reinterpret_cast<unsigned long long*>(tally);
     ta.B = ctx->opt.n_batches;
@@ -1899,6 +2035,13 @@ int surrogate_rows(pmc_ctx* ctx, const float* x, int rows, float* y, bool check_
 int pmc_surrogate_infer(pmc_ctx* ctx, const float* x, int rows, float* y) {
   if (!ctx || !x || !y || rows < 1 || rows > (1 << 20)) return PMC_E_INVALID;
   return surrogate_rows(ctx, x, rows, y, false);
+}
+
+int pmc_debug_vavilov_table(float* out, size_t n) {
+  const std::vector<float>& t = vavilov_table();
+  if (!out || n != t.size()) return PMC_E_INVALID;
+  std::memcpy(out, t.data(), n * sizeof(float));
+  return PMC_OK;
 }
 
 int pmc_debug_surrogate_waits(pmc_ctx* ctx) {

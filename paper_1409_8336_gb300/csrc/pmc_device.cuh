@@ -20,6 +20,8 @@ constexpr float kEcut = 0.1f;                  // Sec. II.A.3
 constexpr float kFix = 16777216.0f;            // tally unit 2^-24 MeV
 constexpr double kFixD = 16777216.0;
 constexpr float kCoulomb = 1.439964548f;       // e^2 / 4 pi eps0, MeV fm
+constexpr float kMe = 0.51099895f;             // electron mass, MeV
+constexpr float kKBethe = 0.307075f;           // 4 pi N_A r_e^2 m_e c^2, MeV cm^2 / mol
 constexpr float kFm2PerMb = 0.1f;
 // Tables are uniform in ln E or ln R with spacing 2^-6, so the table coordinate
 // (ln x - origin) * 64 is computed without a rounded scale factor: a rounded
@@ -39,7 +41,13 @@ constexpr int kIncCrossings = 1000;
 constexpr int kIncIterations = 100000;          // flights per nucleon
 constexpr int kEvapSteps = 64;
 constexpr unsigned kMaxSteps = 100000u;        // per particle; exceeding it is an error
-constexpr unsigned kNoStraggling = 1u, kNoMcs = 2u, kNoElastic = 4u, kNoInelastic = 8u, kMoliere = 16u;
+constexpr unsigned kNoStraggling = 1u, kNoMcs = 2u, kNoElastic = 4u, kNoInelastic = 8u, kMoliere = 16u,
+                   kVavilov = 32u;
+// Vavilov straggling table: quantiles of z = (loss - mean loss) / xi on kVavNB values of beta^2
+// in [0, kVavB2Max], kVavNK values of ln kappa in [ln kVavK0, ln kVavK1] and kVavNU values of u
+// in [kVavU0, 1 - kVavU0], each row shifted to mean zero (trilinear sampling keeps it).
+constexpr int kVavNK = 31, kVavNB = 6, kVavNU = 513;
+constexpr double kVavK0 = 0.01, kVavK1 = 10.0, kVavB2Max = 0.5, kVavU0 = 1e-4;
 constexpr int kMolN = 1025;                    // Moliere distribution-function nodes on v in [0, kMolVmax]
 constexpr float kMolVmax = 8.0f;
 constexpr float kMolBmin = 4.5f;               // validity floor of the expansion (Bethe)
@@ -300,6 +308,28 @@ __device__ __forceinline__ float moliere_b(const float4* T, int m, float lnE, fl
 #pragma unroll
   for (int it = 0; it < 4; ++it) B -= (B - logf(B) - b) / (1.0f - 1.0f / B);
   return B;
+}
+
+// Vavilov straggling: the centred loss z (units of xi) for the uniform u at (kappa, beta^2),
+// trilinear in (ln kappa, beta^2, u); kappa is clamped to the table's range.
+__device__ __forceinline__ float vavilov_z(const float* __restrict__ T, float kappa, float b2, float u) {
+  const float lk0 = static_cast<float>(-4.605170185988091), lk1 = static_cast<float>(2.302585092994046);
+  const float a = (fminf(fmaxf(logf(kappa), lk0), lk1) - lk0) * ((kVavNK - 1) / (lk1 - lk0));
+  const float b = fminf(fmaxf(b2, 0.0f), static_cast<float>(kVavB2Max)) * ((kVavNB - 1) / static_cast<float>(kVavB2Max));
+  const float c = u * (kVavNU - 1);
+  const int ia = min(static_cast<int>(a), kVavNK - 2), ib = min(static_cast<int>(b), kVavNB - 2);
+  const int ic = min(static_cast<int>(c), kVavNU - 2);
+  const float fa = a - ia, fb = b - ib, fc = c - ic;
+  float v[2][2];
+#pragma unroll
+  for (int jb = 0; jb < 2; ++jb)
+#pragma unroll
+    for (int ja = 0; ja < 2; ++ja) {
+      const float* row = T + (static_cast<size_t>(ib + jb) * kVavNK + (ia + ja)) * kVavNU + ic;
+      v[jb][ja] = row[0] + fc * (row[1] - row[0]);
+    }
+  const float lo = v[0][0] + fa * (v[0][1] - v[0][0]), hi = v[1][0] + fa * (v[1][1] - v[1][0]);
+  return lo + fb * (hi - lo);
 }
 
 // ---------------------------------------------------------------------------

@@ -26,6 +26,7 @@ struct TransportArgs {
   const float2* etab;              // [n_cls][kNR] inverse splines
   const float* stab;               // [n_mat][kNS] total cross-section per unit density
   const float4* mol;               // [kMolN] Moliere distribution functions, or NULL (Highland)
+  const float* vav;                // Vavilov straggling table [kVavNB][kVavNK][kVavNU], or NULL (Bohr)
   Geometry g;
   unsigned long long* tally;       // [n_voxels][B]
   int B;

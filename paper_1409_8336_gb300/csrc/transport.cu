@@ -143,10 +143,10 @@ __device__ __forceinline__ Particle make_record(const PState& p, float E, float 
   return r;
 }
 
-// One condensed-history step (Sec. II.A.3).  Returns false when the particle ends.  kLet and
-// kMol compile the LET scoring and the Moliere option in; without them the step carries no
-// test for either.
-template <bool kLet, bool kMol>
+// One condensed-history step (Sec. II.A.3).  Returns false when the particle ends.  kLet, kMol
+// and kVav compile the LET scoring, the Moliere option and the Vavilov option in; without
+// them the step carries no test for any of them.
+template <bool kLet, bool kMol, bool kVav>
 __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt, const float2* et,
                      const float* st, const float4* mol, uint2 key, PState& p, Acc& acc) {
   const int v = vindex(a.g, p.ix, p.iy, p.iz);
@@ -237,8 +237,23 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   if (!(ph.flags & kNoStraggling)) {
     const float g = 1.0f + E0 / kMp;
     const float b2 = 1.0f - 1.0f / (g * g);
-    const float var = mc.bohr_k * rho * s * (1.0f - 0.5f * b2) / (1.0f - b2);
-    dE += sqrtf(var) * sqrtf(-2.0f * logf(ua.u2)) * cospif(2.0f * ua.u3);
+    bool vav = false;
+    if (kVav) {
+      // Vavilov where kappa = xi / T_max <= 10: xi = (K/2)(Z/A) rho s / beta^2, T_max the
+      // largest transfer to a free electron; beyond it Bohr's Gaussian (the same variance)
+      const float r = kMe / kMp;
+      const float tmax = 2.0f * kMe * b2 * g * g / (1.0f + 2.0f * g * r + r * r);
+      const float xi = 0.5f * kKBethe * mc.ZA * rho * s / b2;
+      const float kappa = xi / tmax;
+      if (kappa <= 10.0f) {
+        dE += xi * vavilov_z(a.vav, kappa, b2, ua.u2);
+        vav = true;
+      }
+    }
+    if (!vav) {
+      const float var = mc.bohr_k * rho * s * (1.0f - 0.5f * b2) / (1.0f - b2);
+      dE += sqrtf(var) * sqrtf(-2.0f * logf(ua.u2)) * cospif(2.0f * ua.u3);
+    }
   }
   dE = fminf(fmaxf(dE, 0.0f), E0);
   const float E1 = E0 - dE;
@@ -348,7 +363,7 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
 #define PMC_TRANSPORT_MIN_BLOCKS_SECONDARY 2
 #endif
 
-template <bool kLet, bool kMol, int kMinBlocks>
+template <bool kLet, bool kMol, bool kVav, int kMinBlocks>
 __global__ void __launch_bounds__(256, kMinBlocks) transport_kernel(const TransportArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned long long n_items =
@@ -411,7 +426,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) transport_kernel(const Transp
       }
     }
     if (__all_sync(0xffffffffu, !alive && drained)) break;
-    if (alive) alive = step<kLet, kMol>(a, ph, rt, et, st, mol, key, p, acc);
+    if (alive) alive = step<kLet, kMol, kVav>(a, ph, rt, et, st, mol, key, p, acc);
   }
 
   // flush the lane counters (warp reduction, one atomic per warp and counter)
@@ -448,19 +463,22 @@ size_t transport_smem_bytes(int n_cls, int n_mat, bool moliere) {
 }
 
 namespace {
-// the specialisations: [primaries, secondaries][(LET scored) + 2 (Moliere scattering)]
+// the specialisations: [primaries, secondaries][(LET scored) + 2 (Moliere) + 4 (Vavilov)]
 constexpr int kP = PMC_TRANSPORT_MIN_BLOCKS, kS = PMC_TRANSPORT_MIN_BLOCKS_SECONDARY;
-void (*const kTransportKernels[2][4])(const TransportArgs) = {
-    {transport_kernel<false, false, kP>, transport_kernel<true, false, kP>, transport_kernel<false, true, kP>,
-     transport_kernel<true, true, kP>},
-    {transport_kernel<false, false, kS>, transport_kernel<true, false, kS>, transport_kernel<false, true, kS>,
-     transport_kernel<true, true, kS>}};
+template <int kB>
+constexpr void (*kFamily[8])(const TransportArgs) = {
+    transport_kernel<false, false, false, kB>, transport_kernel<true, false, false, kB>,
+    transport_kernel<false, true, false, kB>,  transport_kernel<true, true, false, kB>,
+    transport_kernel<false, false, true, kB>,  transport_kernel<true, false, true, kB>,
+    transport_kernel<false, true, true, kB>,   transport_kernel<true, true, true, kB>};
+void (*const* const kTransportKernels[2])(const TransportArgs) = {kFamily<kP>, kFamily<kS>};
 }  // namespace
 
 cudaError_t transport_occupancy(int block, size_t smem, int* blocks_primary, int* blocks_secondary) {
   for (int g = 0; g < 2; ++g) {
     int lo = 1 << 30;
-    for (auto k : kTransportKernels[g]) {
+    for (int i = 0; i < 8; ++i) {
+      const auto k = kTransportKernels[g][i];
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
       if (e != cudaSuccess) return e;
       int b = 0;
@@ -474,7 +492,8 @@ cudaError_t transport_occupancy(int block, size_t smem, int* blocks_primary, int
 }
 
 cudaError_t launch_transport(const TransportArgs& a, int grid, int block, size_t smem, cudaStream_t s) {
-  kTransportKernels[a.source ? 1 : 0][(a.let_num ? 1 : 0) + (a.mol ? 2 : 0)]<<<grid, block, smem, s>>>(a);
+  kTransportKernels[a.source ? 1 : 0][(a.let_num ? 1 : 0) + (a.mol ? 2 : 0) + (a.vav ? 4 : 0)]<<<grid, block, smem, s>>>(
+      a);
   return cudaGetLastError();
 }
 

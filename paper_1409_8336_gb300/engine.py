@@ -19,7 +19,7 @@ LIB_FAST_PATH = os.path.join(HERE, "libpmc_fast.so")   # the -use_fast_math buil
 
 PMC_OK = 0
 ERRORS = {-1: "PMC_E_INVALID", -2: "PMC_E_OOM", -3: "PMC_E_QUEUE_OVERFLOW", -4: "PMC_E_TIMEOUT", -5: "PMC_E_CUDA"}
-NO_STRAGGLING, NO_MCS, NO_ELASTIC, NO_INELASTIC = 1, 2, 4, 8
+NO_STRAGGLING, NO_MCS, NO_ELASTIC, NO_INELASTIC, MOLIERE, VAVILOV = 1, 2, 4, 8, 16, 32
 FULL_CASCADE, SURROGATE = 0, 1
 MAX_NUC_PER_MAT = 12
 
@@ -33,7 +33,7 @@ EXPORTS = [
     "pmc_set_launch", "pmc_autotune", "pmc_transport_noalloc", "pmc_surrogate_dataset", "pmc_train_surrogate",
     "pmc_surrogate_params", "pmc_surrogate_load", "pmc_surrogate_grad", "pmc_surrogate_infer", "pmc_gamma_plan_bytes", "pmc_gamma_plan", "pmc_gamma_device",
     "pmc_gamma_index", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables",
-    "pmc_debug_inc", "pmc_debug_elastic", "pmc_debug_surrogate_waits",
+    "pmc_debug_inc", "pmc_debug_elastic", "pmc_debug_surrogate_waits", "pmc_debug_vavilov_table",
 ]
 
 AllocFn = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -156,6 +156,7 @@ def lib(path: str = LIB_PATH):
             L.pmc_surrogate_grad.argtypes = [vp, pf, pf, pf, pf, pf, i, pf, pf, pf]
             L.pmc_surrogate_infer.argtypes = [vp, pf, i, pf]
             L.pmc_debug_surrogate_waits.argtypes = [vp]
+            L.pmc_debug_vavilov_table.argtypes = [pf, C.c_size_t]
             L.pmc_gamma_plan_bytes.argtypes = [d, d, d, d, d, C.POINTER(C.c_size_t)]
             L.pmc_gamma_plan.argtypes = [d, d, d, d, d, vp, C.c_size_t, vp]
             L.pmc_gamma_device.argtypes = [vp, vp, vp, i, i, i, d, d, vp, vp]
@@ -649,4 +650,14 @@ def debug_philox(ctr, key, fast_math=False):
     rc = lib(LIB_FAST_PATH if fast_math else LIB_PATH).pmc_debug_philox(ctr.ctypes.data_as(P), key.ctypes.data_as(P), out.ctypes.data_as(P), len(ctr))
     if rc != PMC_OK:
         raise PmcError(rc, "pmc_debug_philox failed")
+    return out
+
+
+def debug_vavilov_table(library: str | None = None):
+    """The Vavilov straggling table as built by the library's host code [6][31][513] (no device)."""
+    L = lib(library or LIB_PATH)
+    out = np.empty((6, 31, 513), dtype=np.float32)
+    rc = L.pmc_debug_vavilov_table(_fp(out), out.size)
+    if rc != PMC_OK:
+        raise PmcError(rc, "bad table size")
     return out

@@ -109,3 +109,14 @@ def test_transported_spread_keeps_mean_and_variance_and_gains_the_tail():
     assert abs(b.mean() - v.mean()) < 4 * se
     assert v.std() == pytest.approx(b.std(), rel=0.03)
     assert stats.skew(v) < -0.2 and abs(stats.skew(b)) < 0.1
+
+
+def test_library_builds_the_same_table_independently():
+    """The library's host code builds its own table (its own sine/cosine integrals and Fourier
+    transform, no device needed): it equals the oracle's to float precision."""
+    from paper_1409_8336_gb300 import engine
+
+    G = engine.debug_vavilov_table()
+    T = V.table()
+    assert G.shape == T.shape
+    assert np.abs(G - T).max() <= 1e-5 * max(1.0, np.abs(T).max())
