@@ -483,14 +483,23 @@ double or_sigma_nn(double T, int like)
     return 34.10 / (b * b) - 82.2 / b + 82.2;
 }
 
+/* Proton-nucleus non-elastic cross-section.  The paper tabulates Geant4's values (Sec.
+ * II.A.4), which are not available here; the reading is the empirical fit of Letaw,
+ * Silberberg & Tsao (Astrophys. J. Suppl. 51 (1983) 271) to measured proton reaction
+ * cross-sections,
+ *   sigma_HE = 45 A^0.7 [1 + 0.016 sin(5.3 - 2.63 ln A)] mb,
+ *   sigma(E) = sigma_HE [1 - 0.62 exp(-E/200) sin(10.9 E^-0.28)]   (E in MeV),
+ * closed below the Coulomb barrier B_c = e^2 Z / (1.16 (A^1/3 + 1) fm) by the factor
+ * (1 - B_c/E). */
 double or_sigma_inelastic(int Z, int A, double E)
 {
     if (A <= 1 || E <= 0.0) return 0.0;
     double a13 = cbrt((double)A);
     double bc = COULOMB_E2 * Z / (1.16 * (a13 + 1.0));
     if (E <= bc) return 0.0;
-    double geo = PI * 1.16 * 1.16 * (a13 + 0.8) * (a13 + 0.8) / FM2_PER_MB;
-    return 0.65 * geo * (1.0 - bc / E) * (1.0 - exp(-E / 15.0));
+    double s_he = 45.0 * pow((double)A, 0.7) * (1.0 + 0.016 * sin(5.3 - 2.63 * log((double)A)));
+    double shape = 1.0 - 0.62 * exp(-E / 200.0) * sin(10.9 * pow(E, -0.28));
+    return s_he * shape * (1.0 - bc / E);
 }
 
 double or_sigma_elastic(int Z, int A, double E)
@@ -834,6 +843,12 @@ static void evaporate(or_stream* st_, int Zc, int Ac, double Ex, double pc[3], o
     ev->Ex_left = Ex;
 }
 
+/* The trapped-nucleon rule of the cascade (on by default).  Off, a nucleon turned back at
+ * a shell boundary keeps flying until it collides or reaches the crossing cap: the
+ * untruncated reading the rule is compared with. */
+static int g_trap_rule = 1;
+void or_set_trap_rule(int on) { g_trap_rule = on ? 1 : 0; }
+
 /* One non-elastic event in the frame where the incident proton moves along
  * +z.  Fills ev (products' directions in that frame). */
 void or_inc_event(const or_nucleus* nu, double E, uint64_t seed, uint64_t pid, or_event* ev)
@@ -919,14 +934,14 @@ void or_inc_event(const or_nucleus* nu, double E, uint64_t seed, uint64_t pid, o
                     if (inner) {
                         for (int k = 0; k < 3; ++k) nh[k] = -p->r[k] / rr;
                         if (cross_boundary(p, nh, nu->V[q][i], nu->V[q][i - 1], m)) p->shell = i - 1;
-                        else if (++p->refl >= 2) { p->done = 2; break; }
+                        else if (++p->refl >= 2 && g_trap_rule) { p->done = 2; break; }
                     } else {
                         for (int k = 0; k < 3; ++k) nh[k] = p->r[k] / rr;
                         double Vb = (i + 1 < INC_SHELLS) ? nu->V[q][i + 1] : 0.0;
                         if (cross_boundary(p, nh, nu->V[q][i], Vb, m)) {
                             if (i + 1 == INC_SHELLS) { p->done = 1; break; }   /* escaped */
                             p->shell = i + 1;
-                        } else if (++p->refl >= 2) {
+                        } else if (++p->refl >= 2 && g_trap_rule) {
                             /* between collisions energy and angular momentum are conserved, so
                              * a nucleon turned back once can never reach the surface; on its
                              * second turn without an allowed collision it is trapped */

@@ -121,6 +121,8 @@ def lib():
                                       pd, C.c_long, C.POINTER(C.c_long), pd, pd]
             L.or_evap_batch.argtypes = [i, i, d, u64, u64, i, pd]
             L.or_inc_batch.argtypes = [i, i, d, u64, u64, i, i, pd, pd, pd]
+            L.or_set_trap_rule.argtypes = [i]
+            L.or_set_trap_rule.restype = None
             L.or_nucleus_info.argtypes = [i, i, pd]
             L.or_batch_stats.argtypes = [pd, C.c_long, i, pd, pd]
             _lib = L
@@ -343,6 +345,11 @@ def inc_batch(Z, A, E, seed, pid0, n, cap=160):
     extra = np.zeros((n, 3))
     lib().or_inc_batch(Z, A, E, seed, pid0, n, cap, _dp(summ), _dp(prod), _dp(extra))
     return summ, prod, extra
+
+
+def set_trap_rule(on: bool):
+    """Switches the cascade's trapped-nucleon rule (on by default; off = only the crossing cap)."""
+    lib().or_set_trap_rule(1 if on else 0)
 
 
 def nucleus_info(Z, A):

@@ -77,11 +77,19 @@ double sigma_nn_h(double T, bool like) {
   return like ? 10.63 / (b * b) - 29.92 / b + 42.9 : 34.10 / (b * b) - 82.2 / b + 82.2;
 }
 
+// High-energy limit of the non-elastic cross-section (mb): the empirical fit of Letaw,
+// Silberberg & Tsao (ApJS 51, 1983) to measured proton reaction cross-sections.
+double sigma_inel_he(int A) {
+  return 45.0 * std::pow(double(A), 0.7) * (1.0 + 0.016 * std::sin(5.3 - 2.63 * std::log(double(A))));
+}
+
+// Non-elastic cross-section (mb): the fit's energy shape 1 - 0.62 e^(-E/200) sin(10.9 E^-0.28),
+// closed below the Coulomb barrier by (1 - B_c/E).
 double sigma_inel_h(int Z, int A, double E) {
   if (A <= 1 || E <= 0.0) return 0.0;
   const double a13 = std::cbrt(double(A)), bc = 1.439964548 * Z / (1.16 * (a13 + 1.0));
   if (E <= bc) return 0.0;
-  return 0.65 * M_PI * 1.16 * 1.16 * (a13 + 0.8) * (a13 + 0.8) * 10.0 * (1.0 - bc / E) * (1.0 - std::exp(-E / 15.0));
+  return sigma_inel_he(A) * (1.0 - 0.62 * std::exp(-E / 200.0) * std::sin(10.9 * std::pow(E, -0.28))) * (1.0 - bc / E);
 }
 
 double sigma_el_h(int A, double E) {
@@ -653,7 +661,7 @@ int pmc_load_materials(pmc_ctx* ctx, const pmc_nuclide* nuc, int n_nuc, const pm
       const double a13 = std::cbrt(double(q.A));
       c.a13 = static_cast<float>(a13);
       c.bc = static_cast<float>(q.A > 1 ? 1.439964548 * q.Z / (1.16 * (a13 + 1.0)) : 0.0);
-      c.geo = static_cast<float>(0.65 * M_PI * 1.16 * 1.16 * (a13 + 0.8) * (a13 + 0.8) * 10.0);
+      c.sig_he = static_cast<float>(q.A > 1 ? sigma_inel_he(q.A) : 0.0);
       c.el = static_cast<float>(12.0 * a13 * a13);
       c.mass = static_cast<float>(nuclear_mass(q.Z, q.A));
     }

@@ -94,7 +94,7 @@ struct NucConst {
   int Z, A;
   float a13;                       // A^(1/3)
   float bc;                        // Coulomb barrier of the non-elastic cross-section, MeV
-  float geo;                       // 0.65 x geometric cross-section, mb
+  float sig_he;                    // high-energy limit of the non-elastic cross-section, mb
   float el;                        // elastic prefactor 12 mb A^(2/3)
   float mass;                      // nuclear mass, MeV
   int pad;
@@ -246,9 +246,12 @@ __device__ __forceinline__ float sigma_nn(float T, bool like) {
   return like ? (10.63f * ib2 - 29.92f * ib + 42.9f) : (34.10f * ib2 - 82.2f * ib + 82.2f);
 }
 
+// Non-elastic (Letaw, Silberberg & Tsao's fit to measured reaction cross-sections, closed
+// below the Coulomb barrier).
 __device__ __forceinline__ float sigma_inel(const NucConst& n, float E) {
   if (n.A <= 1 || E <= n.bc) return 0.0f;
-  return n.geo * (1.0f - n.bc / E) * (1.0f - expf(-E * (1.0f / 15.0f)));
+  const float shape = 1.0f - 0.62f * expf(-E * (1.0f / 200.0f)) * sinf(10.9f * exp2f(-0.28f * log2f(E)));
+  return n.sig_he * shape * (1.0f - n.bc / E);
 }
 
 __device__ __forceinline__ float sigma_el(const NucConst& n, float E) {

@@ -113,12 +113,44 @@ def test_cross_section_properties():
     for Z, A in ((6, 12), (8, 16), (20, 40), (22, 48)):
         bc = 1.439964548 * Z / (1.16 * (A ** (1 / 3) + 1))
         assert si(Z, A, 0.999 * bc) == 0.0                  # closed below the Coulomb barrier
-        geo = 0.65 * math.pi * 1.16 ** 2 * (A ** (1 / 3) + 0.8) ** 2 * 10.0   # mb
-        assert si(Z, A, 1e6) == pytest.approx(geo, rel=1e-4)
-        assert 150 < si(Z, A, 150.0) < 1500                 # hundreds of mb, like measured data
+        assert si(Z, A, 1.5 * bc) > 0.0
     assert se(1, 1, 100.0) == snn(100.0, 1)
     assert snn(5.0, 1) == snn(10.0, 1)                     # clamped below 10 MeV
-    assert 15 < snn(200.0, 1) < 35 and 25 < snn(200.0, 0) < 60
+
+
+def test_nonelastic_cross_section_against_measured_data():
+    """Sec. II.A.4 (non-elastic cross-sections): the reading against measured proton reaction
+    cross-sections of 12C, 16O and 40Ca at 30-200 MeV, each within its stated band."""
+    si = O.f("or_sigma_inelastic")
+    rows = golden("proton_reaction_xs.txt")
+    assert len(rows) >= 9
+    for Z, A, E, ref, band in rows:
+        got = si(int(Z), int(A), float(E))
+        assert abs(got / float(ref) - 1.0) <= float(band), (Z, A, E, got, ref)
+    # the measured energy shape: larger near 30 MeV than at 100-200 MeV, for every target
+    for Z, A in ((6, 12), (8, 16), (20, 40)):
+        assert si(Z, A, 30.0) > 1.2 * si(Z, A, 150.0)
+
+
+def test_nn_cross_section_against_measured_data():
+    """Sec. II.A.4 (the cascade's NN cross-sections): the smooth fit against measured pp and np
+    total cross-sections."""
+    snn = O.f("or_sigma_nn")
+    for pair, T, ref, band in golden("nn_total_xs.txt"):
+        got = snn(float(T), 1 if pair == "pp" else 0)
+        assert abs(got / float(ref) - 1.0) <= float(band), (pair, T, got, ref)
+
+
+def test_elastic_cross_section_hand_worked_and_bounded():
+    """Sec. II.A.5 (total elastic cross-section): the reading at three hand-worked points, and
+    below the reaction cross-section wherever the nucleus absorbs (E >= 20 MeV): for a real,
+    non-negative profile S(b) <= 1, |1 - S|^2 <= 1 - S^2, so sigma_el <= sigma_R."""
+    si, se = O.f("or_sigma_inelastic"), O.f("or_sigma_elastic")
+    for Z, A, E, ref in golden("elastic_hand_worked.txt"):
+        assert se(int(Z), int(A), float(E)) == pytest.approx(float(ref), rel=1e-5)
+    for Z, A in ((6, 12), (7, 14), (8, 16), (15, 31), (20, 40), (22, 48)):
+        for E in np.geomspace(20.0, 250.0, 12):
+            assert 0.0 < se(Z, A, E) <= si(Z, A, E), (Z, A, E)
 
 
 def test_mass_formula_against_measured_binding():
@@ -279,6 +311,35 @@ def test_cascade_yields_are_physical():
     n_n = ((sp == 0) & valid).sum(1).mean()
     assert 0.8 < n_p < 4.0 and 0.5 < n_n < 3.5
     assert summ[:, 6].mean() < 10                                # few retries per event
+
+
+@pytest.mark.parametrize("Z,A", [(8, 16), (20, 40)])
+def test_trap_rule_leaves_yields_and_spectra_unchanged(Z, A):
+    """The cascade traps a nucleon on its second reflection without an allowed collision (a
+    reading, Sec. II.A.4: between collisions energy and angular momentum are conserved, so it
+    cannot reach the surface).  Against the untruncated rule (only the crossing cap), the
+    emitted proton and neutron yields per event agree within 3 standard errors and their
+    energy spectra are indistinguishable (KS); what the rule shifts is the excitation left
+    after the cascade (by a few per cent; it is then evaporated)."""
+    n, E = 5000, 200.0
+
+    def yields(on):
+        O.set_trap_rule(on)
+        try:
+            summ, prod, extra = O.inc_batch(Z, A, E, 21, 0, n)
+        finally:
+            O.set_trap_rule(True)
+        k = summ[:, 0].astype(int)
+        valid = np.arange(prod.shape[1])[None, :] < k[:, None]
+        sp, T = prod[:, :, 0], prod[:, :, 1]
+        return ((sp == 1) & valid).sum(1), ((sp == 0) & valid).sum(1), T[(sp == 1) & valid], T[(sp == 0) & valid]
+
+    a, b = yields(True), yields(False)
+    for x, y in ((a[0], b[0]), (a[1], b[1])):
+        se = math.sqrt(x.var() / n + y.var() / n)
+        assert abs(x.mean() - y.mean()) < 3 * se, (x.mean(), y.mean(), se)
+    for x, y in ((a[2], b[2]), (a[3], b[3])):
+        assert stats.ks_2samp(x, y).pvalue > 1e-3
 
 
 # ---------------------------------------------------------------- bookkeeping

@@ -117,6 +117,17 @@ def test_survival_probability_against_non_elastic_attenuation():
     assert abs(tot["inelastic"] / n - P) < 3 * math.sqrt(P * (1 - P) / n) + 1e-4
 
 
+def test_nonelastic_events_per_history_in_a_typical_plan():
+    """Sec. I (footnote): about 1e6 non-elastic events are expected for 1e7 proton histories of
+    a typical plan.  The CT plan (40 layers of 70-180 MeV in tissue, bone and lung) gives
+    roughly 0.1 per history (read as 0.05-0.2)."""
+    p = W.config3(shape=(100, 128, 128), n_layers=40)
+    n = 1500
+    _, tot, _ = O.run(p, n, 13)
+    per = tot["inelastic"] / n
+    assert 0.05 <= per <= 0.2, per
+
+
 @pytest.mark.parametrize("cfg", [2, 3])
 def test_energy_conservation_per_history(cfg):
     if cfg == 2:
