@@ -167,6 +167,28 @@ int pmc_read_history_ledger(pmc_ctx* ctx, int64_t* out, uint64_t n_histories);
 int pmc_enable_escape_record(pmc_ctx* ctx, uint64_t cap);
 int pmc_read_escape_record(pmc_ctx* ctx, float* out, uint64_t cap, uint64_t* n);
 
+/* Debug deposit log: pins the fixed-point tally (Sec. II.B.3: dose tallies updated by
+ * atomic operations; here 64-bit integers in units of 2^-24 MeV).  With the log enabled,
+ * every deposit of the next transports (condensed-history steps, absorbed protons, elastic
+ * recoils, cascade and evaporation fragments, residual nuclei) is also recorded as the
+ * energies it was computed from: tally entry [voxel][group] received
+ *   llrint(e[0] 2^24) - llrint(e[1] 2^24) - llrint(e[2] 2^24)   (round half to even),
+ * so the integer sum of the log equals the tally bit for bit.  Meant for small runs
+ * (<= about 1e3 histories: some 200 records per history).  The log runs the full cascade
+ * with the paper's physics options only (Highland, Bohr, no LET): pmc_transport returns
+ * PMC_E_INVALID otherwise.
+ * pmc_enable_deposit_log: room for cap records on the device (32 bytes each); 0 frees it.
+ * pmc_read_deposit_log: copies min(records, cap) records of the last transport to out and
+ *   the number logged to *n; PMC_E_QUEUE_OVERFLOW when the log was too small (the records
+ *   beyond its capacity are lost), PMC_E_INVALID when it is not enabled. */
+typedef struct {
+  int32_t voxel;             /* v = (iz * ny + iy) * nx + ix */
+  int32_t group;             /* statistical group h mod n_batches */
+  double e[3];               /* MeV: deposit = fix(e[0]) - fix(e[1]) - fix(e[2]) */
+} pmc_deposit;
+int pmc_enable_deposit_log(pmc_ctx* ctx, uint64_t cap);
+int pmc_read_deposit_log(pmc_ctx* ctx, pmc_deposit* out, uint64_t cap, uint64_t* n);
+
 /* Dose-averaged LET scored beside the dose (Sec. IV: LET_d computed together with
  * the physical dose).  Every energy loss q of a transported proton (the steps, and
  * the remainder of a proton absorbed below E_cut or within its residual range) is
@@ -215,27 +237,34 @@ int pmc_enable_profile(pmc_ctx* ctx, int on);
 int pmc_read_profile(pmc_ctx* ctx, double* ms, int64_t* launches, int64_t* primary_steps);
 
 /* Transport that allocates no device memory (the paper has no counterpart).
- * For callers that cannot call cudaMalloc during a dose calculation -- a host
- * callback or real-time loop that must not synchronise or stall on the
- * allocator, or an application that gave its whole device memory to its own
- * pool.  Runs the same kernels and physics as pmc_transport and produces the
- * same tallies for the same seed, with all scratch (particle queues, the
- * residual nuclei between cascade and evaporation, counters, spot table, seed)
- * in one static device array of
- * PMC_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
- * the process exits.  Inputs are the context's loaded materials, phantom and
- * spots; outputs are caller-owned device arrays: tally [n_voxels][n_batches]
- * int64 (units of 2^-24 MeV, zeroed by the call) and, optionally (both or
- * neither), dose_gy and sigma_gy [n_voxels].  At most PMC_NOALLOC_MAX_SPOTS
- * spots may receive histories; more is rejected with PMC_E_INVALID.  All
- * calls on a device share the array and it keeps the last call's contents;
- * calls whose work overlaps on the GPU race on it.  The first call on a
- * device looks up the array's address, so make it before any stream capture.
- * Blocks until done; pmc_read_ledger then reports this run. */
+ * For callers that cannot call cudaMalloc during a dose calculation -- a
+ * real-time loop that must not stall on the allocator, or an application that
+ * gave its whole device memory to its own pool.  The call itself synchronises
+ * its stream after every generation and blocks until the run is done, so it
+ * cannot be made from a CUDA stream callback (no CUDA call is allowed there) or
+ * inside a stream capture.  It runs the full cascade (never the learned
+ * stand-in), with the context's physics options, and produces the same tallies
+ * as pmc_transport for the same seed; it does not score LET, the per-history
+ * ledger, the escape record or the deposit log, and pmc_read_dose / pmc_read_let
+ * keep returning the last allocating run's results (the caller's arrays hold
+ * this run's).  All scratch (three particle queues, the residual nuclei
+ * between cascade and evaporation, counters, spot table, seed) lives in one
+ * static device array of PMC_NOALLOC_SCRATCH_BYTES that every GPU loading this
+ * library holds until the process exits.  Inputs are the context's loaded
+ * materials, phantom and spots; outputs are caller-owned device arrays: tally
+ * [n_voxels][n_batches] int64 (units of 2^-24 MeV, zeroed by the call) and,
+ * optionally (both or neither), dose_gy and sigma_gy [n_voxels].  At most
+ * PMC_NOALLOC_MAX_SPOTS spots may receive histories; more is rejected with
+ * PMC_E_INVALID.  All calls on a device share the array and it keeps the last
+ * call's contents (each call clears what must start at zero); calls from
+ * several host threads of one process are serialised per device by a lock, and
+ * work of another process never shares it.  The first call on a device looks up
+ * the array's device address (once per device, thread-safe).  Blocks until done;
+ * pmc_read_ledger then reports this run. */
 #define PMC_NOALLOC_CHUNK 65536          /* histories per sub-group */
 #define PMC_NOALLOC_MAX_SPOTS 4096
 #define PMC_NOALLOC_SCRATCH_BYTES \
-    (4ull * PMC_NOALLOC_CHUNK * 48ull + PMC_NOALLOC_CHUNK * 128ull + 768ull + PMC_NOALLOC_MAX_SPOTS * 56ull)
+    (3ull * PMC_NOALLOC_CHUNK * 48ull + PMC_NOALLOC_CHUNK * 128ull + 768ull + PMC_NOALLOC_MAX_SPOTS * 56ull)
 int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int64_t* tally,
                           double* dose_gy, double* sigma_gy, void* stream);
 
@@ -400,6 +429,18 @@ int pmc_debug_tables(pmc_ctx* ctx, int material, const double* E, double* r_out,
 int pmc_debug_inc(pmc_ctx* ctx, int nuclide, double E, uint64_t seed, uint64_t pid0, int n,
                   double* summary, double* products, int cap);
 int pmc_debug_elastic(pmc_ctx* ctx, int nuclide, double E, const double* u, double* out, int n);
+
+/* The event stage on its own: n non-elastic events (proton of energy E[i] MeV on nuclide
+ * nuclide[i], A >= 2, moving along +z, random streams keyed by seed and identity i) through
+ * the cascade and evaporation kernels (mode PMC_FULL_CASCADE, Sec. II.A.4) or through the
+ * learned stand-in's event kernel (PMC_SURROGATE; needs a trained or loaded network) -- the
+ * same kernels the transport runs.  Emitted protons (those above E_cut, which the transport
+ * would queue) go to protons [cap][3] as (event index, kinetic energy MeV, cosine to the
+ * incident direction), their number to *n_protons; local[i] (n doubles, or NULL) receives the
+ * energy event i deposits locally (MeV).  PMC_E_QUEUE_OVERFLOW when more than cap protons
+ * were emitted (the first cap are copied). */
+int pmc_debug_event_stage(pmc_ctx* ctx, int mode, const int* nuclide, const double* E, int n, uint64_t seed,
+                          float* protons, uint64_t cap, uint64_t* n_protons, double* local);
 /* pmc_debug_surrogate_waits: runs the tensor-core network on one 128-row tile with its MMAs
  * withheld and short mbarrier waits, so that every wait runs out: returns PMC_E_TIMEOUT
  * (the block stops, frees its tensor memory and reports), and the context stays usable.

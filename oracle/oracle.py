@@ -261,20 +261,28 @@ def run_parallel(prob, n_hist: int, seed: int, procs: int | None = None, let: bo
     fields = {k: getattr(prob, k) for k in _PROBLEM_FIELDS}
     cuts = [n_hist * i // procs for i in range(procs + 1)]
     jobs = [(fields, n_hist, seed, cuts[i], cuts[i + 1], let) for i in range(procs)]
-    if procs == 1:
-        parts = [_run_range(jobs[0])]
-    else:
-        with mp.get_context("spawn").Pool(procs) as pool:
-            parts = pool.map(_run_range, jobs)
-    sums = [np.zeros_like(parts[0][0]) for _ in range(3 if let else 1)]
-    totals = {k: 0.0 for k in parts[0][1]}
-    for part in parts:
+    sums, totals = None, None
+
+    def add(part):
+        nonlocal sums, totals
+        if sums is None:
+            sums = [np.zeros_like(part[0]) for _ in range(3 if let else 1)]
+            totals = {k: 0.0 for k in part[1]}
         sums[0] += part[0]
         if let:
             sums[1] += part[2]
             sums[2] += part[3]
         for k in totals:
             totals[k] += part[1][k]
+
+    if procs == 1:
+        add(_run_range(jobs[0]))
+    else:
+        # parts arrive in range order and are summed as they come (one large tally in flight
+        # at a time, not one per worker)
+        with mp.get_context("spawn").Pool(procs) as pool:
+            for part in pool.imap(_run_range, jobs):
+                add(part)
     if let:
         return sums[0], totals, sums[1], sums[2]
     return sums[0], totals

@@ -421,8 +421,10 @@ struct TransportSink {
   long long dep, esc, bnd;
   unsigned long long sec, dropped, retries, n_transparent;
   long long fE;            // fixed-point energy handed to the event
-  __device__ void add_dep(long long q) {
+  // q = llrint(e 2^24): the deposit of energy e (MeV) at the event's voxel
+  __device__ void add_dep(long long q, double e) {
     atomicAdd(a->tally + static_cast<size_t>(ev.voxel) * a->B + b, static_cast<unsigned long long>(q));
+    if (a->dlog) log_deposit(a->dlog, a->dlog_count, a->dlog_cap, ev.voxel, b, e, 0.0, 0.0);
     dep += q;
     if (a->hist && ev.root < a->hist_n)
       atomicAdd(reinterpret_cast<unsigned long long*>(a->hist + 4ull * ev.root + 1), static_cast<unsigned long long>(q));
@@ -447,22 +449,22 @@ struct TransportSink {
       ++sec;
     } else {
       ++dropped;
-      add_dep(fix(T));
+      add_dep(fix(T), T);
     }
   }
   __device__ void product(int k, int species, double T, float ax, float ay, float az) {
     if (species == 1) {
       const float Tf = static_cast<float>(T);
       if (Tf > kEcut) queue(Tf, frame_to_lab(ev.u, ev.v, ev.w, ax, ay, az), static_cast<unsigned>(k));
-      else add_dep(fixd(T));
+      else add_dep(fixd(T), T);
     } else if (species == 0) {
       add_esc(fixd(T));
     } else {
-      add_dep(fixd(T));
+      add_dep(fixd(T), T);
     }
   }
   __device__ void residual(int, int, double Tres, double Ex, double bind, int r) {
-    add_dep(fixd(Tres));
+    add_dep(fixd(Tres), Tres);
     add_esc(fixd(Ex));
     add_bind(fixd(bind));
     retries += r;

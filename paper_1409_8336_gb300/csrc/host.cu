@@ -460,6 +460,8 @@ struct pmc_ctx {
   DevBuf d_yields;                      // event-generator totals
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   DevBuf d_let_num, d_let_den, d_let, d_let_sigma;   // dose-averaged LET tallies and results
+  DevBuf d_dlog, d_dlog_cnt;            // debug deposit log and its record count
+  uint64_t dlog_cap = 0;
   size_t q_cap = 0;
   int block = 0;
   int64_t chunk = 0;
@@ -622,7 +624,8 @@ void pmc_destroy(pmc_ctx* ctx) {
                     &ctx->d_rho, &ctx->d_hu, &ctx->d_tally, &ctx->d_dose, &ctx->d_sigma, &ctx->d_counters,
                     &ctx->d_counts, &ctx->d_seed, &ctx->d_spots, &ctx->d_q[0], &ctx->d_q[1], &ctx->d_q[2],
                     &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_hist, &ctx->d_esc,
-                    &ctx->d_let_num, &ctx->d_let_den, &ctx->d_let, &ctx->d_let_sigma, &ctx->d_yields};
+                    &ctx->d_let_num, &ctx->d_let_den, &ctx->d_let, &ctx->d_let_sigma, &ctx->d_yields,
+                    &ctx->d_dlog, &ctx->d_dlog_cnt};
   if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
   if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
   for (DevBuf* b : bufs) dfree(ctx, *b);
@@ -950,6 +953,40 @@ int pmc_enable_escape_record(pmc_ctx* ctx, uint64_t cap) {
   return PMC_OK;
 }
 
+int pmc_enable_deposit_log(pmc_ctx* ctx, uint64_t cap) {
+  if (!ctx) return PMC_E_INVALID;
+  if (cap > (1ull << 30)) return fail(ctx, PMC_E_INVALID, "deposit log capacity above 2^30 records");
+  cudaSetDevice(ctx->opt.device);
+  int rc;
+  if (cap == 0) {
+    dfree(ctx, ctx->d_dlog);
+    dfree(ctx, ctx->d_dlog_cnt);
+  } else {
+    if ((rc = dalloc(ctx, ctx->d_dlog, cap * sizeof(DepositRecord)))) return rc;
+    if ((rc = dalloc(ctx, ctx->d_dlog_cnt, sizeof(unsigned long long)))) return rc;
+    CK(cudaMemsetAsync(ctx->d_dlog_cnt.p, 0, sizeof(unsigned long long), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  ctx->dlog_cap = cap;
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  return PMC_OK;
+}
+
+int pmc_read_deposit_log(pmc_ctx* ctx, pmc_deposit* out, uint64_t cap, uint64_t* n) {
+  if (!ctx || !n || (cap && !out)) return PMC_E_INVALID;
+  if (!ctx->dlog_cap) return fail(ctx, PMC_E_INVALID, "the deposit log is not enabled");
+  static_assert(sizeof(pmc_deposit) == sizeof(DepositRecord), "deposit record layout");
+  cudaSetDevice(ctx->opt.device);
+  unsigned long long cnt = 0;
+  CK(cudaMemcpy(&cnt, ctx->d_dlog_cnt.p, sizeof(cnt), cudaMemcpyDeviceToHost));
+  *n = cnt;
+  const uint64_t k = std::min<uint64_t>(std::min<uint64_t>(cnt, ctx->dlog_cap), cap);
+  if (k) CK(cudaMemcpy(out, ctx->d_dlog.p, k * sizeof(DepositRecord), cudaMemcpyDeviceToHost));
+  if (cnt > ctx->dlog_cap)
+    return fail(ctx, PMC_E_QUEUE_OVERFLOW, "%llu deposits, the log holds %llu", cnt, (unsigned long long)ctx->dlog_cap);
+  return PMC_OK;
+}
+
 }  // extern "C"
 
 namespace {
@@ -1044,6 +1081,11 @@ TransportArgs transport_args(pmc_ctx* ctx) {
     a.let_num = static_cast<unsigned long long*>(ctx->d_let_num.p);
     a.let_den = static_cast<unsigned long long*>(ctx->d_let_den.p);
   }
+  if (ctx->dlog_cap) {
+    a.dlog = static_cast<DepositRecord*>(ctx->d_dlog.p);
+    a.dlog_count = static_cast<unsigned long long*>(ctx->d_dlog_cnt.p);
+    a.dlog_cap = ctx->dlog_cap;
+  }
   return a;
 }
 
@@ -1059,6 +1101,11 @@ CascadeArgs cascade_args(pmc_ctx* ctx) {
   c.cnt = static_cast<Counters*>(ctx->d_counters.p);
   c.hist = static_cast<long long*>(ctx->d_hist.p);
   c.hist_n = ctx->hist_n;
+  if (ctx->dlog_cap) {
+    c.dlog = static_cast<DepositRecord*>(ctx->d_dlog.p);
+    c.dlog_count = static_cast<unsigned long long*>(ctx->d_dlog_cnt.p);
+    c.dlog_cap = ctx->dlog_cap;
+  }
   return c;
 }
 
@@ -1143,6 +1190,7 @@ int enqueue_run(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s) {
   CK(cudaMemsetAsync(ctx->d_counters.p, 0, sizeof(Counters), s));
   CK(cudaMemsetAsync(ctx->d_counts.p, 0, (static_cast<size_t>(rp.n_chunks) * kSlots + 1) * sizeof(unsigned), s));
   if (ctx->d_hist.p) CK(cudaMemsetAsync(ctx->d_hist.p, 0, ctx->hist_n * 4 * sizeof(long long), s));
+  if (ctx->dlog_cap) CK(cudaMemsetAsync(ctx->d_dlog_cnt.p, 0, sizeof(unsigned long long), s));
   if (ctx->let_on) {
     CK(cudaMemsetAsync(ctx->d_let_num.p, 0, static_cast<size_t>(ctx->n_vox) * ctx->opt.n_batches * 8, s));
     CK(cudaMemsetAsync(ctx->d_let_den.p, 0, static_cast<size_t>(ctx->n_vox) * ctx->opt.n_batches * 8, s));
@@ -1203,6 +1251,8 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
   if (mode != PMC_FULL_CASCADE && mode != PMC_SURROGATE) return fail(ctx, PMC_E_INVALID, "unknown mode %d", mode);
   if (mode == PMC_SURROGATE && !ctx->surr_trained)
     return fail(ctx, PMC_E_INVALID, "the surrogate is not trained (pmc_train_surrogate or pmc_surrogate_load)");
+  if (ctx->dlog_cap && (mode != PMC_FULL_CASCADE || ctx->let_on || ctx->d_mol.p || ctx->d_vav.p))
+    return fail(ctx, PMC_E_INVALID, "the deposit log runs the full cascade with Highland, Bohr and no LET only");
   if (n_histories == 0) return fail(ctx, PMC_E_INVALID, "n_histories must be > 0");
   if (n_histories > 0xFFFFFFFFull) return fail(ctx, PMC_E_INVALID, "at most 2^32-1 histories per call");
   double wsum = 0.0;
@@ -1279,9 +1329,10 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     CK(cudaMemcpyAsync(ctx->d_seed.p, &seed, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
     // graph of the whole run, rebuilt when its shape changes
     char key[256];
-    std::snprintf(key, sizeof(key), "%llu/%lld/%zu/%d/%d/%lld/%p/%p/%p/%d", (unsigned long long)n_histories,
+    std::snprintf(key, sizeof(key), "%llu/%lld/%zu/%d/%d/%lld/%p/%p/%p/%d/%p", (unsigned long long)n_histories,
                   (long long)rp.chunk, sd.size(), ctx->block, ctx->opt.n_batches, ctx->n_vox, ctx->d_tally.p,
-                  ctx->d_hist.p, ctx->let_on ? ctx->d_let_num.p : nullptr, ctx->profile + 3 * mode);
+                  ctx->d_hist.p, ctx->let_on ? ctx->d_let_num.p : nullptr, ctx->profile + 3 * mode,
+                  ctx->dlog_cap ? ctx->d_dlog.p : nullptr);
     if (!ctx->gexec || ctx->gkey != key) {
       if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
       cudaGraph_t graph;
@@ -1592,30 +1643,139 @@ int pmc_debug_elastic(pmc_ctx* ctx, int nuclide, double E, const double* u, doub
   return PMC_OK;
 }
 
+int pmc_debug_event_stage(pmc_ctx* ctx, int mode, const int* nuclide, const double* E, int n, uint64_t seed,
+                          float* protons, uint64_t cap, uint64_t* n_protons, double* local) {
+  if (!ctx || !nuclide || !E || n <= 0 || n > (1 << 24) || !n_protons || (cap && !protons)) return PMC_E_INVALID;
+  if (!ctx->have_materials) return fail(ctx, PMC_E_INVALID, "load materials first");
+  if (mode != PMC_FULL_CASCADE && mode != PMC_SURROGATE) return fail(ctx, PMC_E_INVALID, "unknown mode %d", mode);
+  if (mode == PMC_SURROGATE && !ctx->surr_trained) return fail(ctx, PMC_E_INVALID, "the surrogate is not trained");
+  std::vector<Particle> ev(static_cast<size_t>(n));
+  for (int i = 0; i < n; ++i) {
+    const int k = nuclide[i];
+    if (k < 0 || k >= ctx->phys.n_nuc || ctx->phys.nuc[k].A < 2)
+      return fail(ctx, PMC_E_INVALID, "event %d: nuclide %d has no non-elastic channel", i, k);
+    if (!(E[i] > 0.0 && E[i] <= 400.0)) return fail(ctx, PMC_E_INVALID, "event %d: energy %g MeV", i, E[i]);
+    Particle& r = ev[static_cast<size_t>(i)];
+    r.x = r.y = r.z = 0.0f;
+    r.u = r.v = 0.0f;
+    r.w = 1.0f;
+    r.E = static_cast<float>(E[i]);
+    r.voxel = i;
+    r.pid = static_cast<unsigned long long>(i);
+    r.root = static_cast<unsigned>(i);
+    r.target = k;
+  }
+  cudaSetDevice(ctx->opt.device);
+  const unsigned qcap = 32u * static_cast<unsigned>(n) + 1024u;
+  DevBuf d_ev, d_out, d_cnt, d_tal, d_ctr, d_seed, d_rec;
+  auto release_all = [&] {
+    cudaStreamSynchronize(ctx->stream);
+    for (DevBuf* b : {&d_ev, &d_out, &d_cnt, &d_tal, &d_ctr, &d_seed, &d_rec}) dfree(ctx, *b);
+  };
+  int rc = 0;
+  if ((rc = dalloc(ctx, d_ev, ev.size() * sizeof(Particle))) || (rc = dalloc(ctx, d_out, qcap * sizeof(Particle))) ||
+      (rc = dalloc(ctx, d_cnt, 4 * sizeof(unsigned))) || (rc = dalloc(ctx, d_tal, static_cast<size_t>(n) * 8)) ||
+      (rc = dalloc(ctx, d_ctr, sizeof(Counters))) || (rc = dalloc(ctx, d_seed, sizeof(uint64_t))) ||
+      (mode == PMC_FULL_CASCADE && (rc = dalloc(ctx, d_rec, static_cast<size_t>(n) * sizeof(EvapRecord))))) {
+    release_all();
+    return rc;
+  }
+  cudaStream_t s = ctx->stream;
+  unsigned* cnt = static_cast<unsigned*>(d_cnt.p);
+  const unsigned nu = static_cast<unsigned>(n);
+  cudaError_t e = cudaMemcpyAsync(d_ev.p, ev.data(), ev.size() * sizeof(Particle), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, &nu, sizeof(unsigned), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_tal.p, 0, static_cast<size_t>(n) * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_ctr.p, 0, sizeof(Counters), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_seed.p, &seed, sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    if (mode == PMC_FULL_CASCADE) {
+      CascadeArgs c = cascade_args(ctx);
+      c.tally = static_cast<unsigned long long*>(d_tal.p);
+      c.B = 1;
+      c.seed = static_cast<const unsigned long long*>(d_seed.p);
+      c.cnt = static_cast<Counters*>(d_ctr.p);
+      c.hist = nullptr;
+      c.hist_n = 0;
+      c.dlog = nullptr;
+      c.dlog_count = nullptr;
+      c.dlog_cap = 0;
+      c.qne = static_cast<const Particle*>(d_ev.p);
+      c.qne_count = cnt;
+      c.qne_cap = nu;
+      c.qsec = static_cast<Particle*>(d_out.p);
+      c.qsec_count = cnt + 1;
+      c.qsec_cap = qcap;
+      c.work = cnt + 2;
+      c.rec = static_cast<EvapRecord*>(d_rec.p);
+      c.rec_count = cnt + 3;
+      c.rec_cap = nu;
+      e = launch_cascade(c, s);
+    } else {
+      e = launch_surrogate_events(cnt, nu, static_cast<const Particle*>(d_ev.p),
+                                  static_cast<const int*>(ctx->d_nuc_slot.p),
+                                  static_cast<const unsigned long long*>(d_seed.p), ctx->d_swb.p,
+                                  static_cast<const float*>(ctx->d_sp.p), static_cast<unsigned long long*>(d_tal.p), 1,
+                                  static_cast<Particle*>(d_out.p), cnt + 1, qcap, static_cast<Counters*>(d_ctr.p),
+                                  nullptr, 0, ctx->n_sm * 2, s);
+    }
+  }
+  unsigned hc[4] = {0, 0, 0, 0};
+  Counters ctr{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ctr, d_ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  const unsigned emitted = std::min(hc[1], qcap);
+  std::vector<Particle> out(emitted);
+  std::vector<long long> tal(local ? static_cast<size_t>(n) : 0);
+  if (e == cudaSuccess && emitted)
+    e = cudaMemcpy(out.data(), d_out.p, emitted * sizeof(Particle), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && local) e = cudaMemcpy(tal.data(), d_tal.p, static_cast<size_t>(n) * 8, cudaMemcpyDeviceToHost);
+  release_all();
+  if (e != cudaSuccess) return fail(ctx, PMC_E_CUDA, "event stage: %s", cudaGetErrorString(e));
+  if (ctr.errors) return fail(ctx, PMC_E_TIMEOUT, "event stage: %llu device waits timed out", (unsigned long long)ctr.errors);
+  *n_protons = emitted;
+  const uint64_t k = std::min<uint64_t>(emitted, cap);
+  for (uint64_t i = 0; i < k; ++i) {
+    protons[3 * i] = static_cast<float>(out[i].root);
+    protons[3 * i + 1] = out[i].E;
+    protons[3 * i + 2] = out[i].w;
+  }
+  if (local)
+    for (int i = 0; i < n; ++i) local[i] = static_cast<double>(tal[static_cast<size_t>(i)]) / 16777216.0;
+  if (ctr.dropped || hc[1] > qcap) return fail(ctx, PMC_E_QUEUE_OVERFLOW, "event stage: proton queue full");
+  if (emitted > cap) return fail(ctx, PMC_E_QUEUE_OVERFLOW, "%u protons, room for %llu", emitted, (unsigned long long)cap);
+  return PMC_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
 // Transport without device allocation.
 //
 // Some callers cannot allocate device memory while they run a dose
-// calculation: a host callback or a real-time control loop may not call
-// cudaMalloc (it can synchronise the device or stall behind other work), and
-// a caller with its own fixed memory budget may have handed the whole GPU to
-// its pool.  This entry point runs the same kernels as pmc_transport but keeps
-// every piece of scratch (particle queues, counters, spot table, seed) in one
-// static device array; the caller supplies the output arrays.
+// calculation: a real-time control loop may not call cudaMalloc (it can
+// synchronise the device or stall behind other work), and a caller with its
+// own fixed memory budget may have handed the whole GPU to its pool.  This
+// entry point runs the same kernels as pmc_transport (the full cascade) but
+// keeps every piece of scratch (particle queues, counters, spot table, seed)
+// in one static device array; the caller supplies the output arrays.  It
+// synchronises its stream after every generation, so it cannot run inside a
+// stream callback or a stream capture.
 //
 // The array lives in every GPU that loads this library until the process
 // exits.  All calls on a device share it and it keeps the last call's
-// contents: each call clears what must start at zero, and calls whose work
-// overlaps on the GPU (different threads or streams) race on it.  The first
-// call on a device looks up the array's device address; make that first call
-// before any stream capture.
+// contents: each call clears what must start at zero.  Calls from several host
+// threads are serialised per device by a lock (the call is synchronous, so this
+// keeps their work from overlapping on the GPU).  The array's device address
+// is looked up once per device, on the first call there, with that device
+// current.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr size_t kNaQueue = static_cast<size_t>(PMC_NOALLOC_CHUNK) * sizeof(Particle);
-constexpr size_t kNaRec = 4 * kNaQueue;
+constexpr size_t kNaRec = 3 * kNaQueue;   // queues: generation input, output, events
 constexpr size_t kNaCounters = kNaRec + static_cast<size_t>(PMC_NOALLOC_CHUNK) * sizeof(EvapRecord);
 constexpr size_t kNaCounts = kNaCounters + 256;
 constexpr size_t kNaSeed = kNaCounts + 256;
@@ -1627,7 +1787,13 @@ static_assert(sizeof(Counters) <= 256, "counters fit their slot");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
 constexpr int kNaMaxDevices = 64;
-unsigned char* g_noalloc_addr[kNaMaxDevices] = {};
+struct NoallocSlot {
+  std::once_flag once;             // the address lookup, once per device
+  cudaError_t status = cudaSuccess;
+  unsigned char* addr = nullptr;
+  std::mutex run;                  // one call at a time per device
+};
+NoallocSlot g_noalloc[kNaMaxDevices];
 
 }  // namespace
 
@@ -1673,15 +1839,20 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
       return fail(ctx, PMC_E_INVALID, "%zu spots with histories exceed the no-allocation limit of %d", sd.size(),
                   PMC_NOALLOC_MAX_SPOTS);
     CK(cudaSetDevice(dev));
-    if (!g_noalloc_addr[dev]) {
+    NoallocSlot& slot = g_noalloc[dev];
+    std::call_once(slot.once, [&slot] {
       void* p = nullptr;
-      CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-      g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
-    }
-    unsigned char* base = g_noalloc_addr[dev];
+      slot.status = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // the current device is dev
+      if (slot.status == cudaSuccess) slot.addr = static_cast<unsigned char*>(p);
+      else cudaGetLastError();
+    });
+    if (slot.status != cudaSuccess)
+      return fail(ctx, PMC_E_CUDA, "address of the no-allocation scratch: %s", cudaGetErrorString(slot.status));
+    std::lock_guard<std::mutex> hold(slot.run);
+    unsigned char* base = slot.addr;
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
-    Particle* q[4];
-    for (int i = 0; i < 4; ++i) q[i] = reinterpret_cast<Particle*>(base + i * kNaQueue);
+    Particle* q[3];
+    for (int i = 0; i < 3; ++i) q[i] = reinterpret_cast<Particle*>(base + i * kNaQueue);
     Counters* counters = reinterpret_cast<Counters*>(base + kNaCounters);
     unsigned* counts = reinterpret_cast<unsigned*>(base + kNaCounts);
     unsigned long long* dseed = reinterpret_cast<unsigned long long*>(base + kNaSeed);

@@ -20,6 +20,28 @@ struct SpotDev {
   unsigned long long h_first, w_first;
 };
 
+// One logged deposit (the debug deposit log): the tally entry (voxel, group) received
+// llrint(e[0] 2^24) - llrint(e[1] 2^24) - llrint(e[2] 2^24) units of 2^-24 MeV.
+struct DepositRecord {
+  int voxel, group;
+  double e[3];
+};
+static_assert(sizeof(DepositRecord) == 32, "deposit record is 32 bytes");
+
+__device__ __forceinline__ void log_deposit(DepositRecord* log, unsigned long long* count, unsigned long long cap,
+                                            int v, unsigned b, double e0, double e1, double e2) {
+  const unsigned long long i = atomicAdd(count, 1ull);
+  if (i < cap) {
+    DepositRecord r;
+    r.voxel = v;
+    r.group = static_cast<int>(b);
+    r.e[0] = e0;
+    r.e[1] = e1;
+    r.e[2] = e2;
+    log[i] = r;
+  }
+}
+
 struct TransportArgs {
   const Physics* phys;
   const float2* rtab;              // [n_cls][kNE] range splines
@@ -52,6 +74,9 @@ struct TransportArgs {
   unsigned long long esc_cap;
   unsigned long long* let_num;     // [n_voxels][B] sum of q * LET (2^-24 MeV keV/um), or NULL
   unsigned long long* let_den;     // [n_voxels][B] sum of q over the same deposits (2^-24 MeV)
+  DepositRecord* dlog;             // debug deposit log [dlog_cap], or NULL
+  unsigned long long* dlog_count;
+  unsigned long long dlog_cap;
 };
 
 // A residual nucleus handed from the cascade kernel to the evaporation kernel:
@@ -87,6 +112,9 @@ struct CascadeArgs {
   unsigned* rec_count;
   unsigned rec_cap;
   unsigned* work;                  // event counter of the cascade kernel
+  DepositRecord* dlog;             // debug deposit log [dlog_cap], or NULL
+  unsigned long long* dlog_count;
+  unsigned long long dlog_cap;
 };
 
 struct StatsArgs {

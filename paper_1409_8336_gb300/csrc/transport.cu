@@ -146,13 +146,14 @@ __device__ __forceinline__ Particle make_record(const PState& p, float E, float 
 // One condensed-history step (Sec. II.A.3).  Returns false when the particle ends.  kLet, kMol
 // and kVav compile the LET scoring, the Moliere option and the Vavilov option in; without
 // them the step carries no test for any of them.
-template <bool kLet, bool kMol, bool kVav>
+template <bool kLet, bool kMol, bool kVav, bool kLog>
 __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt, const float2* et,
                      const float* st, const float4* mol, uint2 key, PState& p, Acc& acc) {
   const int v = vindex(a.g, p.ix, p.iy, p.iz);
   if (p.E <= kEcut) {
     const long long q = fix(p.E);
     deposit(a, v, p, q, acc);
+    if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, 0.0, 0.0);
     if (kLet && p.E > 0.0f) {   // absorbed over its residual range: L = E / R
       int m0;
       float rho0;
@@ -163,7 +164,12 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
     }
     return false;
   }
-  if (p.k >= kMaxSteps) { deposit(a, v, p, fix(p.E), acc); acc.errors++; return false; }
+  if (p.k >= kMaxSteps) {
+    deposit(a, v, p, fix(p.E), acc);
+    if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, 0.0, 0.0);
+    acc.errors++;
+    return false;
+  }
   // the step's uniforms depend only on the particle's identity and step count: drawn
   // first, their Philox rounds interleave with the table lookups below
   const StepUniforms ua = step_uniforms(key, p.pid, p.k);
@@ -184,6 +190,7 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   if (Rcm <= lam && Rcm <= d) {
     const long long q = fix(E0);
     deposit(a, v, p, q, acc);
+    if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, E0, 0.0, 0.0);
     if (kLet && Rcm > 0.0f) score_let(a, v, p, q, 0.1f * E0 / Rcm);
     return false;
   }
@@ -260,6 +267,7 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   {
     const long long q = fix(E0) - fix(E1);
     deposit(a, v, p, q, acc);
+    if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, E0, E1, 0.0);
     if (kLet) {
       // mean stopping power over the path: the CSDA loss over s, taken as a difference
       // of two values of the inverse range table (free of the E -> R -> E round trip,
@@ -322,6 +330,7 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
     if (!push(a.qne, a.qne_count, a.qne_cap, make_record(p, p.E, p.u, p.v, p.w, p.pid, v, nuc))) {
       acc.dropped++;
       deposit(a, v, p, fix(p.E), acc);
+      if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, 0.0, 0.0);
     }
     return false;
   }
@@ -341,12 +350,15 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
     if (push(a.qsec, a.qsec_count, a.qsec_cap, make_record(p, eo.T2, ru, rv, rw, cid, v, -1))) {
       acc.sec++;
       deposit(a, v, p, qE - q1 - fix(eo.T2), acc);   // rounding remainder only
+      if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, eo.T1, eo.T2);
     } else {
       acc.dropped++;
       deposit(a, v, p, qE - q1, acc);
+      if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, eo.T1, 0.0);
     }
   } else {
     deposit(a, v, p, qE - q1, acc);                  // recoil nucleus deposits locally
+    if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, eo.T1, 0.0);
   }
   p.E = eo.T1;
   p.nmfp = -logf(ub.z);
@@ -363,7 +375,7 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
 #define PMC_TRANSPORT_MIN_BLOCKS_SECONDARY 2
 #endif
 
-template <bool kLet, bool kMol, bool kVav, int kMinBlocks>
+template <bool kLet, bool kMol, bool kVav, int kMinBlocks, bool kLog = false>
 __global__ void __launch_bounds__(256, kMinBlocks) transport_kernel(const TransportArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned long long n_items =
@@ -426,7 +438,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) transport_kernel(const Transp
       }
     }
     if (__all_sync(0xffffffffu, !alive && drained)) break;
-    if (alive) alive = step<kLet, kMol, kVav>(a, ph, rt, et, st, mol, key, p, acc);
+    if (alive) alive = step<kLet, kMol, kVav, kLog>(a, ph, rt, et, st, mol, key, p, acc);
   }
 
   // flush the lane counters (warp reduction, one atomic per warp and counter)
@@ -472,6 +484,9 @@ constexpr void (*kFamily[8])(const TransportArgs) = {
     transport_kernel<false, false, true, kB>,  transport_kernel<true, false, true, kB>,
     transport_kernel<false, true, true, kB>,   transport_kernel<true, true, true, kB>};
 void (*const* const kTransportKernels[2])(const TransportArgs) = {kFamily<kP>, kFamily<kS>};
+// the debug deposit log, with the paper's physics options (Highland, Bohr, no LET)
+void (*const kTransportLogKernels[2])(const TransportArgs) = {transport_kernel<false, false, false, kP, true>,
+                                                              transport_kernel<false, false, false, kS, true>};
 }  // namespace
 
 cudaError_t transport_occupancy(int block, size_t smem, int* blocks_primary, int* blocks_secondary) {
@@ -486,12 +501,20 @@ cudaError_t transport_occupancy(int block, size_t smem, int* blocks_primary, int
       if (e != cudaSuccess) return e;
       lo = b < lo ? b : lo;
     }
+    cudaError_t e = cudaFuncSetAttribute(kTransportLogKernels[g], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
     *(g ? blocks_secondary : blocks_primary) = lo;
   }
   return cudaSuccess;
 }
 
 cudaError_t launch_transport(const TransportArgs& a, int grid, int block, size_t smem, cudaStream_t s) {
+  if (a.dlog) {
+    if (a.let_num || a.mol || a.vav) return cudaErrorInvalidValue;   // the log runs the default physics only
+    kTransportLogKernels[a.source ? 1 : 0]<<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+  }
   kTransportKernels[a.source ? 1 : 0][(a.let_num ? 1 : 0) + (a.mol ? 2 : 0) + (a.vav ? 4 : 0)]<<<grid, block, smem, s>>>(
       a);
   return cudaGetLastError();

@@ -34,6 +34,7 @@ EXPORTS = [
     "pmc_surrogate_params", "pmc_surrogate_load", "pmc_surrogate_grad", "pmc_surrogate_infer", "pmc_gamma_plan_bytes", "pmc_gamma_plan", "pmc_gamma_device",
     "pmc_gamma_index", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables",
     "pmc_debug_inc", "pmc_debug_elastic", "pmc_debug_surrogate_waits", "pmc_debug_vavilov_table",
+    "pmc_enable_deposit_log", "pmc_read_deposit_log", "pmc_debug_event_stage",
 ]
 
 AllocFn = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -101,6 +102,8 @@ class PlanResult(C.Structure):
 
 
 SPECIES = ("n", "p", "d", "t", "He3", "alpha")
+# pmc_deposit: tally entry [voxel][group] received llrint(e0 2^24) - llrint(e1 2^24) - llrint(e2 2^24)
+DEPOSIT_DTYPE = np.dtype([("voxel", np.int32), ("group", np.int32), ("e", np.float64, 3)])
 
 _libs = {}
 _lock = threading.Lock()
@@ -134,6 +137,8 @@ def lib(path: str = LIB_PATH):
             L.pmc_enable_escape_record.argtypes = [vp, u64]
             L.pmc_read_escape_record.argtypes = [vp, C.POINTER(C.c_float), u64, C.POINTER(C.c_uint64)]
             L.pmc_enable_let.argtypes = [vp, i]
+            L.pmc_enable_deposit_log.argtypes = [vp, u64]
+            L.pmc_read_deposit_log.argtypes = [vp, vp, u64, C.POINTER(C.c_uint64)]
             L.pmc_nonelastic_events.argtypes = [vp, i, d, u64, u64, u64, C.POINTER(EventYields)]
             L.pmc_plans_create.argtypes = [C.POINTER(vp), C.POINTER(Options), i, u64]
             L.pmc_plans_destroy.argtypes = [vp]
@@ -168,6 +173,7 @@ def lib(path: str = LIB_PATH):
             L.pmc_debug_tables.argtypes = [vp, i, pd, pd, pd, i]
             L.pmc_debug_inc.argtypes = [vp, i, d, u64, u64, i, pd, pd, i]
             L.pmc_debug_elastic.argtypes = [vp, i, d, pd, pd, i]
+            L.pmc_debug_event_stage.argtypes = [vp, i, vp, pd, i, u64, pf, u64, C.POINTER(C.c_uint64), pd]
             _libs[path] = L
     return _libs[path]
 
@@ -361,6 +367,18 @@ class Engine:
                                                    C.byref(n)))
         return out[: n.value]
 
+    def enable_deposit_log(self, cap):
+        """Debug: log every deposit of the next transports (cap records; 0 switches it off)."""
+        self._check(self._L.pmc_enable_deposit_log(self._ctx, cap))
+        self._dlog_cap = cap
+
+    def read_deposit_log(self):
+        """The last transport's deposits: structured array (voxel, group, e[3])."""
+        out = np.empty(self._dlog_cap, dtype=DEPOSIT_DTYPE)
+        n = C.c_uint64(0)
+        self._check(self._L.pmc_read_deposit_log(self._ctx, out.ctypes.data, self._dlog_cap, C.byref(n)))
+        return out[: n.value]
+
     def enable_let(self, on=True):
         """Scores the dose-averaged LET beside the dose in the next transports."""
         self._check(self._L.pmc_enable_let(self._ctx, 1 if on else 0))
@@ -471,6 +489,20 @@ class Engine:
         out = np.empty((len(u), 5))
         self._check(self._L.pmc_debug_elastic(self._ctx, nuclide, E, _dp(u), _dp(out), len(u)))
         return out
+
+
+    def debug_event_stage(self, mode, nuclide, E, seed, cap=None):
+        """The event stage alone on n events: (protons [k, 3] = event, T, cos; local [n] MeV)."""
+        nuc = np.ascontiguousarray(nuclide, dtype=np.int32)
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        n = len(E)
+        cap = cap or 32 * n + 1024
+        out = np.empty((cap, 3), dtype=np.float32)
+        loc = np.empty(n)
+        k = C.c_uint64(0)
+        self._check(self._L.pmc_debug_event_stage(self._ctx, mode, nuc.ctypes.data, _dp(E), n, seed,
+                                                  out.ctypes.data_as(C.POINTER(C.c_float)), cap, C.byref(k), _dp(loc)))
+        return out[: k.value], loc
 
 
 class PlanStream:

@@ -50,6 +50,9 @@ def test_invalid_calls_fail_without_a_device(libpmc):
     assert libpmc.pmc_surrogate_infer(None, None, 1, None) == -1
     assert libpmc.pmc_debug_surrogate_waits(None) == -1
     assert libpmc.pmc_enable_profile(None, 2) == -1
+    libpmc.pmc_enable_deposit_log.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+    assert libpmc.pmc_enable_deposit_log(None, 10) == -1
+    assert libpmc.pmc_read_deposit_log(None, None, 0, None) == -1
 
 
 def test_oracle_and_engine_share_no_code():

@@ -1,12 +1,18 @@
 """The transport entry point that allocates no device memory gives the same results as the
 allocating one.
 
-It exists for callers that cannot call cudaMalloc during a dose calculation (a host callback
-or real-time loop that must not stall on the allocator, or an application whose own pool owns
-the device memory).  Its scratch is a static device array shared by every call on a device,
-so the test makes two calls in a row with different seeds: the second must not see anything
-the first left behind.  This file is collected last so that a run stopping at the first
-failure has already run every other test."""
+It exists for callers that cannot call cudaMalloc during a dose calculation (a real-time loop
+that must not stall on the allocator, or an application whose own pool owns the device
+memory).  Its scratch is a static device array shared by every call on a device, so the test
+makes two calls in a row with different seeds: the second must not see anything the first left
+behind.  Two host threads making their first calls at once (in a fresh process) both get the
+allocating entry point's tally: the array's address is looked up once per device and the calls
+are serialised.  This file is collected last so that a run stopping at the first failure has
+already run every other test."""
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -69,3 +75,56 @@ def test_noalloc_rejects_too_many_spots():
     with pytest.raises(PmcError, match="no-allocation limit"):
         eng.transport_noalloc(10000, 1, tally.data_ptr())
     eng.close()
+
+
+_TWO_THREADS = r"""
+import sys, threading
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_1409_8336_gb300 import Engine
+from paper_1409_8336_gb300 import workloads as W
+
+prob = W.config1()
+n, seed = 20000, 41
+ref = Engine(device=0, n_batches=prob.n_batches)
+ref.load_problem(prob)
+ref.transport(n, seed)
+expected = ref.read_tally().reshape(-1)
+ref.close()
+engines, outs = [], []
+for _ in range(2):
+    e = Engine(device=0, n_batches=prob.n_batches)
+    e.load_problem(prob)
+    engines.append(e)
+    outs.append(torch.full((prob.n_voxels * prob.n_batches,), -1, dtype=torch.int64, device="cuda"))
+torch.cuda.synchronize()
+gate = threading.Barrier(2)
+errors = []
+
+def first_call(e, t):
+    try:
+        gate.wait()
+        e.transport_noalloc(n, seed, t.data_ptr())
+    except Exception as ex:  # reported below
+        errors.append(repr(ex))
+
+th = [threading.Thread(target=first_call, args=(engines[i], outs[i])) for i in range(2)]
+for t in th:
+    t.start()
+for t in th:
+    t.join()
+torch.cuda.synchronize()
+assert not errors, errors
+for t in outs:
+    assert np.array_equal(t.cpu().numpy(), expected)
+for e in engines:
+    e.close()
+print("TWO_THREADS_OK")
+"""
+
+
+def test_noalloc_first_calls_from_two_threads():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _TWO_THREADS, root], capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0 and "TWO_THREADS_OK" in r.stdout, (r.stdout[-2000:], r.stderr[-4000:])
