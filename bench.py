@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--plans-budget-gb", type=float, default=64.0)
     ap.add_argument("--inc-events", type=int, default=2_600_000)
     ap.add_argument("--gamma-histories", type=int, default=10_000_000)
+    ap.add_argument("--no-ct", action="store_true")
+    ap.add_argument("--ct-histories", type=int, default=10_000_000)
+    ap.add_argument("--ct-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -248,6 +251,15 @@ class OraclePool:
         dt = time.perf_counter() - t0
         return done / dt, done, dt
 
+    def ranges(self, starts_counts, seed=1):
+        """Histories/s of the given history ranges (first history, count), one job each."""
+        jobs = [(self.n_total, seed, h0, h0 + k) for h0, k in starts_counts if k > 0]
+        done = sum(j[3] - j[2] for j in jobs)
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_range, jobs, chunksize=1)
+        dt = time.perf_counter() - t0
+        return done / dt, done, dt
+
     def close(self):
         self.pool.close()
         self.pool.join()
@@ -291,6 +303,8 @@ def run_reference(args):
     value = sum(dones) / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.histories / value,
+            "ms_per_step_note": "extrapolated per history: each step times a bounded sample of the workload's "
+                                "histories on all host cores and scales it to the step's %d" % args.histories,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_block(prob, args.histories),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
@@ -386,6 +400,76 @@ def plans_leg(args, device, params):
                      "plan_ms_p50": float(np.percentile(lat, 50)), "plan_ms_p99": float(np.percentile(lat, 99)),
                      "plans_ok": len(ok), "max_plan_gb": max(r["device_bytes"] for r in res) / 2 ** 30}
         del res
+    return out
+
+
+def ct_plan_leg(args, device, stream, flush, with_cpu):
+    """The batched CT plan: 256 x 256 x 160 int16 HU at 1 mm (seeded ellipsoids, 6-bin HU table),
+    40 layers of 70-180 MeV x 50 spots = 2000 spots with lognormal weights, 1e7 histories in one
+    graph launch with the autotuned launch shape, full cascade; L2 flushed between steps.  End to
+    end through the ABI from pinned host buffers (H2D of the HU volume and spots, D2H of dose and
+    error) beside it, and the oracle's per-history rate on the same plan over all host cores (a
+    sample of 50 evenly spaced spots, extrapolated per history)."""
+    import torch
+
+    from paper_1409_8336_gb300 import Engine
+    from paper_1409_8336_gb300 import workloads as W
+
+    prob = W.config3()
+    n = args.ct_histories
+    eng = Engine(device=device, n_batches=prob.n_batches, fast_math=(args.math == "fast"))
+    eng.load_problem(prob)
+    block, chunk = eng.autotune(n)
+    for i in range(2):
+        eng.transport(n, 900 + i, stream=stream)
+    ms = []
+    for i in range(args.ct_steps):
+        flush.fill_(float(i))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        eng.transport(n, 910 + i, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    led = eng.read_ledger()
+    hu_h = torch.from_numpy(np.ascontiguousarray(prob.hu)).pin_memory()
+    dose_h = torch.empty(prob.n_voxels, dtype=torch.float64).pin_memory()
+    sig_h = torch.empty(prob.n_voxels, dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for i in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eng.load_phantom(prob.shape, prob.voxel, prob.origin, hu=hu_h)
+        eng.clear_spots()
+        eng.add_spots(prob.spots)
+        eng.transport(n, 920 + i, stream=stream)
+        eng.read_dose(dose_h, sig_h)
+        e2e_t.append(time.perf_counter() - t0)
+    eng.close()
+    t = sum(ms) / len(ms)
+    out = {"workload": prob.name, "histories_per_step": n, "spots": len(prob.spots), "layers": "40 x 70-180 MeV",
+           "launch": {"block": block, "histories_per_subgroup": chunk or n, "autotuned": True, "graph_launches": 1},
+           "value": n / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "ms_per_step_best": min(ms), "steps": len(ms),
+           "e2e": {"value": n / statistics.median(e2e_t[1:]), "unit": UNIT,
+                   "h2d_bytes_per_step": 2 * prob.n_voxels + 80 * len(prob.spots),
+                   "d2h_bytes_per_step": 16 * prob.n_voxels},
+           "steps_per_history": led["steps"] / n, "inelastic_per_history": led["inelastic"] / n}
+    if with_cpu:
+        pool = OraclePool(prob, n)
+        # one contiguous history range per sampled spot (64 evenly spaced spots of the 2000)
+        picks = list(range(0, len(prob.spots), len(prob.spots) // 64))[:64]
+        target = args.cpu_seconds * 2 / 3
+        rate, _, _ = pool.ranges([(int(pool.first[s]), 20) for s in picks], seed=3)      # pilot: sizes the sample
+        for it in range(3):     # the pilot's per-job overhead underestimates the rate: resize until it fits
+            k = max(20, int(rate * target / len(picks)))
+            rate, done, dt = pool.ranges([(int(pool.first[s]), min(k, int(pool.cnt[s]))) for s in picks], seed=4 + it)
+            if dt >= 0.6 * target:
+                break
+        pool.close()
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
+                               "sample": "%d histories from %d evenly spaced spots of the plan in %.1f s on %d worker "
+                                         "processes, extrapolated per history" % (done, len(picks), dt, pool.procs)}
     return out
 
 
@@ -679,7 +763,8 @@ def main():
         surrogate = {"value": sval, "unit": UNIT, "ms_per_step": sum(sm) / args.steps, "speedup_vs_full": sval / value,
                      "gamma_2pct_2mm_vs_full": gam, "train_events": args.train_events, "train_seconds": train_s,
                      "train_loss_first_last": [tr["first_loss"], tr["last_loss"]],
-                     "network": "MLP 32-256-256-256-256-16, BF16 tensor cores (mma.sync), FP32 accumulate",
+                     "network": "MLP 32-256-256-256-256-16, BF16 operands on 5th-generation tensor cores (tcgen05, accumulators "
+                                "in tensor memory) in the event stage, FP32 accumulate",
                      "event_stage": {"bound": "tensor", "kernel": "surrogate_event_kernel", "events_per_step": n_ev / n_prof,
                                      "ms_per_step": ev_ms / n_prof, "flops_per_event": SURROGATE_FLOPS_PER_EVENT,
                                      "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak,
@@ -690,6 +775,10 @@ def main():
     inc = None
     if not args.no_inc:
         inc = inc_leg(args, local, rank == 0 and world == 1 and not args.no_cpu_baseline)
+
+    ct = None
+    if not args.no_ct:
+        ct = ct_plan_leg(args, local, stream, flush, rank == 0 and world == 1 and not args.no_cpu_baseline)
 
     gamma = None
     if not args.no_gamma:
@@ -750,6 +839,7 @@ def main():
                             "events around the primary-transport launches only" % n_kind_steps,
             "math": args.math,
             "surrogate": surrogate,
+            "ct_plan": ct,
             "gamma": gamma,
             "inc_table1": inc,
             "plans_stream": plans,
