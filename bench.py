@@ -764,7 +764,7 @@ def main():
                      "gamma_2pct_2mm_vs_full": gam, "train_events": args.train_events, "train_seconds": train_s,
                      "train_loss_first_last": [tr["first_loss"], tr["last_loss"]],
                      "network": "MLP 32-256-256-256-256-16, BF16 operands on 5th-generation tensor cores (tcgen05, accumulators "
-                                "in tensor memory) in the event stage, FP32 accumulate",
+                                "in tensor memory) in the event stage and in training, FP32 accumulate",
                      "event_stage": {"bound": "tensor", "kernel": "surrogate_event_kernel", "events_per_step": n_ev / n_prof,
                                      "ms_per_step": ev_ms / n_prof, "flops_per_event": SURROGATE_FLOPS_PER_EVENT,
                                      "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak,

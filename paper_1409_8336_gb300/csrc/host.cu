@@ -480,6 +480,7 @@ struct pmc_ctx {
   int n_slots = 0;                      // non-elastic target slots (nuclides with A >= 2, in order)
   DevBuf d_sp, d_sg, d_sm, d_sv;        // parameters, gradients, Adam moments
   DevBuf d_swb;                         // BF16 inference weights, packed in streaming order
+  DevBuf d_gws, d_gerr;                 // training GEMMs: split-K workspace, tensor-core wait errors
   DevBuf d_slot_nuc, d_nuc_slot;        // slot -> nuclide, nuclide -> slot
   DevBuf d_rec[2];               // residual nuclei between cascade and evaporation, per stream
   size_t surr_cap = 0;
@@ -630,7 +631,7 @@ void pmc_destroy(pmc_ctx* ctx) {
   if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
   for (DevBuf* b : bufs) dfree(ctx, *b);
   DevBuf* sbufs[] = {&ctx->d_swb, &ctx->d_sp, &ctx->d_sg, &ctx->d_sm, &ctx->d_sv, &ctx->d_slot_nuc, &ctx->d_nuc_slot,
-                     &ctx->d_rec[0], &ctx->d_rec[1]};
+                     &ctx->d_rec[0], &ctx->d_rec[1], &ctx->d_gws, &ctx->d_gerr};
   for (DevBuf* b : sbufs) dfree(ctx, *b);
   if (ctx->pool) cudaStreamSynchronize(ctx->stream);   // the stream-ordered frees have run
   cudaStreamDestroy(ctx->stream);
@@ -1026,14 +1027,37 @@ size_t b_off(int l) { return w_off(l) + static_cast<size_t>(kLayerIn[l]) * kLaye
 constexpr size_t kSurrParams = 32 * 256 + 256 + 3 * (256 * 256 + 256) + 256 * 16 + 16;
 static_assert(kSurrParams == PMC_SURROGATE_PARAMS, "parameter count stated in pmc.h");
 
-// Forward pass over rows (or *Mp rows): act[l] = layer l output (ReLU for l < 4).
-int mlp_forward(pmc_ctx* ctx, const float* P, int rows, const unsigned* Mp, const float* X, float* const* act,
-                cudaStream_t s) {
+// The training GEMMs run on the tensor cores (launch_gemm_tc); their split-K workspace
+// (room for 128 splits of a 256 x 256 weight gradient) and wait-error flag.
+constexpr size_t kGemmWsFloats = 128ull * 256 * 256;
+int gemm_buffers(pmc_ctx* ctx) {
+  int rc;
+  if ((rc = dalloc(ctx, ctx->d_gws, kGemmWsFloats * sizeof(float)))) return rc;
+  if (!ctx->d_gerr.p) {
+    if ((rc = dalloc(ctx, ctx->d_gerr, sizeof(int)))) return rc;
+    CK(cudaMemset(ctx->d_gerr.p, 0, sizeof(int)));
+  }
+  return PMC_OK;
+}
+
+int gemm(pmc_ctx* ctx, int M, int N, int K, const float* A, long long sam, long long sak, const float* B, long long sbk,
+         long long sbn, float* C, long long ldc, const float* bias, bool relu, const float* mask, bool accumulate,
+         cudaStream_t s) {
+  CK(launch_gemm_tc(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, relu, mask, accumulate,
+                    static_cast<float*>(ctx->d_gws.p), kGemmWsFloats, static_cast<int*>(ctx->d_gerr.p), ctx->n_sm, s));
+  return PMC_OK;
+}
+
+// Forward pass over rows: act[l] = layer l output (ReLU for l < 4).
+int mlp_forward(pmc_ctx* ctx, const float* P, int rows, const float* X, float* const* act, cudaStream_t s) {
+  int rc;
+  if ((rc = gemm_buffers(ctx))) return rc;
   for (int l = 0; l < kSurrLayers; ++l) {
     const float* in = l == 0 ? X : act[l - 1];
     const int di = kLayerIn[l], dO = kLayerOut[l];
-    CK(launch_gemm(rows, Mp, dO, di, in, di, 1, P + w_off(l), 1, di, act[l], dO, P + b_off(l), l < kSurrLayers - 1,
-                   nullptr, false, s));
+    if ((rc = gemm(ctx, rows, dO, di, in, di, 1, P + w_off(l), 1, di, act[l], dO, P + b_off(l), l < kSurrLayers - 1,
+                   nullptr, false, s)))
+      return rc;
   }
   return PMC_OK;
 }
@@ -1041,20 +1065,36 @@ int mlp_forward(pmc_ctx* ctx, const float* P, int rows, const unsigned* Mp, cons
 // Backward pass from G = d loss / d output; gradients into Gp (same layout as P).
 int mlp_backward(pmc_ctx* ctx, const float* P, float* Gp, int rows, const float* X, float* const* act, float* g0,
                  float* g1, cudaStream_t s) {
+  int rc;
+  if ((rc = gemm_buffers(ctx))) return rc;
   const float* G = act[kSurrLayers];   // d loss / d yhat (rows x 16)
   float* bufs[2] = {g0, g1};
   for (int l = kSurrLayers - 1; l >= 0; --l) {
     const float* in = l == 0 ? X : act[l - 1];
     const int di = kLayerIn[l], dO = kLayerOut[l];
-    CK(launch_gemm(dO, nullptr, di, rows, G, 1, dO, in, di, 1, Gp + w_off(l), di, nullptr, false, nullptr, false, s));
+    // dW = G^T in (K = rows, split over the workspace)
+    if ((rc = gemm(ctx, dO, di, rows, G, 1, dO, in, di, 1, Gp + w_off(l), di, nullptr, false, nullptr, false, s)))
+      return rc;
     CK(launch_colsum(rows, dO, G, Gp + b_off(l), s));
     if (l > 0) {
+      // dX = G W, masked by the ReLU of the layer below
       float* Gn = bufs[l & 1];
-      CK(launch_gemm(rows, nullptr, di, dO, G, dO, 1, P + w_off(l), di, 1, Gn, di, nullptr, false, act[l - 1], false, s));
+      if ((rc = gemm(ctx, rows, di, dO, G, dO, 1, P + w_off(l), di, 1, Gn, di, nullptr, false, act[l - 1], false, s)))
+        return rc;
       G = Gn;
     }
   }
   return PMC_OK;
+}
+
+// Raises the tensor-core wait errors of the training GEMMs since the last call.
+int gemm_errors(pmc_ctx* ctx) {
+  if (!ctx->d_gerr.p) return PMC_OK;
+  int e = 0;
+  CK(cudaMemcpy(&e, ctx->d_gerr.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!e) return PMC_OK;
+  CK(cudaMemset(ctx->d_gerr.p, 0, sizeof(int)));
+  return fail(ctx, PMC_E_TIMEOUT, "%d training GEMM tiles: tensor-core waits timed out", e);
 }
 
 // Kernel arguments of one generation.
@@ -2085,7 +2125,7 @@ int pmc_train_surrogate(pmc_ctx* ctx, const pmc_train_opts* o, pmc_train_result*
         CK(launch_train_rows(B, static_cast<const float*>(feat.p), static_cast<const unsigned*>(perm.p), k * B, n,
                              o->seed, static_cast<unsigned>(step), static_cast<float*>(X.p), static_cast<float*>(Y.p),
                              static_cast<float*>(T.p), static_cast<float*>(M.p), s));
-        if ((rc = mlp_forward(ctx, P, rows, nullptr, static_cast<float*>(X.p), A, s))) return rc;
+        if ((rc = mlp_forward(ctx, P, rows, static_cast<float*>(X.p), A, s))) return rc;
         float* lslot = dloss + (k + 1 == steps_per_epoch ? 1 : (k == 0 ? 2 : 0));
         CK(launch_pinball(rows, A[kSurrLayers - 1], static_cast<float*>(Y.p), static_cast<float*>(T.p),
                           static_cast<float*>(M.p), A[kSurrLayers], lslot, s));
@@ -2104,6 +2144,7 @@ int pmc_train_surrogate(pmc_ctx* ctx, const pmc_train_opts* o, pmc_train_result*
     }
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
+    if ((rc = gemm_errors(ctx))) return rc;
     for (DevBuf* b : {&feat, &perm, &X, &Y, &T, &M, &g0, &g1, &loss}) dfree(ctx, *b);
     for (int l = 0; l <= kSurrLayers; ++l) dfree(ctx, act[l]);
     if ((rc = dalloc(ctx, ctx->d_swb, packed_weight_bytes()))) return rc;
@@ -2172,13 +2213,14 @@ int pmc_surrogate_grad(pmc_ctx* ctx, const float* params, const float* x, const 
   float* A[kSurrLayers + 1];
   for (int l = 0; l <= kSurrLayers; ++l) A[l] = static_cast<float*>(act[l].p);
   const float* P = static_cast<const float*>(ctx->d_sp.p);
-  if ((rc = mlp_forward(ctx, P, rows, nullptr, static_cast<float*>(X.p), A, s))) return rc;
+  if ((rc = mlp_forward(ctx, P, rows, static_cast<float*>(X.p), A, s))) return rc;
   CK(launch_pinball(rows, A[kSurrLayers - 1], static_cast<float*>(Y.p), static_cast<float*>(T.p),
                     static_cast<float*>(M.p), A[kSurrLayers], static_cast<float*>(L.p), s));
   if ((rc = mlp_backward(ctx, P, static_cast<float*>(ctx->d_sg.p), rows, static_cast<float*>(X.p), A,
                          static_cast<float*>(g0.p), static_cast<float*>(g1.p), s)))
     return rc;
   CK(cudaStreamSynchronize(s));
+  if ((rc = gemm_errors(ctx))) return rc;
   if (loss) CK(cudaMemcpy(loss, L.p, 4, cudaMemcpyDeviceToHost));
   if (grad) CK(cudaMemcpy(grad, ctx->d_sg.p, kSurrParams * 4, cudaMemcpyDeviceToHost));
   if (yhat) CK(cudaMemcpy(yhat, A[kSurrLayers - 1], static_cast<size_t>(rows) * kSurrOut * 4, cudaMemcpyDeviceToHost));

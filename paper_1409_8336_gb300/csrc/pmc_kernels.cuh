@@ -143,9 +143,15 @@ cudaError_t launch_stats(const StatsArgs& a, cudaStream_t s);
 cudaError_t launch_surrogate_dataset(const NucleusModel* nuclei, const float* btab, const int* slot_nuc, int n_slots,
                                      unsigned long long seed, unsigned long long n, float* out, cudaStream_t s);
 
-cudaError_t launch_gemm(int M, const unsigned* Mp, int N, int K, const float* A, long long sam, long long sak,
-                        const float* B, long long sbk, long long sbn, float* C, long long ldc, const float* bias,
-                        bool relu, const float* mask, bool accumulate, cudaStream_t s);
+// C[m][n] (=|+=) sum_k A(m,k) B(k,n) (+ bias[n]) (ReLU) (* [mask[m][n] > 0]) with
+// A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn], FP32 in memory, BF16 operands on the
+// 5th-generation tensor cores (tcgen05, 128-row tiles, FP32 accumulators in tensor memory); K is
+// split over ws (room for ws_floats partial sums) when the tiles alone would leave SMs idle.  A
+// tensor-core wait that ran out raises *err.
+cudaError_t launch_gemm_tc(int M, int N, int K, const float* A, long long sam, long long sak, const float* B,
+                          long long sbk, long long sbn, float* C, long long ldc, const float* bias, bool relu,
+                          const float* mask, bool accumulate, float* ws, size_t ws_floats, int* err, int n_sm,
+                          cudaStream_t s);
 cudaError_t launch_mlp_rows(int rows, const float* X, const void* Wb, const float* P, float* Y, int* err, int n_sm,
                             bool check_waits, cudaStream_t s);
 // The inference weights: BF16, each streamed chunk in the byte order of its shared-memory buffer.

@@ -10,114 +10,17 @@
 // with the token "unknown" for the multiplicity, then with the sampled
 // multiplicity for the rest.
 //
-// Dense layers run on the tensor cores with BF16 operands and FP32 accumulation.
-// Inference (the event stage inside the transport, and pmc_surrogate_infer) uses
-// the 5th-generation tcgen05 MMAs with accumulators in tensor memory (namespace
-// tc below); training uses a generic strided GEMM on the warp-level mma.sync
-// m16n8k16 instruction (weights and activations rounded from FP32 master copies
-// when a tile is staged in shared memory).
+// Dense layers run on the 5th-generation tensor cores (tcgen05 MMAs, BF16 operands,
+// FP32 accumulators in tensor memory; namespace tc below): inference (the event stage
+// inside the transport, and pmc_surrogate_infer) and the training GEMMs (forward and both
+// backward products, from FP32 master copies rounded when a tile is staged in shared
+// memory).
 #include <cuda_bf16.h>
 
 #include "pmc_kernels.cuh"
 
 namespace pmc {
 namespace {
-
-constexpr int kTileM = 64, kTileN = 64, kTileK = 32, kPad = 8;
-
-__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x (low half) = lo
-  return *reinterpret_cast<const unsigned*>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// C[m][n] (=|+=) sum_k A(m,k) B(k,n) (+ bias[n]) (ReLU) (* [mask[m][n] > 0]).
-// A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn]; FP32 in memory, BF16 math.
-// The row count is *Mp when Mp is given (device-resident), else M.
-__global__ void __launch_bounds__(128) gemm_kernel(int M, const unsigned* Mp, int N, int K, const float* __restrict__ A,
-                                                   long long sam, long long sak, const float* __restrict__ B,
-                                                   long long sbk, long long sbn, float* __restrict__ C, long long ldc,
-                                                   const float* __restrict__ bias, int relu,
-                                                   const float* __restrict__ mask, int accumulate) {
-  const int rows = Mp ? static_cast<int>(min(*Mp, static_cast<unsigned>(M))) : M;
-  const int m0 = blockIdx.x * kTileM, n0 = blockIdx.y * kTileN;
-  if (m0 >= rows) return;
-  __shared__ __nv_bfloat16 As[kTileM][kTileK + kPad];
-  __shared__ __nv_bfloat16 Bs[kTileN][kTileK + kPad];   // stored [n][k]
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;   // warp's 32x32 sub-tile
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
-  for (int k0 = 0; k0 < K; k0 += kTileK) {
-    for (int e = tid; e < kTileM * kTileK; e += 128) {
-      const int mm = e / kTileK, kk = e % kTileK;
-      const int gm = m0 + mm, gk = k0 + kk;
-      As[mm][kk] = __float2bfloat16_rn(gm < rows && gk < K ? A[gm * sam + gk * sak] : 0.0f);
-    }
-    for (int e = tid; e < kTileN * kTileK; e += 128) {
-      const int nn = e / kTileK, kk = e % kTileK;
-      const int gn = n0 + nn, gk = k0 + kk;
-      Bs[nn][kk] = __float2bfloat16_rn(gn < N && gk < K ? B[gk * sbk + gn * sbn] : 0.0f);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kTileK; kk += 16) {
-      unsigned af[2][4], bfr[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + 16 * i + g;
-        const int c = kk + 2 * t;
-        af[i][0] = pack_bf16(__bfloat162float(As[r][c]), __bfloat162float(As[r][c + 1]));
-        af[i][1] = pack_bf16(__bfloat162float(As[r + 8][c]), __bfloat162float(As[r + 8][c + 1]));
-        af[i][2] = pack_bf16(__bfloat162float(As[r][c + 8]), __bfloat162float(As[r][c + 9]));
-        af[i][3] = pack_bf16(__bfloat162float(As[r + 8][c + 8]), __bfloat162float(As[r + 8][c + 9]));
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n = wn + 8 * j + g;
-        const int c = kk + 2 * t;
-        bfr[j][0] = pack_bf16(__bfloat162float(Bs[n][c]), __bfloat162float(Bs[n][c + 1]));
-        bfr[j][1] = pack_bf16(__bfloat162float(Bs[n][c + 8]), __bfloat162float(Bs[n][c + 9]));
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int m = m0 + wm + 16 * i + g + (r >= 2 ? 8 : 0);
-        const int n = n0 + wn + 8 * j + 2 * t + (r & 1);
-        if (m >= rows || n >= N) continue;
-        float v = acc[i][j][r];
-        if (bias) v += bias[n];
-        if (relu) v = fmaxf(v, 0.0f);
-        if (mask && !(mask[static_cast<long long>(m) * ldc + n] > 0.0f)) v = 0.0f;
-        float* dst = C + static_cast<long long>(m) * ldc + n;
-        *dst = accumulate ? *dst + v : v;
-      }
-    }
-  }
-}
 
 // Pinball loss of quantile predictions yhat against targets y at levels tau, per
 // masked entry; gradient w.r.t. yhat scaled by 1/rows.
@@ -663,6 +566,154 @@ __global__ void __launch_bounds__(128, 2) surrogate_event_kernel(const unsigned*
   tc::end(pp);
 }
 
+// ---------------------------------------------------------------------------
+// Training GEMM on the 5th-generation tensor cores.  C[m][n] (=|+=) sum_k A(m,k) B(k,n)
+// (+ bias[n]) (ReLU) (* [mask[m][n] > 0]), A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn],
+// FP32 in memory, BF16 operands, FP32 accumulation in tensor memory.  One CTA (4 warps) owns a
+// 128 x BN tile (BN <= 256) and a range of K: each 64-wide K chunk is loaded by all threads
+// (FP32 -> BF16, written into the canonical no-swizzle K-major layout of the inference kernel,
+// transposed on the way when the source is M- or N-major), then one thread issues its
+// tcgen05 MMAs and commits them to the chunk's buffer mbarrier; two buffers, so the next
+// chunk loads while the MMAs run.  With a K split (the weight gradients, whose K is the batch),
+// each CTA writes its partial tile to a workspace that gemm_reduce_kernel sums in a fixed
+// order (deterministic) before the epilogue.
+// ---------------------------------------------------------------------------
+constexpr int kGemmBK = 64;
+constexpr int kGemmABytes = tc::kRows * kGemmBK * 2;            // 16 KB
+constexpr int kGemmBBytes = 256 * kGemmBK * 2;                  // 32 KB at BN = 256
+constexpr int kGemmSmem = 2 * (kGemmABytes + kGemmBBytes) + 64;
+
+__device__ __forceinline__ void gemm_epilogue(float v, int m, int n, float* C, long long ldc, const float* bias,
+                                              int relu, const float* mask, int accumulate) {
+  if (bias) v += bias[n];
+  if (relu) v = fmaxf(v, 0.0f);
+  if (mask && !(mask[static_cast<long long>(m) * ldc + n] > 0.0f)) v = 0.0f;
+  float* dst = C + static_cast<long long>(m) * ldc + n;
+  *dst = accumulate ? *dst + v : v;
+}
+
+// Eight consecutive k of one row (of A) or one column (of B) as a 16-byte BF16 unit.
+__device__ __forceinline__ uint4 load_unit(const float* __restrict__ X, long long s_row, long long s_k, int row,
+                                           int rows, int k, int kend) {
+  float v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    v[j] = (row < rows && k + j < kend) ? X[static_cast<long long>(row) * s_row + static_cast<long long>(k + j) * s_k]
+                                        : 0.0f;
+  uint32_t h[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 t2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    h[i] = *reinterpret_cast<const uint32_t*>(&t2);
+  }
+  return make_uint4(h[0], h[1], h[2], h[3]);
+}
+
+__global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, int BN, int k_split,
+                                                      const float* __restrict__ A, long long sam, long long sak,
+                                                      const float* __restrict__ B, long long sbk, long long sbn,
+                                                      float* __restrict__ C, long long ldc,
+                                                      const float* __restrict__ bias, int relu,
+                                                      const float* __restrict__ mask, int accumulate,
+                                                      float* __restrict__ ws, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned char* abuf[2] = {smem, smem + kGemmABytes};
+  unsigned char* bbuf[2] = {smem + 2 * kGemmABytes, smem + 2 * kGemmABytes + kGemmBBytes};
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + 2 * (kGemmABytes + kGemmBBytes));
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
+  int* fail = reinterpret_cast<int*>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m0 = blockIdx.x * tc::kRows, n0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * k_split, kend = min(K, kbeg + k_split);
+  const int ncols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));   // tensor-memory columns
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(mbar + b)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *fail = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::saddr(tslot)), "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const bool a_mfast = sam == 1, b_nfast = sbn == 1;   // the operand's contiguous direction
+  const uint32_t id = tc::idesc(tc::kRows, BN);
+  const int nchunks = (kend - kbeg + kGemmBK - 1) / kGemmBK;
+  uint32_t phase = 0;   // bit b: parity of buffer b's next completion; bit 2: the final barrier
+  bool ok = true;
+  for (int c = 0; c < nchunks; ++c) {
+    const int b = c & 1, k0 = kbeg + c * kGemmBK;
+    if (c >= 2) {   // the MMAs that read this buffer two chunks ago are done
+      ok = tc::wait(tc::saddr(mbar + b), (phase >> b) & 1u, tc::kSpin) && ok;
+      phase ^= 1u << b;
+    }
+    // A: 128 rows x 64 k (1024 units of 8 k), B: BN columns x 64 k
+#pragma unroll 2
+    for (int i = 0; i < 8; ++i) {
+      const int u = tid + 128 * i;
+      const int r = a_mfast ? (u & 127) : (u >> 3), k8 = a_mfast ? (u >> 7) : (u & 7);
+      *reinterpret_cast<uint4*>(abuf[b] + tc::act_off(r, 8 * k8)) = load_unit(A, sam, sak, m0 + r, M, k0 + 8 * k8, kend);
+    }
+    for (int u = tid; u < BN * 8; u += 128) {
+      const int nn = b_nfast ? (u % BN) : (u >> 3), k8 = b_nfast ? (u / BN) : (u & 7);
+      *reinterpret_cast<uint4*>(bbuf[b] + tc::w_off(nn, 8 * k8, BN)) =
+          load_unit(B, sbn, sbk, n0 + nn, N, k0 + 8 * k8, kend);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0 && ok) {
+      const int nks = (min(kGemmBK, kend - k0) + 15) / 16;
+      for (int s = 0; s < nks; ++s)
+        tc::mma(tmem, tc::desc(tc::saddr(abuf[b] + s * 4096), 128, 256), tc::desc(tc::saddr(bbuf[b] + s * (BN * 32)), 128, 256),
+                id, c > 0 || s > 0);
+      tc::commit(tc::saddr(mbar + b));
+      if (c + 1 == nchunks) tc::commit(tc::saddr(mbar + 2));
+    }
+  }
+  // every MMA of the tile is done (the last commit tracks all earlier ones)
+  if (nchunks > 0) ok = tc::wait(tc::saddr(mbar + 2), (phase >> 2) & 1u, tc::kSpin) && ok;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  ok = __all_sync(0xffffffffu, ok);   // warp-uniform: tcgen05.ld is warp-collective
+  if (!ok) atomicOr(fail, 1);
+  if (ok) {
+    const int m = m0 + warp * 32 + (tid & 31);
+    const uint32_t trow = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tc::ld16(trow + c0, v);
+      if (m >= M) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int n = n0 + c0 + i;
+        if (n >= N) break;
+        if (ws) ws[(static_cast<long long>(blockIdx.z) * M + m) * N + n] = v[i];
+        else gemm_epilogue(v[i], m, n, C, ldc, bias, relu, mask, accumulate);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+  if (tid == 0 && *fail) atomicAdd(err, 1);
+}
+
+// The K split's partial tiles summed in split order, then the epilogue.
+__global__ void gemm_reduce_kernel(int M, int N, int splits, const float* __restrict__ ws, float* __restrict__ C,
+                                   long long ldc, const float* __restrict__ bias, int relu,
+                                   const float* __restrict__ mask, int accumulate) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= static_cast<long long>(M) * N) return;
+  const int m = static_cast<int>(i / N), n = static_cast<int>(i % N);
+  float v = 0.0f;
+  for (int z = 0; z < splits; ++z) v += ws[(static_cast<long long>(z) * M + m) * N + n];
+  gemm_epilogue(v, m, n, C, ldc, bias, relu, mask, accumulate);
+}
+
 // The inference weights: BF16 of the FP32 parameters (round to nearest even), each chunk in
 // the byte order of its shared-memory buffer (one 16-byte unit = 8 consecutive columns of one
 // output row per thread).
@@ -709,12 +760,34 @@ cudaError_t launch_pack_weights(const float* P, void* packed, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm(int M, const unsigned* Mp, int N, int K, const float* A, long long sam, long long sak,
-                        const float* B, long long sbk, long long sbn, float* C, long long ldc, const float* bias,
-                        bool relu, const float* mask, bool accumulate, cudaStream_t s) {
-  const dim3 grid((M + kTileM - 1) / kTileM, (N + kTileN - 1) / kTileN);
-  gemm_kernel<<<grid, 128, 0, s>>>(M, Mp, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, relu ? 1 : 0, mask,
-                                   accumulate ? 1 : 0);
+cudaError_t launch_gemm_tc(int M, int N, int K, const float* A, long long sam, long long sak, const float* B,
+                          long long sbk, long long sbn, float* C, long long ldc, const float* bias, bool relu,
+                          const float* mask, bool accumulate, float* ws, size_t ws_floats, int* err, int n_sm,
+                          cudaStream_t s) {
+  // set once per process (a function-local static is initialised exactly once)
+  static const cudaError_t attr = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  if (attr != cudaSuccess) return attr;
+  if (M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+  const int BN = min(256, (N + 15) / 16 * 16);
+  const int mt = (M + tc::kRows - 1) / tc::kRows, nt = (N + BN - 1) / BN;
+  const int kchunks = (K + kGemmBK - 1) / kGemmBK;
+  // split K when the tiles alone would leave most SMs idle (the weight gradients: K = batch rows)
+  int splits = 1;
+  if (ws && 2 * mt * nt < n_sm) {
+    splits = min(kchunks, (2 * n_sm + mt * nt - 1) / (mt * nt));
+    while (splits > 1 && static_cast<size_t>(splits) * M * N > ws_floats) --splits;
+  }
+  const int k_split = (kchunks + splits - 1) / splits * kGemmBK;
+  splits = (K + k_split - 1) / k_split;   // every split has at least one chunk
+  const dim3 grid(mt, nt, splits);
+  gemm_tc_kernel<<<grid, tc::kRows, kGemmSmem, s>>>(M, N, K, BN, k_split, A, sam, sak, B, sbk, sbn, C, ldc, bias,
+                                                    relu ? 1 : 0, mask, accumulate ? 1 : 0, splits > 1 ? ws : nullptr,
+                                                    err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  const long long total = static_cast<long long>(M) * N;
+  gemm_reduce_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(M, N, splits, ws, C, ldc, bias,
+                                                                                relu ? 1 : 0, mask, accumulate ? 1 : 0);
   return cudaGetLastError();
 }
 
