@@ -48,12 +48,29 @@ BYTES_PER_STEP = 21
 # 2 x (32*256 + 3*256*256 + 256*16) multiply-add FLOPs.
 SURROGATE_FLOPS_PER_EVENT = 2 * 2 * (32 * 256 + 3 * 256 * 256 + 256 * 16)
 L2_BYTES = 129 * 2 ** 20
-# DRAM bytes (read + write) of the primary-transport launch per primary history, from a
-# 1-pass ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on this workload
-# (1e6 histories in one launch: 48.0 MB), valid only for the kernel sources it was taken
-# on (their SHA-256 below); otherwise the roofline's traffic is reported as null.
-TRAFFIC = {"bytes_per_history": 48.0, "sources": ("transport.cu", "pmc_device.cuh", "pmc_kernels.cuh"),
-           "sha256": "f3bbc6d8d302b606c4da958f04760b0fd9045a7499df1364ad1dfcac810383a3"}
+# Measurements of the primary-transport kernel that need a profiler, valid only for the kernel
+# sources they were taken on (their SHA-256 below; otherwise reported as null).
+#   ncu: one ncu capture of the first primary launch of the 2e5-history slab case (-k
+#        transport_kernel -c 1): issue slots busy, threads per executed instruction (SIMT
+#        efficiency = that / 32) and thread instructions per condensed-history step.
+#   bytes_per_history: DRAM bytes (read + write) of a full 1e6-history primary launch per
+#        primary history: dram__bytes_read.sum + dram__bytes_write.sum alone (reported as one
+#        pass on the 2e5-history case first), one launch (-c 1): 45.35 + 4.56 MB.
+KERNEL_SOURCES = ("transport.cu", "transport_step.cuh", "pmc_device.cuh", "pmc_kernels.cuh")
+KERNEL_SHA256 = "a4ab02dfdc74b2038868dd32e206adb2c7642da9d638a9d8fcfb684284b6b348"
+NCU = {"issue_slots_busy": 0.7570, "threads_per_instruction": 21.38, "thread_instructions_per_step": 585.6,
+       "capture": "slab workload, 2e5 histories, first primary launch (-k regex:transport_kernel -c 1)"}
+TRAFFIC = {"bytes_per_history": 49.90}
+
+
+def _sources_match():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1409_8336_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest() == KERNEL_SHA256
 
 
 def parse():
@@ -81,21 +98,25 @@ def parse():
     ap.add_argument("--inc-events", type=int, default=2_600_000)
     ap.add_argument("--gamma-histories", type=int, default=10_000_000)
     ap.add_argument("--no-ct", action="store_true")
+    ap.add_argument("--no-other-build", action="store_true", help="skip timing the other math build")
     ap.add_argument("--ct-histories", type=int, default=10_000_000)
     ap.add_argument("--ct-steps", type=int, default=5)
     return ap.parse_args()
 
 
 def traffic_per_launch(histories_per_launch):
-    import hashlib
-
-    h = hashlib.sha256()
-    for f in TRAFFIC["sources"]:
-        with open(os.path.join(ROOT, "paper_1409_8336_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    if h.hexdigest() != TRAFFIC["sha256"]:
+    if TRAFFIC["bytes_per_history"] is None or not _sources_match():
         return None
     return TRAFFIC["bytes_per_history"] * histories_per_launch
+
+
+def ncu_fractions():
+    """The profiler's view of the primary launch beside the operation-count roofline."""
+    if not _sources_match():
+        return None
+    return {"issue_slots_busy": NCU["issue_slots_busy"],
+            "simt_efficiency": NCU["threads_per_instruction"] / 32.0,
+            "thread_instructions_per_step": NCU["thread_instructions_per_step"], "capture": NCU["capture"]}
 
 
 def memory_fractions(pk, steps_per_step, span_ms, traffic, launches_per_step):
@@ -583,13 +604,15 @@ def main():
     # the other build, timed beside the headline one
     fixed = args.launch is not None
     blk, chk = (int(v) for v in args.launch.split(",")) if fixed else (0, 0)
-    other = Engine(device=local, n_batches=prob.n_batches, fast_math=(args.math != "fast"), block_size=blk)
-    other.load_problem(prob)
-    if fixed:
-        other.set_launch(blk, chk)
-    timed_steps(other, args.warmup, 5000)
-    other_ms = timed_steps(other, args.steps, 6000)
-    other.close()
+    other_ms = None
+    if not args.no_other_build:
+        other = Engine(device=local, n_batches=prob.n_batches, fast_math=(args.math != "fast"), block_size=blk)
+        other.load_problem(prob)
+        if fixed:
+            other.set_launch(blk, chk)
+        timed_steps(other, args.warmup, 5000)
+        other_ms = timed_steps(other, args.steps, 6000)
+        other.close()
 
     eng = Engine(device=local, n_batches=prob.n_batches, fast_math=(args.math == "fast"))
     eng.load_problem(prob)
@@ -829,6 +852,7 @@ def main():
                          "ops_per_step": OPS_PER_STEP, "steps_per_launch": steps_per_launch,
                          "launch_ms": launch_ms, "primary_span_ms": span_ms,
                          "primary_launches_per_step": prof_n / args.steps,
+                         "ncu": ncu_fractions(),
                          "memory": memory_fractions(pk, steps_per_step, span_ms,
                                                     traffic_per_launch(n / max(prof_n / args.steps, 1)),
                                                     prof_n / args.steps)},
@@ -846,9 +870,9 @@ def main():
             "let": let_leg,
             "moliere": moliere,
             "vavilov": vavilov,
-            "other_build": {"math": "ieee" if args.math == "fast" else "fast",
-                            "value": world * n * args.steps / (sum(other_ms) / 1e3),
-                            "ms_per_step": sum(other_ms) / args.steps},
+            "other_build": None if other_ms is None else {
+                "math": "ieee" if args.math == "fast" else "fast",
+                "value": world * n * args.steps / (sum(other_ms) / 1e3), "ms_per_step": sum(other_ms) / args.steps},
             "cpu_baseline": cpu,
             "stats": {"steps_per_history": led["steps"] / n, "inelastic": led["inelastic"],
                       "elastic": led["elastic"], "secondaries": led["secondaries"],

@@ -252,6 +252,19 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+static_assert(kSurrHidden % 64 == 0, "the epilogue reads the hidden layers 64 columns at a time");
+// 64 consecutive FP32 accumulator columns of this thread's row, one load and one wait.
+__device__ __forceinline__ void ld64(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
+               "tcgen05.wait::ld.sync.aligned;"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+               : "r"(taddr)
+               : "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Byte offsets in the canonical layout: activation (row r, column k) of the 128-row tile, and
 // weight (output n, chunk column kl) of a chunk of kKC columns for N outputs.
 constexpr int kRows = 128, kKC = 32;
@@ -378,18 +391,21 @@ __device__ __forceinline__ void mlp_pass(unsigned char* act, unsigned char* wb, 
     if (pp.ok) {
       if (l + 1 < kSurrLayers) {
 #pragma unroll 1
-        for (int c0 = 0; c0 < N; c0 += 16) {
-          float v[16];
-          ld16(trow + c0, v);
-          uint32_t h[8];
+        for (int c0 = 0; c0 < N; c0 += 64) {   // 64 columns per tensor-memory load (one wait)
+          float v[64];
+          ld64(trow + c0, v);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const __nv_bfloat162 t2 = __floats2bfloat162_rn(fmaxf(v[2 * i] + __ldg(bias + c0 + 2 * i), 0.0f),
-                                                            fmaxf(v[2 * i + 1] + __ldg(bias + c0 + 2 * i + 1), 0.0f));
-            h[i] = *reinterpret_cast<const uint32_t*>(&t2);
+          for (int q = 0; q < 8; ++q) {
+            uint32_t h[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int c = 8 * q + 2 * i;
+              const __nv_bfloat162 t2 = __floats2bfloat162_rn(fmaxf(v[c] + __ldg(bias + c0 + c), 0.0f),
+                                                              fmaxf(v[c + 1] + __ldg(bias + c0 + c + 1), 0.0f));
+              h[i] = *reinterpret_cast<const uint32_t*>(&t2);
+            }
+            *reinterpret_cast<uint4*>(act + act_off(tid, c0 + 8 * q)) = make_uint4(h[0], h[1], h[2], h[3]);
           }
-          *reinterpret_cast<uint4*>(act + act_off(tid, c0)) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(act + act_off(tid, c0 + 8)) = make_uint4(h[4], h[5], h[6], h[7]);
         }
       } else {
         float v[16];

@@ -34,9 +34,15 @@ def test_memory_fractions():
     assert bench.memory_fractions(pk, 1e8, 2.0, None, 1.0)["dram_frac"] is None
 
 
-def test_traffic_is_null_for_other_sources(monkeypatch):
+def test_profiler_figures_are_null_for_other_sources(monkeypatch):
     import bench
 
-    assert bench.traffic_per_launch(1e6) in (None, pytest.approx(bench.TRAFFIC["bytes_per_history"] * 1e6))
-    monkeypatch.setitem(bench.TRAFFIC, "sha256", "0" * 64)
+    monkeypatch.setitem(bench.TRAFFIC, "bytes_per_history", 50.0)
+    if bench._sources_match():
+        assert bench.traffic_per_launch(1e6) == pytest.approx(5e7)
+        assert bench.ncu_fractions()["simt_efficiency"] == pytest.approx(bench.NCU["threads_per_instruction"] / 32)
+    monkeypatch.setattr(bench, "KERNEL_SHA256", "0" * 64)
+    assert bench.traffic_per_launch(1e6) is None
+    assert bench.ncu_fractions() is None
+    monkeypatch.setitem(bench.TRAFFIC, "bytes_per_history", None)
     assert bench.traffic_per_launch(1e6) is None
