@@ -383,6 +383,42 @@ def inc_leg(args, device, with_cpu):
     return out
 
 
+def event_stage_ks(eng, prob, n_per_target=5000, seed=321):
+    """The shipped event kernels on the same events: the learned stand-in's tensor-core event
+    kernel against the cascade and evaporation kernels, per target nucleus (E uniform in
+    10-250 MeV): KS statistics of the leading proton's energy / E and polar cosine, of the
+    energies and cosines of the (up to four) most energetic protons, and the mean multiplicity
+    (capped at four, the network's slots) of each."""
+    from scipy import stats
+
+    rng = np.random.default_rng(seed)
+    out = {}
+    for t, nu in enumerate(prob.nuclides):
+        if nu[1] < 2:
+            continue
+        E = rng.uniform(10.0, 250.0, n_per_target)
+        nuc = np.full(n_per_target, t, dtype=np.int32)
+        res = []
+        for mode in (0, 1):
+            pr, _ = eng.debug_event_stage(mode, nuc, E, seed + t)
+            ev = pr[:, 0].astype(np.int64)
+            order = np.lexsort((-pr[:, 1], ev))
+            pr, ev = pr[order], ev[order]
+            first = np.r_[True, ev[1:] != ev[:-1]]
+            rank = np.arange(len(ev)) - np.maximum.accumulate(np.where(first, np.arange(len(ev)), 0))
+            top = pr[rank < 4]
+            res.append((pr[first, 1] / E[ev[first]], pr[first, 2], top[:, 1] / E[top[:, 0].astype(np.int64)], top[:, 2],
+                        float(np.minimum(np.bincount(ev, minlength=n_per_target), 4).mean())))
+        (a, b) = res
+        out["%d-%d" % (int(nu[0]), int(nu[1]))] = {
+            "ks_leading_T": round(float(stats.ks_2samp(a[0], b[0]).statistic), 4),
+            "ks_leading_cos": round(float(stats.ks_2samp(a[1], b[1]).statistic), 4),
+            "ks_T": round(float(stats.ks_2samp(a[2], b[2]).statistic), 4),
+            "ks_cos": round(float(stats.ks_2samp(a[3], b[3]).statistic), 4),
+            "multiplicity_cascade_surrogate": [round(a[4], 3), round(b[4], 3)]}
+    return out
+
+
 def plans_leg(args, device, params):
     """The multi-plan stream: 64 synthetic CT plans (50-3000 spots, 70-230 MeV, phantoms
     128x128x96 to 320x320x200 at 1 mm, 1e6-1e7 histories each) through one GPU, several at
@@ -779,12 +815,16 @@ def main():
         eng.transport(n, 77, mode=1, stream=stream)
         Ds, _ = eng.read_dose()
         _, gam = gamma_index(Df.reshape(prob.shape), Ds.reshape(prob.shape), prob.voxel, want_map=False)
+        ks = event_stage_ks(eng, prob)
         sval = world * n * args.steps / (sum(sm) / 1e3)
         pk_s, src_s = peaks()
         tflops = SURROGATE_FLOPS_PER_EVENT * n_ev / (ev_ms * 1e-3) / 1e12
         tpeak = float(pk_s.get("bf16_tflops_sustained", 1700.0))
         surrogate = {"value": sval, "unit": UNIT, "ms_per_step": sum(sm) / args.steps, "speedup_vs_full": sval / value,
-                     "gamma_2pct_2mm_vs_full": gam, "train_events": args.train_events, "train_seconds": train_s,
+                     "gamma_2pct_2mm_vs_full": gam,
+                     "secondary_spectra_ks": {"sample": "5000 events per target, E uniform in 10-250 MeV, the same "
+                                                         "events through both event kernels", "per_target": ks},
+                     "train_events": args.train_events, "train_seconds": train_s,
                      "train_loss_first_last": [tr["first_loss"], tr["last_loss"]],
                      "network": "MLP 32-256-256-256-256-16, BF16 operands on 5th-generation tensor cores (tcgen05, accumulators "
                                 "in tensor memory) in the event stage and in training, FP32 accumulate",

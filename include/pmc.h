@@ -52,7 +52,7 @@ extern "C" {
  * and prints no Vavilov formula).  Where kappa = xi / T_max <= 10 (xi = (K/2)(Z/A) rho s /
  * beta^2 over the step's path s, T_max the largest transfer to a free electron) the loss
  * fluctuation about the CSDA mean is drawn from Vavilov's distribution for the Bethe spectrum
- * of transfers, tabulated from its characteristic function (kappa clamped to [0.01, 10], the
+ * of transfers, tabulated from its characteristic function (kappa clamped to [0.001, 10], the
  * quantile tails cut at 1e-4, each row centred so the mean loss stays the CSDA loss); above
  * 10, Bohr's Gaussian of the same variance. */
 #define PMC_VAVILOV 32u

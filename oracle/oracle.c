@@ -414,9 +414,9 @@ double or_moliere_theta(double u, double chic2, double B)
 /* Vavilov straggling (optional; the paper uses Bohr's Gaussian).  The table, built by the
  * oracle's Python side from the characteristic function of the Bethe collision spectrum
  * (oracle/vavilov.py), holds quantiles of z = (loss - mean loss) / xi on OR_VAV_NB values of
- * beta^2 in [0, 0.5], OR_VAV_NK values of ln kappa in [ln 0.01, ln 10] and OR_VAV_NU values of
+ * beta^2 in [0, 0.5], OR_VAV_NK values of ln kappa in [ln 0.001, ln 10] and OR_VAV_NU values of
  * u in [1e-4, 1 - 1e-4], each row shifted to mean zero; sampled by trilinear interpolation. */
-#define OR_VAV_NK 31
+#define OR_VAV_NK 41
 #define OR_VAV_NB 6
 #define OR_VAV_NU 513
 static double or_vav_tab[OR_VAV_NB * OR_VAV_NK * OR_VAV_NU];
@@ -441,8 +441,8 @@ void or_vavilov_params(double E, double rho, double ZA, double x, double* xi, do
 
 double or_vavilov_z(double kappa, double b2, double u)
 {
-    double lk = log(kappa < 0.01 ? 0.01 : (kappa > 10.0 ? 10.0 : kappa));
-    double a = (lk - log(0.01)) / (log(10.0) - log(0.01)) * (OR_VAV_NK - 1);
+    double lk = log(kappa < 0.001 ? 0.001 : (kappa > 10.0 ? 10.0 : kappa));
+    double a = (lk - log(0.001)) / (log(10.0) - log(0.001)) * (OR_VAV_NK - 1);
     double b = (b2 < 0.0 ? 0.0 : (b2 > 0.5 ? 0.5 : b2)) / 0.5 * (OR_VAV_NB - 1);
     double cc = u * (OR_VAV_NU - 1);
     int ia = (int)a, ib = (int)b, ic = (int)cc;

@@ -16,7 +16,7 @@ eps_max, the fluctuation about the mean loss has the characteristic function
 (I2 by parts from I1).  The density follows by a discrete Fourier inversion on a grid wide
 enough to hold all the mass; its quantiles give the table the transport samples from.
 
-The table: ln kappa on NK nodes over [ln 0.01, ln 10], beta^2 on NB nodes over [0, 0.5], and
+The table: ln kappa on NK nodes over [ln 0.001, ln 10], beta^2 on NB nodes over [0, 0.5], and
 NU quantiles at u = U0 + i (1 - 2 U0)/(NU - 1) of z = (loss - mean loss)/xi, each node's values
 shifted by their mean so that the sampled fluctuation has mean zero.  Sampling: trilinear
 interpolation in (ln kappa, beta^2, u).
@@ -27,8 +27,8 @@ import numpy as np
 from scipy import special
 
 EULER = 0.5772156649015329
-NK, NB, NU = 31, 6, 513
-LNK0, LNK1 = np.log(0.01), np.log(10.0)
+NK, NB, NU = 41, 6, 513
+LNK0, LNK1 = np.log(0.001), np.log(10.0)
 B2MAX = 0.5
 U0 = 1e-4
 
@@ -48,8 +48,16 @@ def log_phi(tau, kappa, b2):
     return out
 
 
-def density(kappa, b2, n=1 << 14):
+def grid_points(kappa):
+    """Points of the inversion grid: the core of the distribution is about kappa wide (in units of
+    eps_max) while the grid spans a few eps_max, so thin layers need a finer grid (below kappa =
+    0.01 the step stays under 0.06 xi)."""
+    return 1 << 14 if kappa >= 0.01 else 1 << 16
+
+
+def density(kappa, b2, n=None):
     """(y, f, dy): the density f of the centred loss y (units of eps_max) on a uniform grid."""
+    n = n or grid_points(kappa)
     s = np.sqrt(kappa * (1.0 - 0.5 * b2))
     ylo, yhi = -10.0 * s - 0.05, 10.0 * s + 3.0
     L = yhi - ylo
@@ -89,7 +97,7 @@ def table():
 
 def sample_z(tab, kappa, b2, u):
     """Trilinear interpolation of the table (the sampler's definition)."""
-    a = (np.log(np.clip(kappa, 0.01, 10.0)) - LNK0) / (LNK1 - LNK0) * (NK - 1)
+    a = (np.log(np.clip(kappa, 0.001, 10.0)) - LNK0) / (LNK1 - LNK0) * (NK - 1)
     b = np.clip(b2, 0.0, B2MAX) / B2MAX * (NB - 1)
     c = np.asarray(u) * (NU - 1)
     ia = np.minimum(a.astype(int), NK - 2); fa = a - ia

@@ -241,7 +241,9 @@ void dft_forward(std::vector<std::complex<double>>& a) {
 
 // One table row: the kVavNU quantiles of z at (kappa, beta^2), shifted to mean zero.
 std::vector<double> vavilov_row(double kappa, double b2) {
-  const int n = 1 << 14;
+  // the distribution's core is about kappa wide (units of eps_max) and the grid spans a few
+  // eps_max: thin layers (kappa < 0.01) get a finer grid, keeping its step under 0.06 xi
+  const int n = kappa >= 0.01 ? 1 << 14 : 1 << 16;
   const double sd = std::sqrt(kappa * (1.0 - 0.5 * b2));
   const double ylo = -10.0 * sd - 0.05, yhi = 10.0 * sd + 3.0, L = yhi - ylo, dy = L / n;
   std::vector<std::complex<double>> a(n);

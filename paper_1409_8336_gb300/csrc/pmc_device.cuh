@@ -46,8 +46,8 @@ constexpr unsigned kNoStraggling = 1u, kNoMcs = 2u, kNoElastic = 4u, kNoInelasti
 // Vavilov straggling table: quantiles of z = (loss - mean loss) / xi on kVavNB values of beta^2
 // in [0, kVavB2Max], kVavNK values of ln kappa in [ln kVavK0, ln kVavK1] and kVavNU values of u
 // in [kVavU0, 1 - kVavU0], each row shifted to mean zero (trilinear sampling keeps it).
-constexpr int kVavNK = 31, kVavNB = 6, kVavNU = 513;
-constexpr double kVavK0 = 0.01, kVavK1 = 10.0, kVavB2Max = 0.5, kVavU0 = 1e-4;
+constexpr int kVavNK = 41, kVavNB = 6, kVavNU = 513;
+constexpr double kVavK0 = 0.001, kVavK1 = 10.0, kVavB2Max = 0.5, kVavU0 = 1e-4;
 constexpr int kMolN = 1025;                    // Moliere distribution-function nodes on v in [0, kMolVmax]
 constexpr float kMolVmax = 8.0f;
 constexpr float kMolBmin = 4.5f;               // validity floor of the expansion (Bethe)
@@ -316,7 +316,7 @@ __device__ __forceinline__ float moliere_b(const float4* T, int m, float lnE, fl
 // Vavilov straggling: the centred loss z (units of xi) for the uniform u at (kappa, beta^2),
 // trilinear in (ln kappa, beta^2, u); kappa is clamped to the table's range.
 __device__ __forceinline__ float vavilov_z(const float* __restrict__ T, float kappa, float b2, float u) {
-  const float lk0 = static_cast<float>(-4.605170185988091), lk1 = static_cast<float>(2.302585092994046);
+  const float lk0 = static_cast<float>(-6.907755278982137), lk1 = static_cast<float>(2.302585092994046);
   const float a = (fminf(fmaxf(logf(kappa), lk0), lk1) - lk0) * ((kVavNK - 1) / (lk1 - lk0));
   const float b = fminf(fmaxf(b2, 0.0f), static_cast<float>(kVavB2Max)) * ((kVavNB - 1) / static_cast<float>(kVavB2Max));
   const float c = u * (kVavNU - 1);

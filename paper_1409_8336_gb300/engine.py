@@ -686,9 +686,9 @@ def debug_philox(ctr, key, fast_math=False):
 
 
 def debug_vavilov_table(library: str | None = None):
-    """The Vavilov straggling table as built by the library's host code [6][31][513] (no device)."""
+    """The Vavilov straggling table as built by the library's host code [6][41][513] (no device)."""
     L = lib(library or LIB_PATH)
-    out = np.empty((6, 31, 513), dtype=np.float32)
+    out = np.empty((6, 41, 513), dtype=np.float32)
     rc = L.pmc_debug_vavilov_table(_fp(out), out.size)
     if rc != PMC_OK:
         raise PmcError(rc, "bad table size")

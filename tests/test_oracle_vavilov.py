@@ -13,7 +13,8 @@ from oracle import vavilov as V
 from paper_1409_8336_gb300 import workloads as W
 
 
-@pytest.mark.parametrize("kappa,b2", [(0.01, 0.0), (0.05, 0.3), (0.5, 0.1), (3.0, 0.45), (10.0, 0.2)])
+@pytest.mark.parametrize("kappa,b2", [(0.001, 0.2), (0.003, 0.0), (0.01, 0.0), (0.05, 0.3), (0.5, 0.1), (3.0, 0.45),
+                                     (10.0, 0.2)])
 def test_density_has_unit_mass_zero_mean_and_the_spectrum_variance(kappa, b2):
     """Var = int eps^2 w(eps) d eps = xi eps_max (1 - beta^2/2), i.e. kappa (1 - beta^2/2) in
     units of eps_max^2 (worked by hand from the spectrum)."""
@@ -54,6 +55,39 @@ def test_distribution_equals_collision_by_collision_simulation(kappa, b2):
     assert ks < 1.63 / np.sqrt(len(sample))          # 1 % critical value
 
 
+def test_thin_layer_distribution_equals_collision_by_collision_simulation():
+    """kappa = 0.001 (a 0.1 mm step in lung at 200 MeV): the Landau-like core is about kappa
+    eps_max wide, so the simulation keeps transfers down to x = 1e-7 (some 1e4 per sample; the
+    omitted ones add a variance kappa x_c, 1e-3 of the core's squared width) and the table's
+    quantiles are compared with the simulation's over the body of the distribution."""
+    kappa, b2, xc, n = 0.001, 0.35, 1e-7, 2000
+    rng = np.random.default_rng(11)
+    lam = kappa * ((1.0 / xc - 1.0) - b2 * np.log(1.0 / xc))
+    mean = kappa * (np.log(1.0 / xc) - b2 * (1.0 - xc))
+    m = rng.poisson(lam, size=n)
+    sample = np.empty(n)
+    for i in range(n):
+        u = rng.uniform(size=(2, int(1.3 * m[i]) + 16))
+        x = 1.0 / (1.0 / xc - u[0] * (1.0 / xc - 1.0))
+        x = x[u[1] < 1.0 - b2 * x][: m[i]]
+        assert len(x) == m[i]
+        sample[i] = x.sum() - mean
+    y, f, dy = V.density(kappa, b2)
+    cdf = np.cumsum(f) * dy
+    ks = stats.kstest(sample, lambda q: np.interp(q, y + 0.5 * dy, cdf)).statistic
+    assert ks < 1.63 / np.sqrt(n)                    # 1 % critical value
+    # the table row (units of xi, centred on its truncated mean) holds the density's quantiles
+    T = V.table()
+    u = np.array([0.05, 0.25, 0.5, 0.75, 0.95])
+    z_tab = np.array([float(V.sample_z(T, np.array(kappa), b2, q)) for q in u])
+    z_den = np.interp(u, cdf, y + 0.5 * dy) / kappa
+    assert np.all(np.abs(z_den - z_tab - np.median(z_den - z_tab)) < 0.05), (z_den, z_tab)
+    # below the old lower end of the table the spread keeps growing as kappa falls
+    s_tab = [float(V.sample_z(T, np.array(k), b2, 0.75)) - float(V.sample_z(T, np.array(k), b2, 0.25))
+             for k in (0.001, 0.01)]
+    assert s_tab[0] > s_tab[1] * 0.9
+
+
 def test_large_kappa_approaches_the_gaussian():
     u = V.U0 + np.arange(V.NU) * (1 - 2 * V.U0) / (V.NU - 1)
     sel = (u > 0.1) & (u < 0.9)
@@ -73,7 +107,7 @@ def test_table_rows_are_centred_and_the_samplers_agree():
     O._ensure_vavilov(L)
     rng = np.random.default_rng(3)
     for _ in range(50):
-        kappa, b2, u = np.exp(rng.uniform(np.log(0.005), np.log(12))), rng.uniform(0, 0.55), rng.uniform()
+        kappa, b2, u = np.exp(rng.uniform(np.log(0.0005), np.log(12))), rng.uniform(0, 0.55), rng.uniform()
         assert L.or_vavilov_z(kappa, b2, u) == pytest.approx(float(V.sample_z(T, np.array(kappa), b2, u)), abs=1e-12)
 
 
