@@ -55,10 +55,10 @@ L2_BYTES = 129 * 2 ** 20
 #        efficiency = that / 32) and thread instructions per condensed-history step.
 #   bytes_per_history: DRAM bytes (read + write) of a full 1e6-history primary launch per
 #        primary history: dram__bytes_read.sum + dram__bytes_write.sum alone (reported as one
-#        pass on the 2e5-history case first), one launch (-c 1): 45.35 + 4.56 MB.
+#        pass on the 2e5-history case first), one launch (-c 1): 45.40 + 4.51 MB.
 KERNEL_SOURCES = ("transport.cu", "transport_step.cuh", "pmc_device.cuh", "pmc_kernels.cuh")
-KERNEL_SHA256 = "a4ab02dfdc74b2038868dd32e206adb2c7642da9d638a9d8fcfb684284b6b348"
-NCU = {"issue_slots_busy": 0.7570, "threads_per_instruction": 21.38, "thread_instructions_per_step": 585.6,
+KERNEL_SHA256 = "0a9627c4fde6f62d80df72367203dd94e80833304d34a9ecb366ce3d28ed2e30"
+NCU = {"issue_slots_busy": 0.7570, "threads_per_instruction": 21.46, "thread_instructions_per_step": 585.4,
        "capture": "slab workload, 2e5 histories, first primary launch (-k regex:transport_kernel -c 1)"}
 TRAFFIC = {"bytes_per_history": 49.90}
 

@@ -453,6 +453,7 @@ struct pmc_ctx {
   DevBuf d_mat, d_rho, d_hu;
   // spots
   std::vector<pmc_spot> spots;
+  int n_spots_dev = 0;                  // spots in the device table of the last run (those with histories)
   // run buffers
   // queues: [0..2] ping, pong and events of stream A, [3..5] of stream B, [6] carry
   DevBuf d_tally, d_dose, d_sigma, d_counters, d_counts, d_seed, d_spots, d_q[kQueues];
@@ -1113,7 +1114,7 @@ TransportArgs transport_args(pmc_ctx* ctx) {
   a.B = ctx->opt.n_batches;
   a.seed = static_cast<const unsigned long long*>(ctx->d_seed.p);
   a.spots = static_cast<const SpotDev*>(ctx->d_spots.p);
-  a.n_spots = static_cast<int>(ctx->spots.size());
+  a.n_spots = ctx->n_spots_dev;
   a.cnt = static_cast<Counters*>(ctx->d_counters.p);
   a.hist = static_cast<long long*>(ctx->d_hist.p);
   a.hist_n = ctx->hist_n;
@@ -1358,6 +1359,7 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     if ((rc = dalloc(ctx, ctx->d_counts, (static_cast<size_t>(rp.n_chunks) * kSlots + 1) * sizeof(unsigned)))) return rc;
     if ((rc = dalloc(ctx, ctx->d_seed, sizeof(uint64_t)))) return rc;
     if ((rc = dalloc(ctx, ctx->d_spots, sd.size() * sizeof(SpotDev)))) return rc;
+    ctx->n_spots_dev = static_cast<int>(sd.size());   // spots without histories are not in the table
     const size_t qcap = static_cast<size_t>(std::max<int64_t>(rp.chunk, 1024));
     for (int i = 0; i < kQueues; ++i)
       if ((rc = dalloc(ctx, ctx->d_q[i], qcap * sizeof(Particle)))) return rc;
