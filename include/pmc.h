@@ -107,11 +107,20 @@ typedef struct { int lo, hi, material; double rho_a, rho_b; } pmc_hu_bin;
 typedef struct { double E, sigma_E, x, y, sigma_x, sigma_y, u, v, w, weight; } pmc_spot;
 
 /* Energy ledger of the last transport, in units of 2^-24 MeV:
- * incident = deposited + escaped + binding (+ rounding of a few units per event). */
+ * incident = deposited + escaped + binding (+ rounding of a few units per event).
+ * The counts: histories, condensed-history steps, elastic and non-elastic nuclear
+ * collisions, secondary protons queued, events without an allowed cascade
+ * (transparent) and cascade attempts redrawn, queue_high_water (unused, 0),
+ * generations (launch rounds: 2, the primaries and the drain of all later
+ * generations), particles dropped for want of queue room, errors (step limit or
+ * a bounded device wait that ran out), and the non-elastic events generated by
+ * the learned stand-in (surrogate mode: the primaries' events; the few events of
+ * later generations run the full cascade inside the drain). */
 typedef struct {
     int64_t incident, deposited, escaped, binding;
     int64_t histories, steps, elastic, inelastic, secondaries, transparent, inc_retries;
     int64_t queue_high_water, generations, dropped, errors;
+    int64_t surrogate_events;
 } pmc_ledger;
 
 /* Creates a context on opt->device (opt may be NULL for defaults). */
@@ -222,17 +231,21 @@ int pmc_set_launch(pmc_ctx* ctx, int block_size, int64_t chunk);
  * the trial runs overwrite the tallies. */
 int pmc_autotune(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int* block_out, int64_t* chunk_out);
 
-/* Kernel timing: with on = 1 the run records CUDA events around every kernel
- * launch on the run's stream (inside the captured graph); with on = 2 around
- * the primary-transport launches only (the lightest: about 3 % of a step
- * less than on = 1 on the slab workload); 0 turns it off.  Other values are
- * PMC_E_INVALID.
- * pmc_read_profile returns, per kernel kind (0 primary transport, 1 secondary
- * transport, 2 cascade, 3 dose statistics), for the last transport: in ms[0..3]
- * the summed milliseconds of its launches, in ms[4..7] the span from the first
- * launch's start to the last launch's end (launches of two sub-groups may run
- * concurrently), the number of launches in launches[4], and the
- * primary-transport step count in *primary_steps. */
+/* Kernel timing: with on = 1 the run records CUDA events around every launch
+ * group on the run's stream (inside the captured graph); with on = 2 around
+ * the primary-transport groups only (the lightest: about 3 % of a step less
+ * than on = 1 on the slab workload); 0 turns it off.  Other values are
+ * PMC_E_INVALID.  A group is the kernels of one stage launched back to back:
+ * phase space + transport for the primaries, cascade + evaporation, the
+ * secondary drain's set-up + drain, the dose statistics.
+ * pmc_read_profile returns, per kind (0 primary transport, 1 secondary
+ * transport -- the drain, which also runs the secondaries' cascades --,
+ * 2 cascade of the primaries' events, 3 dose statistics), for the last
+ * transport: in ms[0..3] the summed milliseconds of its groups, in ms[4..7]
+ * the span from the first group's start to the last group's end (groups of two
+ * sub-groups may run concurrently), in launches[0..3] the number of groups and
+ * in launches[4..7] the number of kernels they launched (launches has 8
+ * entries), and the primary-transport step count in *primary_steps. */
 int pmc_enable_profile(pmc_ctx* ctx, int on);
 int pmc_read_profile(pmc_ctx* ctx, double* ms, int64_t* launches, int64_t* primary_steps);
 
@@ -240,15 +253,15 @@ int pmc_read_profile(pmc_ctx* ctx, double* ms, int64_t* launches, int64_t* prima
  * For callers that cannot call cudaMalloc during a dose calculation -- a
  * real-time loop that must not stall on the allocator, or an application that
  * gave its whole device memory to its own pool.  The call itself synchronises
- * its stream after every generation and blocks until the run is done, so it
- * cannot be made from a CUDA stream callback (no CUDA call is allowed there) or
- * inside a stream capture.  It runs the full cascade (never the learned
+ * its stream and blocks until the run is done, so it cannot be made from a CUDA
+ * stream callback (no CUDA call is allowed there) or inside a stream capture.  It runs the full cascade (never the learned
  * stand-in), with the context's physics options, and produces the same tallies
  * as pmc_transport for the same seed; it does not score LET, the per-history
  * ledger, the escape record or the deposit log, and pmc_read_dose / pmc_read_let
  * keep returning the last allocating run's results (the caller's arrays hold
  * this run's).  All scratch (three particle queues, the residual nuclei
- * between cascade and evaporation, counters, spot table, seed) lives in one
+ * between cascade and evaporation, counters, the secondary drain's control block
+ * and ready marks, spot table, seed) lives in one
  * static device array of PMC_NOALLOC_SCRATCH_BYTES that every GPU loading this
  * library holds until the process exits.  Inputs are the context's loaded
  * materials, phantom and spots; outputs are caller-owned device arrays: tally
@@ -263,8 +276,9 @@ int pmc_read_profile(pmc_ctx* ctx, double* ms, int64_t* launches, int64_t* prima
  * pmc_read_ledger then reports this run. */
 #define PMC_NOALLOC_CHUNK 65536          /* histories per sub-group */
 #define PMC_NOALLOC_MAX_SPOTS 4096
-#define PMC_NOALLOC_SCRATCH_BYTES \
-    (3ull * PMC_NOALLOC_CHUNK * 48ull + PMC_NOALLOC_CHUNK * 128ull + 768ull + PMC_NOALLOC_MAX_SPOTS * 56ull)
+#define PMC_NOALLOC_SCRATCH_BYTES                                                                  \
+    (3ull * PMC_NOALLOC_CHUNK * 48ull + PMC_NOALLOC_CHUNK * 128ull + 1792ull + PMC_NOALLOC_CHUNK * 8ull + \
+     PMC_NOALLOC_MAX_SPOTS * 56ull)
 int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int64_t* tally,
                           double* dose_gy, double* sigma_gy, void* stream);
 

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libpmc.so")
 # -use_fast_math (hardware approximations of division, sqrt, log, exp, sin/cos),
 # the build option the method's authors timed and verified equivalent.
 VARIANTS = {"libpmc.so": [], "libpmc_fast.so": ["-use_fast_math"]}
-SOURCES = ["transport.cu", "cascade.cu", "stats.cu", "surrogate.cu", "gamma.cu", "host.cu"]
+SOURCES = ["transport.cu", "drain.cu", "cascade.cu", "stats.cu", "surrogate.cu", "gamma.cu", "host.cu"]
 HEADERS = ["pmc_device.cuh", "pmc_kernels.cuh", "transport_step.cuh", "cascade_event.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

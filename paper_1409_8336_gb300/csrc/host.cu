@@ -1,7 +1,8 @@
 // host.cu -- C ABI of the engine (include/pmc.h): physics-table construction in
 // double precision (Sec. II.A.2, II.A.4-5), device memory, the per-run kernel
-// sequence captured in a CUDA graph (Sec. II.B.2: primaries, then generations
-// of transport -> cascade until no secondary proton is left, then the dose
+// sequence captured in a CUDA graph (Sec. II.B.2: phase space and transport of
+// the primaries, the event stage of their non-elastic collisions, the drain of
+// every later generation until no secondary proton is left, then the dose
 // statistics), and the result read-back.
 #include <algorithm>
 #include <chrono>
@@ -25,7 +26,6 @@ using namespace pmc;
 
 namespace {
 
-constexpr int kGenerations = 10;        // transport -> cascade rounds captured per sub-group
 constexpr double kNA = 6.02214076e23;
 
 // ---------------------------------------------------------------------------
@@ -429,7 +429,7 @@ struct DevBuf {
 
 }  // namespace
 
-constexpr int kQueues = 7;
+constexpr int kQueues = 6;
 
 struct pmc_ctx {
   pmc_options opt{};
@@ -455,7 +455,8 @@ struct pmc_ctx {
   std::vector<pmc_spot> spots;
   int n_spots_dev = 0;                  // spots in the device table of the last run (those with histories)
   // run buffers
-  // queues: [0..2] ping, pong and events of stream A, [3..5] of stream B, [6] carry
+  // queues of stream A [0..2] and B [3..5]: phase space of the primaries, protons for the
+  // drain, events
   DevBuf d_tally, d_dose, d_sigma, d_counters, d_counts, d_seed, d_spots, d_q[kQueues];
   DevBuf d_hist, d_esc;
   uint64_t hist_n = 0, esc_cap = 0;
@@ -473,10 +474,12 @@ struct pmc_ctx {
   int profile = 0;                  // 0 off, 1 every launch, 2 primary-transport launches only
   std::vector<cudaEvent_t> events;      // pairs around launches
   std::vector<int> event_kind;          // kind per pair
+  std::vector<int> event_kernels;       // kernels launched inside each pair
   size_t n_events_used = 0;
   double prof_ms[4] = {0, 0, 0, 0};
   double prof_span[4] = {0, 0, 0, 0};   // first start to last end per kind (launches may overlap)
   int64_t prof_launches[4] = {0, 0, 0, 0};
+  int64_t prof_kernels[4] = {0, 0, 0, 0};
   int64_t steps_primary = 0;
   // learned stand-in of the event generator
   bool surr_trained = false;
@@ -486,6 +489,8 @@ struct pmc_ctx {
   DevBuf d_gws, d_gerr;                 // training GEMMs: split-K workspace, tensor-core wait errors
   DevBuf d_slot_nuc, d_nuc_slot;        // slot -> nuclide, nuclide -> slot
   DevBuf d_rec[2];               // residual nuclei between cascade and evaporation, per stream
+  DevBuf d_drain;                // per stream: drain control block, ready marks of its two queues
+  size_t drain_qcap = 0;         // the queue capacity the marks are laid out for
   size_t surr_cap = 0;
   int mode = PMC_FULL_CASCADE;          // mode of the captured graph
   // graph
@@ -627,14 +632,14 @@ void pmc_destroy(pmc_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->d_phys, &ctx->d_rt, &ctx->d_et, &ctx->d_st, &ctx->d_nuclei, &ctx->d_btab, &ctx->d_mol, &ctx->d_vav, &ctx->d_mat,
                     &ctx->d_rho, &ctx->d_hu, &ctx->d_tally, &ctx->d_dose, &ctx->d_sigma, &ctx->d_counters,
                     &ctx->d_counts, &ctx->d_seed, &ctx->d_spots, &ctx->d_q[0], &ctx->d_q[1], &ctx->d_q[2],
-                    &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_hist, &ctx->d_esc,
+                    &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_hist, &ctx->d_esc,
                     &ctx->d_let_num, &ctx->d_let_den, &ctx->d_let, &ctx->d_let_sigma, &ctx->d_yields,
                     &ctx->d_dlog, &ctx->d_dlog_cnt};
   if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
   if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
   for (DevBuf* b : bufs) dfree(ctx, *b);
   DevBuf* sbufs[] = {&ctx->d_swb, &ctx->d_sp, &ctx->d_sg, &ctx->d_sm, &ctx->d_sv, &ctx->d_slot_nuc, &ctx->d_nuc_slot,
-                     &ctx->d_rec[0], &ctx->d_rec[1], &ctx->d_gws, &ctx->d_gerr};
+                     &ctx->d_rec[0], &ctx->d_rec[1], &ctx->d_gws, &ctx->d_gerr, &ctx->d_drain};
   for (DevBuf* b : sbufs) dfree(ctx, *b);
   if (ctx->pool) cudaStreamSynchronize(ctx->stream);   // the stream-ordered frees have run
   cudaStreamDestroy(ctx->stream);
@@ -910,7 +915,7 @@ int pmc_read_profile(pmc_ctx* ctx, double* ms, int64_t* launches, int64_t* prima
   if (!ctx) return PMC_E_INVALID;
   for (int k = 0; k < 4; ++k) {
     if (ms) { ms[k] = ctx->prof_ms[k]; ms[4 + k] = ctx->prof_span[k]; }
-    if (launches) launches[k] = ctx->prof_launches[k];
+    if (launches) { launches[k] = ctx->prof_launches[k]; launches[4 + k] = ctx->prof_kernels[k]; }
   }
   if (primary_steps) *primary_steps = ctx->steps_primary;
   return PMC_OK;
@@ -999,13 +1004,17 @@ struct RunPlan {
   uint64_t n;
   int64_t chunk;
   int n_chunks;
-  int grid_t, grid_s, grid_c;   // transport grids of the primary and the secondary generations
+  int grid_t, grid_c;           // grids of the primary transport and of the cascade
   size_t smem;
+  int grid_d;                   // the drain's grid and shared memory
+  size_t smem_d;
 };
+
+
 
 // Records a timing event opening (open) or closing a pair around a launch of the given kind,
 // when that kind is profiled.
-int mark(pmc_ctx* ctx, cudaStream_t s, int kind, bool open) {
+int mark(pmc_ctx* ctx, cudaStream_t s, int kind, bool open, int kernels = 1) {
   if (!ctx->profile || (ctx->profile == 2 && kind != 0)) return PMC_OK;
   if (ctx->n_events_used == ctx->events.size()) {
     cudaEvent_t e;
@@ -1014,6 +1023,7 @@ int mark(pmc_ctx* ctx, cudaStream_t s, int kind, bool open) {
   }
   cudaEvent_t e = ctx->events[ctx->n_events_used++];
   if (open) ctx->event_kind.push_back(kind);
+  else ctx->event_kernels.push_back(kernels);
   CK(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
   return PMC_OK;
 }
@@ -1100,7 +1110,7 @@ int gemm_errors(pmc_ctx* ctx) {
   return fail(ctx, PMC_E_TIMEOUT, "%d training GEMM tiles: tensor-core waits timed out", e);
 }
 
-// Kernel arguments of one generation.
+// Kernel arguments of the primaries' transport.
 TransportArgs transport_args(pmc_ctx* ctx) {
   TransportArgs a{};
   a.phys = static_cast<const Physics*>(ctx->d_phys.p);
@@ -1152,16 +1162,16 @@ CascadeArgs cascade_args(pmc_ctx* ctx) {
   return c;
 }
 
-// Enqueues one transport -> cascade generation.
-int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int source, uint64_t w0, uint64_t w1,
-                       Particle* qin, unsigned* qin_count, Particle* qout, unsigned* qout_count, Particle* qne,
-                       unsigned* qne_count, unsigned* work, unsigned* cwork, unsigned* rcount) {
+// Enqueues the primaries w0..w1-1 (phase space into qin, transport) and the event stage of
+// their non-elastic collisions (cascade + evaporation, or the learned stand-in); secondary
+// protons go to qout, counted in *qout_count, for the drain.
+int enqueue_primaries(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, uint64_t w0, uint64_t w1, Particle* qin,
+                      Particle* qout, unsigned* qout_count, Particle* qne, unsigned* qne_count, unsigned* work,
+                      unsigned* cwork, unsigned* rcount) {
   TransportArgs a = transport_args(ctx);
-  a.source = source;
   a.w_begin = w0;
   a.w_end = w1;
   a.qin = qin;
-  a.qin_count = qin_count;
   a.qin_cap = static_cast<unsigned>(ctx->q_cap);
   a.qsec = qout;
   a.qsec_count = qout_count;
@@ -1171,10 +1181,9 @@ int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int sour
   a.qne_cap = static_cast<unsigned>(ctx->q_cap);
   a.work = work;
   int rc;
-  const int kind = source == 0 ? 0 : 1;
-  if ((rc = mark(ctx, s, kind, true))) return rc;
-  CK(launch_transport(a, source == 0 ? rp.grid_t : rp.grid_s, ctx->block, rp.smem, s));
-  if ((rc = mark(ctx, s, kind, false))) return rc;
+  if ((rc = mark(ctx, s, 0, true))) return rc;
+  CK(launch_transport(a, rp.grid_t, ctx->block, rp.smem, s));
+  if ((rc = mark(ctx, s, 0, false, 2))) return rc;   // phase space + transport
   if (ctx->mode == PMC_SURROGATE) {
     const float* P = static_cast<const float*>(ctx->d_sp.p);
     const unsigned cap = static_cast<unsigned>(ctx->q_cap);
@@ -1199,7 +1208,41 @@ int enqueue_generation(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int sour
   c.work = cwork;
   if ((rc = mark(ctx, s, 2, true))) return rc;
   CK(launch_cascade(c, s));
-  if ((rc = mark(ctx, s, 2, false))) return rc;
+  if ((rc = mark(ctx, s, 2, false, 2))) return rc;   // cascade + evaporation
+  return PMC_OK;
+}
+
+// The drain's buffers of queue set qs (0, 1): its control block and the ready marks of its
+// particle and event queues.
+DrainCtl* drain_ctl(pmc_ctx* ctx, int qs) {
+  return reinterpret_cast<DrainCtl*>(static_cast<unsigned char*>(ctx->d_drain.p) + qs * sizeof(DrainCtl));
+}
+unsigned* drain_ready(pmc_ctx* ctx, int qs, int which) {
+  unsigned* r = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(ctx->d_drain.p) + 2 * sizeof(DrainCtl));
+  return r + (2 * qs + which) * ctx->q_cap;
+}
+size_t drain_buffer_bytes(size_t q_cap) { return 2 * sizeof(DrainCtl) + 4 * q_cap * sizeof(unsigned); }
+
+// Enqueues the drain of a sub-group: its particle queue pq already holds *pq_n the protons of
+// the first generation; its events, if eq_n is given, are still queued in eq.
+int enqueue_drain(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int qs, Particle* pq, const unsigned* pq_n,
+                  Particle* eq, const unsigned* eq_n) {
+  DrainArgs d{};
+  d.t = transport_args(ctx);
+  d.c = cascade_args(ctx);
+  d.pq = pq;
+  d.pq_ready = drain_ready(ctx, qs, 0);
+  d.pq_cap = static_cast<unsigned>(ctx->q_cap);
+  d.pq_n0 = pq_n;
+  d.eq = eq;
+  d.eq_ready = drain_ready(ctx, qs, 1);
+  d.eq_cap = static_cast<unsigned>(ctx->q_cap);
+  d.eq_n0 = eq_n;
+  d.ctl = drain_ctl(ctx, qs);
+  int rc;
+  if ((rc = mark(ctx, s, 1, true))) return rc;
+  CK(launch_drain(d, rp.grid_d, ctx->block, rp.smem_d, s));
+  if ((rc = mark(ctx, s, 1, false, 2))) return rc;   // control block set-up + drain
   return PMC_OK;
 }
 
@@ -1221,17 +1264,18 @@ StatsArgs stats_args(pmc_ctx* ctx) {
   return sa;
 }
 
-// Count slots per sub-group: [0, G]: secondary queue counts; [G+1, 2G]: event
-// queue counts; [2G+1, 3G]: transport work counters; [3G+1, 4G]: cascade work
-// counters; [4G+1, 5G]: residual counts.  A final slot holds the carry count.
-constexpr int kSlots = 5 * kGenerations + 1;
+// Count slots per sub-group: [0] unused (the primaries' count is the work range), [1] protons
+// queued for the drain, [2] events of the primaries, [3] transport work counter, [4] cascade
+// work counter, [5] residual nuclei.
+constexpr int kSlots = 8;
 
 int enqueue_run(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s) {
   ctx->n_events_used = 0;
   ctx->event_kind.clear();
+  ctx->event_kernels.clear();
   CK(cudaMemsetAsync(ctx->d_tally.p, 0, static_cast<size_t>(ctx->n_vox) * ctx->opt.n_batches * 8, s));
   CK(cudaMemsetAsync(ctx->d_counters.p, 0, sizeof(Counters), s));
-  CK(cudaMemsetAsync(ctx->d_counts.p, 0, (static_cast<size_t>(rp.n_chunks) * kSlots + 1) * sizeof(unsigned), s));
+  CK(cudaMemsetAsync(ctx->d_counts.p, 0, static_cast<size_t>(rp.n_chunks) * kSlots * sizeof(unsigned), s));
   if (ctx->d_hist.p) CK(cudaMemsetAsync(ctx->d_hist.p, 0, ctx->hist_n * 4 * sizeof(long long), s));
   if (ctx->dlog_cap) CK(cudaMemsetAsync(ctx->d_dlog_cnt.p, 0, sizeof(unsigned long long), s));
   if (ctx->let_on) {
@@ -1239,13 +1283,14 @@ int enqueue_run(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s) {
     CK(cudaMemsetAsync(ctx->d_let_den.p, 0, static_cast<size_t>(ctx->n_vox) * ctx->opt.n_batches * 8, s));
   }
   unsigned* counts = static_cast<unsigned*>(ctx->d_counts.p);
-  unsigned* carry_count = counts + static_cast<size_t>(rp.n_chunks) * kSlots;
   Particle* q[kQueues];
   for (int i = 0; i < kQueues; ++i) q[i] = static_cast<Particle*>(ctx->d_q[i].p);
-  // Sub-groups alternate between two streams (forked and joined inside the
-  // graph): the latency-bound tail generations of one sub-group overlap the
-  // full-width launches of the next.  Each stream has its own three queues;
-  // tallies and counters are shared through atomics.
+  // Per sub-group: the primaries (phase space, transport), the event stage of their
+  // non-elastic collisions (cascade and evaporation, or the learned stand-in), then the drain
+  // of everything that left (every later generation, with the full cascade, in one launch).
+  // Sub-groups alternate between two streams (forked and joined inside the graph): the
+  // latency-bound drain of one sub-group overlaps the full-width launches of the next.  Each
+  // stream has its own three queues; tallies and counters are shared through atomics.
   const bool two = rp.n_chunks > 1;
   if (two) {
     CK(cudaEventRecord(ctx->fork_ev, s));
@@ -1257,15 +1302,10 @@ int enqueue_run(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s) {
     unsigned* cs = counts + static_cast<size_t>(c) * kSlots;
     const uint64_t w0 = static_cast<uint64_t>(c) * rp.chunk;
     const uint64_t w1 = std::min<uint64_t>(rp.n, w0 + rp.chunk);
-    for (int g = 0; g < kGenerations; ++g) {
-      const bool last = g == kGenerations - 1;
-      Particle* out = last ? q[6] : qs[(g + 1) & 1];
-      unsigned* out_count = last ? carry_count : cs + g + 1;
-      int rc = enqueue_generation(ctx, rp, sc, g == 0 ? 0 : 1, w0, w1, qs[g & 1], cs + g, out, out_count, qs[2],
-                                  cs + kGenerations + 1 + g, cs + 2 * kGenerations + 1 + g,
-                                  cs + 3 * kGenerations + 1 + g, cs + 4 * kGenerations + 1 + g);
-      if (rc) return rc;
-    }
+    int rc = enqueue_primaries(ctx, rp, sc, w0, w1, qs[0], qs[1], cs + 1, qs[2], cs + 2, cs + 3, cs + 4, cs + 5);
+    if (rc) return rc;
+    rc = enqueue_drain(ctx, rp, sc, (two && (c & 1)) ? 1 : 0, qs[1], cs + 1, qs[2], nullptr);
+    if (rc) return rc;
   }
   if (two) {
     CK(cudaEventRecord(ctx->join_ev, ctx->stream2));
@@ -1336,13 +1376,17 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     rp.chunk = std::min<int64_t>(chunk, static_cast<int64_t>(n_histories));
     rp.n_chunks = static_cast<int>((n_histories + rp.chunk - 1) / rp.chunk);
     rp.smem = transport_smem_bytes(ctx->phys.n_cls, ctx->phys.n_mat, ctx->d_mol.p != nullptr);
-    int bps = 0, bps2 = 0;
-    CK(transport_occupancy(ctx->block, rp.smem, &bps, &bps2));
-    if (bps < 1 || bps2 < 1)
+    int bps = 0;
+    CK(transport_occupancy(ctx->block, rp.smem, &bps));
+    if (bps < 1)
       return fail(ctx, PMC_E_CUDA, "transport kernel does not fit (block %d, smem %zu)", ctx->block, rp.smem);
     rp.grid_t = ctx->n_sm * bps;
-    rp.grid_s = ctx->n_sm * bps2;
     rp.grid_c = ctx->n_sm * 8;      // one tile of 128 events per block for typical event counts
+    rp.smem_d = drain_smem_bytes(ctx->phys.n_cls, ctx->phys.n_mat, ctx->d_mol.p != nullptr, ctx->phys.n_nuc);
+    int bpd = 0;
+    CK(drain_occupancy(ctx->block, rp.smem_d, &bpd));
+    if (bpd < 1) return fail(ctx, PMC_E_CUDA, "drain kernel does not fit (block %d, smem %zu)", ctx->block, rp.smem_d);
+    rp.grid_d = ctx->n_sm * bpd;
     // buffers
     int rc;
     const size_t B = ctx->opt.n_batches;
@@ -1356,7 +1400,7 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
       if ((rc = dalloc(ctx, ctx->d_let_sigma, static_cast<size_t>(ctx->n_vox) * 8))) return rc;
     }
     if ((rc = dalloc(ctx, ctx->d_counters, sizeof(Counters)))) return rc;
-    if ((rc = dalloc(ctx, ctx->d_counts, (static_cast<size_t>(rp.n_chunks) * kSlots + 1) * sizeof(unsigned)))) return rc;
+    if ((rc = dalloc(ctx, ctx->d_counts, static_cast<size_t>(rp.n_chunks) * kSlots * sizeof(unsigned)))) return rc;
     if ((rc = dalloc(ctx, ctx->d_seed, sizeof(uint64_t)))) return rc;
     if ((rc = dalloc(ctx, ctx->d_spots, sd.size() * sizeof(SpotDev)))) return rc;
     ctx->n_spots_dev = static_cast<int>(sd.size());   // spots without histories are not in the table
@@ -1364,6 +1408,13 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     for (int i = 0; i < kQueues; ++i)
       if ((rc = dalloc(ctx, ctx->d_q[i], qcap * sizeof(Particle)))) return rc;
     ctx->q_cap = ctx->d_q[0].n / sizeof(Particle);
+    if (!ctx->d_drain.p || ctx->drain_qcap != ctx->q_cap) {
+      // control blocks and ready marks start at zero together (the stamps count up from
+      // there), again whenever the marks' layout changes with the queue capacity
+      if ((rc = dalloc(ctx, ctx->d_drain, drain_buffer_bytes(ctx->q_cap)))) return rc;
+      CK(cudaMemsetAsync(ctx->d_drain.p, 0, ctx->d_drain.n, s));
+      ctx->drain_qcap = ctx->q_cap;
+    }
     if (mode == PMC_FULL_CASCADE) {
       for (int si = 0; si < 2; ++si)
         if ((rc = dalloc(ctx, ctx->d_rec[si], ctx->q_cap * sizeof(EvapRecord)))) return rc;
@@ -1391,13 +1442,13 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
       ctx->gkey = key;
     }
     CK(cudaGraphLaunch(ctx->gexec, s));
-    // secondaries beyond the captured generations: drain them eagerly
-    unsigned* counts = static_cast<unsigned*>(ctx->d_counts.p);
-    unsigned* carry_count = counts + static_cast<size_t>(rp.n_chunks) * kSlots;
-    unsigned carry = 0;
-    CK(cudaMemcpyAsync(&carry, carry_count, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    for (int k = 0; k < 4; ++k) { ctx->prof_ms[k] = 0.0; ctx->prof_launches[k] = 0; ctx->prof_span[k] = 0.0; }
+    for (int k = 0; k < 4; ++k) {
+      ctx->prof_ms[k] = 0.0;
+      ctx->prof_launches[k] = 0;
+      ctx->prof_kernels[k] = 0;
+      ctx->prof_span[k] = 0.0;
+    }
     if (ctx->profile && !ctx->event_kind.empty()) {
       double lo[4] = {1e300, 1e300, 1e300, 1e300}, hi[4] = {-1e300, -1e300, -1e300, -1e300};
       for (size_t i = 0; i < ctx->event_kind.size(); ++i) {
@@ -1408,32 +1459,12 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
         CK(cudaEventElapsedTime(&t1, ctx->events[0], ctx->events[2 * i + 1]));
         ctx->prof_ms[k] += ms;
         ctx->prof_launches[k] += 1;
+        ctx->prof_kernels[k] += i < ctx->event_kernels.size() ? ctx->event_kernels[i] : 1;
         lo[k] = std::min(lo[k], static_cast<double>(t0));
         hi[k] = std::max(hi[k], static_cast<double>(t1));
       }
       for (int k = 0; k < 4; ++k)
         if (ctx->prof_launches[k]) ctx->prof_span[k] = hi[k] - lo[k];
-    }
-    int extra = 0;
-    if (carry > 0) {
-      Particle* q[kQueues];
-      for (int i = 0; i < kQueues; ++i) q[i] = static_cast<Particle*>(ctx->d_q[i].p);
-      unsigned* cs = counts;   // reuse the first sub-group's slots
-      CK(cudaMemcpyAsync(q[0], q[6], static_cast<size_t>(std::min<size_t>(carry, ctx->q_cap)) * sizeof(Particle),
-                         cudaMemcpyDeviceToDevice, s));
-      unsigned n_in = carry;
-      while (n_in > 0) {
-        if (++extra > 100000) return fail(ctx, PMC_E_TIMEOUT, "secondary generations did not terminate");
-        CK(cudaMemcpyAsync(cs, &n_in, sizeof(unsigned), cudaMemcpyHostToDevice, s));
-        CK(cudaMemsetAsync(cs + 1, 0, 5 * sizeof(unsigned), s));
-        int r2 = enqueue_generation(ctx, rp, s, 1, 0, 0, q[0], cs, q[1], cs + 1, q[2], cs + 2, cs + 3, cs + 4, cs + 5);
-        if (r2) return r2;
-        CK(cudaMemcpyAsync(&n_in, cs + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        n_in = std::min<unsigned>(n_in, static_cast<unsigned>(ctx->q_cap));
-        if (n_in) CK(cudaMemcpyAsync(q[0], q[1], n_in * sizeof(Particle), cudaMemcpyDeviceToDevice, s));
-      }
-      CK(launch_stats(stats_args(ctx), s));
     }
     Counters hc{};
     CK(cudaMemcpyAsync(&hc, ctx->d_counters.p, sizeof(Counters), cudaMemcpyDeviceToHost, s));
@@ -1452,9 +1483,10 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     L.transparent = static_cast<int64_t>(hc.transparent);
     L.inc_retries = static_cast<int64_t>(hc.inc_retries);
     L.queue_high_water = 0;
-    L.generations = kGenerations + extra;
+    L.generations = 2;   // the primaries, then the drain of all later generations
     L.dropped = static_cast<int64_t>(hc.dropped);
     L.errors = static_cast<int64_t>(hc.errors);
+    L.surrogate_events = static_cast<int64_t>(hc.surrogate_events);
     ctx->steps_primary = static_cast<int64_t>(hc.steps_primary);
     ctx->have_run = true;
     ctx->let_valid = ctx->let_on;
@@ -1805,8 +1837,8 @@ int pmc_debug_event_stage(pmc_ctx* ctx, int mode, const int* nuclide, const doub
 // entry point runs the same kernels as pmc_transport (the full cascade) but
 // keeps every piece of scratch (particle queues, counters, spot table, seed)
 // in one static device array; the caller supplies the output arrays.  It
-// synchronises its stream after every generation, so it cannot run inside a
-// stream callback or a stream capture.
+// synchronises its stream before it returns, so it cannot run inside a stream
+// callback or a stream capture.
 //
 // The array lives in every GPU that loads this library until the process
 // exits.  All calls on a device share it and it keeps the last call's
@@ -1819,11 +1851,14 @@ int pmc_debug_event_stage(pmc_ctx* ctx, int mode, const int* nuclide, const doub
 namespace {
 
 constexpr size_t kNaQueue = static_cast<size_t>(PMC_NOALLOC_CHUNK) * sizeof(Particle);
-constexpr size_t kNaRec = 3 * kNaQueue;   // queues: generation input, output, events
+constexpr size_t kNaRec = 3 * kNaQueue;   // queues: primaries' phase space, protons for the drain, events
 constexpr size_t kNaCounters = kNaRec + static_cast<size_t>(PMC_NOALLOC_CHUNK) * sizeof(EvapRecord);
 constexpr size_t kNaCounts = kNaCounters + 256;
 constexpr size_t kNaSeed = kNaCounts + 256;
-constexpr size_t kNaSpots = kNaSeed + 256;
+constexpr size_t kNaDrain = kNaSeed + 256;       // the drain's control block
+constexpr size_t kNaReady = kNaDrain + 1024;     // ready marks of the drain's particle and event queues
+static_assert(sizeof(DrainCtl) <= 1024, "the drain's control block fits its slot");
+constexpr size_t kNaSpots = kNaReady + 2ull * PMC_NOALLOC_CHUNK * sizeof(unsigned);
 constexpr size_t kNaBytes = kNaSpots + static_cast<size_t>(PMC_NOALLOC_MAX_SPOTS) * sizeof(SpotDev);
 static_assert(kNaBytes == PMC_NOALLOC_SCRATCH_BYTES, "scratch size stated in pmc.h");
 static_assert(sizeof(Counters) <= 256, "counters fit their slot");
@@ -1907,11 +1942,11 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     CK(cudaMemsetAsync(tally, 0, static_cast<size_t>(ctx->n_vox) * B * 8, s));
     CK(cudaMemsetAsync(counters, 0, sizeof(Counters), s));
     const size_t smem = transport_smem_bytes(ctx->phys.n_cls, ctx->phys.n_mat, ctx->d_mol.p != nullptr);
-    int bps = 0, bps2 = 0;
-    CK(transport_occupancy(ctx->block, smem, &bps, &bps2));
-    if (bps < 1 || bps2 < 1)
+    int bps = 0;
+    CK(transport_occupancy(ctx->block, smem, &bps));
+    if (bps < 1)
       return fail(ctx, PMC_E_CUDA, "transport kernel does not fit (block %d, smem %zu)", ctx->block, smem);
-    const int grid_t = ctx->n_sm * bps, grid_s = ctx->n_sm * bps2;
+    const int grid_t = ctx->n_sm * bps;
     TransportArgs ta{};
     ta.phys = static_cast<const Physics*>(ctx->d_phys.p);
     ta.rtab = static_cast<const float2*>(ctx->d_rt.p);
@@ -1939,42 +1974,47 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     ca.qne_cap = ca.qsec_cap = PMC_NOALLOC_CHUNK;
     ca.rec = reinterpret_cast<EvapRecord*>(base + kNaRec);
     ca.rec_cap = PMC_NOALLOC_CHUNK;
-    // sub-groups of PMC_NOALLOC_CHUNK primaries; each runs its generations until no
-    // secondary proton is left (counts: [0] input, [1] output, [2] events, [3] transport
-    // work, [4] cascade work, [5] residuals)
+    DrainArgs da{};
+    da.t = ta;
+    da.c = ca;
+    da.pq = q[1];
+    da.pq_ready = reinterpret_cast<unsigned*>(base + kNaReady);
+    da.pq_cap = PMC_NOALLOC_CHUNK;
+    da.pq_n0 = counts + 1;
+    da.eq = q[2];
+    da.eq_ready = da.pq_ready + PMC_NOALLOC_CHUNK;
+    da.eq_cap = PMC_NOALLOC_CHUNK;
+    da.eq_n0 = nullptr;
+    da.ctl = reinterpret_cast<DrainCtl*>(base + kNaDrain);
+    const size_t smem_d = drain_smem_bytes(ctx->phys.n_cls, ctx->phys.n_mat, ctx->d_mol.p != nullptr, ctx->phys.n_nuc);
+    int bpd = 0;
+    CK(drain_occupancy(ctx->block, smem_d, &bpd));
+    if (bpd < 1) return fail(ctx, PMC_E_CUDA, "drain kernel does not fit (block %d, smem %zu)", ctx->block, smem_d);
+    // sub-groups of PMC_NOALLOC_CHUNK primaries: the primaries (phase space, transport, the
+    // cascades of their events), then the drain of everything they left (counts: [1] protons
+    // queued for the drain, [2] events, [3] transport work, [4] cascade work, [5] residuals)
     for (uint64_t w0 = 0; w0 < n_histories; w0 += PMC_NOALLOC_CHUNK) {
       const uint64_t w1 = std::min<uint64_t>(n_histories, w0 + PMC_NOALLOC_CHUNK);
-      unsigned n_in = 0;
-      for (int g = 0;; ++g) {
-        if (g > 100000) return fail(ctx, PMC_E_TIMEOUT, "secondary generations did not terminate");
-        Particle* qin = q[g & 1];
-        Particle* qout = q[(g + 1) & 1];
-        CK(cudaMemsetAsync(counts + 1, 0, 5 * sizeof(unsigned), s));
-        CK(cudaMemcpyAsync(counts, &n_in, sizeof(unsigned), cudaMemcpyHostToDevice, s));
-        ta.source = g == 0 ? 0 : 1;
-        ta.w_begin = w0;
-        ta.w_end = w1;
-        ta.qin = qin;
-        ta.qin_count = counts;
-        ta.qsec = qout;
-        ta.qsec_count = counts + 1;
-        ta.qne = q[2];
-        ta.qne_count = counts + 2;
-        ta.work = counts + 3;
-        CK(launch_transport(ta, ta.source == 0 ? grid_t : grid_s, ctx->block, smem, s));
-        ca.qne = q[2];
-        ca.qne_count = counts + 2;
-        ca.qsec = qout;
-        ca.qsec_count = counts + 1;
-        ca.work = counts + 4;
-        ca.rec_count = counts + 5;
-        CK(launch_cascade(ca, s));
-        unsigned n_out = 0;
-        CK(cudaMemcpyAsync(&n_out, counts + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        n_in = std::min<unsigned>(n_out, PMC_NOALLOC_CHUNK);
-        if (n_in == 0) break;
-      }
+      CK(cudaMemsetAsync(counts, 0, 6 * sizeof(unsigned), s));
+      ta.w_begin = w0;
+      ta.w_end = w1;
+      ta.qin = q[0];
+      ta.qsec = q[1];
+      ta.qsec_count = counts + 1;
+      ta.qne = q[2];
+      ta.qne_count = counts + 2;
+      ta.work = counts + 3;
+      CK(launch_transport(ta, grid_t, ctx->block, smem, s));
+      ca.qne = q[2];
+      ca.qne_count = counts + 2;
+      ca.qsec = q[1];
+      ca.qsec_count = counts + 1;
+      ca.work = counts + 4;
+      ca.rec_count = counts + 5;
+      CK(launch_cascade(ca, s));
+      da.t = ta;
+      da.c = ca;
+      CK(launch_drain(da, ctx->n_sm * bpd, ctx->block, smem_d, s));
     }
     if (dose_gy) {
       StatsArgs sa{};
@@ -2401,8 +2441,8 @@ extern "C" int pmc_gamma_index(const double* ref, const double* eval, int nx, in
 // serves a list of plans in order.  A plan is admitted when its device
 // footprint fits in what the budget leaves; its slot then uploads the phantom,
 // transports, copies the dose out and releases the plan's buffers.  The slots'
-// persistent kernels share the SMs, so the tail generations of one plan overlap
-// the full-width launches of another.  All allocation is stream-ordered from
+// persistent kernels share the SMs, so the latency-bound drain of one plan
+// overlaps the full-width launches of another.  All allocation is stream-ordered from
 // one memory pool: a plan starting or ending never synchronises the device.
 struct pmc_plan_stream {
   pmc_options opt{};
@@ -2438,7 +2478,8 @@ uint64_t plan_footprint(const pmc_options& opt, const pmc_plan& pl, int mode) {
   b += pl.hu ? pool_round(nv * 2) : pool_round(nv) + pool_round(nv * 4);
   b += pool_round(nv * B * 8) + 2 * pool_round(nv * 8);
   b += kQueues * pool_round(qcap * sizeof(Particle));
-  b += pool_round((n_chunks * (3 * kGenerations + 1) + 1) * sizeof(unsigned));
+  b += pool_round(n_chunks * kSlots * sizeof(unsigned));
+  b += pool_round(drain_buffer_bytes(qcap));
   b += pool_round(sizeof(Counters)) + pool_round(8) + pool_round(static_cast<uint64_t>(pl.n_spots) * sizeof(SpotDev));
   if (mode != PMC_SURROGATE) b += 2 * pool_round(qcap * sizeof(EvapRecord));
   return b;
@@ -2448,9 +2489,10 @@ uint64_t plan_footprint(const pmc_options& opt, const pmc_plan& pl, int mode) {
 void release_plan(pmc_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->d_mat, &ctx->d_rho, &ctx->d_hu, &ctx->d_tally, &ctx->d_dose, &ctx->d_sigma,
                     &ctx->d_counters, &ctx->d_counts, &ctx->d_seed, &ctx->d_spots, &ctx->d_q[0], &ctx->d_q[1],
-                    &ctx->d_q[2], &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_q[6], &ctx->d_rec[0],
-                    &ctx->d_rec[1]};
+                    &ctx->d_q[2], &ctx->d_q[3], &ctx->d_q[4], &ctx->d_q[5], &ctx->d_rec[0], &ctx->d_rec[1],
+                    &ctx->d_drain};
   for (DevBuf* b : bufs) dfree(ctx, *b);
+  ctx->drain_qcap = 0;
   if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
   ctx->have_phantom = false;
   ctx->have_run = false;

@@ -142,6 +142,7 @@ struct Counters {
   unsigned long long incident, deposited, escaped, binding;
   unsigned long long steps, elastic, inelastic, secondaries, transparent, inc_retries;
   unsigned long long dropped, errors, esc_count, steps_primary;
+  unsigned long long surrogate_events;   // events generated by the learned stand-in
 };
 
 // ---------------------------------------------------------------------------

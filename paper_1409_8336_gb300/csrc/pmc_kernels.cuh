@@ -53,12 +53,10 @@ struct TransportArgs {
   unsigned long long* tally;       // [n_voxels][B]
   int B;
   const unsigned long long* seed;  // device scalar
-  int source;                      // 0: primaries w_begin..w_end; 1: queue qin
   const SpotDev* spots;
   int n_spots;
-  unsigned long long w_begin, w_end;
-  const Particle* qin;
-  const unsigned* qin_count;
+  unsigned long long w_begin, w_end;   // the primaries of this launch, in work order
+  Particle* qin;                   // their sampled states (PrimaryRecord, one per slot) [qin_cap]
   unsigned qin_cap;
   Particle* qsec;
   unsigned* qsec_count;
@@ -117,6 +115,41 @@ struct CascadeArgs {
   unsigned long long dlog_cap;
 };
 
+// Control block of a drain launch (device memory; the stamp survives from run to run, so
+// the block and the ready flags are zeroed together once, when they are allocated).  Each
+// counter that many warps update or poll has a 128-byte line of its own.
+struct DrainCounter {
+  unsigned v;
+  unsigned pad[31];
+};
+struct DrainCtl {
+  DrainCounter pq_tail, pq_head;   // particle queue: slots reserved by producers / taken by lanes
+  DrainCounter eq_tail, eq_head;   // event queue: the same
+  DrainCounter completed;          // items finished (or dropped for want of room)
+  unsigned pq_n0, eq_n0;           // slots written before the launch
+  unsigned error;                  // a bounded wait ran out
+  unsigned stamp;                  // this launch's ready mark
+  unsigned pad[28];
+};
+static_assert(sizeof(DrainCtl) == 768, "drain control block is six 128-byte lines");
+
+// The secondary generations of a sub-group in one launch: the transport and cascade
+// argument blocks (their queue fields unused), the particle and event queues with a ready
+// mark per slot, and where the items already queued are counted.
+struct DrainArgs {
+  TransportArgs t;
+  CascadeArgs c;
+  Particle* pq;                    // protons to transport [pq_cap]
+  unsigned* pq_ready;
+  unsigned pq_cap;
+  const unsigned* pq_n0;           // protons queued before the launch
+  Particle* eq;                    // non-elastic events [eq_cap]
+  unsigned* eq_ready;
+  unsigned eq_cap;
+  const unsigned* eq_n0;           // events queued before the launch, or NULL
+  DrainCtl* ctl;
+};
+
 struct StatsArgs {
   const unsigned long long* tally;
   int B;
@@ -132,13 +165,19 @@ struct StatsArgs {
 };
 
 size_t transport_smem_bytes(int n_cls, int n_mat, bool moliere);
+// The primaries w_begin..w_end-1: phase space into a.qin (capacity a.qin_cap), then transport.
 cudaError_t launch_transport(const TransportArgs& a, int grid, int block, size_t smem, cudaStream_t s);
-// Resident blocks per SM of the primary- and secondary-generation transport kernels.
-cudaError_t transport_occupancy(int block, size_t smem, int* blocks_primary, int* blocks_secondary);
+// Resident blocks per SM of the transport kernel.
+cudaError_t transport_occupancy(int block, size_t smem, int* blocks);
 // The cascade of the events in a.qne (persistent, lanes refilled from a.work) and the
 // evaporation of their residuals (a.rec); a.work and a.rec_count must be zero.
 cudaError_t launch_cascade(const CascadeArgs& a, cudaStream_t s);
 cudaError_t launch_stats(const StatsArgs& a, cudaStream_t s);
+// Shared memory, resident blocks per SM and launch of the drain (its control block is set up
+// by a one-thread kernel launched first, on the same stream).
+size_t drain_smem_bytes(int n_cls, int n_mat, bool moliere, int n_nuc);
+cudaError_t drain_occupancy(int block, size_t smem, int* blocks);
+cudaError_t launch_drain(const DrainArgs& d, int grid, int block, size_t smem, cudaStream_t s);
 
 cudaError_t launch_surrogate_dataset(const NucleusModel* nuclei, const float* btab, const int* slot_nuc, int n_slots,
                                      unsigned long long seed, unsigned long long n, float* out, cudaStream_t s);

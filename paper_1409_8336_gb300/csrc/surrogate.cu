@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(128, 2) surrogate_event_kernel(const unsigned*
   const unsigned long long seed = *seedp;
   const uint2 key = make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32));
   long long dep = 0, esc = 0;
-  unsigned long long sec = 0, dropped = 0;
+  unsigned long long sec = 0, dropped = 0, n_done = 0;
   for (unsigned r0 = blockIdx.x * tc::kRows; r0 < rows; r0 += gridDim.x * tc::kRows) {
     const int nvalid = static_cast<int>(min(static_cast<unsigned>(tc::kRows), rows - r0));
     float x[kSurrIn], y1[kSurrOut], y2[kSurrOut];
@@ -565,6 +565,7 @@ __global__ void __launch_bounds__(128, 2) surrogate_event_kernel(const unsigned*
     if (tid < nvalid)
       emit_event(qne[r0 + tid], y1, y2, key, tally, B, qsec, qsec_count, qsec_cap, hist, hist_n, dep, esc, sec,
                  dropped);
+    n_done += static_cast<unsigned long long>(nvalid);
   }
   auto wsum = [](unsigned long long v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -579,6 +580,7 @@ __global__ void __launch_bounds__(128, 2) surrogate_event_kernel(const unsigned*
     if (dr) atomicAdd(&cnt->dropped, dr);
   }
   if (tid == 0 && *m.fail) atomicAdd(&cnt->errors, 1ull);
+  if (tid == 0 && n_done) atomicAdd(&cnt->surrogate_events, n_done);
   tc::end(pp);
 }
 

@@ -1,8 +1,9 @@
-// transport.cu -- persistent, event-based proton stepping kernel.
+// transport.cu -- the primaries: phase space, then the persistent, event-based stepping
+// kernel (the secondary generations run in drain.cu).
 //
 // One lane carries one proton (Sec. II.B.1, one history per thread); when its
 // proton stops, leaves the grid or is absorbed in a non-elastic collision, the
-// lane takes the next work item from a global counter (warp-aggregated), so
+// lane takes the next sampled primary from a global counter (warp-aggregated), so
 // warps stay full until the work runs out.  Per step (Sec. II.A.3):
 //   step = min(lambda, d, R), random hinge with Highland x 1.07 deflection,
 //   mean loss by range-table inversion (Eq. 2) plus Bohr straggling,
@@ -18,18 +19,39 @@ namespace {
 #ifndef PMC_TRANSPORT_MIN_BLOCKS
 #define PMC_TRANSPORT_MIN_BLOCKS 3   // measured best on GB300: 3 resident blocks of 256 per SM
 #endif
-// Secondary generations hold few particles and last as long as their longest track: there a
-// step's latency counts more than the number of resident warps, and with 2 blocks per SM the
-// step has the registers to be shorter (secondary stage 1.50 against 1.61 ms on the slab).
-#ifndef PMC_TRANSPORT_MIN_BLOCKS_SECONDARY
-#define PMC_TRANSPORT_MIN_BLOCKS_SECONDARY 2
-#endif
 
-template <bool kLet, bool kMol, bool kVav, int kMinBlocks, bool kLog = false>
+// Phase space of the primaries (Sec. II.B.2): spot sampling of work items w_begin..w_end-1,
+// one thread per history, written to the generation's input queue as records the transport
+// lanes take when they refill.  Sampling here, at full width, keeps two Philox blocks, the
+// Box-Muller transforms and the spot search out of the transport kernel's refill, where
+// they ran on the one or two lanes of a warp that had just finished a history.
+__global__ void __launch_bounds__(256) phase_space_kernel(const TransportArgs a) {
+  const unsigned long long n = a.w_end - a.w_begin;
+  const unsigned long long seed = *a.seed;
+  const uint2 key = make_uint2(static_cast<unsigned>(seed), static_cast<unsigned>(seed >> 32));
+  PrimaryRecord* out = reinterpret_cast<PrimaryRecord*>(a.qin);
+  Acc acc;
+  for (unsigned long long i = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<unsigned long long>(gridDim.x) * blockDim.x) {
+    PState p;
+    const bool alive = init_primary(a, key, a.w_begin + i, p, acc);
+    out[i] = pack_primary(p, alive);
+  }
+  unsigned long long inc = static_cast<unsigned long long>(acc.inc), esc = static_cast<unsigned long long>(acc.esc);
+  for (int o = 16; o > 0; o >>= 1) {
+    inc += __shfl_xor_sync(0xffffffffu, inc, o);
+    esc += __shfl_xor_sync(0xffffffffu, esc, o);
+  }
+  if ((threadIdx.x & 31u) == 0) {
+    if (inc) atomicAdd(&a.cnt->incident, inc);
+    if (esc) atomicAdd(&a.cnt->escaped, esc);
+  }
+}
+
+template <bool kLet, bool kMol, bool kVav, int kMinBlocks>
 __global__ void __launch_bounds__(256, kMinBlocks) transport_kernel(const TransportArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const unsigned long long n_items =
-      a.source == 0 ? (a.w_end - a.w_begin) : static_cast<unsigned long long>(min(*a.qin_count, a.qin_cap));
+  const unsigned long long n_items = a.w_end - a.w_begin;
   if (n_items == 0) return;
   if (static_cast<unsigned long long>(blockIdx.x) * blockDim.x >= n_items) return;
 
@@ -56,44 +78,17 @@ __global__ void __launch_bounds__(256, kMinBlocks) transport_kernel(const Transp
       if (!alive && !drained) {
         const unsigned long long idx = base + __popc(need & ((1u << lane) - 1u));
         if (idx < n_items) {
-          if (a.source == 0) {
-            alive = init_primary(a, key, a.w_begin + idx, p, acc);
-          } else {
-            init_queued(a, key, a.qin[idx], p);
-            alive = true;
-          }
+          alive = load_primary(reinterpret_cast<const PrimaryRecord*>(a.qin)[idx], p);
         } else {
           drained = true;
         }
       }
     }
     if (__all_sync(0xffffffffu, !alive && drained)) break;
-    if (alive) alive = step<kLet, kMol, kVav, kLog>(a, ph, rt, et, st, mol, key, p, acc, q);
+    if (alive) alive = step<kLet, kMol, kVav>(a, ph, rt, et, st, mol, key, p, acc, q);
   }
 
-  // flush the lane counters (warp reduction, one atomic per warp and counter)
-  auto wsum = [](unsigned long long x) {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-  };
-  const unsigned long long inc = wsum(static_cast<unsigned long long>(acc.inc));
-  const unsigned long long dep = wsum(static_cast<unsigned long long>(acc.dep));
-  const unsigned long long esc = wsum(static_cast<unsigned long long>(acc.esc));
-  const unsigned long long steps = wsum(acc.steps), el = wsum(acc.el), inel = wsum(acc.inel);
-  const unsigned long long sec = wsum(acc.sec), dropped = wsum(acc.dropped), errors = wsum(acc.errors);
-  if (lane == 0) {
-    Counters* c = a.cnt;
-    if (inc) atomicAdd(&c->incident, inc);
-    if (dep) atomicAdd(&c->deposited, dep);
-    if (esc) atomicAdd(&c->escaped, esc);
-    if (steps) atomicAdd(&c->steps, steps);
-    if (steps && a.source == 0) atomicAdd(&c->steps_primary, steps);
-    if (el) atomicAdd(&c->elastic, el);
-    if (inel) atomicAdd(&c->inelastic, inel);
-    if (sec) atomicAdd(&c->secondaries, sec);
-    if (dropped) atomicAdd(&c->dropped, dropped);
-    if (errors) atomicAdd(&c->errors, errors);
-  }
+  flush_transport_counters(acc, a.cnt, true);
 }
 
 }  // namespace
@@ -105,48 +100,42 @@ size_t transport_smem_bytes(int n_cls, int n_mat, bool moliere) {
 }
 
 namespace {
-// the specialisations: [primaries, secondaries][(LET scored) + 2 (Moliere) + 4 (Vavilov)]
-constexpr int kP = PMC_TRANSPORT_MIN_BLOCKS, kS = PMC_TRANSPORT_MIN_BLOCKS_SECONDARY;
-template <int kB>
-constexpr void (*kFamily[8])(const TransportArgs) = {
-    transport_kernel<false, false, false, kB>, transport_kernel<true, false, false, kB>,
-    transport_kernel<false, true, false, kB>,  transport_kernel<true, true, false, kB>,
-    transport_kernel<false, false, true, kB>,  transport_kernel<true, false, true, kB>,
-    transport_kernel<false, true, true, kB>,   transport_kernel<true, true, true, kB>};
-void (*const* const kTransportKernels[2])(const TransportArgs) = {kFamily<kP>, kFamily<kS>};
-// the debug deposit log, with the paper's physics options (Highland, Bohr, no LET)
-void (*const kTransportLogKernels[2])(const TransportArgs) = {transport_kernel<false, false, false, kP, true>,
-                                                              transport_kernel<false, false, false, kS, true>};
+// the specialisations: (LET scored) + 2 (Moliere) + 4 (Vavilov)
+constexpr int kP = PMC_TRANSPORT_MIN_BLOCKS;
+void (*const kTransportKernels[8])(const TransportArgs) = {
+    transport_kernel<false, false, false, kP>, transport_kernel<true, false, false, kP>,
+    transport_kernel<false, true, false, kP>,  transport_kernel<true, true, false, kP>,
+    transport_kernel<false, false, true, kP>,  transport_kernel<true, false, true, kP>,
+    transport_kernel<false, true, true, kP>,   transport_kernel<true, true, true, kP>};
 }  // namespace
 
-cudaError_t transport_occupancy(int block, size_t smem, int* blocks_primary, int* blocks_secondary) {
-  for (int g = 0; g < 2; ++g) {
-    int lo = 1 << 30;
-    for (int i = 0; i < 8; ++i) {
-      const auto k = kTransportKernels[g][i];
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-      if (e != cudaSuccess) return e;
-      int b = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, block, smem);
-      if (e != cudaSuccess) return e;
-      lo = b < lo ? b : lo;
-    }
-    cudaError_t e = cudaFuncSetAttribute(kTransportLogKernels[g], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+cudaError_t transport_occupancy(int block, size_t smem, int* blocks) {
+  int lo = 1 << 30;
+  for (int i = 0; i < 8; ++i) {
+    const auto k = kTransportKernels[i];
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    *(g ? blocks_secondary : blocks_primary) = lo;
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, block, smem);
+    if (e != cudaSuccess) return e;
+    lo = b < lo ? b : lo;
   }
+  *blocks = lo;
   return cudaSuccess;
 }
 
 cudaError_t launch_transport(const TransportArgs& a, int grid, int block, size_t smem, cudaStream_t s) {
-  if (a.dlog) {
-    if (a.let_num || a.mol || a.vav) return cudaErrorInvalidValue;   // the log runs the default physics only
-    kTransportLogKernels[a.source ? 1 : 0]<<<grid, block, smem, s>>>(a);
-    return cudaGetLastError();
-  }
-  kTransportKernels[a.source ? 1 : 0][(a.let_num ? 1 : 0) + (a.mol ? 2 : 0) + (a.vav ? 4 : 0)]<<<grid, block, smem, s>>>(
-      a);
+  // the debug deposit log runs the paper's physics options only (Highland, Bohr, no LET)
+  if (a.dlog && (a.let_num || a.mol || a.vav)) return cudaErrorInvalidValue;
+  // the primaries are sampled into the generation's (otherwise unused) input queue first
+  const unsigned long long n = a.w_end - a.w_begin;
+  if (!a.qin || n > a.qin_cap) return cudaErrorInvalidValue;
+  if (n == 0) return cudaSuccess;
+  const unsigned long long blocks = (n + 255) / 256;
+  phase_space_kernel<<<static_cast<unsigned>(blocks < 65536 ? blocks : 65536), 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  kTransportKernels[(a.let_num ? 1 : 0) + (a.mol ? 2 : 0) + (a.vav ? 4 : 0)]<<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -1,8 +1,7 @@
 // transport_step.cuh -- the condensed-history step of one proton (Sec. II.A.3) and what it
 // needs: particle state, birth of primaries and queued particles, fixed-point deposits.
-// Shared by the generation kernel (transport.cu) and the persistent drain kernel (drain.cu).
-// Where a step hands on a non-elastic event or an elastic recoil proton is a policy: the
-// generation kernel appends to global queues, the drain kernel to its warp's own buffers.
+// Where a step hands on a non-elastic event or an elastic recoil proton is a policy (the
+// generation kernel of transport.cu appends to global queues).
 #pragma once
 
 #include "pmc_kernels.cuh"
@@ -80,7 +79,8 @@ __device__ __forceinline__ bool push(Particle* q, unsigned* count, unsigned cap,
 }
 
 // Birth of primary work item wi: spot sampling (Sec. II.B.2, phase-space kernel).
-__device__ bool init_primary(const TransportArgs& a, uint2 key, unsigned long long wi, PState& p, Acc& acc) {
+__device__ __forceinline__ bool init_primary(const TransportArgs& a, uint2 key, unsigned long long wi, PState& p,
+                                             Acc& acc) {
   int lo = 0, hi = a.n_spots;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -116,6 +116,38 @@ __device__ bool init_primary(const TransportArgs& a, uint2 key, unsigned long lo
   return true;
 }
 
+// A primary as the phase-space kernel leaves it for the transport kernel: the state after
+// spot sampling, ready to step.  Primaries start on the entrance face (iz = 0); ix < 0 marks
+// one that was born outside the grid (its energy is already booked as escaped).
+struct __align__(16) PrimaryRecord {
+  float x, y, z, u;
+  float v, w, E, nmfp;
+  int ix, iy;
+  unsigned root, b;
+};
+static_assert(sizeof(PrimaryRecord) == sizeof(Particle), "a primary record takes one queue slot");
+
+__device__ __forceinline__ PrimaryRecord pack_primary(const PState& p, bool alive) {
+  PrimaryRecord r;
+  r.x = p.x; r.y = p.y; r.z = p.z; r.u = p.u; r.v = p.v; r.w = p.w; r.E = p.E; r.nmfp = p.nmfp;
+  r.ix = alive ? p.ix : -1;
+  r.iy = p.iy;
+  r.root = p.root;
+  r.b = p.b;
+  return r;
+}
+
+// Takes a sampled primary; false for one born outside the grid.
+__device__ __forceinline__ bool load_primary(const PrimaryRecord& r, PState& p) {
+  p.x = r.x; p.y = r.y; p.z = r.z; p.u = r.u; p.v = r.v; p.w = r.w; p.E = r.E; p.nmfp = r.nmfp;
+  p.ix = r.ix; p.iy = r.iy; p.iz = 0;
+  p.root = r.root;
+  p.pid = r.root;
+  p.b = r.b;
+  p.k = 0;
+  return r.ix >= 0;
+}
+
 __device__ void init_queued(const TransportArgs& a, uint2 key, const Particle& r, PState& p) {
   p.x = r.x; p.y = r.y; p.z = r.z; p.u = r.u; p.v = r.v; p.w = r.w; p.E = r.E;
   p.pid = r.pid;
@@ -140,15 +172,17 @@ __device__ __forceinline__ Particle make_record(const PState& p, float E, float 
 
 // One condensed-history step (Sec. II.A.3).  Returns false when the particle ends.  kLet, kMol
 // and kVav compile the LET scoring, the Moliere option and the Vavilov option in; without
-// them the step carries no test for any of them.
-template <bool kLet, bool kMol, bool kVav, bool kLog, class Q>
+// them the step carries no test for any of them.  The debug deposit log is a run-time switch
+// (a.dlog) rather than a specialisation, so that a logged run executes the very instructions
+// of an unlogged one: a separately compiled kernel may contract multiply-adds differently.
+template <bool kLet, bool kMol, bool kVav, class Q>
 __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt, const float2* et,
                      const float* st, const float4* mol, uint2 key, PState& p, Acc& acc, Q& q) {
   const int v = vindex(a.g, p.ix, p.iy, p.iz);
   if (p.E <= kEcut) {
     const long long q = fix(p.E);
     deposit(a, v, p, q, acc);
-    if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, 0.0, 0.0);
+    if (a.dlog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, 0.0, 0.0);
     if (kLet && p.E > 0.0f) {   // absorbed over its residual range: L = E / R
       int m0;
       float rho0;
@@ -161,7 +195,7 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   }
   if (p.k >= kMaxSteps) {
     deposit(a, v, p, fix(p.E), acc);
-    if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, 0.0, 0.0);
+    if (a.dlog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, 0.0, 0.0);
     acc.errors++;
     return false;
   }
@@ -185,7 +219,7 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   if (Rcm <= lam && Rcm <= d) {
     const long long q = fix(E0);
     deposit(a, v, p, q, acc);
-    if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, E0, 0.0, 0.0);
+    if (a.dlog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, E0, 0.0, 0.0);
     if (kLet && Rcm > 0.0f) score_let(a, v, p, q, 0.1f * E0 / Rcm);
     return false;
   }
@@ -262,7 +296,7 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   {
     const long long q = fix(E0) - fix(E1);
     deposit(a, v, p, q, acc);
-    if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, E0, E1, 0.0);
+    if (a.dlog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, E0, E1, 0.0);
     if (kLet) {
       // mean stopping power over the path: the CSDA loss over s, taken as a difference
       // of two values of the inverse range table (free of the E -> R -> E round trip,
@@ -316,16 +350,16 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
                             : ((ph.flags & kNoElastic) ? 0.0f : mc.n_per_g[j] * sigma_el(nc, E0));
     if (part > 0.0f) last = j;
     cum += part;
-    if (t < 0 && ut < cum) t = j;
+    if (ut < cum) { t = j; break; }
   }
-  if (t < 0) t = last;
+  if (t < 0) t = last;   // ut at the rounded total: the last nucleus with a share
   const int nuc = mc.nuc[t];
   if (inel) {
     acc.inel++;
     if (!q.event(make_record(p, p.E, p.u, p.v, p.w, p.pid, v, nuc))) {
       acc.dropped++;
       deposit(a, v, p, fix(p.E), acc);
-      if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, 0.0, 0.0);
+      if (a.dlog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, 0.0, 0.0);
     }
     return false;
   }
@@ -345,21 +379,46 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
     if (q.secondary(make_record(p, eo.T2, ru, rv, rw, cid, v, -1))) {
       acc.sec++;
       deposit(a, v, p, qE - q1 - fix(eo.T2), acc);   // rounding remainder only
-      if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, eo.T1, eo.T2);
+      if (a.dlog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, eo.T1, eo.T2);
     } else {
       acc.dropped++;
       deposit(a, v, p, qE - q1, acc);
-      if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, eo.T1, 0.0);
+      if (a.dlog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, eo.T1, 0.0);
     }
   } else {
     deposit(a, v, p, qE - q1, acc);                  // recoil nucleus deposits locally
-    if (kLog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, eo.T1, 0.0);
+    if (a.dlog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, eo.T1, 0.0);
   }
   p.E = eo.T1;
   p.nmfp = -logf(ub.z);
   return true;
 }
 
+
+// Adds the lanes' counters to the run's (warp reduction, one atomic per warp and counter).
+__device__ __forceinline__ void flush_transport_counters(const Acc& acc, Counters* c, bool primary) {
+  auto wsum = [](unsigned long long x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+  };
+  const unsigned long long inc = wsum(static_cast<unsigned long long>(acc.inc));
+  const unsigned long long dep = wsum(static_cast<unsigned long long>(acc.dep));
+  const unsigned long long esc = wsum(static_cast<unsigned long long>(acc.esc));
+  const unsigned long long steps = wsum(acc.steps), el = wsum(acc.el), inel = wsum(acc.inel);
+  const unsigned long long sec = wsum(acc.sec), dropped = wsum(acc.dropped), errors = wsum(acc.errors);
+  if ((threadIdx.x & 31u) == 0) {
+    if (inc) atomicAdd(&c->incident, inc);
+    if (dep) atomicAdd(&c->deposited, dep);
+    if (esc) atomicAdd(&c->escaped, esc);
+    if (steps) atomicAdd(&c->steps, steps);
+    if (steps && primary) atomicAdd(&c->steps_primary, steps);
+    if (el) atomicAdd(&c->elastic, el);
+    if (inel) atomicAdd(&c->inelastic, inel);
+    if (sec) atomicAdd(&c->secondaries, sec);
+    if (dropped) atomicAdd(&c->dropped, dropped);
+    if (errors) atomicAdd(&c->errors, errors);
+  }
+}
 
 // Queue policy of the generation kernel: events and recoil protons appended to global queues.
 struct GlobalQueues {

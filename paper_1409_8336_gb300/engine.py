@@ -79,7 +79,8 @@ class TrainResult(C.Structure):
 class Ledger(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("incident", "deposited", "escaped", "binding", "histories", "steps",
                                          "elastic", "inelastic", "secondaries", "transparent", "inc_retries",
-                                         "queue_high_water", "generations", "dropped", "errors")]
+                                         "queue_high_water", "generations", "dropped", "errors",
+                                         "surrogate_events")]
 
 
 class EventYields(C.Structure):
@@ -405,14 +406,18 @@ class Engine:
 
     def read_profile(self):
         """Per kernel kind (primary transport, secondary transport, cascade, statistics):
-        summed ms and launches of the last transport, and the primary-transport step count."""
+        summed ms, launch groups and kernels of the last transport, and the primary-transport
+        step count."""
         ms = np.zeros(8)
-        n = np.zeros(4, dtype=np.int64)
+        n = np.zeros(8, dtype=np.int64)
         steps = C.c_int64(0)
         self._check(self._L.pmc_read_profile(self._ctx, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64)),
                                              C.byref(steps)))
-        kinds = ("transport_primary", "transport_secondary", "cascade", "stats")
-        return {k: {"ms": float(ms[i]), "span_ms": float(ms[4 + i]), "launches": int(n[i])}
+        # the primaries (phase space + transport), the drain of all later generations (their
+        # transport and cascades), the event stage of the primaries' non-elastic collisions
+        # (cascade + evaporation, or the learned stand-in), the dose statistics
+        kinds = ("transport_primary", "drain", "cascade", "stats")
+        return {k: {"ms": float(ms[i]), "span_ms": float(ms[4 + i]), "launches": int(n[i]), "kernels": int(n[4 + i])}
                 for i, k in enumerate(kinds)}, int(steps.value)
 
     # --- learned stand-in of the event generator --------------------------
