@@ -55,13 +55,13 @@ L2_BYTES = 129 * 2 ** 20
 #        transport_kernel -c 1): issue slots busy, threads per executed instruction (SIMT
 #        efficiency = that / 32) and thread instructions per condensed-history step.
 #   bytes_per_history: DRAM bytes (read + write) of a full 1e6-history primary launch per
-#        primary history: dram__bytes_read.sum + dram__bytes_write.sum alone (reported as one
-#        pass on the 2e5-history case first), one launch (-c 1): 45.40 + 4.51 MB.
+#        primary history: dram__bytes_read.sum + dram__bytes_write.sum alone (one pass), one
+#        launch (-c 1): 93.65 + 7.74 MB (the reads include the 48-byte phase-space records).
 KERNEL_SOURCES = ("transport.cu", "transport_step.cuh", "pmc_device.cuh", "pmc_kernels.cuh")
-KERNEL_SHA256 = "0a9627c4fde6f62d80df72367203dd94e80833304d34a9ecb366ce3d28ed2e30"
-NCU = {"issue_slots_busy": 0.7570, "threads_per_instruction": 21.46, "thread_instructions_per_step": 585.4,
-       "capture": "slab workload, 2e5 histories, first primary launch (-k regex:transport_kernel -c 1)"}
-TRAFFIC = {"bytes_per_history": 49.90}
+KERNEL_SHA256 = "e0980fd15a49bf3be2e3ed670f755a5a69dbfc0bd50ceb61450b86dfb1475c72"
+NCU = {"issue_slots_busy": 0.7520, "threads_per_instruction": 21.74, "thread_instructions_per_step": 568.0,
+       "capture": "slab workload, 2e5 histories, first primary launch (-k regex:^transport_kernel -c 1)"}
+TRAFFIC = {"bytes_per_history": 101.38}
 
 
 def _sources_match():

@@ -5,10 +5,10 @@
 // secondary protons, which cause a few 1e4 further events over a handful of generations.
 // Launched generation by generation, each transport and each cascade launch lasts as long as
 // its longest track or cascade while most of the GPU idles, and the generations add up.  Here
-// every lane takes whatever is ready -- a proton to step, or an event to run through the
-// cascade and the evaporation of its residual nucleus -- from two global queues, and what it
-// produces goes back to them, so the long tracks and long cascades of different lineages
-// overlap.  The launch ends when every item ever queued has been finished.
+// lanes take what is ready from two global queues -- protons to step on five SMs in six,
+// events to run through the cascade and the evaporation of the residual nucleus on the sixth
+// -- and what an item produces goes back to them, so the long tracks and long cascades of
+// different lineages overlap.  The launch ends when every item ever queued has been finished.
 //
 // Queues: a producer reserves a slot by an atomic add on the tail, writes it and marks it
 // ready with this launch's stamp (release).  Lanes take slots by an atomic add on the head
@@ -153,6 +153,15 @@ __global__ void drain_init_kernel(DrainCtl* ctl, const unsigned* pq_n0, unsigned
   ctl->stamp = ctl->stamp + 1u;
 }
 
+// SM roles: the blocks on one SM in kEventSm take events, those on the others protons, so that
+// no SM runs both the cascade and the transport code, whose instructions together overflow an
+// SM's instruction caches (measured on the slab workload, drain per transport: every lane
+// taking either kind 1.76 ms; one SM in 3, 4, 6, 8, 12 for events: 1.42, 1.58, 1.31, 1.60, 1.63
+// ms).  A warp idle for kRoleFallback polls takes either kind: the other kind's SMs may hold no
+// block of this launch (another launch occupying them).
+constexpr unsigned kEventSm = 6;
+constexpr int kRoleFallback = 2048;
+// two blocks of 256 per SM (128 registers); with three (85) the spills cost 1.7x
 template <bool kLet, bool kMol, bool kVav>
 __global__ void __launch_bounds__(256, 2) drain_kernel(const DrainArgs d) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -190,7 +199,10 @@ __global__ void __launch_bounds__(256, 2) drain_kernel(const DrainArgs d) {
   // slot not yet written
   int role = 0;
   unsigned slot = 0;
-  int polls = 0, backoff = 0, skip = 0, nap = 128;
+  int polls = 0, backoff = 0, skip = 0, nap = 128, idle_run = 0;
+  unsigned smid;
+  asm("mov.u32 %0, %%smid;" : "=r"(smid));
+  const bool event_sm = smid % kEventSm == 0;
   // takes the item of a written slot (role 3 or 4 -> 1 or 2); false for an invalid event
   auto take = [&](bool is_event, unsigned i) {
     if (is_event) {
@@ -237,15 +249,17 @@ __global__ void __launch_bounds__(256, 2) drain_kernel(const DrainArgs d) {
       look = false;
     }
     if (look) {
-      // Claims for the idle lanes, events first: a cascade is a long serial chain, and the
-      // protons it emits are the next links of their lineage, so it should start early.
-      // (Keeping a warp to the kind of work it already holds measured the same.)
+      // Claims for the idle lanes: the kind of this SM's role; after a long idle spell either
+      // kind, events first (a cascade is a long serial chain whose protons are the next links
+      // of their lineage).
       const int leader = __ffs(idle) - 1;
       unsigned be = 0, ne = 0, bp = 0, np = 0;
+      const bool any = idle_run >= kRoleFallback;
       if (static_cast<int>(lane) == leader) {
         const unsigned want = __popc(idle);
-        ne = drain_take(&ctl->eq_head.v, &ctl->eq_tail.v, d.eq_cap, want, be);
-        if (ne < want) np = drain_take(&ctl->pq_head.v, &ctl->pq_tail.v, d.pq_cap, want - ne, bp);
+        if (event_sm || any) ne = drain_take(&ctl->eq_head.v, &ctl->eq_tail.v, d.eq_cap, want, be);
+        if (ne < want && (!event_sm || any))
+          np = drain_take(&ctl->pq_head.v, &ctl->pq_tail.v, d.pq_cap, want - ne, bp);
       }
       be = __shfl_sync(0xffffffffu, be, leader);
       ne = __shfl_sync(0xffffffffu, ne, leader);
@@ -298,11 +312,13 @@ __global__ void __launch_bounds__(256, 2) drain_kernel(const DrainArgs d) {
         }
         break;
       }
+      ++idle_run;
       __nanosleep(nap);
       nap = min(2 * nap, 4096);
       continue;
     }
     nap = 128;
+    idle_run = 0;
     if (role == 1) {
       if (!step<kLet, kMol, kVav>(a, ph, tb.rt, tb.et, tb.st, tb.mol, key, p, acc, q)) finish();
     } else if (role == 2) {

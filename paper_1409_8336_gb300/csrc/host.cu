@@ -1995,7 +1995,7 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     // queued for the drain, [2] events, [3] transport work, [4] cascade work, [5] residuals)
     for (uint64_t w0 = 0; w0 < n_histories; w0 += PMC_NOALLOC_CHUNK) {
       const uint64_t w1 = std::min<uint64_t>(n_histories, w0 + PMC_NOALLOC_CHUNK);
-      CK(cudaMemsetAsync(counts, 0, 6 * sizeof(unsigned), s));
+      CK(cudaMemsetAsync(counts, 0, 8 * sizeof(unsigned), s));
       ta.w_begin = w0;
       ta.w_end = w1;
       ta.qin = q[0];
