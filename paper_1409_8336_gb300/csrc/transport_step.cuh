@@ -23,6 +23,21 @@ struct Acc {           // per-lane counters flushed once at the end
   unsigned long long steps = 0, el = 0, inel = 0, sec = 0, dropped = 0, errors = 0;
 };
 
+// sin and cos of 2 pi u, u in [0, 1] (the azimuths and Box-Muller angles of a step).  The
+// -use_fast_math build takes the special-function unit's approximations on [-pi, pi] (absolute
+// error ~2^-21; 2 pi u = pi + t with both signs flipped), a few instructions against the ~25
+// of the exactly reduced sincospi; the IEEE build keeps sincospi.
+__device__ __forceinline__ void sincos_2pi(float u, float* sn, float* cs) {
+#ifdef __USE_FAST_MATH__
+  float a, b;
+  __sincosf(6.28318531f * (u - 0.5f), &a, &b);
+  *sn = -a;
+  *cs = -b;
+#else
+  sincospif(2.0f * u, sn, cs);
+#endif
+}
+
 __device__ __forceinline__ int vindex(const Geometry& g, int ix, int iy, int iz) {
   return (iz * g.ny + iy) * g.nx + ix;
 }
@@ -237,26 +252,25 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
     if (th > 0.0f) {
       float s_, c_, sp, cp;
       sincosf(th, &s_, &c_);
-      sincospif(2.0f * ua.u1, &sp, &cp);
+      sincos_2pi(ua.u1, &sp, &cp);
       rotate(p.u, p.v, p.w, c_, s_, cp, sp);
     }
   } else if (!(ph.flags & kNoMcs)) {
-    // Highland x 1.07 at the step-start energy, over the planned step
-    const float pc = sqrtf(E0 * E0 + 2.0f * E0 * kMp);
-    const float beta = pc / (E0 + kMp);
+    // Highland x 1.07 at the step-start energy, over the planned step: with e = E + M and
+    // (pc)^2 = E (E + 2M), 1 / (beta p c) = e / (pc)^2 and x / (X0 beta^2) = (x / X0) e / (beta p c).
+    // The two projected Gaussian angles th0 (r cos phi, r sin phi) deflect by th0 r at azimuth phi.
+    const float e = E0 + kMp;
+    const float pc2 = E0 * (E0 + 2.0f * kMp);
     const float xr = dx * rho * mc.inv_X0;
     if (xr > 0.0f) {
-      const float br = fmaxf(1.0f + 0.038f * logf(xr / (beta * beta)), 0.0f);
-      const float th0 = 1.07f * 13.6f / (beta * pc) * sqrtf(xr) * br;
-      const float r = sqrtf(-2.0f * logf(ua.u0));
-      float sn, cs;
-      sincospif(2.0f * ua.u1, &sn, &cs);
-      const float tx = th0 * r * cs, ty = th0 * r * sn;
-      const float th = sqrtf(tx * tx + ty * ty);
+      const float ibpc = e / pc2;
+      const float br = fmaxf(1.0f + 0.038f * logf(xr * e * ibpc), 0.0f);
+      const float th = (1.07f * 13.6f) * ibpc * sqrtf(xr) * br * sqrtf(-2.0f * logf(ua.u0));
       if (th > 0.0f) {
-        float s_, c_;
+        float sn, cs, s_, c_;
+        sincos_2pi(ua.u1, &sn, &cs);
         sincosf(th, &s_, &c_);
-        rotate(p.u, p.v, p.w, c_, s_, tx / th, ty / th);
+        rotate(p.u, p.v, p.w, c_, s_, cs, sn);
       }
     }
   }
@@ -271,10 +285,12 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   const float E_left = Rleft > 0.0f ? energy_of_range(ph, et, mc.cls, Rleft) : 0.0f;
   float dE = E0 - E_left;
   if (!(ph.flags & kNoStraggling)) {
-    const float g = 1.0f + E0 / kMp;
-    const float b2 = 1.0f - 1.0f / (g * g);
+    const float e = E0 + kMp;
+    const float pc2 = E0 * (E0 + 2.0f * kMp);
     bool vav = false;
     if (kVav) {
+      const float g = e * (1.0f / kMp);
+      const float b2 = pc2 / (e * e);
       // Vavilov where kappa = xi / T_max <= 10: xi = (K/2)(Z/A) rho s / beta^2, T_max the
       // largest transfer to a free electron; beyond it Bohr's Gaussian (the same variance)
       const float r = kMe / kMp;
@@ -287,8 +303,12 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
       }
     }
     if (!vav) {
-      const float var = mc.bohr_k * rho * s * (1.0f - 0.5f * b2) / (1.0f - b2);
-      dE += sqrtf(var) * sqrtf(-2.0f * logf(ua.u2)) * cospif(2.0f * ua.u3);
+      // Bohr's variance with the relativistic factor (1 - beta^2/2) / (1 - beta^2) =
+      // (e^2 - (pc)^2 / 2) / M^2
+      const float var = mc.bohr_k * rho * s * (e * e - 0.5f * pc2) * (1.0f / (kMp * kMp));
+      float sn, cs;
+      sincos_2pi(ua.u3, &sn, &cs);
+      dE += sqrtf(var * (-2.0f * logf(ua.u2))) * cs;
     }
   }
   dE = fminf(fmaxf(dE, 0.0f), E0);
