@@ -38,10 +38,10 @@ N_HISTORIES = 1_000_000
 # multiply, fused multiply-add, compare, select, conversion, integer and special-function
 # instruction as one (a division as reciprocal + multiply, a square root or logarithm as
 # two): Philox4x32-10 block 99, five uniforms 26, two boundary distances 78, multiple
-# scattering with the direction rotation 73, straggling 25, inverse-range spline 24,
+# scattering with the direction rotation 60, straggling 20, inverse-range spline 24,
 # range spline 16, fixed-point deposit 23, cross-section table and lambda 13, and the
-# rest of the step logic 53.  Peak = FP32/INT32 lanes x SM clock.
-OPS_PER_STEP = 430
+# rest of the step logic 50.  Peak = FP32/INT32 lanes x SM clock.
+OPS_PER_STEP = 409
 # Algorithmic bytes of a step at L2 on the slab workload: material id 1 B + density 4 B +
 # the tally's 64-bit read-modify-write 16 B.
 BYTES_PER_STEP = 21
@@ -56,12 +56,12 @@ L2_BYTES = 129 * 2 ** 20
 #        efficiency = that / 32) and thread instructions per condensed-history step.
 #   bytes_per_history: DRAM bytes (read + write) of a full 1e6-history primary launch per
 #        primary history: dram__bytes_read.sum + dram__bytes_write.sum alone (one pass), one
-#        launch (-c 1): 93.65 + 7.74 MB (the reads include the 48-byte phase-space records).
+#        launch (-c 1): 93.79 + 7.81 MB (the reads include the 48-byte phase-space records).
 KERNEL_SOURCES = ("transport.cu", "transport_step.cuh", "pmc_device.cuh", "pmc_kernels.cuh")
-KERNEL_SHA256 = "e0980fd15a49bf3be2e3ed670f755a5a69dbfc0bd50ceb61450b86dfb1475c72"
-NCU = {"issue_slots_busy": 0.7520, "threads_per_instruction": 21.74, "thread_instructions_per_step": 568.0,
+KERNEL_SHA256 = "0cb3cbe40d53736ed4f4891b8af82523116084af2f7a51ac25f283a9fac9fccc"
+NCU = {"issue_slots_busy": 0.7525, "threads_per_instruction": 21.60, "thread_instructions_per_step": 553.3,
        "capture": "slab workload, 2e5 histories, first primary launch (-k regex:^transport_kernel -c 1)"}
-TRAFFIC = {"bytes_per_history": 101.38}
+TRAFFIC = {"bytes_per_history": 101.60}
 
 
 def _sources_match():

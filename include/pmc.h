@@ -460,6 +460,12 @@ int pmc_debug_event_stage(pmc_ctx* ctx, int mode, const int* nuclide, const doub
  * (the block stops, frees its tensor memory and reports), and the context stays usable.
  * PMC_E_INVALID without a loaded network. */
 int pmc_debug_surrogate_waits(pmc_ctx* ctx);
+/* pmc_debug_drain_waits: a full-cascade pmc_transport whose drain of the secondary
+ * generations counts one item that never comes, so that it never sees its work finished and
+ * every warp's bounded wait for more work runs out (after 4096 polls instead of ~1e6):
+ * returns PMC_E_TIMEOUT with the run's real work done, and the context stays usable.
+ * PMC_E_INVALID as pmc_transport. */
+int pmc_debug_drain_waits(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed);
 /* pmc_debug_vavilov_table: the Vavilov straggling table the transport samples from, built on
  * the host (no device needed): quantiles of z = (loss - mean loss) / xi, [6 values of beta^2 in
  * [0, 0.5]][31 values of ln kappa in [ln 0.01, ln 10]][513 values of u in [1e-4, 1 - 1e-4]],

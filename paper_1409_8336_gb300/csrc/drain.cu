@@ -300,12 +300,12 @@ __global__ void __launch_bounds__(256, 2) drain_kernel(const DrainArgs d) {
       unsigned stop = 0;
       if (lane == 0) {
         const unsigned fin = ld_acquire(&ctl->completed.v);
-        const unsigned pushed = ld_relaxed(&ctl->pq_tail.v) + ld_relaxed(&ctl->eq_tail.v);
+        const unsigned pushed = ld_relaxed(&ctl->pq_tail.v) + ld_relaxed(&ctl->eq_tail.v) + d.phantom;
         stop = (fin == pushed || ld_relaxed(&ctl->error) != 0u) ? 1u : 0u;
       }
       stop = __shfl_sync(0xffffffffu, stop, 0);
       if (stop) break;
-      if (++polls > kIdlePolls) {
+      if (++polls > (d.idle_limit > 0 ? d.idle_limit : kIdlePolls)) {
         if (lane == 0) {
           atomicExch(&ctl->error, 1u);
           acc.errors++;

@@ -491,6 +491,7 @@ struct pmc_ctx {
   DevBuf d_rec[2];               // residual nuclei between cascade and evaporation, per stream
   DevBuf d_drain;                // per stream: drain control block, ready marks of its two queues
   size_t drain_qcap = 0;         // the queue capacity the marks are laid out for
+  bool drain_debug = false;      // next drain: one phantom item and short waits (they run out)
   size_t surr_cap = 0;
   int mode = PMC_FULL_CASCADE;          // mode of the captured graph
   // graph
@@ -1239,6 +1240,10 @@ int enqueue_drain(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int qs, Parti
   d.eq_cap = static_cast<unsigned>(ctx->q_cap);
   d.eq_n0 = eq_n;
   d.ctl = drain_ctl(ctx, qs);
+  if (ctx->drain_debug) {
+    d.phantom = 1;
+    d.idle_limit = 4096;
+  }
   int rc;
   if ((rc = mark(ctx, s, 1, true))) return rc;
   CK(launch_drain(d, rp.grid_d, ctx->block, rp.smem_d, s));
@@ -1424,10 +1429,10 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
     CK(cudaMemcpyAsync(ctx->d_seed.p, &seed, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
     // graph of the whole run, rebuilt when its shape changes
     char key[256];
-    std::snprintf(key, sizeof(key), "%llu/%lld/%zu/%d/%d/%lld/%p/%p/%p/%d/%p", (unsigned long long)n_histories,
+    std::snprintf(key, sizeof(key), "%llu/%lld/%zu/%d/%d/%lld/%p/%p/%p/%d/%p/%d", (unsigned long long)n_histories,
                   (long long)rp.chunk, sd.size(), ctx->block, ctx->opt.n_batches, ctx->n_vox, ctx->d_tally.p,
                   ctx->d_hist.p, ctx->let_on ? ctx->d_let_num.p : nullptr, ctx->profile + 3 * mode,
-                  ctx->dlog_cap ? ctx->d_dlog.p : nullptr);
+                  ctx->dlog_cap ? ctx->d_dlog.p : nullptr, ctx->drain_debug ? 1 : 0);
     if (!ctx->gexec || ctx->gkey != key) {
       if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
       cudaGraph_t graph;
@@ -2307,6 +2312,14 @@ int pmc_debug_vavilov_table(float* out, size_t n) {
   if (!out || n != t.size()) return PMC_E_INVALID;
   std::memcpy(out, t.data(), n * sizeof(float));
   return PMC_OK;
+}
+
+int pmc_debug_drain_waits(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed) {
+  if (!ctx) return PMC_E_INVALID;
+  ctx->drain_debug = true;
+  const int rc = pmc_transport(ctx, n_histories, seed, PMC_FULL_CASCADE, nullptr);
+  ctx->drain_debug = false;
+  return rc;
 }
 
 int pmc_debug_surrogate_waits(pmc_ctx* ctx) {

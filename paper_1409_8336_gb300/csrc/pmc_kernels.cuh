@@ -148,6 +148,8 @@ struct DrainArgs {
   unsigned eq_cap;
   const unsigned* eq_n0;           // events queued before the launch, or NULL
   DrainCtl* ctl;
+  unsigned phantom;                // items counted as queued that never come (debug: 0)
+  int idle_limit;                  // polls of an idle warp before it gives up (0: the default)
 };
 
 struct StatsArgs {

@@ -38,8 +38,17 @@ __global__ void __launch_bounds__(256) stats_kernel(const StatsArgs a) {
     int m;
     float rho;
     voxel_props(*a.phys, a.g, static_cast<int>(v), m, rho);
-    // MeV (2^-24 units) -> Gy: E * 1.602176634e-13 J / (rho * V * 1e-3 kg)
-    const double scale = rho > 0.0f ? (1.602176634e-10 / (static_cast<double>(rho) * vol)) / kFixD : 0.0;
+    // MeV (2^-24 units) -> Gy: E * 1.602176634e-13 J / (rho * V * 1e-3 kg).  1 / (rho V) from
+    // a single-precision reciprocal refined by one Newton step in double (relative error
+    // ~1e-14): a double division would take a dozen instructions of the narrow FP64 pipe per
+    // voxel, which bound this kernel.
+    double scale = 0.0;
+    if (rho > 0.0f) {
+      const double rv = static_cast<double>(rho) * vol;
+      double r = static_cast<double>(__frcp_rn(static_cast<float>(rv)));
+      r = r * fma(-rv, r, 2.0);
+      scale = (1.602176634e-10 / kFixD) * r;
+    }
     a.dose[v] = static_cast<double>(sum) * scale;
     a.sigma[v] = static_cast<double>(sqrtf(corr * ss)) * scale;
     if (a.let_num) {

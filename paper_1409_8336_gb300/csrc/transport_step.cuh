@@ -11,6 +11,7 @@ namespace {
 
 struct PState {
   float x, y, z, u, v, w, E, nmfp;
+  long long fE;        // fix(E), carried from step to step (a step's deposit is fE - fix(E1))
   int ix, iy, iz;
   unsigned k;          // step counter of this particle
   unsigned root;       // primary history
@@ -160,6 +161,7 @@ __device__ __forceinline__ bool load_primary(const PrimaryRecord& r, PState& p) 
   p.pid = r.root;
   p.b = r.b;
   p.k = 0;
+  p.fE = fix(p.E);
   return r.ix >= 0;
 }
 
@@ -169,6 +171,7 @@ __device__ void init_queued(const TransportArgs& a, uint2 key, const Particle& r
   p.root = r.root;
   p.b = r.root % static_cast<unsigned>(a.B);
   p.k = 0;
+  p.fE = fix(p.E);
   p.nmfp = -logf(draw4(key, r.pid, 1u, 4u).x);
   const int nxy = a.g.nx * a.g.ny;
   p.iz = r.voxel / nxy;
@@ -314,7 +317,9 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
   dE = fminf(fmaxf(dE, 0.0f), E0);
   const float E1 = E0 - dE;
   {
-    const long long q = fix(E0) - fix(E1);
+    const long long f1 = fix(E1);
+    const long long q = p.fE - f1;
+    p.fE = f1;
     deposit(a, v, p, q, acc);
     if (a.dlog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, E0, E1, 0.0);
     if (kLet) {
@@ -410,6 +415,7 @@ __device__ bool step(const TransportArgs& a, const Physics& ph, const float2* rt
     if (a.dlog) log_deposit(a.dlog, a.dlog_count, a.dlog_cap, v, p.b, p.E, eo.T1, 0.0);
   }
   p.E = eo.T1;
+  p.fE = q1;
   p.nmfp = -logf(ub.z);
   return true;
 }

@@ -33,7 +33,8 @@ EXPORTS = [
     "pmc_set_launch", "pmc_autotune", "pmc_transport_noalloc", "pmc_surrogate_dataset", "pmc_train_surrogate",
     "pmc_surrogate_params", "pmc_surrogate_load", "pmc_surrogate_grad", "pmc_surrogate_infer", "pmc_gamma_plan_bytes", "pmc_gamma_plan", "pmc_gamma_device",
     "pmc_gamma_index", "pmc_enable_profile", "pmc_read_profile", "pmc_debug_philox", "pmc_debug_tables",
-    "pmc_debug_inc", "pmc_debug_elastic", "pmc_debug_surrogate_waits", "pmc_debug_vavilov_table",
+    "pmc_debug_inc", "pmc_debug_elastic", "pmc_debug_surrogate_waits", "pmc_debug_drain_waits",
+    "pmc_debug_vavilov_table",
     "pmc_enable_deposit_log", "pmc_read_deposit_log", "pmc_debug_event_stage",
 ]
 
@@ -162,6 +163,7 @@ def lib(path: str = LIB_PATH):
             L.pmc_surrogate_grad.argtypes = [vp, pf, pf, pf, pf, pf, i, pf, pf, pf]
             L.pmc_surrogate_infer.argtypes = [vp, pf, i, pf]
             L.pmc_debug_surrogate_waits.argtypes = [vp]
+            L.pmc_debug_drain_waits.argtypes = [vp, u64, u64]
             L.pmc_debug_vavilov_table.argtypes = [pf, C.c_size_t]
             L.pmc_gamma_plan_bytes.argtypes = [d, d, d, d, d, C.POINTER(C.c_size_t)]
             L.pmc_gamma_plan.argtypes = [d, d, d, d, d, vp, C.c_size_t, vp]
@@ -461,6 +463,11 @@ class Engine:
         return y
 
     # --- single-routine device checks ------------------------------------
+    def debug_drain_waits(self, n_histories: int, seed: int):
+        """A full-cascade transport whose drain never sees its work finished, so that every
+        warp's bounded wait runs out; returns the library's status (PMC_E_TIMEOUT expected)."""
+        return int(self._L.pmc_debug_drain_waits(self._ctx, n_histories, seed))
+
     def debug_surrogate_waits(self):
         """Runs the tensor-core network with its MMAs withheld so every wait runs out;
         returns the library's status (PMC_E_TIMEOUT expected)."""

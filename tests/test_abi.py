@@ -49,6 +49,8 @@ def test_invalid_calls_fail_without_a_device(libpmc):
     assert libpmc.pmc_transport(None, 10, 1, 0, None) == -1
     assert libpmc.pmc_surrogate_infer(None, None, 1, None) == -1
     assert libpmc.pmc_debug_surrogate_waits(None) == -1
+    libpmc.pmc_debug_drain_waits.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]
+    assert libpmc.pmc_debug_drain_waits(None, 10, 1) == -1
     assert libpmc.pmc_enable_profile(None, 2) == -1
     libpmc.pmc_enable_deposit_log.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
     assert libpmc.pmc_enable_deposit_log(None, 10) == -1

@@ -173,3 +173,27 @@ def test_refused_calls():
     with pytest.raises(PmcError):
         e.transport(100, 1)                      # no spots
     e.close()
+
+
+def test_drain_waits_are_bounded_and_the_context_recovers():
+    """The drain of the secondary generations waits for work only boundedly: a drain made to
+    count one item that never comes (so it never sees its work finished) returns PMC_E_TIMEOUT
+    instead of hanging, with the run's real work done, and the same context then transports
+    exactly as a fresh one does."""
+    from paper_1409_8336_gb300 import Engine
+    from paper_1409_8336_gb300.engine import ERRORS
+
+    prob = W.config1()
+    n, seed = 3000, 9
+    e = Engine(device=0, n_batches=prob.n_batches)
+    e.load_problem(prob)
+    e.set_launch(256, 0)
+    assert ERRORS[e.debug_drain_waits(n, seed)] == "PMC_E_TIMEOUT"
+    L = e.read_ledger()
+    assert L["errors"] > 0 and L["dropped"] == 0
+    assert abs(L["incident"] - L["deposited"] - L["escaped"] - L["binding"]) < 1e-6 * L["incident"]
+    e.transport(n, seed)
+    t = e.read_tally()
+    assert e.read_ledger()["errors"] == 0
+    e.close()
+    assert np.array_equal(t, _gpu(prob, n, seed)["tally"])
