@@ -277,7 +277,7 @@ int pmc_read_profile(pmc_ctx* ctx, double* ms, int64_t* launches, int64_t* prima
 #define PMC_NOALLOC_CHUNK 65536          /* histories per sub-group */
 #define PMC_NOALLOC_MAX_SPOTS 4096
 #define PMC_NOALLOC_SCRATCH_BYTES                                                                  \
-    (3ull * PMC_NOALLOC_CHUNK * 48ull + PMC_NOALLOC_CHUNK * 128ull + 1792ull + PMC_NOALLOC_CHUNK * 8ull + \
+    (3ull * PMC_NOALLOC_CHUNK * 48ull + PMC_NOALLOC_CHUNK * 128ull + 1792ull + PMC_NOALLOC_CHUNK * 12ull + \
      PMC_NOALLOC_MAX_SPOTS * 56ull)
 int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int64_t* tally,
                           double* dose_gy, double* sigma_gy, void* stream);

@@ -5,9 +5,9 @@
 // secondary protons, which cause a few 1e4 further events over a handful of generations.
 // Launched generation by generation, each transport and each cascade launch lasts as long as
 // its longest track or cascade while most of the GPU idles, and the generations add up.  Here
-// lanes take what is ready from two global queues -- protons to step on five SMs in six,
-// events to run through the cascade and the evaporation of the residual nucleus on the sixth
-// -- and what an item produces goes back to them, so the long tracks and long cascades of
+// lanes take what is ready from three global queues -- protons to step on five SMs in six;
+// events to run through the cascade, and the residual nuclei those leave, to evaporate, on the
+// sixth -- and what an item produces goes back to them, so the long tracks and long cascades of
 // different lineages overlap.  The launch ends when every item ever queued has been finished.
 //
 // Queues: a producer reserves a slot by an atomic add on the tail, writes it and marks it
@@ -69,6 +69,18 @@ __device__ __forceinline__ unsigned drain_take(unsigned* head, const unsigned* t
   return k;
 }
 
+// Appends a residual nucleus for evaporation: false (nothing queued) when the queue is full.
+__device__ __forceinline__ bool drain_push_residual(const DrainArgs& d, unsigned stamp, const EvapRecord& r) {
+  const unsigned i = atomicAdd(&d.ctl->xq_tail.v, 1u);
+  if (i >= d.xq_cap) {
+    atomicAdd(&d.ctl->completed.v, 1u);
+    return false;
+  }
+  d.xq[i] = r;
+  st_release(d.xq_ready + i, stamp);
+  return true;
+}
+
 // Queue policy of the transport step inside the drain.
 struct DrainQueues {
   const DrainArgs& d;
@@ -99,8 +111,11 @@ struct DrainEnv {
 };
 
 // One lane's event: the cascade's steps in the order the sequential event routine takes
-// them (so the event's random stream is consumed identically), one per iteration, then the
-// evaporation chain of the residual.
+// them (so the event's random stream is consumed identically), one per iteration; the
+// residual nucleus, with the position of the stream, is then queued for its evaporation.
+// (Evaporated in place, a lane's chain of tens of microseconds held up the cascades of the
+// other 31 lanes of its warp, one finishing lane after another; queued, residuals are
+// evaporated by warps that take 32 of them at once, as the evaporation kernel does.)
 struct LaneEvent {
   Stream st;
   IncState s;
@@ -135,8 +150,25 @@ __device__ __forceinline__ bool event_step(LaneEvent& e, IncP* P, const float* b
     return true;
   }
   const int k = inc_emit(P, e.s.n, sk);
-  evaporate(bt, e.st, r, k, e.retries, sk);
+  EvapRecord x;
+  x.ev = sk.ev;
+  x.Ex = r.Ex; x.px = r.px; x.py = r.py; x.pz = r.pz; x.bind = r.bind;
+  x.buf = e.st.buf; x.draw = e.st.draw; x.pos = e.st.pos;
+  x.Z = r.Z; x.A = r.A; x.k = k; x.retries = e.retries;
+  if (!drain_push_residual(*sk.env.d, sk.env.stamp, x)) evaporate(bt, e.st, r, k, e.retries, sk);   // no room
   return true;
+}
+
+// The evaporation of a queued residual nucleus (its random stream resumes where the cascade
+// left it).
+__device__ __forceinline__ void evaporate_record(const EvapRecord& x, const float* bt, int B,
+                                                 EventSink<DrainEnv>& sk) {
+  sk.ev = x.ev;
+  sk.b = x.ev.root % static_cast<unsigned>(B);
+  Stream st{sk.key, x.ev.pid, x.draw, x.pos, x.buf};
+  Residual r;
+  r.Ex = x.Ex; r.px = x.px; r.py = x.py; r.pz = x.pz; r.bind = x.bind; r.Z = x.Z; r.A = x.A;
+  evaporate(bt, st, r, x.k, x.retries, sk);
 }
 
 __global__ void drain_init_kernel(DrainCtl* ctl, const unsigned* pq_n0, unsigned pq_cap, const unsigned* eq_n0,
@@ -146,6 +178,8 @@ __global__ void drain_init_kernel(DrainCtl* ctl, const unsigned* pq_n0, unsigned
   ctl->pq_head.v = 0;
   ctl->eq_tail.v = e0;
   ctl->eq_head.v = 0;
+  ctl->xq_tail.v = 0;
+  ctl->xq_head.v = 0;
   ctl->completed.v = 0;
   ctl->pq_n0 = p0;
   ctl->eq_n0 = e0;
@@ -195,17 +229,18 @@ __global__ void __launch_bounds__(256, 2) drain_kernel(const DrainArgs d) {
   IncP P[kIncStack];
   LaneEvent ev;
   ev.nu = nuc;
-  // 0: idle, 1: a proton in hand, 2: an event in hand, 3 / 4: a ticket for a proton / event
-  // slot not yet written
+  // 0: idle, 1: a proton in hand, 2: an event in hand, 5: a residual nucleus to evaporate;
+  // 3 / 4 / 6: a ticket for a proton / event / residual slot not yet written
   int role = 0;
   unsigned slot = 0;
   int polls = 0, backoff = 0, skip = 0, nap = 128, idle_run = 0;
   unsigned smid;
   asm("mov.u32 %0, %%smid;" : "=r"(smid));
   const bool event_sm = smid % kEventSm == 0;
-  // takes the item of a written slot (role 3 or 4 -> 1 or 2); false for an invalid event
-  auto take = [&](bool is_event, unsigned i) {
-    if (is_event) {
+  // takes the item of a written slot of queue `kind` (0 protons, 1 events, 2 residuals);
+  // false for an invalid event
+  auto take = [&](int kind, unsigned i) {
+    if (kind == 1) {
       const Particle r = d.eq[i];
       if (r.target < 0 || r.target >= d.c.n_nuc) return false;
       sk.ev = r;
@@ -216,6 +251,9 @@ __global__ void __launch_bounds__(256, 2) drain_kernel(const DrainArgs d) {
       ev.retries = 0;
       ev.setup = true;
       role = 2;
+    } else if (kind == 2) {
+      slot = i;
+      role = 5;
     } else {
       init_queued(a, key, d.pq[i], p);
       role = 1;
@@ -229,10 +267,11 @@ __global__ void __launch_bounds__(256, 2) drain_kernel(const DrainArgs d) {
   };
   for (;;) {
     // tickets: is the slot written yet?
-    if (role >= 3) {
-      const bool is_event = role == 4;
-      if (ld_acquire((is_event ? d.eq_ready : d.pq_ready) + slot) == stamp) {
-        if (!take(is_event, slot)) {
+    if (role == 3 || role == 4 || role == 6) {
+      const int kind = role == 3 ? 0 : (role == 4 ? 1 : 2);
+      const unsigned* ready = kind == 0 ? d.pq_ready : (kind == 1 ? d.eq_ready : d.xq_ready);
+      if (ld_acquire(ready + slot) == stamp) {
+        if (!take(kind, slot)) {
           atomicExch(&ctl->error, 1u);
           acc.errors++;
           finish();
@@ -240,7 +279,7 @@ __global__ void __launch_bounds__(256, 2) drain_kernel(const DrainArgs d) {
       }
     }
     const unsigned idle = __ballot_sync(0xffffffffu, role == 0);
-    const unsigned busy = __ballot_sync(0xffffffffu, role == 1 || role == 2);
+    const unsigned busy = __ballot_sync(0xffffffffu, role == 1 || role == 2 || role == 5);
     // A warp that still holds work and found the queues empty looks again only after a few
     // steps (up to 16): the claim's loads would otherwise lengthen every step of its tracks.
     bool look = idle != 0u;
@@ -249,35 +288,40 @@ __global__ void __launch_bounds__(256, 2) drain_kernel(const DrainArgs d) {
       look = false;
     }
     if (look) {
-      // Claims for the idle lanes: the kind of this SM's role; after a long idle spell either
-      // kind, events first (a cascade is a long serial chain whose protons are the next links
-      // of their lineage).
+      // Claims for the idle lanes, by the SM's role (after a long idle spell any kind).  An
+      // event SM's warp that holds no cascade takes residual nuclei first, and then nothing
+      // else that round, so that its lanes evaporate together; otherwise events.  A proton
+      // SM's warp takes protons.
+      const bool holds_inc = __ballot_sync(0xffffffffu, role == 2 || role == 4) != 0u;
       const int leader = __ffs(idle) - 1;
-      unsigned be = 0, ne = 0, bp = 0, np = 0;
+      unsigned b0 = 0, n0 = 0, b1 = 0, n1 = 0, b2 = 0, n2 = 0;
       const bool any = idle_run >= kRoleFallback;
       if (static_cast<int>(lane) == leader) {
         const unsigned want = __popc(idle);
-        if (event_sm || any) ne = drain_take(&ctl->eq_head.v, &ctl->eq_tail.v, d.eq_cap, want, be);
-        if (ne < want && (!event_sm || any))
-          np = drain_take(&ctl->pq_head.v, &ctl->pq_tail.v, d.pq_cap, want - ne, bp);
+        if ((event_sm || any) && !holds_inc) n2 = drain_take(&ctl->xq_head.v, &ctl->xq_tail.v, d.xq_cap, want, b2);
+        if ((event_sm || any) && n2 == 0) n1 = drain_take(&ctl->eq_head.v, &ctl->eq_tail.v, d.eq_cap, want, b1);
+        if ((!event_sm || any) && n1 + n2 < want)
+          n0 = drain_take(&ctl->pq_head.v, &ctl->pq_tail.v, d.pq_cap, want - n1 - n2, b0);
       }
-      be = __shfl_sync(0xffffffffu, be, leader);
-      ne = __shfl_sync(0xffffffffu, ne, leader);
-      bp = __shfl_sync(0xffffffffu, bp, leader);
-      np = __shfl_sync(0xffffffffu, np, leader);
+      b0 = __shfl_sync(0xffffffffu, b0, leader);
+      n0 = __shfl_sync(0xffffffffu, n0, leader);
+      b1 = __shfl_sync(0xffffffffu, b1, leader);
+      n1 = __shfl_sync(0xffffffffu, n1, leader);
+      b2 = __shfl_sync(0xffffffffu, b2, leader);
+      n2 = __shfl_sync(0xffffffffu, n2, leader);
       if (role == 0) {
         const unsigned r = __popc(idle & ((1u << lane) - 1u));
-        if (r < ne + np) {
-          const bool is_event = r < ne;
-          const unsigned i = is_event ? be + r : bp + (r - ne);
-          const unsigned cap = is_event ? d.eq_cap : d.pq_cap;
+        if (r < n0 + n1 + n2) {
+          const int kind = r < n2 ? 2 : (r < n2 + n1 ? 1 : 0);
+          const unsigned i = kind == 2 ? b2 + r : (kind == 1 ? b1 + (r - n2) : b0 + (r - n2 - n1));
+          const unsigned cap = kind == 0 ? d.pq_cap : (kind == 1 ? d.eq_cap : d.xq_cap);
+          const unsigned* ready = kind == 0 ? d.pq_ready : (kind == 1 ? d.eq_ready : d.xq_ready);
+          const unsigned nb = kind == 0 ? pq_n0 : (kind == 1 ? eq_n0 : 0u);
           if (i < cap) {   // a slot at or beyond the capacity can never be written: none taken
-            const bool written = i < (is_event ? eq_n0 : pq_n0) ||
-                                 ld_acquire((is_event ? d.eq_ready : d.pq_ready) + i) == stamp;
-            if (!written) {
-              role = is_event ? 4 : 3;
+            if (!(i < nb || ld_acquire(ready + i) == stamp)) {
+              role = kind == 0 ? 3 : (kind == 1 ? 4 : 6);
               slot = i;
-            } else if (!take(is_event, i)) {
+            } else if (!take(kind, i)) {
               atomicExch(&ctl->error, 1u);
               acc.errors++;
               finish();
@@ -285,14 +329,14 @@ __global__ void __launch_bounds__(256, 2) drain_kernel(const DrainArgs d) {
           }
         }
       }
-      if (ne + np > 0) {
+      if (n0 + n1 + n2 > 0) {
         backoff = 0;
       } else if (busy) {
         backoff = min(2 * backoff + 1, 15);
         skip = backoff;
       }
     }
-    if (__ballot_sync(0xffffffffu, role == 1 || role == 2) == 0u) {
+    if (__ballot_sync(0xffffffffu, role == 1 || role == 2 || role == 5) == 0u) {
       // nothing in hand: done, stopped, or waiting for work.  The decision is lane 0's,
       // broadcast, so that the whole warp leaves the loop together (the counter flush after it
       // uses full-warp shuffles).  Done: every item ever queued is finished (read the finished
@@ -300,7 +344,8 @@ __global__ void __launch_bounds__(256, 2) drain_kernel(const DrainArgs d) {
       unsigned stop = 0;
       if (lane == 0) {
         const unsigned fin = ld_acquire(&ctl->completed.v);
-        const unsigned pushed = ld_relaxed(&ctl->pq_tail.v) + ld_relaxed(&ctl->eq_tail.v) + d.phantom;
+        const unsigned pushed = ld_relaxed(&ctl->pq_tail.v) + ld_relaxed(&ctl->eq_tail.v) +
+                                ld_relaxed(&ctl->xq_tail.v) + d.phantom;
         stop = (fin == pushed || ld_relaxed(&ctl->error) != 0u) ? 1u : 0u;
       }
       stop = __shfl_sync(0xffffffffu, stop, 0);
@@ -323,6 +368,9 @@ __global__ void __launch_bounds__(256, 2) drain_kernel(const DrainArgs d) {
       if (!step<kLet, kMol, kVav>(a, ph, tb.rt, tb.et, tb.st, tb.mol, key, p, acc, q)) finish();
     } else if (role == 2) {
       if (event_step(ev, P, bt, sk)) finish();
+    } else if (role == 5) {
+      evaporate_record(d.xq[slot], bt, a.B, sk);
+      finish();
     }
   }
   flush_transport_counters(acc, a.cnt, false);
@@ -359,7 +407,8 @@ cudaError_t drain_occupancy(int block, size_t smem, int* blocks) {
 }
 
 cudaError_t launch_drain(const DrainArgs& d, int grid, int block, size_t smem, cudaStream_t s) {
-  if (!d.pq || !d.eq || !d.pq_ready || !d.eq_ready || !d.ctl || !d.pq_n0) return cudaErrorInvalidValue;
+  if (!d.pq || !d.eq || !d.xq || !d.pq_ready || !d.eq_ready || !d.xq_ready || !d.ctl || !d.pq_n0)
+    return cudaErrorInvalidValue;
   if (d.t.dlog && (d.t.let_num || d.t.mol || d.t.vav)) return cudaErrorInvalidValue;
   drain_init_kernel<<<1, 1, 0, s>>>(d.ctl, d.pq_n0, d.pq_cap, d.eq_n0, d.eq_cap);
   cudaError_t e = cudaGetLastError();

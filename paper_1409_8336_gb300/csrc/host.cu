@@ -1214,15 +1214,15 @@ int enqueue_primaries(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, uint64_t 
 }
 
 // The drain's buffers of queue set qs (0, 1): its control block and the ready marks of its
-// particle and event queues.
+// particle, event and residual-nucleus queues.
 DrainCtl* drain_ctl(pmc_ctx* ctx, int qs) {
   return reinterpret_cast<DrainCtl*>(static_cast<unsigned char*>(ctx->d_drain.p) + qs * sizeof(DrainCtl));
 }
 unsigned* drain_ready(pmc_ctx* ctx, int qs, int which) {
   unsigned* r = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(ctx->d_drain.p) + 2 * sizeof(DrainCtl));
-  return r + (2 * qs + which) * ctx->q_cap;
+  return r + (3 * qs + which) * ctx->q_cap;
 }
-size_t drain_buffer_bytes(size_t q_cap) { return 2 * sizeof(DrainCtl) + 4 * q_cap * sizeof(unsigned); }
+size_t drain_buffer_bytes(size_t q_cap) { return 2 * sizeof(DrainCtl) + 6 * q_cap * sizeof(unsigned); }
 
 // Enqueues the drain of a sub-group: its particle queue pq already holds *pq_n the protons of
 // the first generation; its events, if eq_n is given, are still queued in eq.
@@ -1239,6 +1239,9 @@ int enqueue_drain(pmc_ctx* ctx, const RunPlan& rp, cudaStream_t s, int qs, Parti
   d.eq_ready = drain_ready(ctx, qs, 1);
   d.eq_cap = static_cast<unsigned>(ctx->q_cap);
   d.eq_n0 = eq_n;
+  d.xq = static_cast<EvapRecord*>(ctx->d_rec[qs].p);   // free again: the evaporation kernel has run
+  d.xq_ready = drain_ready(ctx, qs, 2);
+  d.xq_cap = static_cast<unsigned>(ctx->d_rec[qs].n / sizeof(EvapRecord));
   d.ctl = drain_ctl(ctx, qs);
   if (ctx->drain_debug) {
     d.phantom = 1;
@@ -1420,10 +1423,9 @@ int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, v
       CK(cudaMemsetAsync(ctx->d_drain.p, 0, ctx->d_drain.n, s));
       ctx->drain_qcap = ctx->q_cap;
     }
-    if (mode == PMC_FULL_CASCADE) {
-      for (int si = 0; si < 2; ++si)
-        if ((rc = dalloc(ctx, ctx->d_rec[si], ctx->q_cap * sizeof(EvapRecord)))) return rc;
-    }
+    // residual nuclei between cascade and evaporation (and inside the drain, in either mode)
+    for (int si = 0; si < 2; ++si)
+      if ((rc = dalloc(ctx, ctx->d_rec[si], ctx->q_cap * sizeof(EvapRecord)))) return rc;
     ctx->mode = mode;
     CK(cudaMemcpyAsync(ctx->d_spots.p, sd.data(), sd.size() * sizeof(SpotDev), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->d_seed.p, &seed, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
@@ -1863,7 +1865,7 @@ constexpr size_t kNaSeed = kNaCounts + 256;
 constexpr size_t kNaDrain = kNaSeed + 256;       // the drain's control block
 constexpr size_t kNaReady = kNaDrain + 1024;     // ready marks of the drain's particle and event queues
 static_assert(sizeof(DrainCtl) <= 1024, "the drain's control block fits its slot");
-constexpr size_t kNaSpots = kNaReady + 2ull * PMC_NOALLOC_CHUNK * sizeof(unsigned);
+constexpr size_t kNaSpots = kNaReady + 3ull * PMC_NOALLOC_CHUNK * sizeof(unsigned);
 constexpr size_t kNaBytes = kNaSpots + static_cast<size_t>(PMC_NOALLOC_MAX_SPOTS) * sizeof(SpotDev);
 static_assert(kNaBytes == PMC_NOALLOC_SCRATCH_BYTES, "scratch size stated in pmc.h");
 static_assert(sizeof(Counters) <= 256, "counters fit their slot");
@@ -1990,6 +1992,9 @@ extern "C" int pmc_transport_noalloc(pmc_ctx* ctx, uint64_t n_histories, uint64_
     da.eq_ready = da.pq_ready + PMC_NOALLOC_CHUNK;
     da.eq_cap = PMC_NOALLOC_CHUNK;
     da.eq_n0 = nullptr;
+    da.xq = reinterpret_cast<EvapRecord*>(base + kNaRec);   // free again once the evaporation kernel has run
+    da.xq_ready = da.eq_ready + PMC_NOALLOC_CHUNK;
+    da.xq_cap = PMC_NOALLOC_CHUNK;
     da.ctl = reinterpret_cast<DrainCtl*>(base + kNaDrain);
     const size_t smem_d = drain_smem_bytes(ctx->phys.n_cls, ctx->phys.n_mat, ctx->d_mol.p != nullptr, ctx->phys.n_nuc);
     int bpd = 0;
@@ -2494,7 +2499,7 @@ uint64_t plan_footprint(const pmc_options& opt, const pmc_plan& pl, int mode) {
   b += pool_round(n_chunks * kSlots * sizeof(unsigned));
   b += pool_round(drain_buffer_bytes(qcap));
   b += pool_round(sizeof(Counters)) + pool_round(8) + pool_round(static_cast<uint64_t>(pl.n_spots) * sizeof(SpotDev));
-  if (mode != PMC_SURROGATE) b += 2 * pool_round(qcap * sizeof(EvapRecord));
+  b += 2 * pool_round(qcap * sizeof(EvapRecord));
   return b;
 }
 

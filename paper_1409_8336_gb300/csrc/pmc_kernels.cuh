@@ -125,13 +125,14 @@ struct DrainCounter {
 struct DrainCtl {
   DrainCounter pq_tail, pq_head;   // particle queue: slots reserved by producers / taken by lanes
   DrainCounter eq_tail, eq_head;   // event queue: the same
+  DrainCounter xq_tail, xq_head;   // residual nuclei waiting for their evaporation: the same
   DrainCounter completed;          // items finished (or dropped for want of room)
   unsigned pq_n0, eq_n0;           // slots written before the launch
   unsigned error;                  // a bounded wait ran out
   unsigned stamp;                  // this launch's ready mark
   unsigned pad[28];
 };
-static_assert(sizeof(DrainCtl) == 768, "drain control block is six 128-byte lines");
+static_assert(sizeof(DrainCtl) == 1024, "drain control block is eight 128-byte lines");
 
 // The secondary generations of a sub-group in one launch: the transport and cascade
 // argument blocks (their queue fields unused), the particle and event queues with a ready
@@ -147,6 +148,9 @@ struct DrainArgs {
   unsigned* eq_ready;
   unsigned eq_cap;
   const unsigned* eq_n0;           // events queued before the launch, or NULL
+  EvapRecord* xq;                  // residual nuclei of finished cascades, to evaporate [xq_cap]
+  unsigned* xq_ready;
+  unsigned xq_cap;
   DrainCtl* ctl;
   unsigned phantom;                // items counted as queued that never come (debug: 0)
   int idle_limit;                  // polls of an idle warp before it gives up (0: the default)
