@@ -56,12 +56,12 @@ L2_BYTES = 129 * 2 ** 20
 #        efficiency = that / 32) and thread instructions per condensed-history step.
 #   bytes_per_history: DRAM bytes (read + write) of a full 1e6-history primary launch per
 #        primary history: dram__bytes_read.sum + dram__bytes_write.sum alone (one pass), one
-#        launch (-c 1): 93.79 + 7.81 MB (the reads include the 48-byte phase-space records).
+#        launch (-c 1): 93.59 + 7.95 MB (the reads include the 48-byte phase-space records).
 KERNEL_SOURCES = ("transport.cu", "transport_step.cuh", "pmc_device.cuh", "pmc_kernels.cuh")
-KERNEL_SHA256 = "0cb3cbe40d53736ed4f4891b8af82523116084af2f7a51ac25f283a9fac9fccc"
-NCU = {"issue_slots_busy": 0.7525, "threads_per_instruction": 21.60, "thread_instructions_per_step": 553.3,
+KERNEL_SHA256 = "5c5104197768be75e1b9d53009253bd1444afb8c5d21b1009623b929060c583e"
+NCU = {"issue_slots_busy": 0.7499, "threads_per_instruction": 21.64, "thread_instructions_per_step": 553.3,
        "capture": "slab workload, 2e5 histories, first primary launch (-k regex:^transport_kernel -c 1)"}
-TRAFFIC = {"bytes_per_history": 101.60}
+TRAFFIC = {"bytes_per_history": 101.55}
 
 
 def _sources_match():
