@@ -23,7 +23,11 @@ __device__ __forceinline__ void stage_tables(const CascadeArgs& a, NucleusModel*
 // for the longest cascade of the warp.  A finished cascade emits its escaping
 // nucleons and leaves its residual nucleus, with the position of its random
 // stream, for the evaporation kernel.
-__global__ void __launch_bounds__(128) inc_kernel(const CascadeArgs a) {
+// Resident blocks: the primaries' ~1.2e5 events take one or two per lane, so more lanes shorten
+// the launch while the registers stay spill-free: 4 blocks of 128 (117 registers) for the
+// cascade, 7 (72) for the evaporation, whose ~940 tiles then fit one wave (uncapped: 153 and 156
+// registers, 3 blocks per SM; slab step 5.37 -> 5.28 ms; 6 cascade blocks spill, 1.08 ms).
+__global__ void __launch_bounds__(128, 4) inc_kernel(const CascadeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned n = min(*a.qne_count, a.qne_cap);
   if (n == 0) return;
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(128) inc_kernel(const CascadeArgs a) {
 
 // Evaporation stage: one residual per thread; each block sorts its tile of 128
 // residuals by (mass number, excitation) so that a warp's chains are alike.
-__global__ void __launch_bounds__(128) evap_kernel(const CascadeArgs a) {
+__global__ void __launch_bounds__(128, 7) evap_kernel(const CascadeArgs a) {
   __shared__ float bt[kBtabFloats];
   __shared__ unsigned long long keys[128];
   const unsigned n = min(*a.rec_count, a.rec_cap);
