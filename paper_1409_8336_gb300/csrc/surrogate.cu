@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(128, 2) mlp_rows_kernel(int rows, const float*
   tc::end(pp);
 }
 
-// The event stage of a generation with the learned stand-in, fused: per tile of 128 queued
+// The event stage of the primaries' events with the learned stand-in, fused: per tile of 128 queued
 // events (one per thread), build the inference rows, run the network on the tensor cores
 // (multiplicity pass), condition on the sampled multiplicity, run it again and emit the
 // events, with rows, activations and outputs in shared memory throughout.
