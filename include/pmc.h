@@ -149,11 +149,17 @@ int pmc_add_spots(pmc_ctx* ctx, const pmc_spot* spots, int n);
 int pmc_clear_spots(pmc_ctx* ctx);
 
 /* Simulates n_histories primary protons, spread over the spots in proportion
- * to weight (largest remainder), with random numbers keyed by seed.  History h
- * scores into group h mod n_batches.  Tallies are zeroed first; the call ends
- * with the batch-statistics kernel, so dose and error are ready on the device.
- * stream: a cudaStream_t or NULL (the context's own stream).  The call blocks
- * until the run has finished. */
+ * to weight (largest remainder), with random numbers keyed by seed (Sec. II.B:
+ * per sub-group, the phase space and transport of the primaries, the event stage
+ * of their non-elastic collisions -- cascade and evaporation, or with mode
+ * PMC_SURROGATE the learned stand-in -- then one drain launch that transports
+ * every later generation and runs its events through the full cascade; one CUDA
+ * graph per run shape).  History h scores into group h mod n_batches.  Tallies
+ * are zeroed first; the call ends with the batch-statistics kernel, so dose and
+ * error are ready on the device.  stream: a cudaStream_t or NULL (the context's
+ * own stream).  The call blocks until the run has finished.  PMC_E_TIMEOUT when a
+ * particle exceeded the step limit or a bounded device wait ran out (the run's
+ * ledger is still readable); PMC_E_QUEUE_OVERFLOW when a queue was full. */
 int pmc_transport(pmc_ctx* ctx, uint64_t n_histories, uint64_t seed, int mode, void* stream);
 
 /* Dose (Gy) and its statistical standard error per voxel, to host arrays of
