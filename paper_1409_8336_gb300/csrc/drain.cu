@@ -191,8 +191,9 @@ __global__ void drain_init_kernel(DrainCtl* ctl, const unsigned* pq_n0, unsigned
 // no SM runs both the cascade and the transport code, whose instructions together overflow an
 // SM's instruction caches (measured on the slab workload, drain per transport: every lane
 // taking either kind 1.76 ms; one SM in 3, 4, 6, 8, 12 for events: 1.42, 1.58, 1.31, 1.60, 1.63
-// ms; with the residual queue, one in 4, 5, 6, 8: 1.43, 1.24, 1.23-1.25, 1.46 ms).  A warp idle for kRoleFallback polls takes either kind: the other kind's SMs may hold no
-// block of this launch (another launch occupying them).
+// ms; with the residual queue, one in 4, 5, 6, 8: 1.43, 1.24, 1.23-1.25, 1.46 ms).  A warp
+// idle for kRoleFallback polls takes either kind: the other kind's SMs may hold no block of
+// this launch (another launch occupying them).
 constexpr unsigned kEventSm = 6;
 constexpr int kRoleFallback = 2048;
 // two blocks of 256 per SM (128 registers); with three (85) the spills cost 1.7x
