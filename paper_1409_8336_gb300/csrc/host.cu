@@ -543,6 +543,11 @@ int dalloc(pmc_ctx* ctx, DevBuf& b, size_t bytes) {
   } else if (ctx->opt.alloc) {
     b.p = ctx->opt.alloc(bytes, ctx->opt.alloc_user);
     if (!b.p) return fail(ctx, PMC_E_OOM, "allocator returned NULL for %zu bytes", bytes);
+    if (reinterpret_cast<uintptr_t>(b.p) & 255u) {
+      release(ctx, b.p);
+      b.p = nullptr;
+      return fail(ctx, PMC_E_OOM, "allocator returned a block not aligned to 256 bytes");
+    }
   } else if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
     cudaGetLastError();
     b.p = nullptr;

@@ -162,8 +162,27 @@ __device__ void emit_event(const Particle& ev, const float (&y1)[kSurrOut], cons
   const unsigned b = ev.root % static_cast<unsigned>(B);
   const float4 ua = draw4(key, ev.pid, 3u, 8u);
   const float uphi[4] = {ua.x, ua.y, ua.z, ua.w};
+  // the protons above the cut take queue slots by one atomic per group of converged lanes:
+  // slot k of every lane, in lane order, then slot k + 1 (the queue's order is immaterial:
+  // each proton's random numbers follow from its identity)
+  static_assert(kSurrSlots <= 4, "four azimuth uniforms per event");
+  const unsigned mask = __activemask(), lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
+  const int leader = __ffs(mask) - 1;
+  unsigned bk[kSurrSlots], total = 0;
+#pragma unroll
+  for (int k = 0; k < kSurrSlots; ++k) {
+    bk[k] = __ballot_sync(mask, k < np && T[k] > kEcut);
+    total += __popc(bk[k]);
+  }
+  unsigned base = 0;
+  if (static_cast<int>(lane) == leader && total) base = atomicAdd(qsec_count, total);
+  base = __shfl_sync(mask, base, leader);
   long long handed = 0;
-  for (int k = 0; k < np; ++k) {
+#pragma unroll
+  for (int k = 0; k < kSurrSlots; ++k) {
+    const unsigned off = base + __popc(bk[k] & lt);
+    base += __popc(bk[k]);
+    if (k >= np) continue;
     if (T[k] <= kEcut) { loc += T[k]; continue; }
     float sp, cp;
     sincospif(2.0f * uphi[k], &sp, &cp);
@@ -172,9 +191,8 @@ __device__ void emit_event(const Particle& ev, const float (&y1)[kSurrOut], cons
     Particle r;
     r.x = ev.x; r.y = ev.y; r.z = ev.z; r.u = d.x; r.v = d.y; r.w = d.z; r.E = T[k];
     r.voxel = ev.voxel; r.pid = child_pid(key, ev.pid, static_cast<unsigned>(k)); r.root = ev.root; r.target = -1;
-    const unsigned slot = atomicAdd(qsec_count, 1u);
-    if (slot < qsec_cap) {
-      qsec[slot] = r;
+    if (off < qsec_cap) {
+      qsec[off] = r;
       ++sec;
       handed += fix(T[k]);
     } else {
@@ -283,26 +301,41 @@ constexpr int kTmemCols = kSurrHidden;               // the widest accumulator: 
 __device__ __forceinline__ int layer_in(int l) { return l == 0 ? kSurrIn : kSurrHidden; }
 __device__ __forceinline__ int layer_out(int l) { return l == kSurrLayers - 1 ? kSurrOut : kSurrHidden; }
 
-// The packed weights: every chunk (layer l, columns c*kKC..c*kKC+kKC-1) stored contiguously in
+// The packed weights: every chunk of a layer (a run of its input columns) stored contiguously in
 // exactly the byte order of its shared-memory buffer (w_off), so that one bulk copy moves it.
-// A pass streams kChunksPerPass chunks: 1 for the first layer, din / kKC for each other.
-constexpr int kChunksPerPass = kSurrIn / kKC + (kSurrLayers - 1) * (kSurrHidden / kKC);
+// A chunk is as many 16-wide K slices as fill one buffer, at most the layer's whole K: kKC
+// columns of the 256-wide layers, all 256 of the 16-wide output layer (8 KB, one copy rather
+// than eight round trips).  A pass streams kChunksPerPass chunks.
 __host__ __device__ constexpr int layer_in_c(int l) { return l == 0 ? kSurrIn : kSurrHidden; }
 __host__ __device__ constexpr int layer_out_c(int l) { return l == kSurrLayers - 1 ? kSurrOut : kSurrHidden; }
+__host__ __device__ constexpr int chunk_cols(int l) {
+  return kWBytes / (2 * layer_out_c(l)) < layer_in_c(l) ? kWBytes / (2 * layer_out_c(l)) : layer_in_c(l);
+}
+__host__ __device__ constexpr int layer_chunks(int l) { return layer_in_c(l) / chunk_cols(l); }
+__host__ __device__ constexpr int chunks_per_pass() {
+  int n = 0;
+  for (int l = 0; l < kSurrLayers; ++l) n += layer_chunks(l);
+  return n;
+}
+constexpr int kChunksPerPass = chunks_per_pass();
+static_assert(chunk_cols(0) % 16 == 0 && chunk_cols(kSurrLayers - 1) % 16 == 0 && kKC % 16 == 0,
+              "chunks are whole 16-wide K slices");
 // Chunk k of the pass -> its layer and column chunk.
 __device__ __forceinline__ void chunk_pos(int k, int& l, int& c) {
-  const int k0 = kSurrIn / kKC;
-  if (k < k0) { l = 0; c = k; return; }
-  l = 1 + (k - k0) / (kSurrHidden / kKC);
-  c = (k - k0) % (kSurrHidden / kKC);
+  l = 0;
+  while (k >= layer_chunks(l)) {
+    k -= layer_chunks(l);
+    ++l;
+  }
+  c = k;
 }
 // Byte offset of chunk (l, c) in the packed weights, and its size.
 __host__ __device__ inline size_t chunk_offset(int l, int c) {
   size_t o = 0;
   for (int i = 0; i < l; ++i) o += static_cast<size_t>(layer_in_c(i)) * layer_out_c(i) * 2;
-  return o + static_cast<size_t>(c) * layer_out_c(l) * kKC * 2;
+  return o + static_cast<size_t>(c) * layer_out_c(l) * chunk_cols(l) * 2;
 }
-__host__ __device__ constexpr uint32_t chunk_bytes(int l) { return static_cast<uint32_t>(layer_out_c(l) * kKC * 2); }
+__host__ __device__ constexpr uint32_t chunk_bytes(int l) { return static_cast<uint32_t>(layer_out_c(l) * chunk_cols(l) * 2); }
 
 // Pipeline state kept across passes.  Barriers at mbar + 8 i: full[b] (i = b: the bulk copy
 // of the chunk in buffer b has landed), empty[b] (i = kStages + b: the MMAs reading buffer b
@@ -315,6 +348,7 @@ struct Pipe {
   bool issue;                   // false only in the wait check: no MMA is issued, so waits run out
   int spin;                     // polls per wait
   int issued;                   // thread 0: chunks of the current pass whose copies were started
+  bool pre;                     // thread 0: the next pass's first kStages copies are already started
   __device__ __forceinline__ uint32_t bar(int i) const { return mbar + 8u * i; }
   __device__ __forceinline__ bool wait_bar(int i) {
     const bool r = wait(bar(i), (phase >> i) & 1u, spin);
@@ -323,7 +357,8 @@ struct Pipe {
   }
 };
 
-// Thread 0: starts the bulk copy of chunk k of the pass into its buffer.
+// Thread 0: starts the bulk copy of chunk k of the pass into its buffer.  Chunk k goes to
+// buffer k % kStages (the pass's stream position, whatever the chunk's size).
 __device__ __forceinline__ void issue_copy(Pipe& pp, int k, const unsigned char* __restrict__ packed,
                                            unsigned char* wb) {
   int l, c;
@@ -337,20 +372,37 @@ __device__ __forceinline__ void issue_copy(Pipe& pp, int k, const unsigned char*
   pp.issued = k + 1;
 }
 
+// Thread 0, chunk q's MMAs issued (or, with q one past a layer's last chunk, that layer's MMAs
+// all done): refills the buffer of chunk q-1 with chunk q-1+kStages once chunk q-1's MMAs are
+// done, unless that copy was already started.  Every chunk's "empty" completion is waited
+// exactly once: here, or at the end of the pass for the last kStages chunks.
+__device__ __forceinline__ void refill(Pipe& pp, int q, const unsigned char* __restrict__ packed, unsigned char* wb) {
+  if (pp.ok && q >= 1 && pp.issued == q - 1 + kStages && pp.issued < kChunksPerPass) {
+    pp.ok = pp.wait_bar(kStages + (q - 1) % kStages);
+    if (pp.ok) issue_copy(pp, q - 1 + kStages, packed, wb);
+  }
+}
+
 // One pass of the network over the tile: inputs in act columns 0..kSurrIn-1 (written by every
 // thread before the call); each thread's row of the last layer (bias added) goes to its
 // registers out[n].  Thread 0 streams the weight chunks by bulk copies kStages deep and issues
 // the MMAs; after issuing chunk q's it refills the buffer of chunk q-1 (whose MMAs have had
-// chunk q's time to finish).  All threads meet at each layer's end for the epilogue.
+// chunk q's time to finish), and at a layer's end the buffer of its last chunk as soon as the
+// layer's MMAs are done, so that the next layer's chunks load during the epilogue.  All threads
+// meet at each layer's end for the epilogue.  With `next` (another pass follows on this block),
+// thread 0 starts that pass's first copies as soon as this pass's MMAs are done.
 __device__ __forceinline__ void mlp_pass(unsigned char* act, unsigned char* wb, Pipe& pp,
                                          const unsigned char* __restrict__ packed, const float* __restrict__ P,
-                                         float (&out)[kSurrOut]) {
+                                         float (&out)[kSurrOut], bool next) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t trow = pp.tmem + (static_cast<uint32_t>(warp * 32) << 16);
   if (tid == 0) {
-    pp.issued = 0;
-    if (pp.ok)
-      for (int k = 0; k < kStages; ++k) issue_copy(pp, k, packed, wb);
+    if (!pp.pre) {
+      pp.issued = 0;
+      if (pp.ok)
+        for (int k = 0; k < kStages; ++k) issue_copy(pp, k, packed, wb);
+    }
+    pp.pre = false;
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the layer-0 operand rows
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -360,7 +412,7 @@ __device__ __forceinline__ void mlp_pass(unsigned char* act, unsigned char* wb, 
   int q = 0;
 #pragma unroll 1
   for (int l = 0; l < kSurrLayers; ++l) {
-    const int din = layer_in_c(l), N = layer_out_c(l), nc = din / kKC;
+    const int din = layer_in_c(l), N = layer_out_c(l), cs = chunk_cols(l) / 16, nc = din / chunk_cols(l);
     const float* __restrict__ bias = P + off + static_cast<size_t>(din) * N;
     if (tid == 0) {
       const uint32_t id = idesc(kRows, N);
@@ -369,18 +421,14 @@ __device__ __forceinline__ void mlp_pass(unsigned char* act, unsigned char* wb, 
         const int b = q % kStages;
         if (q < pp.issued) pp.ok = pp.wait_bar(b) && pp.ok;   // the chunk landed (waited even after a failure)
         if (pp.ok && pp.issue) {
-#pragma unroll
-          for (int s2 = 0; s2 < kKC / 16; ++s2)
-            mma(pp.tmem, desc(saddr(act + (c * (kKC / 16) + s2) * 4096), 128, 256),
+#pragma unroll 1
+          for (int s2 = 0; s2 < cs; ++s2)
+            mma(pp.tmem, desc(saddr(act + (c * cs + s2) * 4096), 128, 256),
                 desc(saddr(wb + b * kWBytes + s2 * (N * 32)), 128, 256), id, c > 0 || s2 > 0);
           commit(pp.bar(kStages + b));
           if (c + 1 == nc) commit(pp.bar(2 * kStages));
         }
-        // refill the buffer of chunk q-1 with chunk q-1+kStages once its MMAs are done
-        if (pp.ok && q >= 1 && q - 1 + kStages < kChunksPerPass) {
-          pp.ok = pp.wait_bar(kStages + (q - 1) % kStages);
-          if (pp.ok) issue_copy(pp, q - 1 + kStages, packed, wb);
-        }
+        refill(pp, q, packed, wb);
       }
     }
     // every thread: the layer's MMAs are done (warp-uniform outcome: tcgen05.ld is warp-collective)
@@ -388,6 +436,8 @@ __device__ __forceinline__ void mlp_pass(unsigned char* act, unsigned char* wb, 
     pp.phase ^= 1u << (2 * kStages);
     pp.ok = __all_sync(0xffffffffu, r);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) refill(pp, q, packed, wb);   // the layer's last buffer: free now
+    pp.ok = __all_sync(0xffffffffu, pp.ok);     // warp 0 stays converged and of one mind for tcgen05.ld
     if (pp.ok) {
       if (l + 1 < kSurrLayers) {
 #pragma unroll 1
@@ -396,12 +446,17 @@ __device__ __forceinline__ void mlp_pass(unsigned char* act, unsigned char* wb, 
           ld64(trow + c0, v);
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
+            // the bias of a hidden layer starts on a 64-byte boundary of P (every block of P is a
+            // multiple of 16 floats long), so eight columns are two 16-byte loads
+            const float4 b0 = __ldg(reinterpret_cast<const float4*>(bias + c0 + 8 * q));
+            const float4 b1 = __ldg(reinterpret_cast<const float4*>(bias + c0 + 8 * q + 4));
+            const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
             uint32_t h[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
               const int c = 8 * q + 2 * i;
-              const __nv_bfloat162 t2 = __floats2bfloat162_rn(fmaxf(v[c] + __ldg(bias + c0 + c), 0.0f),
-                                                              fmaxf(v[c + 1] + __ldg(bias + c0 + c + 1), 0.0f));
+              const __nv_bfloat162 t2 = __floats2bfloat162_rn(fmaxf(v[c] + bb[2 * i], 0.0f),
+                                                              fmaxf(v[c + 1] + bb[2 * i + 1], 0.0f));
               h[i] = *reinterpret_cast<const uint32_t*>(&t2);
             }
             *reinterpret_cast<uint4*>(act + act_off(tid, c0 + 8 * q)) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -420,9 +475,16 @@ __device__ __forceinline__ void mlp_pass(unsigned char* act, unsigned char* wb, 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
-  // thread 0: the MMA completions of the last chunks, whose buffers were not refilled
-  if (tid == 0 && pp.ok && pp.issue)
+  // thread 0: the MMA completions of the last chunks, whose buffers were not refilled; then,
+  // with another pass to come, that pass's first copies into the freed buffers
+  if (tid == 0 && pp.ok && pp.issue) {
     for (int k = kChunksPerPass - kStages; k < kChunksPerPass; ++k) pp.ok = pp.wait_bar(kStages + k % kStages) && pp.ok;
+    if (pp.ok && next) {
+      pp.issued = 0;
+      for (int k = 0; k < kStages; ++k) issue_copy(pp, k, packed, wb);
+      pp.pre = true;
+    }
+  }
 }
 static_assert(kChunksPerPass > kStages, "the stream is deeper than the pipeline");
 
@@ -442,12 +504,15 @@ __device__ __forceinline__ Pipe begin(unsigned long long* mbar, uint32_t* tslot,
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  return Pipe{*tslot, saddr(mbar), 0u, true, issue, spin, 0};
+  return Pipe{*tslot, saddr(mbar), 0u, true, issue, spin, 0, false};
 }
 
 // Frees the block's tensor memory (every thread calls it, after its last tcgen05.ld), with no
-// copy of its own still in flight.
-__device__ __forceinline__ void end(const Pipe& pp) {
+// copy of its own still in flight: thread 0 first waits (bounded) for the copies it started for
+// a pass that did not run (a block that stopped on a failure).
+__device__ __forceinline__ void end(Pipe& pp) {
+  if (threadIdx.x == 0 && pp.pre)
+    for (int k = 0; k < kStages; ++k) pp.wait_bar(k);
   asm volatile("cp.async.wait_all;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -510,7 +575,8 @@ __global__ void __launch_bounds__(128, 2) mlp_rows_kernel(int rows, const float*
 #pragma unroll
     for (int j = 0; j < kSurrIn; ++j) x[j] = tid < nvalid ? X[static_cast<size_t>(r0 + tid) * kSurrIn + j] : 0.0f;
     tc::put_row(m.act, x);
-    tc::mlp_pass(m.act, m.wb, pp, reinterpret_cast<const unsigned char*>(Wb), P, y);
+    tc::mlp_pass(m.act, m.wb, pp, reinterpret_cast<const unsigned char*>(Wb), P, y,
+                 r0 + gridDim.x * tc::kRows < rows);
     if (!pp.ok) atomicOr(m.fail, 1);
     __syncthreads();
     if (*m.fail) break;
@@ -555,10 +621,11 @@ __global__ void __launch_bounds__(128, 2) surrogate_event_kernel(const unsigned*
       for (int j = 0; j < kSurrIn; ++j) x[j] = 0.0f;
     }
     tc::put_row(m.act, x);
-    tc::mlp_pass(m.act, m.wb, pp, reinterpret_cast<const unsigned char*>(Wb), P, y1);   // multiplicity pass
+    tc::mlp_pass(m.act, m.wb, pp, reinterpret_cast<const unsigned char*>(Wb), P, y1, true);   // multiplicity pass
     x[1 + kSurrTargets] = static_cast<float>(multiplicity(y1[0])) / kSurrSlots;
     tc::put_row(m.act, x);
-    tc::mlp_pass(m.act, m.wb, pp, reinterpret_cast<const unsigned char*>(Wb), P, y2);   // conditioned on it
+    tc::mlp_pass(m.act, m.wb, pp, reinterpret_cast<const unsigned char*>(Wb), P, y2,
+                 r0 + gridDim.x * tc::kRows < rows);                                         // conditioned on it
     if (!pp.ok) atomicOr(m.fail, 1);
     __syncthreads();
     if (*m.fail) break;                               // a tensor-core wait timed out: stop
@@ -741,7 +808,7 @@ __global__ void pack_weights_kernel(const float* __restrict__ P, unsigned char* 
   for (int l = 0; l < kSurrLayers; ++l) {
     const int din = tc::layer_in_c(l), N = tc::layer_out_c(l), units = N * din / 8;
     if (u < units) {
-      const int n = u / (din / 8), k = (u % (din / 8)) * 8, c = k / tc::kKC, kl = k % tc::kKC;
+      const int n = u / (din / 8), k = (u % (din / 8)) * 8, c = k / tc::chunk_cols(l), kl = k % tc::chunk_cols(l);
       const float* w = P + off + static_cast<size_t>(n) * din + k;
       uint32_t h[4];
       for (int i = 0; i < 4; ++i) {
