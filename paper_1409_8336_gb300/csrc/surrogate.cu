@@ -350,8 +350,10 @@ struct Pipe {
   int issued;                   // thread 0: chunks of the current pass whose copies were started
   bool pre;                     // thread 0: the next pass's first kStages copies are already started
   __device__ __forceinline__ uint32_t bar(int i) const { return mbar + 8u * i; }
+  // A copy always lands, so the "full" waits keep the long bound even in the wait check: only
+  // the waits on MMAs run out there, and no copy is left in flight when the block stops.
   __device__ __forceinline__ bool wait_bar(int i) {
-    const bool r = wait(bar(i), (phase >> i) & 1u, spin);
+    const bool r = wait(bar(i), (phase >> i) & 1u, i < kStages ? kSpin : spin);
     phase ^= 1u << i;
     return r;
   }
