@@ -68,11 +68,12 @@ extern "C" {
 
 typedef struct pmc_ctx pmc_ctx;
 
-/* Optional device allocator (e.g. a framework's caching allocator).  It must
- * return memory of the context's device aligned to 256 bytes, as cudaMalloc
- * does (the kernels move records and weights in 16-byte units and by bulk
- * copies); a misaligned block is handed back to `free` and the call that
- * needed it fails with PMC_E_OOM. */
+/* Optional device allocator (e.g. a framework's caching allocator).  `alloc`
+ * and `free` are given together or not at all (pmc_create returns
+ * PMC_E_INVALID for one without the other).  `alloc` must return memory of the
+ * context's device aligned to 256 bytes, as cudaMalloc does (the kernels move
+ * records and weights in 16-byte units and by bulk copies); a misaligned block
+ * is handed back to `free` and the call that needed it fails with PMC_E_OOM. */
 typedef void* (*pmc_alloc_fn)(size_t bytes, void* user);
 typedef void (*pmc_free_fn)(void* ptr, void* user);
 

@@ -608,7 +608,8 @@ int pmc_create(pmc_ctx** out, const pmc_options* opt) {
   if (!ctx) return PMC_E_OOM;
   if (opt) ctx->opt = *opt;
   if (ctx->opt.n_batches == 0) ctx->opt.n_batches = 10;
-  if (ctx->opt.n_batches < 2 || ctx->opt.n_batches > 1024) {
+  // the allocator hooks come as a pair: a block from one must go back to the other
+  if (ctx->opt.n_batches < 2 || ctx->opt.n_batches > 1024 || (ctx->opt.alloc == nullptr) != (ctx->opt.free == nullptr)) {
     delete ctx;
     return PMC_E_INVALID;
   }

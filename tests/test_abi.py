@@ -57,6 +57,23 @@ def test_invalid_calls_fail_without_a_device(libpmc):
     assert libpmc.pmc_read_deposit_log(None, None, 0, None) == -1
 
 
+def test_create_rejects_bad_options_before_touching_a_device(libpmc):
+    """Option checks that need no GPU: the statistical group count, and allocator hooks that
+    come without their partner (a block from a caller's allocator must not reach cudaFree)."""
+    from paper_1409_8336_gb300 import engine
+
+    libpmc.pmc_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    ctx = ctypes.c_void_p()
+    keep = engine.AllocFn(lambda n, user: None)
+    for n_batches, alloc in ((1, None), (1025, None), (10, keep)):
+        o = engine.Options()
+        o.n_batches = n_batches
+        if alloc is not None:
+            o.alloc = alloc
+        assert libpmc.pmc_create(ctypes.byref(ctx), ctypes.byref(o)) == -1
+        assert not ctx.value
+
+
 def test_oracle_and_engine_share_no_code():
     """The CUDA path and the oracle are independent: neither includes nor imports the other."""
     csrc = os.path.join(ROOT, "paper_1409_8336_gb300", "csrc")
